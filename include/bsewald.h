@@ -1,0 +1,215 @@
+/*
+ * bsewald.h -- C ABI of the GB300 (sm_103a) library that evaluates the
+ * periodic Biot-Savart velocity (and optionally the streamfunction) induced
+ * by a set of closed or periodic vortex filaments at their own nodes, with
+ * the Ewald splitting of J. I. Polanco, "Fast and accurate evaluation of
+ * Biot-Savart integrals over spatial curves in periodic domains"
+ * (arXiv:2406.07366):
+ *
+ *     v(s0) = v_local(s0) + v^(n)(s0) + v^(f)(s0) - v^(f)_self(s0)
+ *                                        (Sec. 3, Eq. ewald_velocity_splitting)
+ *
+ * Conventions shared by every call:
+ *   - Every function returns a status code (BS_OK = 0); on failure a
+ *     thread-local message is available from bs_last_error().  No call
+ *     aborts the process and none falls back to a CPU path.
+ *   - Arrays of 3-vectors are row-major (x, y, z) per entry, float64.
+ *   - "device" pointers are CUDA global-memory pointers on the context's
+ *     device; "host" pointers are ordinary or pinned host memory.
+ *   - The caller owns every input and output buffer.  The library owns its
+ *     workspace, which it allocates only in bs_create / bs_set_filaments
+ *     and frees in bs_destroy.  The compute calls allocate nothing.
+ *   - All device work is issued on the stream given to bs_create (or set
+ *     with bs_set_stream); the compute calls return before that work ends,
+ *     except bs_compute_host and bs_status, which synchronise that stream.
+ *   - Node positions are the unwrapped curve coordinates; the library wraps
+ *     them into the box [0, L) only to bin them.
+ */
+#ifndef BSEWALD_H
+#define BSEWALD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+    BS_OK = 0,
+    BS_ERR_ARG = 1,            /* invalid argument or parameter            */
+    BS_ERR_RC_GT_HALF_L = 2,   /* r_c > min(L)/2 (minimum-image rule, Sec. 5.2 footnote) */
+    BS_ERR_NET_VORTICITY = 3,  /* sum of closing offsets n_l is not zero: the
+                                  mean vorticity must vanish (Sec. 2.2) */
+    BS_ERR_SPLINE = 4,         /* a filament has fewer nodes than the spline order */
+    BS_ERR_NONFINITE = 5,      /* a non-finite node position was seen        */
+    BS_ERR_OOM = 6,            /* device allocation failed                   */
+    BS_ERR_CUDA = 7,           /* a CUDA runtime call failed                 */
+    BS_ERR_CUFFT = 8,          /* a cuFFT call failed                        */
+    BS_ERR_TIMEOUT = 9,        /* a bounded device wait gave up              */
+    BS_ERR_STATE = 10,         /* call out of order (e.g. no filaments set)  */
+    BS_ERR_GEOMETRY = 11       /* a segment is longer than min(L)/4, so its
+                                  minimum image is not the curve itself     */
+};
+
+/* ---- precision forms ------------------------------------------------- */
+enum {
+    BS_FP64 = 0,   /* every stage in float64 (cuFFT D2Z/Z2D)                */
+    BS_MIXED = 1   /* float32 spread/FFT/k-space/interp/short range; float64
+                      node positions, cell-relative offsets and the final sum */
+};
+
+/* ---- flags ----------------------------------------------------------- */
+enum {
+    BS_WANT_PSI = 1,   /* also produce the streamfunction (Eq. ewald_streamfunction_splitting) */
+    BS_TIMING = 2      /* record per-stage CUDA-event times (bs_stage_times) */
+};
+
+/*
+ * Problem and method parameters (Sec. 2 problem statement; Sec. 3 split;
+ * Sec. 4 cut-offs; Appendix A NUFFT).
+ *   L[3]          periods of the box (Sec. 2.1)
+ *   kappa         circulation (Sec. 2.2)
+ *   a, delta      core radius and core-profile constant Delta (Sec. 2.3)
+ *   alpha         Ewald splitting parameter (Eq. ewald_green_functions)
+ *   rc            short-range cut-off, rc <= min(L)/2
+ *   M[3]          resolved Fourier modes per axis; the mode cube is
+ *                 |m_d| <= floor((M_d - 1)/2), k_max,d = (2 pi / L_d) floor((M_d-1)/2)
+ *                 (Sec. 3.3, the Nyquist mode of even M is not used)
+ *   quad_Q        Gauss-Legendre points per segment, 1..8 (Eq. line_integral_quadrature)
+ *   spline_order  4 (cubic); the paper's 6 (quintic) is not built yet
+ *   nufft_sigma   oversampling factor sigma > 1 (Appendix A)
+ *   nufft_w       spreading width in grid points, even, 2..16 (Appendix A)
+ *   precision     BS_FP64 or BS_MIXED
+ *   flags         BS_WANT_PSI | BS_TIMING
+ *   cell_div      cells per cut-off length m (cells of edge >= rc/m); the
+ *                 paper uses 3 (Sec. 5.3); 0 selects the library default
+ */
+typedef struct {
+    double L[3];
+    double kappa;
+    double a;
+    double delta;
+    double alpha;
+    double rc;
+    int M[3];
+    int quad_Q;
+    int spline_order;
+    double nufft_sigma;
+    int nufft_w;
+    int precision;
+    int flags;
+    int cell_div;
+} bs_params;
+
+typedef struct bs_ctx bs_ctx;
+
+/*
+ * Fill *out from the accuracy coefficient beta (Sec. 4, after Eq.
+ * error_trunc_streamfunction: r_c = beta/alpha, k_max = 2 beta alpha).
+ *   M > 0 : M modes per axis are kept and alpha = k_max / (2 beta) with
+ *           k_max = (2 pi / min L) floor((M-1)/2).
+ *   M == 0: alpha = C_beta N^(1/3) / min L (Eq. alpha_optimal_performance,
+ *           C_beta from Table tab:performance, interpolated in beta), and
+ *           M = 2 ceil(beta alpha min(L) / pi) + 1, then alpha re-derived.
+ * nufft_w is the Table tab:performance width for beta (sigma = 1.5).
+ * The other fields take the paper's defaults (kappa = 1, a = 1e-8,
+ * delta = 1/4, Q = 3, cubic, BS_FP64).  Host-only; returns BS_ERR_ARG for
+ * beta <= 0, non-positive L or N < 0 with M == 0.
+ */
+int bs_params_from_beta(double beta, const double L[3], int M, long long N, bs_params* out);
+
+/*
+ * Truncation error estimates of Sec. 4 (Eqs. error_trunc_velocity,
+ * error_trunc_streamfunction) for a total vortex length total_length, with
+ * beta = alpha * rc.  Host-only.  Either output may be NULL.
+ */
+int bs_error_estimate(const bs_params* p, double total_length, double* eps_v, double* eps_psi);
+
+/*
+ * Host-side helper (Appendix A, Eq. kaiser_bessel_bw): the spread grid size
+ * n_g[3] the context will use and, if table != NULL, the per-axis
+ * deconvolution factors F_d(m), m = 0..floor((M_d-1)/2), concatenated over
+ * the three axes, where F(m) = (w/2) phi_hat(pi m w / n_g) / phi(0) is the
+ * Fourier transform of the normalised spreading kernel divided by the grid
+ * spacing.  table must hold sum_d (floor((M_d-1)/2) + 1) doubles.
+ */
+int bs_nufft_setup(const bs_params* p, int n_g[3], double* table);
+
+/* Create a context on the current CUDA device; stream is a cudaStream_t
+ * (NULL = legacy default stream).  Validates *p: BS_ERR_ARG,
+ * BS_ERR_RC_GT_HALF_L. */
+int bs_create(bs_ctx** out, const bs_params* p, void* stream);
+
+/* Replace the stream used for subsequent calls. */
+int bs_set_stream(bs_ctx* ctx, void* stream);
+
+/*
+ * Set the filament topology and allocate the workspace for it.
+ *   nfil              number of filaments, >= 0
+ *   offsets  (host)   nfil+1 int64, offsets[0] = 0, filament l owns nodes
+ *                     offsets[l] .. offsets[l+1]-1 (Sec. 3.3: N_l may differ)
+ *   closing  (host)   nfil x 3 int32, n_l with s(tau + T) = s(tau) + n_l L
+ *                     (Sec. 2.1); NULL means every filament is closed.
+ * Errors: BS_ERR_ARG (bad offsets), BS_ERR_SPLINE (N_l < spline order),
+ * BS_ERR_NET_VORTICITY (sum_l n_l != 0), BS_ERR_OOM.
+ */
+int bs_set_filaments(bs_ctx* ctx, int nfil, const int64_t* offsets, const int32_t* closing);
+
+/*
+ * Velocity (and streamfunction) at every node.
+ *   nodes (device) N x 3 node positions
+ *   vel   (device) N x 3 output
+ *   psi   (device) N x 3 output, or NULL; needs BS_WANT_PSI at bs_create
+ * Allocates nothing; asynchronous on the context stream.  Device-side
+ * problems (non-finite input, over-long segments) are recorded in a status
+ * word that bs_status() reports.
+ */
+int bs_compute(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
+
+/* As bs_compute with HOST buffers: copies nodes in, computes, copies the
+ * results out and synchronises the stream.  Use pinned memory for speed. */
+int bs_compute_host(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
+
+/*
+ * The four parts of Eq. ewald_velocity_splitting separately, for parity
+ * tests: parts (device) 4 x N x 3 = [v_local, v^(n), v^(f), v^(f)_self];
+ * psi_parts (device) the same for the streamfunction, or NULL.
+ */
+int bs_compute_parts(bs_ctx* ctx, const double* nodes, double* parts, double* psi_parts);
+
+/*
+ * Quadrature points and charges of the curves through nodes (Eq.
+ * vorticity_fourier_coefs: q = w_i dtau_j s'(tau)): nodes (device) N x 3;
+ * qX, qq (device) N*Q x 3 float64 outputs, point (j, i) at row j*Q + i,
+ * positions wrapped into [0, L).  Refits the splines; allocates nothing.
+ */
+int bs_get_quadrature(bs_ctx* ctx, const double* nodes, double* qX, double* qq);
+
+/* Synchronise the stream and return the device status word as a status
+ * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY); clears it. */
+int bs_status(bs_ctx* ctx);
+
+/*
+ * Per-stage times of the last compute call in milliseconds (needs
+ * BS_TIMING).  ms[0..n-1] receive, in order: geometry, short-range binning,
+ * short range, spread binning, spread, forward FFT, k-space, inverse FFT,
+ * interpolation + sum.  Synchronises the stream.  Returns the number of
+ * stages through *n_out.
+ */
+int bs_stage_times(bs_ctx* ctx, float* ms, int n, int* n_out);
+
+/* Device bytes held by the context's workspace. */
+int bs_workspace_bytes(bs_ctx* ctx, long long* bytes);
+
+/* Free the context and its workspace (NULL is a no-op). */
+void bs_destroy(bs_ctx* ctx);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* bs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSEWALD_H */

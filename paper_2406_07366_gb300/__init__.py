@@ -1,0 +1,275 @@
+"""GB300 (sm_103a) Ewald-split periodic Biot-Savart velocity on vortex filaments.
+
+Thin ctypes binding of the C ABI in ``include/bsewald.h``: the functions
+below carry the same names as the C entry points and only marshal
+arguments; every step of the computation runs in the CUDA library
+``lib/libbsewald.so``, loaded on the first call.  That call raises if the
+library is missing: there is no CPU fallback.  PyTorch is used only for device memory
+and streams (``BiotSavart`` takes and returns torch tensors).
+
+Method: J. I. Polanco, "Fast and accurate evaluation of Biot-Savart
+integrals over spatial curves in periodic domains", arXiv:2406.07366.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libbsewald.so")
+
+BS_OK, BS_ERR_ARG, BS_ERR_RC_GT_HALF_L, BS_ERR_NET_VORTICITY, BS_ERR_SPLINE = 0, 1, 2, 3, 4
+BS_ERR_NONFINITE, BS_ERR_OOM, BS_ERR_CUDA, BS_ERR_CUFFT, BS_ERR_TIMEOUT = 5, 6, 7, 8, 9
+BS_ERR_STATE, BS_ERR_GEOMETRY = 10, 11
+BS_FP64, BS_MIXED = 0, 1
+BS_WANT_PSI, BS_TIMING = 1, 2
+
+STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", "kspace", "fft_inv", "interp"]
+
+# Every exported symbol of include/bsewald.h.
+EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_create", "bs_set_stream",
+           "bs_set_filaments", "bs_compute", "bs_compute_host", "bs_compute_parts", "bs_get_quadrature",
+           "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error"]
+
+
+class bs_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3), ("kappa", ctypes.c_double), ("a", ctypes.c_double),
+                ("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("rc", ctypes.c_double),
+                ("M", ctypes.c_int * 3), ("quad_Q", ctypes.c_int), ("spline_order", ctypes.c_int),
+                ("nufft_sigma", ctypes.c_double), ("nufft_w", ctypes.c_int), ("precision", ctypes.c_int),
+                ("flags", ctypes.c_int), ("cell_div", ctypes.c_int)]
+
+    def as_dict(self):
+        return dict(L=list(self.L), kappa=self.kappa, a=self.a, delta=self.delta, alpha=self.alpha, rc=self.rc,
+                    M=list(self.M), quad_Q=self.quad_Q, spline_order=self.spline_order,
+                    nufft_sigma=self.nufft_sigma, nufft_w=self.nufft_w, precision=self.precision,
+                    flags=self.flags, cell_div=self.cell_div)
+
+
+class BSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bsewald error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    sig = {
+        "bs_params_from_beta": ([ctypes.c_double, P(ctypes.c_double), ctypes.c_int, ctypes.c_longlong,
+                                 P(bs_params)], ctypes.c_int),
+        "bs_error_estimate": ([P(bs_params), ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double)], ctypes.c_int),
+        "bs_nufft_setup": ([P(bs_params), P(ctypes.c_int), P(ctypes.c_double)], ctypes.c_int),
+        "bs_create": ([P(vp), P(bs_params), vp], ctypes.c_int),
+        "bs_set_stream": ([vp, vp], ctypes.c_int),
+        "bs_set_filaments": ([vp, ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32)], ctypes.c_int),
+        "bs_compute": ([vp, vp, vp, vp], ctypes.c_int),
+        "bs_compute_host": ([vp, vp, vp, vp], ctypes.c_int),
+        "bs_compute_parts": ([vp, vp, vp, vp], ctypes.c_int),
+        "bs_get_quadrature": ([vp, vp, vp, vp], ctypes.c_int),
+        "bs_status": ([vp], ctypes.c_int),
+        "bs_stage_times": ([vp, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
+        "bs_workspace_bytes": ([vp, P(ctypes.c_longlong)], ctypes.c_int),
+        "bs_destroy": ([vp], None),
+        "bs_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib_handle = None
+
+
+def lib():
+    """The loaded CUDA library (loaded on first use; raises if missing)."""
+    global _lib_handle
+    if _lib_handle is None:
+        _lib_handle = _load()
+    return _lib_handle
+
+
+def _check(rc):
+    if rc != BS_OK:
+        raise BSError(rc, bs_last_error())
+    return rc
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+# ------------------------------------------------------------- C entry points
+def bs_last_error() -> str:
+    return (lib().bs_last_error() or b"").decode()
+
+
+def bs_params_from_beta(beta, L, M=0, N=0) -> bs_params:
+    p = bs_params()
+    Lc = (ctypes.c_double * 3)(*np.broadcast_to(np.asarray(L, dtype=float), (3,)))
+    _check(lib().bs_params_from_beta(float(beta), Lc, int(M), int(N), ctypes.byref(p)))
+    return p
+
+
+def bs_error_estimate(p: bs_params, total_length: float):
+    ev, ep = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bs_error_estimate(ctypes.byref(p), float(total_length), ctypes.byref(ev), ctypes.byref(ep)))
+    return ev.value, ep.value
+
+
+def bs_nufft_setup(p: bs_params, want_table=True):
+    ng = (ctypes.c_int * 3)()
+    K = [(m - 1) // 2 for m in p.M]
+    tab = np.zeros(sum(k + 1 for k in K)) if want_table else None
+    _check(lib().bs_nufft_setup(ctypes.byref(p), ng,
+                               tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_table else None))
+    if not want_table:
+        return list(ng), None
+    out, o = [], 0
+    for k in K:
+        out.append(tab[o:o + k + 1].copy())
+        o += k + 1
+    return list(ng), out
+
+
+def bs_create(p: bs_params, stream=None):
+    ctx = ctypes.c_void_p()
+    _check(lib().bs_create(ctypes.byref(ctx), ctypes.byref(p), stream))
+    return ctx
+
+
+def bs_set_stream(ctx, stream):
+    _check(lib().bs_set_stream(ctx, stream))
+
+
+def bs_set_filaments(ctx, offsets, closing=None):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nfil = off.size - 1
+    cl = None if closing is None else np.ascontiguousarray(closing, dtype=np.int32).reshape(nfil, 3)
+    _check(lib().bs_set_filaments(ctx, nfil, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+
+def bs_compute(ctx, nodes, vel, psi=None):
+    _check(lib().bs_compute(ctx, _ptr(nodes), _ptr(vel), _ptr(psi)))
+
+
+def bs_compute_host(ctx, nodes, vel, psi=None):
+    _check(lib().bs_compute_host(ctx, _ptr(nodes), _ptr(vel), _ptr(psi)))
+
+
+def bs_compute_parts(ctx, nodes, parts, psi_parts=None):
+    _check(lib().bs_compute_parts(ctx, _ptr(nodes), _ptr(parts), _ptr(psi_parts)))
+
+
+def bs_get_quadrature(ctx, nodes, qX, qq):
+    _check(lib().bs_get_quadrature(ctx, _ptr(nodes), _ptr(qX), _ptr(qq)))
+
+
+def bs_status(ctx):
+    return _check(lib().bs_status(ctx))
+
+
+def bs_stage_times(ctx):
+    ms = (ctypes.c_float * 16)()
+    n = ctypes.c_int()
+    _check(lib().bs_stage_times(ctx, ms, 16, ctypes.byref(n)))
+    return {STAGES[i]: float(ms[i]) for i in range(n.value)}
+
+
+def bs_workspace_bytes(ctx):
+    b = ctypes.c_longlong()
+    _check(lib().bs_workspace_bytes(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def bs_destroy(ctx):
+    if ctx:
+        lib().bs_destroy(ctx)
+
+
+# ------------------------------------------------------------- convenience
+def make_params(L, kappa=1.0, a=1e-6, delta=0.25, beta=3.5, M=32, Q=2, order=4, sigma=1.5, w=8,
+                precision=BS_FP64, flags=0, cell_div=0, alpha=None, rc=None) -> bs_params:
+    """Parameters from beta and M (Sec. 4): k_max = (2 pi/L) floor((M-1)/2),
+    alpha = k_max / (2 beta), r_c = beta / alpha, unless alpha / rc are given."""
+    p = bs_params_from_beta(beta, L, M=M)
+    p.kappa, p.a, p.delta = kappa, a, delta
+    p.quad_Q, p.spline_order = Q, order
+    p.nufft_sigma, p.nufft_w = sigma, w
+    p.precision, p.flags, p.cell_div = precision, flags, cell_div
+    if alpha is not None:
+        p.alpha = alpha
+        p.rc = beta / alpha if rc is None else rc
+    elif rc is not None:
+        p.rc = rc
+    return p
+
+
+class BiotSavart:
+    """Context holder working on torch tensors (device memory and streams only)."""
+
+    def __init__(self, params: bs_params, offsets, closing=None, stream=None):
+        import torch
+        self.torch = torch
+        self.params = params
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.ctx = bs_create(params, ctypes.c_void_p(stream.cuda_stream))
+        bs_set_filaments(self.ctx, offsets, closing)
+        self.N = int(np.asarray(offsets)[-1])
+
+    def _out(self):
+        return self.torch.empty((self.N, 3), dtype=self.torch.float64, device="cuda")
+
+    def velocity(self, nodes, vel=None, psi=None, want_psi=False):
+        vel = self._out() if vel is None else vel
+        if want_psi and psi is None:
+            psi = self._out()
+        bs_compute(self.ctx, nodes, vel, psi)
+        return (vel, psi) if want_psi else vel
+
+    def parts(self, nodes, want_psi=False):
+        parts = self.torch.empty((4, self.N, 3), dtype=self.torch.float64, device="cuda")
+        pp = self.torch.empty((4, self.N, 3), dtype=self.torch.float64, device="cuda") if want_psi else None
+        bs_compute_parts(self.ctx, nodes, parts, pp)
+        return (parts, pp) if want_psi else parts
+
+    def quadrature(self, nodes):
+        Q = self.params.quad_Q
+        qX = self.torch.empty((self.N * Q, 3), dtype=self.torch.float64, device="cuda")
+        qq = self.torch.empty((self.N * Q, 3), dtype=self.torch.float64, device="cuda")
+        bs_get_quadrature(self.ctx, nodes, qX, qq)
+        return qX, qq
+
+    def status(self):
+        return bs_status(self.ctx)
+
+    def stage_times(self):
+        return bs_stage_times(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            bs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,815 @@
+// C ABI of the bsewald library: parameter helpers (Sec. 4, Sec. 5.3, Table
+// tab:performance), NUFFT set-up (Appendix A), context lifecycle and the
+// evaluation pipeline of Eq. ewald_velocity_splitting:
+//
+//   main stream : spline -> nodes (sources, local - self) --fork--+
+//                 tile sort -> spread -> FFT -> k-space -> FFT^-1  |
+//                 --join-- interpolation + sum                     |
+//   side stream : cell sort -> short range  <---------------------+
+//
+// The compute calls allocate nothing: every buffer, the cuFFT plans and
+// their work area are made in bs_create / bs_set_filaments.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "bs_internal.cuh"
+
+using namespace bsw;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                                     \
+    do {                                                                                                   \
+        cudaError_t _e = (expr);                                                                           \
+        if (_e != cudaSuccess) {                                                                           \
+            return fail(_e == cudaErrorMemoryAllocation ? BS_ERR_OOM : BS_ERR_CUDA, "%s: %s", #expr,      \
+                        cudaGetErrorString(_e));                                                           \
+        }                                                                                                  \
+    } while (0)
+
+#define CUFFT_TRY(expr)                                                                                    \
+    do {                                                                                                   \
+        cufftResult _r = (expr);                                                                           \
+        if (_r != CUFFT_SUCCESS) return fail(BS_ERR_CUFFT, "%s: cufft error %d", #expr, (int)_r);         \
+    } while (0)
+
+// ---------------------------------------------------------------- host numerics
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence).
+void gauss_legendre(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(kPi * (i + 0.75) / (n + 0.5));
+        double pp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double z1 = z;
+            z = z1 - p1 / pp;
+            if (fabs(z - z1) < 1e-16) break;
+        }
+        double p1 = 1.0, p2 = 0.0;
+        for (int k = 1; k <= n; ++k) {
+            double p3 = p2;
+            p2 = p1;
+            p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+        }
+        pp = n * (z * p1 - p2) / (z * z - 1.0);
+        x[i] = -z;  // ascending
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+// Smallest m >= n, m % 8 == 0, m = 2^a 3^b 5^c 7^d.
+int fft_friendly(int n)
+{
+    for (int m = std::max(n, 8);; ++m) {
+        if (m % 8) continue;
+        int r = m;
+        for (int p : { 2, 3, 5, 7 })
+            while (r % p == 0) r /= p;
+        if (r == 1) return m;
+    }
+}
+
+// Normalised backwards Kaiser-Bessel kernel psi(z) = sinh(zeta s)/(s sinh zeta).
+double kb_host(double z, double zeta)
+{
+    double s2 = 1.0 - z * z;
+    if (s2 < 0) s2 = 0;
+    const double s = sqrt(s2);
+    const double num = s > 1e-12 ? -expm1(-2.0 * zeta * s) / s : 2.0 * zeta;
+    return exp(zeta * (s - 1.0)) * num / (1.0 - exp(-2.0 * zeta));
+}
+
+// F(m) = (w/2) int_{-1}^{1} psi(z) cos(kappa z) dz, kappa = pi m w / n_g: the
+// continuous Fourier transform of the spreading kernel as used (width w grid
+// points) divided by the grid spacing.  Gauss-Legendre with 400 points (the
+// integrand is entire in z).
+void kb_fourier(double zeta, int w, int ng, int K, double* F)
+{
+    const int nq = 400;
+    std::vector<double> x(nq), wt(nq);
+    gauss_legendre(nq, x.data(), wt.data());
+    std::vector<double> pz(nq);
+    for (int i = 0; i < nq; ++i) pz[i] = kb_host(x[i], zeta);
+    for (int m = 0; m <= K; ++m) {
+        const double kap = kPi * m * w / ng;
+        double s = 0;
+        for (int i = 0; i < nq; ++i) s += wt[i] * pz[i] * cos(kap * x[i]);
+        F[m] = 0.5 * w * s;
+    }
+}
+
+struct Derived {
+    int ng[3], nh, K[3];
+    double zeta;
+    double hg[3];
+    int tile[3], ntile[3], ntiles;
+    int nc[3], m;
+    long long ncells;
+    double hc[3];
+};
+
+int derive(const bs_params* p, Derived* d)
+{
+    const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
+    for (int c = 0; c < 3; ++c)
+        if (!(p->L[c] > 0) || !isfinite(p->L[c])) return fail(BS_ERR_ARG, "L[%d] must be positive and finite", c);
+    if (!isfinite(p->kappa)) return fail(BS_ERR_ARG, "kappa must be finite");
+    if (!(p->a > 0) || !isfinite(p->a)) return fail(BS_ERR_ARG, "core radius a must be positive");
+    if (!isfinite(p->delta)) return fail(BS_ERR_ARG, "delta must be finite");
+    if (!(p->alpha > 0) || !isfinite(p->alpha)) return fail(BS_ERR_ARG, "alpha must be positive");
+    if (!(p->rc > 0) || !isfinite(p->rc)) return fail(BS_ERR_ARG, "rc must be positive");
+    if (p->rc > 0.5 * Lmin * (1 + 1e-12))
+        return fail(BS_ERR_RC_GT_HALF_L, "rc = %g exceeds min(L)/2 = %g", p->rc, 0.5 * Lmin);
+    if (p->quad_Q < 1 || p->quad_Q > kMaxQ) return fail(BS_ERR_ARG, "quad_Q must be in 1..%d", kMaxQ);
+    if (p->spline_order != 4) return fail(BS_ERR_ARG, "spline_order %d not supported (4 = cubic)", p->spline_order);
+    if (p->nufft_w < 2 || p->nufft_w > kMaxW || (p->nufft_w & 1))
+        return fail(BS_ERR_ARG, "nufft_w must be even in 2..16");
+    if (!(p->nufft_sigma > 1.0) || p->nufft_sigma > 4.0) return fail(BS_ERR_ARG, "nufft_sigma must be in (1, 4]");
+    if (p->precision != BS_FP64 && p->precision != BS_MIXED) return fail(BS_ERR_ARG, "unknown precision");
+    if (p->cell_div < 0 || p->cell_div > 8) return fail(BS_ERR_ARG, "cell_div must be in 0..8");
+    for (int c = 0; c < 3; ++c) {
+        if (p->M[c] < 3) return fail(BS_ERR_ARG, "M[%d] must be >= 3", c);
+        d->K[c] = (p->M[c] - 1) / 2;
+        int n = fft_friendly((int)ceil(p->nufft_sigma * p->M[c]));
+        n = std::max(n, fft_friendly(2 * p->nufft_w));
+        if (n > 1024) return fail(BS_ERR_ARG, "spread grid %d > 1024 along axis %d", n, c);
+        d->ng[c] = n;
+        d->hg[c] = p->L[c] / n;
+        d->tile[c] = 8;
+        d->ntile[c] = n / 8;
+    }
+    if (d->ng[2] % 32 == 0) d->tile[2] = 32;
+    else if (d->ng[2] % 16 == 0) d->tile[2] = 16;
+    d->ntile[2] = d->ng[2] / d->tile[2];
+    d->ntiles = d->ntile[0] * d->ntile[1] * d->ntile[2];
+    d->nh = d->ng[2] / 2 + 1;
+    // zeta = gamma w pi (1 - 1/(2 sigma)), gamma = 0.995 (Appendix A); with
+    // the effective sigma of the rounded grid of the first axis.
+    const double sig = (double)d->ng[0] / p->M[0];
+    d->zeta = 0.995 * p->nufft_w * kPi * (1.0 - 1.0 / (2.0 * sig));
+    d->m = p->cell_div > 0 ? p->cell_div : 2;
+    for (;;) {
+        long long tot = 1;
+        for (int c = 0; c < 3; ++c) {
+            int n = (int)floor(p->L[c] * d->m / p->rc);
+            n = std::max(n, 1);
+            d->nc[c] = n;
+            d->hc[c] = p->L[c] / n;
+            tot *= n;
+        }
+        d->ncells = tot;
+        if (tot <= (1LL << 27) || d->m == 1) break;
+        d->m -= 1;
+    }
+    if (d->ncells > (1LL << 28)) return fail(BS_ERR_ARG, "too many short-range cells (rc too small)");
+    return BS_OK;
+}
+
+}  // namespace
+
+struct bs_ctx {
+    bs_params p;
+    Derived d;
+    cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    static constexpr int kStages = 10;
+    cudaEvent_t ev_t[kStages] = {};
+    bool timed = false;
+    int nfil = 0;
+    long long N = 0, NQ = 0;
+    bool have_fil = false;
+    Work w;
+    cufftHandle plan_fwd = 0, plan_inv = 0;
+    bool plans = false;
+    long long bytes = 0;
+    std::vector<std::pair<void*, size_t>> alloc_n, alloc_g;
+    int device = 0;
+};
+
+namespace {
+
+int dalloc(bs_ctx* c, std::vector<std::pair<void*, size_t>>& list, void** ptr, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(BS_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    list.push_back({ *ptr, bytes });
+    c->bytes += (long long)bytes;
+    return BS_OK;
+}
+
+void free_list(bs_ctx* c, std::vector<std::pair<void*, size_t>>& list)
+{
+    for (auto& pr : list) {
+        cudaFree(pr.first);
+        c->bytes -= (long long)pr.second;
+    }
+    list.clear();
+}
+
+#define TRY(expr)                   \
+    do {                            \
+        int _rc = (expr);           \
+        if (_rc != BS_OK) return _rc; \
+    } while (0)
+
+template <typename T>
+int make_plans(bs_ctx* c)
+{
+    const Derived& d = c->d;
+    int n[3] = { d.ng[0], d.ng[1], d.ng[2] };
+    const long long rsz = (long long)d.ng[0] * d.ng[1] * d.ng[2];
+    const long long csz = (long long)d.ng[0] * d.ng[1] * d.nh;
+    CUFFT_TRY(cufftCreate(&c->plan_fwd));
+    CUFFT_TRY(cufftCreate(&c->plan_inv));
+    c->plans = true;
+    CUFFT_TRY(cufftSetAutoAllocation(c->plan_fwd, 0));
+    CUFFT_TRY(cufftSetAutoAllocation(c->plan_inv, 0));
+    size_t ws1 = 0, ws2 = 0;
+    const bool f32 = sizeof(T) == 4;
+    CUFFT_TRY(cufftMakePlanMany(c->plan_fwd, 3, n, nullptr, 1, (int)rsz, nullptr, 1, (int)csz,
+                                f32 ? CUFFT_R2C : CUFFT_D2Z, 3, &ws1));
+    CUFFT_TRY(cufftMakePlanMany(c->plan_inv, 3, n, nullptr, 1, (int)csz, nullptr, 1, (int)rsz,
+                                f32 ? CUFFT_C2R : CUFFT_Z2D, 3, &ws2));
+    TRY(dalloc(c, c->alloc_g, &c->w.fft_work, std::max(ws1, ws2)));
+    CUFFT_TRY(cufftSetWorkArea(c->plan_fwd, c->w.fft_work));
+    CUFFT_TRY(cufftSetWorkArea(c->plan_inv, c->w.fft_work));
+    return BS_OK;
+}
+
+template <typename T>
+int alloc_grids(bs_ctx* c)
+{
+    const Derived& d = c->d;
+    const size_t rsz = (size_t)d.ng[0] * d.ng[1] * d.ng[2];
+    const size_t csz = (size_t)d.ng[0] * d.ng[1] * d.nh;
+    TRY(dalloc(c, c->alloc_g, &c->w.grid, 3 * rsz * sizeof(T)));
+    TRY(dalloc(c, c->alloc_g, &c->w.spec, 3 * csz * 2 * sizeof(T)));
+    if (c->p.flags & BS_WANT_PSI) TRY(dalloc(c, c->alloc_g, &c->w.spec_psi, 3 * csz * 2 * sizeof(T)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.tile_cnt, sizeof(int) * (size_t)(d.ntiles + 1)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.tile_cur, sizeof(int) * (size_t)(d.ntiles + 1)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp2, sizeof(int) * (size_t)scan_blocks(d.ntiles)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cnt, sizeof(int) * (size_t)(d.ncells + 1)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cur, sizeof(int) * (size_t)(d.ncells + 1)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp, sizeof(int) * (size_t)scan_blocks((int)d.ncells)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.status, sizeof(int)));
+    CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
+    // k-space tables e^{-k_d^2 / 4 alpha^2} / F_d(m)^2, m = 0..K_d
+    const int ntab = d.K[0] + d.K[1] + d.K[2] + 3;
+    std::vector<T> tab(ntab);
+    int o = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        std::vector<double> F(d.K[ax] + 1);
+        kb_fourier(d.zeta, c->p.nufft_w, d.ng[ax], d.K[ax], F.data());
+        for (int m = 0; m <= d.K[ax]; ++m) {
+            const double k = 2.0 * kPi * m / c->p.L[ax];
+            tab[o++] = (T)(exp(-k * k / (4.0 * c->p.alpha * c->p.alpha)) / (F[m] * F[m]));
+        }
+    }
+    TRY(dalloc(c, c->alloc_g, &c->w.ktab, sizeof(T) * ntab));
+    CUDA_TRY(cudaMemcpy(c->w.ktab, tab.data(), sizeof(T) * ntab, cudaMemcpyHostToDevice));
+    return make_plans<T>(c);
+}
+
+template <typename T>
+int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vector<int>& fil_of,
+                    const std::vector<int>& prev, const std::vector<double>& shift)
+{
+    const size_t N = (size_t)c->N, NQ = (size_t)c->NQ, nf = (size_t)c->nfil;
+    Work& w = c->w;
+    std::vector<std::pair<void*, size_t>>& L = c->alloc_n;
+    TRY(dalloc(c, L, (void**)&w.off, sizeof(int64_t) * (nf + 1)));
+    TRY(dalloc(c, L, (void**)&w.fil_of, sizeof(int) * N));
+    TRY(dalloc(c, L, (void**)&w.prev, sizeof(int) * N));
+    TRY(dalloc(c, L, (void**)&w.shift, sizeof(double) * 3 * nf));
+    TRY(dalloc(c, L, &w.hseg, sizeof(T) * N));
+    TRY(dalloc(c, L, &w.dp, sizeof(T) * 3 * N));
+    TRY(dalloc(c, L, &w.ds, sizeof(T) * 3 * N));
+    TRY(dalloc(c, L, &w.Mm, sizeof(T) * 3 * N));
+    TRY(dalloc(c, L, &w.cpr, sizeof(T) * N));
+    TRY(dalloc(c, L, &w.zz, sizeof(T) * N));
+    TRY(dalloc(c, L, &w.Tper, sizeof(T) * nf));
+    TRY(dalloc(c, L, (void**)&w.vls, sizeof(double) * 3 * N));
+    TRY(dalloc(c, L, (void**)&w.pls, sizeof(double) * 3 * N));
+    TRY(dalloc(c, L, &w.vsr, sizeof(T) * 3 * N));
+    TRY(dalloc(c, L, &w.psr, sizeof(T) * 3 * N));
+    TRY(dalloc(c, L, &w.tgt, sizeof(SrTgt<T>) * N));
+    TRY(dalloc(c, L, &w.sr_rec, sizeof(SrRec<T>) * NQ));
+    TRY(dalloc(c, L, &w.sr_sorted, sizeof(SrRec<T>) * NQ));
+    TRY(dalloc(c, L, (void**)&w.sr_key, sizeof(int) * NQ));
+    TRY(dalloc(c, L, &w.lr_rec, sizeof(LrRec<T>) * NQ));
+    TRY(dalloc(c, L, &w.lr_sorted, sizeof(LrRec<T>) * NQ));
+    TRY(dalloc(c, L, (void**)&w.lr_key, sizeof(int) * NQ));
+    TRY(dalloc(c, L, (void**)&w.nodes_in, sizeof(double) * 3 * N));
+    TRY(dalloc(c, L, (void**)&w.vel_out, sizeof(double) * 3 * N));
+    TRY(dalloc(c, L, (void**)&w.psi_out, sizeof(double) * 3 * N));
+    CUDA_TRY(cudaMemcpy(w.off, off.data(), sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice));
+    if (N) {
+        CUDA_TRY(cudaMemcpy(w.fil_of, fil_of.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(w.prev, prev.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+    }
+    if (nf) CUDA_TRY(cudaMemcpy(w.shift, shift.data(), sizeof(double) * 3 * nf, cudaMemcpyHostToDevice));
+    return BS_OK;
+}
+
+void fill_geom(const bs_ctx* c, GeomP& G)
+{
+    const bs_params& p = c->p;
+    const Derived& d = c->d;
+    memset(&G, 0, sizeof G);
+    for (int k = 0; k < 3; ++k) {
+        G.L[k] = p.L[k];
+        G.nc[k] = d.nc[k];
+        G.hc[k] = d.hc[k];
+        G.ng[k] = d.ng[k];
+        G.hg[k] = d.hg[k];
+        G.tile[k] = d.tile[k];
+        G.ntile[k] = d.ntile[k];
+    }
+    G.N = (int)c->N;
+    G.nfil = c->nfil;
+    G.Q = p.quad_Q;
+    double x[kMaxQ], wq[kMaxQ];
+    gauss_legendre(p.quad_Q, x, wq);
+    for (int i = 0; i < p.quad_Q; ++i) {
+        G.gh[i] = 0.5 * (x[i] + 1.0);
+        G.gw[i] = 0.5 * wq[i];
+    }
+    G.kappa = p.kappa;
+    G.a = p.a;
+    G.delta = p.delta;
+    G.alpha = p.alpha;
+    G.w = p.nufft_w;
+    G.seg_max = 0.25 * std::min(p.L[0], std::min(p.L[1], p.L[2]));
+    G.want_psi = (p.flags & BS_WANT_PSI) ? 1 : 0;
+}
+
+void rec(bs_ctx* c, int i, cudaStream_t s)
+{
+    if (c->timed && i < bs_ctx::kStages) cudaEventRecord(c->ev_t[i], s);
+}
+
+#define CE(expr)                                                                                    \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) return fail(BS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e));   \
+    } while (0)
+
+template <typename T>
+int fft_fwd(bs_ctx* c, cudaStream_t s)
+{
+    CUFFT_TRY(cufftSetStream(c->plan_fwd, s));
+    if (sizeof(T) == 4)
+        CUFFT_TRY(cufftExecR2C(c->plan_fwd, (cufftReal*)c->w.grid, (cufftComplex*)c->w.spec));
+    else
+        CUFFT_TRY(cufftExecD2Z(c->plan_fwd, (cufftDoubleReal*)c->w.grid, (cufftDoubleComplex*)c->w.spec));
+    return BS_OK;
+}
+
+template <typename T>
+int fft_inv(bs_ctx* c, void* spec, cudaStream_t s)
+{
+    CUFFT_TRY(cufftSetStream(c->plan_inv, s));
+    if (sizeof(T) == 4)
+        CUFFT_TRY(cufftExecC2R(c->plan_inv, (cufftComplex*)spec, (cufftReal*)c->w.grid));
+    else
+        CUFFT_TRY(cufftExecZ2D(c->plan_inv, (cufftDoubleComplex*)spec, (cufftDoubleReal*)c->w.grid));
+    return BS_OK;
+}
+
+// The pipeline.  parts (4 x N x 3) / psi_parts switch the output to the
+// separate parts of Eq. ewald_velocity_splitting.
+template <typename T>
+int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts, double* psi_parts)
+{
+    const bs_params& p = c->p;
+    const Derived& d = c->d;
+    const Work& w = c->w;
+    cudaStream_t s = c->stream;
+    const size_t N3 = (size_t)c->N * 3;
+    const bool want_psi = (psi != nullptr) || (psi_parts != nullptr);
+    c->timed = (p.flags & BS_TIMING) != 0;
+
+    GeomP G;
+    fill_geom(c, G);
+    G.want_psi = want_psi ? 1 : 0;
+
+    rec(c, 0, s);
+    CE(launch_spline<T>(nodes, w, c->nfil, s));
+    CE(launch_nodes<T>(G, nodes, w, parts ? parts : nullptr, parts ? parts + 3 * N3 : nullptr,
+                       psi_parts ? psi_parts : nullptr, psi_parts ? psi_parts + 3 * N3 : nullptr, s));
+    rec(c, 1, s);
+
+    // short range on the side stream (serial on the main one when timing)
+    cudaStream_t ss = s;
+    if (!c->timed) {
+        CE(cudaEventRecord(c->ev_fork, s));
+        CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        ss = c->side;
+    }
+    CE(launch_sort_sr<T>(w, (int)c->NQ, (int)d.ncells, ss));
+    rec(c, 2, ss);
+    ShortP S;
+    memset(&S, 0, sizeof S);
+    S.N = (int)c->N;
+    for (int k = 0; k < 3; ++k) {
+        S.nc[k] = d.nc[k];
+        S.hc[k] = d.hc[k];
+        S.L[k] = p.L[k];
+    }
+    S.m = d.m;
+    S.rc2 = p.rc * p.rc;
+    S.alpha = p.alpha;
+    S.pref = p.kappa / (4.0 * kPi);
+    S.want_psi = want_psi ? 1 : 0;
+    CE(launch_short<T>(S, w, ss));
+    rec(c, 3, ss);
+    if (!c->timed) CE(cudaEventRecord(c->ev_join, ss));
+
+    // long range on the main stream
+    CE(launch_sort_lr<T>(w, (int)c->NQ, d.ntiles, s));
+    rec(c, 4, s);
+    SpreadP SP;
+    for (int k = 0; k < 3; ++k) {
+        SP.ng[k] = d.ng[k];
+        SP.tile[k] = d.tile[k];
+        SP.ntile[k] = d.ntile[k];
+    }
+    SP.w = p.nufft_w;
+    SP.zeta = d.zeta;
+    CE(launch_spread<T>(SP, w, d.ntiles, s));
+    rec(c, 5, s);
+    TRY(fft_fwd<T>(c, s));
+    rec(c, 6, s);
+    KspaceP K;
+    for (int k = 0; k < 3; ++k) {
+        K.ng[k] = d.ng[k];
+        K.K[k] = d.K[k];
+        K.kk[k] = 2.0 * kPi / p.L[k];
+    }
+    K.nh = d.nh;
+    K.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
+    K.want_psi = want_psi ? 1 : 0;
+    CE(launch_kspace<T>(K, w, s));
+    rec(c, 7, s);
+    TRY(fft_inv<T>(c, w.spec, s));
+    rec(c, 8, s);
+    if (!c->timed) CE(cudaStreamWaitEvent(s, c->ev_join, 0));
+
+    InterpP I;
+    I.N = (int)c->N;
+    for (int k = 0; k < 3; ++k) {
+        I.ng[k] = d.ng[k];
+        I.hg[k] = d.hg[k];
+        I.L[k] = p.L[k];
+    }
+    I.w = p.nufft_w;
+    I.zeta = d.zeta;
+    I.want_psi = want_psi ? 1 : 0;
+    if (parts) {
+        CE(launch_interp<T>(I, nodes, w, w.grid, 2, nullptr, parts + 2 * N3, s));
+        CE(launch_to_double<T>(w.vsr, parts + N3, (int)N3, s));
+    } else {
+        CE(launch_interp<T>(I, nodes, w, w.grid, 0, vel, nullptr, s));
+    }
+    if (want_psi) {
+        TRY(fft_inv<T>(c, w.spec_psi, s));
+        if (psi_parts) {
+            CE(launch_interp<T>(I, nodes, w, w.grid, 2, nullptr, psi_parts + 2 * N3, s));
+            CE(launch_to_double<T>(w.psr, psi_parts + N3, (int)N3, s));
+        } else {
+            CE(launch_interp<T>(I, nodes, w, w.grid, 1, psi, nullptr, s));
+        }
+    }
+    rec(c, 9, s);
+    return BS_OK;
+}
+
+int check_ctx(bs_ctx* c)
+{
+    if (!c) return fail(BS_ERR_ARG, "null context");
+    if (!c->have_fil) return fail(BS_ERR_STATE, "bs_set_filaments has not been called");
+    CUDA_TRY(cudaSetDevice(c->device));
+    return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bs_last_error(void) { return g_err.c_str(); }
+
+int bs_params_from_beta(double beta, const double L[3], int M, long long N, bs_params* out)
+{
+    if (!out || !L) return fail(BS_ERR_ARG, "null argument");
+    if (!(beta > 0)) return fail(BS_ERR_ARG, "beta must be positive");
+    for (int c = 0; c < 3; ++c)
+        if (!(L[c] > 0)) return fail(BS_ERR_ARG, "L must be positive");
+    if (M <= 0 && N <= 0) return fail(BS_ERR_ARG, "need M > 0 or N > 0");
+    // Table tab:performance: beta, C_beta, w (sigma = 1.5)
+    static const double tb[7][3] = { { 2.0, 2.06, 4 }, { 2.5, 1.92, 6 }, { 3.5, 1.71, 8 }, { 4.0, 1.64, 10 },
+                                     { 4.5, 1.57, 12 }, { 5.0, 1.52, 14 }, { 5.5, 1.47, 16 } };
+    memset(out, 0, sizeof *out);
+    const double Lmin = std::min(L[0], std::min(L[1], L[2]));
+    int best = 0;
+    for (int i = 1; i < 7; ++i)
+        if (fabs(tb[i][0] - beta) < fabs(tb[best][0] - beta)) best = i;
+    double Cb;
+    if (beta < tb[0][0] || beta > tb[6][0]) {
+        Cb = 2.6 * pow(beta, -1.0 / 3.0);  // empirical fit of Sec. 5.3
+    } else {
+        int i = 0;
+        while (i < 5 && beta > tb[i + 1][0]) ++i;
+        const double t = (beta - tb[i][0]) / (tb[i + 1][0] - tb[i][0]);
+        Cb = tb[i][1] + t * (tb[i + 1][1] - tb[i][1]);
+    }
+    int Mv = M;
+    if (M <= 0) {
+        double alpha = Cb * cbrt((double)N) / Lmin;          // Eq. alpha_optimal_performance
+        alpha = std::max(alpha, 2.0 * beta / Lmin);          // keeps rc <= L/2
+        const int K = (int)ceil(beta * alpha * Lmin / kPi);  // k_max = 2 beta alpha
+        Mv = 2 * K + 1;
+    }
+    const int K = (Mv - 1) / 2;
+    const double kmax = 2.0 * kPi * K / Lmin;
+    out->alpha = kmax / (2.0 * beta);
+    out->rc = beta / out->alpha;
+    for (int c = 0; c < 3; ++c) {
+        out->L[c] = L[c];
+        // the same k_max on every axis: K_c = floor(K L_c / min L)
+        out->M[c] = (L[c] == Lmin) ? Mv : 2 * (int)floor(K * L[c] / Lmin + 1e-9) + 1;
+    }
+    out->kappa = 1.0;
+    out->a = 1e-8;
+    out->delta = 0.25;
+    out->quad_Q = 3;
+    out->spline_order = 4;
+    out->nufft_sigma = 1.5;
+    out->nufft_w = (int)tb[best][2];
+    out->precision = BS_FP64;
+    out->flags = 0;
+    out->cell_div = 0;
+    return BS_OK;
+}
+
+int bs_error_estimate(const bs_params* p, double total_length, double* eps_v, double* eps_psi)
+{
+    if (!p || !(total_length >= 0)) return fail(BS_ERR_ARG, "bad argument");
+    const double V = p->L[0] * p->L[1] * p->L[2];
+    const double beta = p->alpha * p->rc;
+    const double k = p->kappa, a = p->alpha, Lt = total_length;
+    const double g = sqrt(Lt / (8.0 * kPi * V));
+    if (eps_v) *eps_v = k * (Lt / (sqrt(kPi) * a * V) + g / beta) * exp(-beta * beta);
+    if (eps_psi) *eps_psi = k / (2.0 * a) * (Lt / (a * V) + g / sqrt(beta)) * exp(-beta * beta) / pow(beta, 1.5);
+    return BS_OK;
+}
+
+int bs_nufft_setup(const bs_params* p, int n_g[3], double* table)
+{
+    if (!p || !n_g) return fail(BS_ERR_ARG, "null argument");
+    Derived d;
+    TRY(derive(p, &d));
+    int o = 0;
+    for (int c = 0; c < 3; ++c) {
+        n_g[c] = d.ng[c];
+        if (table) {
+            kb_fourier(d.zeta, p->nufft_w, d.ng[c], d.K[c], table + o);
+            o += d.K[c] + 1;
+        }
+    }
+    return BS_OK;
+}
+
+int bs_create(bs_ctx** out, const bs_params* p, void* stream)
+{
+    if (!out || !p) return fail(BS_ERR_ARG, "null argument");
+    *out = nullptr;
+    bs_ctx* c = new bs_ctx();
+    c->p = *p;
+    int rc = derive(p, &c->d);
+    if (rc != BS_OK) {
+        delete c;
+        return rc;
+    }
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    for (int i = 0; i < bs_ctx::kStages && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_t[i]);
+    if (e != cudaSuccess) {
+        rc = fail(BS_ERR_CUDA, "CUDA set-up failed: %s", cudaGetErrorString(e));
+        bs_destroy(c);
+        return rc;
+    }
+    c->stream = (cudaStream_t)stream;
+    rc = (p->precision == BS_FP64) ? alloc_grids<double>(c) : alloc_grids<float>(c);
+    if (rc != BS_OK) {
+        std::string msg = g_err;
+        bs_destroy(c);
+        g_err = msg;
+        return rc;
+    }
+    *out = c;
+    return BS_OK;
+}
+
+int bs_set_stream(bs_ctx* c, void* stream)
+{
+    if (!c) return fail(BS_ERR_ARG, "null context");
+    c->stream = (cudaStream_t)stream;
+    return BS_OK;
+}
+
+int bs_set_filaments(bs_ctx* c, int nfil, const int64_t* offsets, const int32_t* closing)
+{
+    if (!c) return fail(BS_ERR_ARG, "null context");
+    if (nfil < 0 || (nfil > 0 && !offsets)) return fail(BS_ERR_ARG, "bad filament count or offsets");
+    std::vector<int64_t> off(nfil + 1, 0);
+    if (nfil > 0) {
+        if (offsets[0] != 0) return fail(BS_ERR_ARG, "offsets[0] must be 0");
+        for (int l = 0; l <= nfil; ++l) off[l] = offsets[l];
+    }
+    long long sumn[3] = { 0, 0, 0 };
+    for (int l = 0; l < nfil; ++l) {
+        const int64_t n = off[l + 1] - off[l];
+        if (n < c->p.spline_order)
+            return fail(BS_ERR_SPLINE, "filament %d has %lld nodes < spline order %d", l, (long long)n,
+                        c->p.spline_order);
+        if (closing)
+            for (int k = 0; k < 3; ++k) sumn[k] += closing[3 * l + k];
+    }
+    if (sumn[0] || sumn[1] || sumn[2])
+        return fail(BS_ERR_NET_VORTICITY, "sum of closing offsets is (%lld,%lld,%lld), must be 0", sumn[0], sumn[1],
+                    sumn[2]);
+    const long long N = off[nfil];
+    if (N * c->p.quad_Q > (1LL << 31) - 1) return fail(BS_ERR_ARG, "too many quadrature points");
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    free_list(c, c->alloc_n);  // drop the buffers of a previous topology
+    c->w.off = nullptr;
+    std::vector<int> fil_of((size_t)N), prev((size_t)N);
+    std::vector<double> shift(3 * (size_t)nfil, 0.0);
+    for (int l = 0; l < nfil; ++l) {
+        for (int64_t j = off[l]; j < off[l + 1]; ++j) {
+            fil_of[(size_t)j] = l;
+            prev[(size_t)j] = (int)(j == off[l] ? off[l + 1] - 1 : j - 1);
+        }
+        if (closing)
+            for (int k = 0; k < 3; ++k) shift[3 * l + k] = closing[3 * l + k] * c->p.L[k];
+    }
+    c->nfil = nfil;
+    c->N = N;
+    c->NQ = N * c->p.quad_Q;
+    c->have_fil = false;
+    int rc = (c->p.precision == BS_FP64) ? alloc_filaments<double>(c, off, fil_of, prev, shift)
+                                         : alloc_filaments<float>(c, off, fil_of, prev, shift);
+    if (rc != BS_OK) return rc;
+    c->have_fil = true;
+    return BS_OK;
+}
+
+int bs_compute(bs_ctx* c, const double* nodes, double* vel, double* psi)
+{
+    TRY(check_ctx(c));
+    if (c->N == 0) return BS_OK;
+    if (!nodes || !vel) return fail(BS_ERR_ARG, "null nodes or vel");
+    if (psi && !(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "psi requested without BS_WANT_PSI");
+    return c->p.precision == BS_FP64 ? run<double>(c, nodes, vel, psi, nullptr, nullptr)
+                                     : run<float>(c, nodes, vel, psi, nullptr, nullptr);
+}
+
+int bs_compute_host(bs_ctx* c, const double* nodes, double* vel, double* psi)
+{
+    TRY(check_ctx(c));
+    if (c->N == 0) return BS_OK;
+    if (!nodes || !vel) return fail(BS_ERR_ARG, "null nodes or vel");
+    if (psi && !(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "psi requested without BS_WANT_PSI");
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
+    CUDA_TRY(cudaMemcpyAsync(c->w.nodes_in, nodes, bytes, cudaMemcpyHostToDevice, c->stream));
+    int rc = c->p.precision == BS_FP64
+                 ? run<double>(c, c->w.nodes_in, c->w.vel_out, psi ? c->w.psi_out : nullptr, nullptr, nullptr)
+                 : run<float>(c, c->w.nodes_in, c->w.vel_out, psi ? c->w.psi_out : nullptr, nullptr, nullptr);
+    if (rc != BS_OK) return rc;
+    CUDA_TRY(cudaMemcpyAsync(vel, c->w.vel_out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (psi) CUDA_TRY(cudaMemcpyAsync(psi, c->w.psi_out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return BS_OK;
+}
+
+int bs_compute_parts(bs_ctx* c, const double* nodes, double* parts, double* psi_parts)
+{
+    TRY(check_ctx(c));
+    if (c->N == 0) return BS_OK;
+    if (!nodes || !parts) return fail(BS_ERR_ARG, "null nodes or parts");
+    if (psi_parts && !(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "psi requested without BS_WANT_PSI");
+    return c->p.precision == BS_FP64 ? run<double>(c, nodes, nullptr, nullptr, parts, psi_parts)
+                                     : run<float>(c, nodes, nullptr, nullptr, parts, psi_parts);
+}
+
+int bs_get_quadrature(bs_ctx* c, const double* nodes, double* qX, double* qq)
+{
+    TRY(check_ctx(c));
+    if (c->N == 0) return BS_OK;
+    if (!nodes || !qX || !qq) return fail(BS_ERR_ARG, "null argument");
+    GeomP G;
+    fill_geom(c, G);
+    if (c->p.precision == BS_FP64) {
+        CE(launch_spline<double>(nodes, c->w, c->nfil, c->stream));
+        CE(launch_export_quadrature<double>(G, nodes, c->w, qX, qq, c->stream));
+    } else {
+        CE(launch_spline<float>(nodes, c->w, c->nfil, c->stream));
+        CE(launch_export_quadrature<float>(G, nodes, c->w, qX, qq, c->stream));
+    }
+    return BS_OK;
+}
+
+int bs_status(bs_ctx* c)
+{
+    if (!c) return fail(BS_ERR_ARG, "null context");
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->side));
+    int st = 0;
+    if (c->w.status) {
+        CUDA_TRY(cudaMemcpy(&st, c->w.status, sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
+    }
+    if (st & ST_NONFINITE) return fail(BS_ERR_NONFINITE, "non-finite node position");
+    if (st & ST_GEOMETRY) return fail(BS_ERR_GEOMETRY, "a segment is longer than min(L)/4");
+    return BS_OK;
+}
+
+int bs_stage_times(bs_ctx* c, float* ms, int n, int* n_out)
+{
+    if (!c || !ms) return fail(BS_ERR_ARG, "null argument");
+    if (!(c->p.flags & BS_TIMING)) return fail(BS_ERR_STATE, "context created without BS_TIMING");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const int ns = bs_ctx::kStages - 1;
+    for (int i = 0; i < ns && i < n; ++i) {
+        float t = 0;
+        CUDA_TRY(cudaEventElapsedTime(&t, c->ev_t[i], c->ev_t[i + 1]));
+        ms[i] = t;
+    }
+    if (n_out) *n_out = ns;
+    return BS_OK;
+}
+
+int bs_workspace_bytes(bs_ctx* c, long long* bytes)
+{
+    if (!c || !bytes) return fail(BS_ERR_ARG, "null argument");
+    *bytes = c->bytes;
+    return BS_OK;
+}
+
+void bs_destroy(bs_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
+    if (c->plans) {
+        if (c->plan_fwd) cufftDestroy(c->plan_fwd);
+        if (c->plan_inv) cufftDestroy(c->plan_inv);
+    }
+    free_list(c, c->alloc_n);
+    free_list(c, c->alloc_g);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int i = 0; i < bs_ctx::kStages; ++i)
+        if (c->ev_t[i]) cudaEventDestroy(c->ev_t[i]);
+    if (c->side) cudaStreamDestroy(c->side);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Internal declarations of the bsewald CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include "bsewald.h"
+
+namespace bsw {
+
+constexpr int kMaxQ = 8;
+constexpr int kMaxW = 16;
+constexpr int kThreads = 256;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// Device status bits (bs_status).
+enum : int { ST_NONFINITE = 1, ST_GEOMETRY = 2 };
+
+// Short-range source: offset from its cell origin, charge, x-cell index and
+// the global index of its segment (the node at the segment start).
+template <typename T> struct SrRec;
+template <> struct __align__(16) SrRec<float> {
+    float o[3];
+    int cx;
+    float q[3];
+    int seg;
+};
+template <> struct __align__(16) SrRec<double> {
+    double o[3];
+    double q[3];
+    int cx;
+    int seg;
+    int pad[2];
+};
+
+// Short-range target: node offset from its cell origin and packed cell.
+template <typename T> struct __align__(16) SrTgt {
+    T o[3];
+    int cell;
+};
+
+// Long-range source: fractional grid position, charge, packed base index
+// (10 bits per axis).
+template <typename T> struct LrRec;
+template <> struct __align__(16) LrRec<float> {
+    float f[3];
+    int base;
+    float q[3];
+    int pad;
+};
+template <> struct __align__(16) LrRec<double> {
+    double f[3];
+    double q[3];
+    int base;
+    int pad[3];
+};
+
+// Parameters of the geometry / node kernel.
+struct GeomP {
+    double L[3];
+    int N;
+    int nfil;
+    int Q;
+    double gh[kMaxQ];   // Gauss-Legendre nodes on [0,1]
+    double gw[kMaxQ];   // weights, sum 1
+    double kappa, a, delta, alpha;
+    int nc[3];          // short-range cells per axis
+    double hc[3];       // cell edge
+    int ng[3];          // spread grid
+    double hg[3];       // grid spacing
+    int w;              // kernel width (even)
+    int tile[3];        // spread tile edge
+    int ntile[3];
+    double seg_max;     // longest allowed segment chord (min L / 4)
+    int want_psi;
+};
+
+struct ShortP {
+    int N;
+    int nc[3];
+    double hc[3];
+    double L[3];
+    int m;              // cells per cut-off
+    double rc2;
+    double alpha;
+    double pref;        // kappa / 4 pi
+    int want_psi;
+};
+
+struct SpreadP {
+    int ng[3];
+    int tile[3];
+    int ntile[3];
+    int w;
+    double zeta;
+};
+
+struct KspaceP {
+    int ng[3];
+    int nh;             // ng[2]/2 + 1
+    int K[3];           // mode cube
+    double kk[3];       // 2 pi / L
+    double scale;       // kappa / V
+    int want_psi;
+};
+
+struct InterpP {
+    int N;
+    int ng[3];
+    double hg[3];
+    double L[3];
+    int w;
+    double zeta;
+    int want_psi;
+};
+
+// Workspace buffers (device) of one context; T-typed buffers are void*.
+struct Work {
+    // topology
+    int64_t* off = nullptr;
+    int* fil_of = nullptr;
+    int* prev = nullptr;
+    double* shift = nullptr;
+    // spline
+    void* hseg = nullptr;   // N
+    void* dp = nullptr;     // N x 3 periodic increments
+    void* ds = nullptr;     // N x 3 chord vectors
+    void* Mm = nullptr;     // N x 3 moments
+    void* cpr = nullptr;    // N Thomas scratch
+    void* zz = nullptr;     // N Sherman-Morrison vector
+    void* Tper = nullptr;   // nfil
+    // node outputs
+    double* vls = nullptr;  // N x 3  v_local - v_self
+    double* pls = nullptr;  // N x 3  psi_local - psi_self
+    void* vsr = nullptr;    // N x 3  short range
+    void* psr = nullptr;
+    void* tgt = nullptr;    // N SrTgt
+    // sources
+    void* sr_rec = nullptr;   // NQ
+    void* sr_sorted = nullptr;
+    int* sr_key = nullptr;
+    void* lr_rec = nullptr;
+    void* lr_sorted = nullptr;
+    int* lr_key = nullptr;
+    // counting sorts
+    int* cell_cnt = nullptr;  // ncells + 1
+    int* cell_cur = nullptr;
+    int* tile_cnt = nullptr;  // ntiles + 1
+    int* tile_cur = nullptr;
+    int* scan_tmp = nullptr;   // short-range sort (side stream)
+    int* scan_tmp2 = nullptr;  // long-range sort (main stream)
+    // grids
+    void* grid = nullptr;     // 3 x ng^3 real
+    void* spec = nullptr;     // 3 x ng0 ng1 nh complex
+    void* spec_psi = nullptr; // 3 x ... (psi)
+    void* ktab = nullptr;     // per-axis k-space tables
+    void* fft_work = nullptr;
+    // host staging for bs_compute_host
+    double* nodes_in = nullptr;
+    double* vel_out = nullptr;
+    double* psi_out = nullptr;
+    int* status = nullptr;
+};
+
+// Launchers (explicit instantiations for float and double live in the .cu files).
+template <typename T>
+cudaError_t launch_spline(const double* nodes, const Work& w, int nfil, cudaStream_t s);
+template <typename T>
+cudaError_t launch_nodes(const GeomP& P, const double* nodes, const Work& w, double* part_local, double* part_self,
+                         double* psi_local, double* psi_self, cudaStream_t s);
+template <typename T>
+cudaError_t launch_export_quadrature(const GeomP& P, const double* nodes, const Work& w, double* qX, double* qq,
+                                     cudaStream_t s);
+template <typename T>
+cudaError_t launch_sort_sr(const Work& w, int NQ, int ncells, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sort_lr(const Work& w, int NQ, int ntiles, cudaStream_t s);
+template <typename T>
+cudaError_t launch_short(const ShortP& P, const Work& w, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread(const SpreadP& P, const Work& w, int ntiles, cudaStream_t s);
+template <typename T>
+cudaError_t launch_kspace(const KspaceP& P, const Work& w, cudaStream_t s);
+template <typename T>
+cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, const void* grid, int what,
+                          double* out, double* part_long, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);
+
+// Exclusive scan of n ints in place (cnt[n] receives the total); tmp holds
+// scan_blocks(n) ints.
+cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s);
+int scan_blocks(int n);
+
+}  // namespace bsw

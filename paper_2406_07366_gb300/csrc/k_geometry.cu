@@ -1,0 +1,469 @@
+// Curve geometry on the GPU: periodic cubic spline fit per filament, then one
+// pass per node that produces the quadrature sources of its outgoing segment
+// (Sec. 2.6, Eq. line_integral_quadrature; Sec. 3.3 charges
+// q = w_i dtau_j s'(tau)), the local term (Eqs. BS_local,
+// streamfunction_local) and the long-range self term on the 2Q points of
+// the two adjacent segments (Eqs. velocity_longrange_self,
+// streamfunction_longrange_self).
+//
+// Spline form.  Appendix B fits a periodic B-spline with knots at the
+// chord-length parameters.  For order 4 the same curve (the unique periodic
+// C2 cubic through the nodes with those knots) is obtained here from its
+// second derivatives M_j at the knots, which solve the cyclic tridiagonal
+// system
+//   h_{j-1} M_{j-1} + 2 (h_{j-1} + h_j) M_j + h_j M_{j+1}
+//       = 6 (dp_j / h_j - dp_{j-1} / h_{j-1}),
+// solved with the Sherman-Morrison correction and the Thomas algorithm (the
+// procedure the appendix names for the cyclic system).  On segment j, with
+// u = tau - tau_j in [0, h_j],
+//   p(u) - p_j = b_j u + M_j u^2 / 2 + (M_{j+1} - M_j) u^3 / (6 h_j),
+//   b_j = dp_j / h_j - h_j (2 M_j + M_{j+1}) / 6.
+// Unclosed curves with s(tau + T) = s(tau) + n L interpolate the periodic
+// part p = s - n L tau / T and add the drift n L / T back.
+//
+// Precision.  Node positions stay float64.  Every quantity that is a small
+// difference (chords, increments, moments, the offset of a quadrature point
+// from its node) is carried in T; the absolute position of a source is
+// s_j (float64) + offset (T), wrapped and split into a cell index plus a
+// T-precision offset from the cell origin.
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bsw {
+
+template <typename T>
+__device__ __forceinline__ T tsqrt(T x) { return sqrt(x); }
+
+// g^(f)(x) = erf(x) - 2x/sqrt(pi) exp(-x^2) (Eq. ewald_derivative_weight_functions).
+// Below x = 1/2 the two terms cancel; there the Taylor series of both terms,
+// combined term by term, gives (2/sqrt(pi)) sum_{n>=1} (-1)^{n+1} 2n x^{2n+1}/(n!(2n+1)).
+template <typename T>
+__device__ __forceinline__ T g_far(T x)
+{
+    const T two_over_sqrtpi = (T)1.12837916709551257390;
+    if (x < (T)0.5) {
+        const int nterms = sizeof(T) == 4 ? 8 : 15;
+        T x2 = x * x, pw = x, s = 0;
+        T fact = 1;
+        for (int n = 1; n <= nterms; ++n) {
+            pw *= x2;          // x^{2n+1}
+            fact *= (T)n;      // n!
+            T t = (T)(2 * n) * pw / (fact * (T)(2 * n + 1));
+            s += (n & 1) ? t : -t;
+        }
+        return two_over_sqrtpi * s;
+    }
+    return erf(x) - two_over_sqrtpi * x * exp(-x * x);
+}
+
+// ---------------------------------------------------------------------------
+// Spline fit: one thread per filament.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_spline(const double* __restrict__ nodes, const int64_t* __restrict__ off,
+                         const double* __restrict__ shift, int nfil, T* __restrict__ hseg, T* __restrict__ dp,
+                         T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ cpr, T* __restrict__ zz,
+                         T* __restrict__ Tper)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfil) return;
+    const int64_t o = off[f];
+    const int n = (int)(off[f + 1] - o);
+    const double sh0 = shift[3 * f], sh1 = shift[3 * f + 1], sh2 = shift[3 * f + 2];
+
+    // chord lengths and period (Appendix B chord-length parameter)
+    double Tsum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double* a = nodes + 3 * (o + j);
+        double b0, b1, b2;
+        if (j + 1 < n) {
+            const double* b = a + 3;
+            b0 = b[0]; b1 = b[1]; b2 = b[2];
+        } else {
+            const double* b = nodes + 3 * o;
+            b0 = b[0] + sh0; b1 = b[1] + sh1; b2 = b[2] + sh2;
+        }
+        const double d0 = b0 - a[0], d1 = b1 - a[1], d2 = b2 - a[2];
+        const double h = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        Tsum += h;
+        hseg[o + j] = (T)h;
+        ds[3 * (o + j) + 0] = (T)d0;
+        ds[3 * (o + j) + 1] = (T)d1;
+        ds[3 * (o + j) + 2] = (T)d2;
+        dp[3 * (o + j) + 0] = (T)d0;  // closed curve: dp = ds; drift removed below otherwise
+        dp[3 * (o + j) + 1] = (T)d1;
+        dp[3 * (o + j) + 2] = (T)d2;
+    }
+    Tper[f] = (T)Tsum;
+    const bool closed = (sh0 == 0.0 && sh1 == 0.0 && sh2 == 0.0);
+    if (!closed) {
+        // periodic increments dp_j = ds_j - n L h_j / T
+        const double invT = 1.0 / Tsum;
+        for (int j = 0; j < n; ++j) {
+            const double h = (double)hseg[o + j];
+            dp[3 * (o + j) + 0] = (T)((double)ds[3 * (o + j) + 0] - sh0 * h * invT);
+            dp[3 * (o + j) + 1] = (T)((double)ds[3 * (o + j) + 1] - sh1 * h * invT);
+            dp[3 * (o + j) + 2] = (T)((double)ds[3 * (o + j) + 2] - sh2 * h * invT);
+        }
+    }
+
+    // Cyclic tridiagonal system, row j: a_j M_{j-1} + b_j M_j + c_j M_{j+1} = r_j,
+    // a_j = h_{j-1}, b_j = 2 (h_{j-1} + h_j), c_j = h_j; corners a_0 (col n-1)
+    // and c_{n-1} (col 0).  Sherman-Morrison with gamma = -b_0:
+    //   B = A - u v^T, u = (gamma, 0, ..., c_{n-1}), v = (1, 0, ..., a_0 / gamma).
+    const T hl = hseg[o + n - 1];
+    const T a0 = hl, cn = hl;
+    const T b0 = (T)2 * (hl + hseg[o]);
+    const T gamma = -b0;
+    T cprev = 0, dprev0 = 0, dprev1 = 0, dprev2 = 0, zprev = 0;
+    T dpm0 = dp[3 * (o + n - 1) + 0], dpm1 = dp[3 * (o + n - 1) + 1], dpm2 = dp[3 * (o + n - 1) + 2];
+    T hm = hl;
+    for (int j = 0; j < n; ++j) {
+        const T hj = hseg[o + j];
+        const T dj0 = dp[3 * (o + j) + 0], dj1 = dp[3 * (o + j) + 1], dj2 = dp[3 * (o + j) + 2];
+        const T a = (j == 0) ? (T)0 : hm;
+        T b = (T)2 * (hm + hj);
+        if (j == 0) b -= gamma;
+        if (j == n - 1) b -= a0 * cn / gamma;
+        const T c = (j == n - 1) ? (T)0 : hj;
+        const T r0 = (T)6 * (dj0 / hj - dpm0 / hm);
+        const T r1 = (T)6 * (dj1 / hj - dpm1 / hm);
+        const T r2 = (T)6 * (dj2 / hj - dpm2 / hm);
+        const T uj = (j == 0) ? gamma : ((j == n - 1) ? cn : (T)0);
+        const T m = b - a * cprev;
+        const T im = (T)1 / m;
+        cprev = c * im;
+        dprev0 = (r0 - a * dprev0) * im;
+        dprev1 = (r1 - a * dprev1) * im;
+        dprev2 = (r2 - a * dprev2) * im;
+        zprev = (uj - a * zprev) * im;
+        cpr[o + j] = cprev;
+        Mm[3 * (o + j) + 0] = dprev0;
+        Mm[3 * (o + j) + 1] = dprev1;
+        Mm[3 * (o + j) + 2] = dprev2;
+        zz[o + j] = zprev;
+        hm = hj;
+        dpm0 = dj0; dpm1 = dj1; dpm2 = dj2;
+    }
+    // back substitution (in place)
+    T x0 = Mm[3 * (o + n - 1) + 0], x1 = Mm[3 * (o + n - 1) + 1], x2 = Mm[3 * (o + n - 1) + 2];
+    T zx = zz[o + n - 1];
+    for (int j = n - 2; j >= 0; --j) {
+        const T cj = cpr[o + j];
+        x0 = Mm[3 * (o + j) + 0] - cj * x0;
+        x1 = Mm[3 * (o + j) + 1] - cj * x1;
+        x2 = Mm[3 * (o + j) + 2] - cj * x2;
+        zx = zz[o + j] - cj * zx;
+        Mm[3 * (o + j) + 0] = x0;
+        Mm[3 * (o + j) + 1] = x1;
+        Mm[3 * (o + j) + 2] = x2;
+        zz[o + j] = zx;
+    }
+    const T vfac = a0 / gamma;
+    const T z0 = zz[o], zn = zz[o + n - 1];
+    const T den = (T)1 + z0 + vfac * zn;
+    const T f0 = (Mm[3 * o + 0] + vfac * Mm[3 * (o + n - 1) + 0]) / den;
+    const T f1 = (Mm[3 * o + 1] + vfac * Mm[3 * (o + n - 1) + 1]) / den;
+    const T f2 = (Mm[3 * o + 2] + vfac * Mm[3 * (o + n - 1) + 2]) / den;
+    for (int j = 0; j < n; ++j) {
+        const T zj = zz[o + j];
+        Mm[3 * (o + j) + 0] -= f0 * zj;
+        Mm[3 * (o + j) + 1] -= f1 * zj;
+        Mm[3 * (o + j) + 2] -= f2 * zj;
+    }
+}
+
+// Wrap x into [0, L); non-finite input maps to 0 and raises the flag.
+__device__ __forceinline__ double wrap_box(double x, double L, bool& bad)
+{
+    if (!isfinite(x)) {
+        bad = true;
+        return 0.0;
+    }
+    double y = x - L * floor(x / L);
+    if (y >= L) y -= L;
+    if (y < 0.0) y = 0.0;
+    return y;
+}
+
+template <typename T>
+struct SegPoly {
+    T b[3], m[3], c3[3], drift[3], h;
+    __device__ __forceinline__ void eval(T u, T* delta, T* sdot) const
+    {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            delta[c] = ((c3[c] * u + (T)0.5 * m[c]) * u + b[c]) * u + drift[c] * u;
+            sdot[c] = ((T)3 * c3[c] * u + m[c]) * u + b[c] + drift[c];
+        }
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void make_poly(SegPoly<T>& P, const T* __restrict__ hseg, const T* __restrict__ dp,
+                                          const T* __restrict__ Mm, int j, int jn, const T drift[3])
+{
+    const T h = hseg[j];
+    P.h = h;
+    const T ih = (T)1 / h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T Mj = Mm[3 * j + c], Mn = Mm[3 * jn + c];
+        P.m[c] = Mj;
+        P.b[c] = dp[3 * j + c] * ih - h * ((T)2 * Mj + Mn) / (T)6;
+        P.c3[c] = (Mn - Mj) * ih / (T)6;
+        P.drift[c] = drift[c];
+    }
+}
+
+// Accumulate the self terms of one C_0 point: r from the node, charge q.
+template <typename T>
+__device__ __forceinline__ void self_add(const T r[3], const T q[3], T alpha, T* vs, T* ps)
+{
+    const T rr = tsqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const T x = alpha * rr;
+    const T fv = g_far(x) / (rr * rr * rr);
+    const T fp = erf(x) / rr;
+    vs[0] += fv * (r[1] * q[2] - r[2] * q[1]);
+    vs[1] += fv * (r[2] * q[0] - r[0] * q[2]);
+    vs[2] += fv * (r[0] * q[1] - r[1] * q[0]);
+    ps[0] += fp * q[0];
+    ps[1] += fp * q[1];
+    ps[2] += fp * q[2];
+}
+
+template <typename T>
+__global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __restrict__ fil_of,
+                        const int* __restrict__ prev, const int64_t* __restrict__ off, const double* __restrict__ shift,
+                        const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ ds,
+                        const T* __restrict__ Mm, const T* __restrict__ Tper, SrRec<T>* __restrict__ sr_rec,
+                        int* __restrict__ sr_key, LrRec<T>* __restrict__ lr_rec, int* __restrict__ lr_key,
+                        SrTgt<T>* __restrict__ tgt, double* __restrict__ vls, double* __restrict__ pls,
+                        double* __restrict__ part_local, double* __restrict__ part_self,
+                        double* __restrict__ psi_local, double* __restrict__ psi_self, int* __restrict__ status)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.N) return;
+    const int f = fil_of[j];
+    const int jp = prev[j];
+    const int jn = (j + 1 < (int)off[f + 1]) ? j + 1 : (int)off[f];
+    const T Tp = Tper[f];
+    const T drift[3] = { (T)shift[3 * f] / Tp, (T)shift[3 * f + 1] / Tp, (T)shift[3 * f + 2] / Tp };
+    const double sj[3] = { nodes[3 * j], nodes[3 * j + 1], nodes[3 * j + 2] };
+    bool bad = false;
+    int flags = 0;
+
+    SegPoly<T> S;
+    make_poly(S, hseg, dp, Mm, j, jn, drift);
+    if ((double)S.h > P.seg_max || !(S.h > (T)0)) flags |= ST_GEOMETRY;
+
+    T vs[3] = { 0, 0, 0 }, ps[3] = { 0, 0, 0 };
+    T lp = 0, lm = 0;
+    const T alpha = (T)P.alpha;
+
+    // Outgoing segment j: sources for both ranges, self term, l^+.
+    for (int i = 0; i < P.Q; ++i) {
+        const T u = (T)P.gh[i] * S.h;
+        T del[3], sd[3];
+        S.eval(u, del, sd);
+        const T wq = (T)P.gw[i] * S.h;
+        T q[3] = { wq * sd[0], wq * sd[1], wq * sd[2] };
+        lp += wq * tsqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+        self_add(del, q, alpha, vs, ps);
+
+        bool b2 = false;
+        double xw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xw[c] = wrap_box(sj[c] + (double)del[c], P.L[c], b2);
+        if (b2) {
+            bad = true;
+            q[0] = q[1] = q[2] = 0;
+        }
+        const int p = j * P.Q + i;
+        // short-range record
+        SrRec<T> R;
+        int ci[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int k = (int)(xw[c] / P.hc[c]);
+            k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
+            ci[c] = k;
+            R.o[c] = (T)(xw[c] - k * P.hc[c]);
+            R.q[c] = q[c];
+        }
+        R.cx = ci[0];
+        R.seg = j;
+        sr_rec[p] = R;
+        sr_key[p] = ci[0] + P.nc[0] * (ci[1] + P.nc[1] * ci[2]);
+        // long-range record
+        LrRec<T> G;
+        int ib[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double g = xw[c] / P.hg[c];
+            int k = (int)floor(g);
+            k = k < 0 ? 0 : (k >= P.ng[c] ? P.ng[c] - 1 : k);
+            ib[c] = k;
+            double fr = g - (double)k;
+            fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
+            G.f[c] = (T)fr;
+            G.q[c] = q[c];
+        }
+        G.base = ib[0] | (ib[1] << 10) | (ib[2] << 20);
+        lr_rec[p] = G;
+        lr_key[p] = ib[0] / P.tile[0] + P.ntile[0] * (ib[1] / P.tile[1] + P.ntile[1] * (ib[2] / P.tile[2]));
+    }
+
+    // Incoming segment jp -> j: self term and l^-.
+    {
+        SegPoly<T> R;
+        make_poly(R, hseg, dp, Mm, jp, j, drift);
+        const T dsx = ds[3 * jp], dsy = ds[3 * jp + 1], dsz = ds[3 * jp + 2];
+        for (int i = 0; i < P.Q; ++i) {
+            const T u = (T)P.gh[i] * R.h;
+            T del[3], sd[3];
+            R.eval(u, del, sd);
+            const T wq = (T)P.gw[i] * R.h;
+            const T q[3] = { wq * sd[0], wq * sd[1], wq * sd[2] };
+            lm += wq * tsqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+            const T r[3] = { del[0] - dsx, del[1] - dsy, del[2] - dsz };
+            self_add(r, q, alpha, vs, ps);
+        }
+    }
+
+    // Node geometry: sdot = b + drift, sddot = M_j; s' x s'' = (sdot x sddot)/|sdot|^3.
+    const T d0 = S.b[0] + drift[0], d1 = S.b[1] + drift[1], d2 = S.b[2] + drift[2];
+    const T sn = tsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    const T is3 = (T)1 / (sn * sn * sn);
+    const T bx = (d1 * S.m[2] - d2 * S.m[1]) * is3;
+    const T by = (d2 * S.m[0] - d0 * S.m[2]) * is3;
+    const T bz = (d0 * S.m[1] - d1 * S.m[0]) * is3;
+    const double lg = log(2.0 * sqrt((double)lm * (double)lp) / P.a);
+    const double pv = P.kappa / (4.0 * kPi);
+    const double vl[3] = { pv * (double)bx * (lg - P.delta), pv * (double)by * (lg - P.delta),
+                           pv * (double)bz * (lg - P.delta) };
+    const double vx[3] = { pv * (double)vs[0], pv * (double)vs[1], pv * (double)vs[2] };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vls[3 * j + c] = vl[c] - vx[c];
+    if (part_local) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            part_local[3 * j + c] = vl[c];
+            part_self[3 * j + c] = vx[c];
+        }
+    }
+    if (P.want_psi) {
+        const double pp = P.kappa / (2.0 * kPi);
+        const double ip = 1.0 / (double)sn;
+        const double pl[3] = { pp * (double)d0 * ip * (lg - (P.delta - 1.0)), pp * (double)d1 * ip * (lg - (P.delta - 1.0)),
+                               pp * (double)d2 * ip * (lg - (P.delta - 1.0)) };
+        const double px[3] = { pv * (double)ps[0], pv * (double)ps[1], pv * (double)ps[2] };
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pls[3 * j + c] = pl[c] - px[c];
+        if (psi_local) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                psi_local[3 * j + c] = pl[c];
+                psi_self[3 * j + c] = px[c];
+            }
+        }
+    }
+
+    // Target record of the node for the short range.
+    {
+        bool b2 = false;
+        SrTgt<T> tg;
+        int ci[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double xw = wrap_box(sj[c], P.L[c], b2);
+            int k = (int)(xw / P.hc[c]);
+            k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
+            ci[c] = k;
+            tg.o[c] = (T)(xw - k * P.hc[c]);
+        }
+        tg.cell = ci[0] + P.nc[0] * (ci[1] + P.nc[1] * ci[2]);
+        tgt[j] = tg;
+        if (b2) bad = true;
+    }
+    if (bad) flags |= ST_NONFINITE;
+    if (flags) atomicOr(status, flags);
+}
+
+// Quadrature export for bs_get_quadrature (float64, wrapped positions).
+template <typename T>
+__global__ void k_export_quad(GeomP P, const double* __restrict__ nodes, const int* __restrict__ fil_of,
+                              const int64_t* __restrict__ off, const double* __restrict__ shift,
+                              const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ Mm,
+                              const T* __restrict__ Tper, double* __restrict__ qX, double* __restrict__ qq)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.N) return;
+    const int f = fil_of[j];
+    const int jn = (j + 1 < (int)off[f + 1]) ? j + 1 : (int)off[f];
+    const T Tp = Tper[f];
+    const T drift[3] = { (T)shift[3 * f] / Tp, (T)shift[3 * f + 1] / Tp, (T)shift[3 * f + 2] / Tp };
+    SegPoly<T> S;
+    make_poly(S, hseg, dp, Mm, j, jn, drift);
+    for (int i = 0; i < P.Q; ++i) {
+        const T u = (T)P.gh[i] * S.h;
+        T del[3], sd[3];
+        S.eval(u, del, sd);
+        const T wq = (T)P.gw[i] * S.h;
+        const int p = j * P.Q + i;
+        bool b = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            qX[3 * p + c] = wrap_box(nodes[3 * j + c] + (double)del[c], P.L[c], b);
+            qq[3 * p + c] = (double)(wq * sd[c]);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_spline(const double* nodes, const Work& w, int nfil, cudaStream_t s)
+{
+    if (nfil <= 0) return cudaSuccess;
+    const int tb = 64;
+    k_spline<T><<<(nfil + tb - 1) / tb, tb, 0, s>>>(nodes, w.off, w.shift, nfil, (T*)w.hseg, (T*)w.dp, (T*)w.ds,
+                                                    (T*)w.Mm, (T*)w.cpr, (T*)w.zz, (T*)w.Tper);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nodes(const GeomP& P, const double* nodes, const Work& w, double* part_local, double* part_self,
+                         double* psi_local, double* psi_self, cudaStream_t s)
+{
+    if (P.N <= 0) return cudaSuccess;
+    const int tb = 128;
+    k_nodes<T><<<(P.N + tb - 1) / tb, tb, 0, s>>>(
+        P, nodes, w.fil_of, w.prev, w.off, w.shift, (const T*)w.hseg, (const T*)w.dp, (const T*)w.ds,
+        (const T*)w.Mm, (const T*)w.Tper, (SrRec<T>*)w.sr_rec, w.sr_key, (LrRec<T>*)w.lr_rec, w.lr_key,
+        (SrTgt<T>*)w.tgt, w.vls, w.pls, part_local, part_self, psi_local, psi_self, w.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_export_quadrature(const GeomP& P, const double* nodes, const Work& w, double* qX, double* qq,
+                                     cudaStream_t s)
+{
+    if (P.N <= 0) return cudaSuccess;
+    const int tb = 128;
+    k_export_quad<T><<<(P.N + tb - 1) / tb, tb, 0, s>>>(P, nodes, w.fil_of, w.off, w.shift, (const T*)w.hseg,
+                                                         (const T*)w.dp, (const T*)w.Mm, (const T*)w.Tper, qX, qq);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_spline<float>(const double*, const Work&, int, cudaStream_t);
+template cudaError_t launch_spline<double>(const double*, const Work&, int, cudaStream_t);
+template cudaError_t launch_nodes<float>(const GeomP&, const double*, const Work&, double*, double*, double*, double*,
+                                         cudaStream_t);
+template cudaError_t launch_nodes<double>(const GeomP&, const double*, const Work&, double*, double*, double*, double*,
+                                          cudaStream_t);
+template cudaError_t launch_export_quadrature<float>(const GeomP&, const double*, const Work&, double*, double*,
+                                                     cudaStream_t);
+template cudaError_t launch_export_quadrature<double>(const GeomP&, const double*, const Work&, double*, double*,
+                                                      cudaStream_t);
+
+}  // namespace bsw

@@ -1,0 +1,164 @@
+// Counting sorts that bin the quadrature sources: by short-range cell (the
+// cell lists of Sec. 5.3) and by spreading tile (the long-range spread).
+// count (atomics) -> exclusive scan (three launches, no inter-block waits)
+// -> scatter of the records into their bins.
+#include "bs_internal.cuh"
+
+namespace bsw {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+int scan_blocks(int n) { return (n + 1 + kScanTile - 1) / kScanTile; }
+
+__global__ void k_count(const int* __restrict__ key, int n, int* __restrict__ cnt)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[key[i]], 1);
+}
+
+// Block-wide inclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ int block_scan_incl(int v, int* sh_warp, int& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) sh_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < (int)(blockDim.x >> 5)) ? sh_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        sh_warp[lane] = w;
+    }
+    __syncthreads();
+    total = sh_warp[(blockDim.x >> 5) - 1];
+    int add = (wid > 0) ? sh_warp[wid - 1] : 0;
+    __syncthreads();
+    return v + add;
+}
+
+// Phase 1: per-tile sums of cnt[0..n] (entry n counts as 0).
+__global__ void k_scan_reduce(const int* __restrict__ cnt, int n, int* __restrict__ part)
+{
+    __shared__ int sh[32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = base + k;
+        if (i < n) s += cnt[i];
+    }
+    int total;
+    block_scan_incl(s, sh, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Phase 2: exclusive scan of the tile sums, one block, looping.
+__global__ void k_scan_parts(int* __restrict__ part, int nb)
+{
+    __shared__ int sh[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int i = b0 + threadIdx.x;
+        const int v = (i < nb) ? part[i] : 0;
+        int total;
+        const int inc = block_scan_incl(v, sh, total);
+        if (i < nb) part[i] = carry + inc - v;
+        carry += total;
+        __syncthreads();
+    }
+}
+
+// Phase 3: exclusive scan within each tile plus its offset, in place over
+// cnt[0..n]; cnt[n] becomes the grand total.
+__global__ void k_scan_apply(int* __restrict__ cnt, int n, const int* __restrict__ part)
+{
+    __shared__ int sh[32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = base + k;
+        v[k] = (i < n) ? cnt[i] : 0;
+        s += v[k];
+    }
+    int total;
+    const int inc = block_scan_incl(s, sh, total);
+    int run = part[blockIdx.x] + inc - s;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = base + k;
+        if (i <= n) cnt[i] = run;
+        run += v[k];
+    }
+}
+
+cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s)
+{
+    const int nb = scan_blocks(n);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(cnt, n, tmp);
+    k_scan_parts<<<1, kScanThreads, 0, s>>>(tmp, nb);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(cnt, n, tmp);
+    return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_scatter(const int* __restrict__ key, const R* __restrict__ in, int n, int* __restrict__ cur,
+                          R* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = atomicAdd(&cur[key[i]], 1);
+        out[p] = in[i];
+    }
+}
+
+template <typename R>
+static cudaError_t sort_records(const int* key, const R* in, R* out, int n, int* cnt, int* cur, int nbins, int* tmp,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nbins + 1), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        const int g = (n + kThreads - 1) / kThreads;
+        k_count<<<g, kThreads, 0, s>>>(key, n, cnt);
+    }
+    e = scan_exclusive(cnt, nbins, tmp, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(cur, cnt, sizeof(int) * (size_t)nbins, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        const int g = (n + kThreads - 1) / kThreads;
+        k_scatter<R><<<g, kThreads, 0, s>>>(key, in, n, cur, out);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sort_sr(const Work& w, int NQ, int ncells, cudaStream_t s)
+{
+    return sort_records<SrRec<T>>(w.sr_key, (const SrRec<T>*)w.sr_rec, (SrRec<T>*)w.sr_sorted, NQ, w.cell_cnt,
+                                  w.cell_cur, ncells, w.scan_tmp, s);
+}
+
+template <typename T>
+cudaError_t launch_sort_lr(const Work& w, int NQ, int ntiles, cudaStream_t s)
+{
+    return sort_records<LrRec<T>>(w.lr_key, (const LrRec<T>*)w.lr_rec, (LrRec<T>*)w.lr_sorted, NQ, w.tile_cnt,
+                                  w.tile_cur, ntiles, w.scan_tmp2, s);
+}
+
+template cudaError_t launch_sort_sr<float>(const Work&, int, int, cudaStream_t);
+template cudaError_t launch_sort_sr<double>(const Work&, int, int, cudaStream_t);
+template cudaError_t launch_sort_lr<float>(const Work&, int, int, cudaStream_t);
+template cudaError_t launch_sort_lr<double>(const Work&, int, int, cudaStream_t);
+
+}  // namespace bsw
