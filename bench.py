@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput of the Ewald-split periodic Biot-Savart velocity evaluation.
+
+One step = one full evaluation (bs_compute) of the velocity at every node
+of the workload: spline fit, quadrature sources, short range, long range
+(spread, FFT, k-space, FFT^-1, interpolation) and local / self terms.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
+replica of the workload (a single configuration does not shard without an
+exchange step) and `value` counts the nodes of all ranks
+over the slowest rank's time.  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "filament nodes/s per Biot–Savart eval at 1e-6 rel. err; FP32/batched vs FP64"
+UNIT = "nodes/s"
+L2_FLUSH_BYTES = 512 << 20
+KERNELS_PER_STEP = 16  # spline, nodes, 2 x (count, 3 scan, scatter), short, spread, k-space, interp
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="tangle1e5")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=16, help="oracle targets timed for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ helpers
+def workload(name):
+    from paper_2406_07366_gb300 import workloads as W
+    spec = W.WORKLOADS[name]
+    return spec, spec["gen"]()
+
+
+def make_params(B, spec, f, precision, flags=0):
+    w = spec["w"] if precision == B.BS_MIXED else max(spec["w"], 8)
+    return B.make_params(f.L, kappa=spec["kappa"], a=spec["a"], delta=spec["delta"], beta=spec["beta"],
+                         M=spec["M"], Q=spec["Q"], w=w, sigma=spec["sigma"], precision=precision, flags=flags)
+
+
+def spread_bytes(p, ng, NQ, real_bytes):
+    """Algorithmic bytes of one spread launch: write three real grids, read the
+    binned records once (32 B float / 64 B double) and the bin offsets."""
+    rec = 32 if real_bytes == 4 else 64
+    ntiles = (ng[0] // 8) * (ng[1] // 8) * (ng[2] // (32 if ng[2] % 32 == 0 else (16 if ng[2] % 16 == 0 else 8)))
+    return 3 * real_bytes * ng[0] * ng[1] * ng[2] + rec * NQ + 4 * (ntiles + 1)
+
+
+def oracle_fixed(f, spec):
+    """The oracle's per-evaluation fixed work: spline fit and quadrature of
+    all filaments, and the Fourier coefficients of all sources."""
+    import oracle
+    t0 = time.perf_counter()
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 4, spec["Q"])
+    alpha, K = oracle.converged_params(f.L)
+    om = oracle.fourier_coefs(g, f.L, spec["kappa"], K)
+    return dict(g=g, alpha=alpha, K=K, om=om, fixed_s=time.perf_counter() - t0, threads=oracle.get_threads())
+
+
+def oracle_targets(f, spec, fx, tg):
+    """The oracle's per-target work on targets tg: short range over all
+    sources and 27 images, Fourier synthesis, self and local terms."""
+    import oracle
+    g, alpha, K = fx["g"], fx["alpha"], fx["K"]
+    t0 = time.perf_counter()
+    vs, _ = oracle.short_range(g, f.L, spec["kappa"], alpha, 0.0, all_images=True, targets=tg)
+    vf, _ = oracle.fourier_eval(g, f.L, alpha, K, fx["om"], targets=tg)
+    vx, _ = oracle.self_term(g, spec["kappa"], alpha, targets=tg)
+    vl, _ = oracle.local(g, spec["kappa"], spec["a"], spec["delta"], targets=tg)
+    return vl + vs + vf - vx, time.perf_counter() - t0
+
+
+def oracle_sample(f, spec, n_sample, seed=0):
+    """Time the oracle on n_sample random targets and extrapolate a full
+    evaluation as fixed work + N x per-target work."""
+    rng = np.random.default_rng(seed)
+    tg = np.sort(rng.choice(f.N, min(n_sample, f.N), replace=False))
+    fx = oracle_fixed(f, spec)
+    v, tt = oracle_targets(f, spec, fx, tg)
+    per_target = tt / tg.size
+    return dict(v=v, targets=tg, geom=fx["g"], fixed_s=fx["fixed_s"], per_target_s=per_target,
+                full_s=fx["fixed_s"] + per_target * f.N, sample_s=fx["fixed_s"] + tt, threads=fx["threads"])
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_2406_07366_gb300 as B
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    spec, f = workload(args.workload)
+    prec = B.BS_MIXED if args.precision == "mixed" else B.BS_FP64
+    p = make_params(B, spec, f, prec, flags=B.BS_TIMING)
+    stream = torch.cuda.current_stream()
+    bs = B.BiotSavart(p, f.offsets, f.closing, stream=stream)
+    nodes = torch.from_numpy(f.nodes).to(dev)
+    vel = torch.empty_like(nodes)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        bs.velocity(nodes, vel)
+    bs.status()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    clocks.start()
+    step_ms, stages = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps, outside the timed events
+        ev[k][0].record(stream)
+        bs.velocity(nodes, vel)
+        ev[k][1].record(stream)
+        stages.append(bs.stage_times())  # synchronises the streams
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    bs.status()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    stage_mean = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+    ng, _ = B.bs_nufft_setup(p, want_table=False)
+    real_bytes = 4 if prec == B.BS_MIXED else 8
+    NQ = f.N * spec["Q"]
+    sb = spread_bytes(p, ng, NQ, real_bytes)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = sb / (stage_mean["spread"] * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (pinned memory)
+    hn = torch.from_numpy(f.nodes).pin_memory()
+    hv = torch.empty_like(hn).pin_memory()
+    ctx2 = B.BiotSavart(make_params(B, spec, f, prec), f.offsets, f.closing, stream=stream)
+    for _ in range(2):
+        B.bs_compute_host(ctx2.ctx, hn, hv)
+    torch.cuda.synchronize()
+    ke = max(5, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        B.bs_compute_host(ctx2.ctx, hn, hv)
+    e2e_s = (time.perf_counter() - t0) / ke
+    ctx2.close()
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # the float64 form on the same workload, for the FP32-vs-FP64 comparison
+    fp64 = None
+    if not args.no_fp64_form and prec == B.BS_MIXED:
+        p64 = make_params(B, spec, f, B.BS_FP64)
+        b64 = B.BiotSavart(p64, f.offsets, f.closing, stream=stream)
+        v64 = torch.empty_like(nodes)
+        for _ in range(2):
+            b64.velocity(nodes, v64)
+        torch.cuda.synchronize()
+        k64 = min(args.steps, 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(k64):
+            flush.zero_()
+            e0.record(stream)
+            b64.velocity(nodes, v64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        b64.close()
+        ms64 = tot / k64
+        fp64 = {"value": f.N * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
+                "nufft_w": p64.nufft_w}
+
+    result = None
+    if rank == 0:
+        cpu = None
+        accuracy = None
+        if world == 1 and not args.no_cpu_baseline:
+            vgpu = vel.cpu().numpy()
+            o = oracle_sample(f, spec, args.cpu_sample)
+            tg = o["targets"]
+            d = vgpu[tg] - o["v"]
+            rms = float(np.sqrt(np.mean(np.sum(d ** 2, 1)) / np.mean(np.sum(o["v"] ** 2, 1))))
+            mx = float(np.max(np.linalg.norm(d, axis=1) / np.linalg.norm(o["v"], axis=1)))
+            eps_v, _ = B.bs_error_estimate(p, float(o["geom"].lp.sum()))
+            vrms = float(np.sqrt(np.mean(np.sum(o["v"] ** 2, 1))))
+            accuracy = {"rms_rel_err": rms, "max_rel_err": mx, "targets": int(tg.size),
+                        "eps_v_over_vrms": eps_v / vrms, "against": "FP64 CPU oracle (converged Ewald sum)"}
+            cpu = {"value": f.N / o["full_s"], "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+                   "sample": (f"{tg.size} random target nodes of the {f.N}-node workload timed in full "
+                              f"({o['sample_s']:.1f} s: spline fit, Fourier coefficients of all sources, "
+                              f"27-image short range); full evaluation extrapolated as fixed "
+                              f"{o['fixed_s']:.2f} s + N x {o['per_target_s'] * 1e3:.2f} ms")}
+        launches = KERNELS_PER_STEP * args.steps
+        result = {
+            "metric": METRIC, "value": f.N * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == B.BS_MIXED else "f64",
+            "data": "synthetic (seeded random-phase Fourier tangles, no dataset)",
+            "config": {"workload": f"{args.workload}: {f.nfil} closed filaments x {f.N // max(f.nfil, 1)} nodes, "
+                                   f"N={f.N}, L=2pi, M={spec['M']}^3 modes, beta={spec['beta']}",
+                       "precision": "mixed: f32 kernels, f64 positions/offsets and final sum"
+                       if prec == B.BS_MIXED else "f64",
+                       "N": f.N, "nfil": f.nfil, "M": spec["M"], "n_g": ng, "Q": spec["Q"], "w": p.nufft_w,
+                       "sigma": spec["sigma"], "beta": spec["beta"], "alpha": p.alpha, "rc": p.rc,
+                       "l2": "512 MiB L2 flush between timed steps (outside the events); grids 1.4 GB > L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                         "algorithmic_bytes": sb, "ms": stage_mean["spread"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": f.N * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(f.N * 24),
+                    "d2h_bytes_per_step": int(f.N * 24), "ms_per_step": e2e_s * 1e3,
+                    "api": "bs_compute_host (pinned host buffers)"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "stages_ms": stage_mean,
+            "fp64_form": fp64,
+            "accuracy": accuracy,
+        }
+    bs.close()
+    return result
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    """The oracle as the reference arm: its fixed work (spline fit, Fourier
+    coefficients of all sources) is timed once; each step then evaluates a
+    fresh random sample of targets in full (all sources, 27 images), and the
+    full-evaluation rate is N / (fixed + N x mean per-target time)."""
+    spec, f = workload(args.workload)
+    n = max(1, min(args.cpu_sample // 2, 8))
+    fx = oracle_fixed(f, spec)
+    rng = np.random.default_rng(1234)
+    for _ in range(args.warmup):
+        oracle_targets(f, spec, fx, np.sort(rng.choice(f.N, n, replace=False)))
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, tt = oracle_targets(f, spec, fx, np.sort(rng.choice(f.N, n, replace=False)))
+        per.append(tt / n)
+    wall = time.perf_counter() - t0
+    full = fx["fixed_s"] + statistics.mean(per) * f.N
+    v = f.N / full
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-phase Fourier tangles)",
+            "impl": "reference",
+            "config": {"workload": args.workload, "N": f.N, "M": spec["M"]},
+            "cpu_baseline": {"kind": "oracle", "cores": fx["threads"], "value": v, "unit": UNIT,
+                             "sample": (f"fixed work once ({fx['fixed_s']:.1f} s: spline fit + Fourier coefficients "
+                                        f"of all {f.N * spec['Q']} sources); each of {args.steps} steps: {n} random "
+                                        f"targets in full ({wall:.1f} s total); ms_per_step = extrapolated full "
+                                        f"evaluation")},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    res = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

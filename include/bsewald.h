@@ -192,10 +192,12 @@ int bs_status(bs_ctx* ctx);
 
 /*
  * Per-stage times of the last compute call in milliseconds (needs
- * BS_TIMING).  ms[0..n-1] receive, in order: geometry, short-range binning,
- * short range, spread binning, spread, forward FFT, k-space, inverse FFT,
- * interpolation + sum.  Synchronises the stream.  Returns the number of
- * stages through *n_out.
+ * BS_TIMING; the short-range branch stays concurrent with the long-range
+ * one, each stage timed by CUDA events on its own stream).  ms[0..n-1]
+ * receive, in order: geometry, short-range binning, short range, spread
+ * binning, spread, forward FFT, k-space, inverse FFT, interpolation + sum
+ * (from the join of both branches), whole evaluation.  Synchronises the
+ * streams.  Returns the number of entries through *n_out.
  */
 int bs_stage_times(bs_ctx* ctx, float* ms, int n, int* n_out);
 

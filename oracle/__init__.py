@@ -75,6 +75,10 @@ def _load():
         lib.or_long_range.argtypes = [ctypes.c_long, _i64p, _dp, ctypes.c_long, _dp, _dp, _dp, ctypes.c_double,
                                       ctypes.c_double, _ip, _dp, _dp, _dp]
         lib.or_long_range.restype = None
+        lib.or_fourier_coefs.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, _ip, _dp]
+        lib.or_fourier_coefs.restype = None
+        lib.or_fourier_eval.argtypes = [ctypes.c_long, _i64p, _dp, _dp, ctypes.c_double, _ip, _dp, _dp, _dp]
+        lib.or_fourier_eval.restype = None
         lib.or_self.argtypes = [ctypes.c_long, _i64p, _dp, _i64p, _i64p, _dp, ctypes.c_int, _dp, _dp,
                                 ctypes.c_double, ctypes.c_double, _dp, _dp]
         lib.or_self.restype = None
@@ -222,6 +226,26 @@ def long_range(g: Geometry, L, kappa, alpha, K, targets=None, want_omega=False):
     if want_omega:
         om = om[..., 0] + 1j * om[..., 1]
         return v, psi, om.reshape(2 * K[0] + 1, 2 * K[1] + 1, 2 * K[2] + 1, 3)
+    return v, psi
+
+
+def fourier_coefs(g: Geometry, L, kappa, K):
+    """omega_k over the cube |m_d| <= K_d (Eq. vorticity_fourier_coefs), shape (2K+1)^3 x 3 complex."""
+    L = np.asarray(L, dtype=np.float64)
+    K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (3,)))
+    om = np.zeros(((2 * K[0] + 1) * (2 * K[1] + 1) * (2 * K[2] + 1), 3, 2))
+    _load().or_fourier_coefs(g.qX.shape[0], _p(g.qX), _p(g.qq), _p(L), kappa, _p(K, _ip), _p(om))
+    return om
+
+
+def fourier_eval(g: Geometry, L, alpha, K, om, targets=None):
+    """v^(f), psi^(f) at the targets from omega_k of fourier_coefs (Eq. velocity_longrange_physical)."""
+    t = _targets(g, targets)
+    L = np.asarray(L, dtype=np.float64)
+    K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (3,)))
+    v = np.zeros((t.size, 3))
+    psi = np.zeros((t.size, 3))
+    _load().or_fourier_eval(t.size, _p(t, _i64p), _p(g.nodes), _p(L), alpha, _p(K, _ip), _p(om), _p(v), _p(psi))
     return v, psi
 
 

@@ -519,18 +519,19 @@ void or_short_range(long ntgt, const int64_t* tgt, const double* nodes, const in
  *   omega_k = (kappa/V) sum_q q e^{-i k.X_q},
  *   v(x)   = sum_k Re[ i k x omega_k e^{-k^2/4 alpha^2} / k^2 e^{i k.x} ],
  *   psi(x) = sum_k Re[ omega_k e^{-k^2/4 alpha^2} / k^2 e^{i k.x} ].
- * omega_out (optional) receives omega_k, layout [m0][m1][m2][c][re,im].
+ * Two steps: or_fourier_coefs (the sum over sources) and or_fourier_eval
+ * (the synthesis at the targets); or_long_range does both.
+ * omega layout: [m0][m1][m2][c][re,im], m_d from -K_d to K_d.
  */
-void or_long_range(long ntgt, const int64_t* tgt, const double* nodes, long NQ, const double* qX, const double* qq,
-                   const double* L, double kappa, double alpha, const int* K, double* v, double* psi,
-                   double* omega_out)
+void or_fourier_coefs(long NQ, const double* qX, const double* qq, const double* L, double kappa, const int* K,
+                      double* om)
 {
     const long n0 = 2 * K[0] + 1, n1 = 2 * K[1] + 1, n2 = 2 * K[2] + 1;
     const long nm = n0 * n1 * n2;
     const long nax = n0 + n1 + n2;
     const double V = L[0] * L[1] * L[2];
     double kk[3] = { 2.0 * OR_PI / L[0], 2.0 * OR_PI / L[1], 2.0 * OR_PI / L[2] };
-    double* om = (double*)calloc((size_t)(nm * 6), sizeof(double));
+    memset(om, 0, (size_t)(nm * 6) * sizeof(double));
     double* omc = (double*)calloc((size_t)(nm * 6), sizeof(double)); /* compensation */
     const long B = 1024;
     double* tab = (double*)malloc((size_t)(B * nax * 2) * sizeof(double));
@@ -574,10 +575,17 @@ void or_long_range(long ntgt, const int64_t* tgt, const double* nodes, long NQ, 
     }
     for (long mi = 0; mi < nm; mi++)
         for (int c = 0; c < 6; c++) om[6 * mi + c] = (om[6 * mi + c] + omc[6 * mi + c]) * kappa / V;
-    if (omega_out) memcpy(omega_out, om, (size_t)(nm * 6) * sizeof(double));
     free(omc);
     free(tab);
+}
 
+void or_fourier_eval(long ntgt, const int64_t* tgt, const double* nodes, const double* L, double alpha, const int* K,
+                     const double* om, double* v, double* psi)
+{
+    const long n0 = 2 * K[0] + 1, n1 = 2 * K[1] + 1, n2 = 2 * K[2] + 1;
+    const long nm = n0 * n1 * n2;
+    const long nax = n0 + n1 + n2;
+    double kk[3] = { 2.0 * OR_PI / L[0], 2.0 * OR_PI / L[1], 2.0 * OR_PI / L[2] };
     /* per-mode multipliers G_k = e^{-k^2/4 alpha^2} / k^2 (0 at k = 0) */
     double* G = (double*)malloc((size_t)nm * sizeof(double));
     for (long mi = 0; mi < nm; mi++) {
@@ -611,7 +619,6 @@ void or_long_range(long ntgt, const int64_t* tgt, const double* nodes, long NQ, 
             double er = ar * br - ai * bi, ei = ar * bi + ai * br;
             double pr = er * cr - ei * ci, pi = er * ci + ei * cr; /* e^{i k.x} */
             const double* w = om + 6 * mi;
-            /* psi_k e^{ikx} real part, psi_k = G omega_k */
             double wr[3] = { w[0], w[2], w[4] }, wi[3] = { w[1], w[3], w[5] };
             /* i k x omega: (k x wr) i - (k x wi) */
             double cxr[3], cxi[3];
@@ -630,6 +637,17 @@ void or_long_range(long ntgt, const int64_t* tgt, const double* nodes, long NQ, 
         free(tb);
     }
     free(G);
+}
+
+void or_long_range(long ntgt, const int64_t* tgt, const double* nodes, long NQ, const double* qX, const double* qq,
+                   const double* L, double kappa, double alpha, const int* K, double* v, double* psi,
+                   double* omega_out)
+{
+    const long nm = (2L * K[0] + 1) * (2L * K[1] + 1) * (2L * K[2] + 1);
+    double* om = (double*)malloc((size_t)(nm * 6) * sizeof(double));
+    or_fourier_coefs(NQ, qX, qq, L, kappa, K, om);
+    if (omega_out) memcpy(omega_out, om, (size_t)(nm * 6) * sizeof(double));
+    or_fourier_eval(ntgt, tgt, nodes, L, alpha, K, om, v, psi);
     free(om);
 }
 

@@ -26,7 +26,8 @@ BS_ERR_STATE, BS_ERR_GEOMETRY = 10, 11
 BS_FP64, BS_MIXED = 0, 1
 BS_WANT_PSI, BS_TIMING = 1, 2
 
-STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", "kspace", "fft_inv", "interp"]
+STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", "kspace", "fft_inv", "interp",
+          "total"]
 
 # Every exported symbol of include/bsewald.h.
 EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_create", "bs_set_stream",

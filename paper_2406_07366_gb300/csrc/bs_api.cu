@@ -199,7 +199,7 @@ struct bs_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    static constexpr int kStages = 10;
+    static constexpr int kStages = 11;
     cudaEvent_t ev_t[kStages] = {};
     bool timed = false;
     int nfil = 0;
@@ -409,7 +409,9 @@ int fft_inv(bs_ctx* c, void* spec, cudaStream_t s)
 }
 
 // The pipeline.  parts (4 x N x 3) / psi_parts switch the output to the
-// separate parts of Eq. ewald_velocity_splitting.
+// separate parts of Eq. ewald_velocity_splitting.  With BS_TIMING, events
+// are recorded on the stream each stage runs on (the two branches stay
+// concurrent); stage i spans events [kStageBeg[i], kStageEnd[i]].
 template <typename T>
 int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts, double* psi_parts)
 {
@@ -431,13 +433,10 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
                        psi_parts ? psi_parts : nullptr, psi_parts ? psi_parts + 3 * N3 : nullptr, s));
     rec(c, 1, s);
 
-    // short range on the side stream (serial on the main one when timing)
-    cudaStream_t ss = s;
-    if (!c->timed) {
-        CE(cudaEventRecord(c->ev_fork, s));
-        CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        ss = c->side;
-    }
+    // short range on the side stream
+    CE(cudaEventRecord(c->ev_fork, s));
+    CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    cudaStream_t ss = c->side;
     CE(launch_sort_sr<T>(w, (int)c->NQ, (int)d.ncells, ss));
     rec(c, 2, ss);
     ShortP S;
@@ -455,7 +454,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     S.want_psi = want_psi ? 1 : 0;
     CE(launch_short<T>(S, w, ss));
     rec(c, 3, ss);
-    if (!c->timed) CE(cudaEventRecord(c->ev_join, ss));
+    CE(cudaEventRecord(c->ev_join, ss));
 
     // long range on the main stream
     CE(launch_sort_lr<T>(w, (int)c->NQ, d.ntiles, s));
@@ -485,7 +484,8 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     rec(c, 7, s);
     TRY(fft_inv<T>(c, w.spec, s));
     rec(c, 8, s);
-    if (!c->timed) CE(cudaStreamWaitEvent(s, c->ev_join, 0));
+    CE(cudaStreamWaitEvent(s, c->ev_join, 0));
+    rec(c, 9, s);
 
     InterpP I;
     I.N = (int)c->N;
@@ -512,7 +512,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             CE(launch_interp<T>(I, nodes, w, w.grid, 1, psi, nullptr, s));
         }
     }
-    rec(c, 9, s);
+    rec(c, 10, s);
     return BS_OK;
 }
 
@@ -775,10 +775,15 @@ int bs_stage_times(bs_ctx* c, float* ms, int n, int* n_out)
     if (!c || !ms) return fail(BS_ERR_ARG, "null argument");
     if (!(c->p.flags & BS_TIMING)) return fail(BS_ERR_STATE, "context created without BS_TIMING");
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    const int ns = bs_ctx::kStages - 1;
+    CUDA_TRY(cudaStreamSynchronize(c->side));
+    // geometry, sr sort, short range, lr sort, spread, fft fwd, k-space,
+    // fft inv, interpolation + sum, whole evaluation
+    static const int beg[10] = { 0, 1, 2, 1, 4, 5, 6, 7, 9, 0 };
+    static const int end[10] = { 1, 2, 3, 4, 5, 6, 7, 8, 10, 10 };
+    const int ns = 10;
     for (int i = 0; i < ns && i < n; ++i) {
         float t = 0;
-        CUDA_TRY(cudaEventElapsedTime(&t, c->ev_t[i], c->ev_t[i + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&t, c->ev_t[beg[i]], c->ev_t[end[i]]));
         ms[i] = t;
     }
     if (n_out) *n_out = ns;
