@@ -125,6 +125,22 @@ def spread_bytes(p, ng, NQ, real_bytes):
     return 3 * real_bytes * ng[0] * ng[1] * ng[2] + rec * NQ + 4 * (ntiles + 1)
 
 
+def ncu_traffic(kernel, workload, source):
+    """Per-launch DRAM traffic from the committed ncu summary of this kernel and
+    workload, if the summary was taken from the current source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    sha = hashlib.sha1(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:12]
+    tb = [ln.split(":")[1].strip() for ln in txt.splitlines() if ln.startswith("traffic_bytes_per_launch:")]
+    src = [ln.split()[-1] for ln in txt.splitlines() if ln.startswith("source:")]
+    if tb and src and src[0] == sha:
+        return int(tb[0])
+    return None
+
+
 def oracle_fixed(f, spec):
     """The oracle's per-evaluation fixed work: spline fit and quadrature of
     all filaments, and the Fourier coefficients of all sources."""
@@ -296,7 +312,10 @@ def run_ours(args, rank, world, dist):
                        "l2": "512 MiB L2 flush between timed steps (outside the events); grids 1.4 GB > L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                         "frac": achieved / peak,
+                         "traffic": ncu_traffic("k_spread", args.workload, "paper_2406_07366_gb300/csrc/k_long.cu")
+                         if prec == B.BS_MIXED else None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
                          "algorithmic_bytes": sb, "ms": stage_mean["spread"]},
             "cpu_baseline": cpu,
             "e2e": {"value": f.N * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(f.N * 24),
