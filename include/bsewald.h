@@ -201,6 +201,41 @@ int bs_status(bs_ctx* ctx);
  */
 int bs_stage_times(bs_ctx* ctx, float* ms, int n, int* n_out);
 
+/*
+ * bs_short_range_static -- the short-range velocity sum (the v^(n) part of
+ * bs_compute_parts, float64) on caller-given sources and targets, for
+ * callers that cannot allocate device memory: an application that owns all
+ * device memory through its own allocator or a fixed budget, or a
+ * latency-critical loop that must avoid the implicit device synchronisation
+ * of cudaMalloc / cudaFree.  The paper has no counterpart; this is a
+ * library-side packaging of its short-range sum.
+ *
+ * It allocates nothing.  Its cell-list scratch is one fixed array of about
+ * 9 MiB compiled into the library, present on every device that loads the
+ * library until the process exits.  Limits: nsrc <= 131072 sources and at
+ * most 65536 cells (cells of edge >= rc/m, m lowered from 3 to 1 to fit;
+ * BS_ERR_ARG with a message beyond that).  The first call on a device looks
+ * up the scratch address there (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the one array and leaves its contents behind; the call clears
+ * what must start at zero.  Calls whose work overlaps on the GPU (two
+ * streams, two threads) race on the array: serialise them.
+ *
+ *   L[3]                 box periods (host)
+ *   kappa, alpha, rc     circulation, Ewald parameter, cut-off (rc <= min L / 2)
+ *   src_pos  (device)    nsrc x 3 source positions (any image)
+ *   src_q    (device)    nsrc x 3 vector charges
+ *   src_seg  (device)    nsrc segment ids
+ *   tgt_pos  (device)    ntgt x 3 target positions
+ *   tgt_omit (device)    ntgt x 2 segment ids each target omits (its C_0)
+ *   vel      (device)    ntgt x 3 output, kappa/4pi included
+ *   stream               cudaStream_t (NULL = legacy default stream)
+ * Asynchronous on stream.  Errors: BS_ERR_ARG, BS_ERR_RC_GT_HALF_L, BS_ERR_CUDA.
+ */
+int bs_short_range_static(const double L[3], double kappa, double alpha, double rc, int nsrc, const double* src_pos,
+                          const double* src_q, const int* src_seg, int ntgt, const double* tgt_pos,
+                          const int* tgt_omit, double* vel, void* stream);
+
 /* Device bytes held by the context's workspace. */
 int bs_workspace_bytes(bs_ctx* ctx, long long* bytes);
 

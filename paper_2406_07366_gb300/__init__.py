@@ -32,7 +32,8 @@ STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", 
 # Every exported symbol of include/bsewald.h.
 EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_create", "bs_set_stream",
            "bs_set_filaments", "bs_compute", "bs_compute_host", "bs_compute_parts", "bs_get_quadrature",
-           "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error"]
+           "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error",
+           "bs_short_range_static"]
 
 
 class bs_params(ctypes.Structure):
@@ -78,6 +79,8 @@ def _load():
         "bs_workspace_bytes": ([vp, P(ctypes.c_longlong)], ctypes.c_int),
         "bs_destroy": ([vp], None),
         "bs_last_error": ([], ctypes.c_char_p),
+        "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -201,6 +204,17 @@ def bs_workspace_bytes(ctx):
 def bs_destroy(ctx):
     if ctx:
         lib().bs_destroy(ctx)
+
+
+def bs_short_range_static(L, kappa, alpha, rc, src_pos, src_q, src_seg, tgt_pos, tgt_omit, vel, stream=None):
+    """Short-range velocity sum with the library's fixed scratch (no device
+    allocation; for callers that cannot allocate).  Arrays are device tensors:
+    src_pos, src_q (nsrc x 3 float64), src_seg (nsrc int32), tgt_pos (ntgt x 3
+    float64), tgt_omit (ntgt x 2 int32), vel (ntgt x 3 float64, written)."""
+    Lc = (ctypes.c_double * 3)(*np.broadcast_to(np.asarray(L, dtype=float), (3,)))
+    _check(lib().bs_short_range_static(Lc, float(kappa), float(alpha), float(rc), int(src_pos.shape[0]),
+                                       _ptr(src_pos), _ptr(src_q), _ptr(src_seg), int(tgt_pos.shape[0]),
+                                       _ptr(tgt_pos), _ptr(tgt_omit), _ptr(vel), stream))
 
 
 # ------------------------------------------------------------- convenience

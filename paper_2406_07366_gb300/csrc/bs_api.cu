@@ -193,6 +193,8 @@ int derive(const bs_params* p, Derived* d)
 
 }  // namespace
 
+void bsw::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct bs_ctx {
     bs_params p;
     Derived d;

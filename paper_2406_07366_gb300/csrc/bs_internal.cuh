@@ -189,6 +189,9 @@ cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, 
 template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);
 
+// Set the thread-local message returned by bs_last_error.
+void set_last_error(const char* msg);
+
 // Exclusive scan of n ints in place (cnt[n] receives the total); tmp holds
 // scan_blocks(n) ints.
 cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s);
