@@ -268,17 +268,22 @@ def test_antiparallel_lines_zero_velocity():
 
 
 def test_three_line_pairs_vs_oracle():
-    """Unclosed periodic lines (velocity purely non-local, Sec. 5.1 case 2):
-    equal to the oracle at the same split up to the NUFFT error, and to the
-    converged sum within the Sec. 4 estimate (|v| is small here, so the
-    relative truncation error is larger than for closed rings)."""
+    """Unclosed periodic lines (velocity purely non-local, Sec. 5.1 case 2).
+    At w = 16, sigma = 2 the GPU equals the oracle at the same split (NUFFT
+    error below rounding); at the workloads' w = 8, sigma = 1.5 it stays
+    within the Sec. 4 truncation estimate of the converged sum.  The
+    long-range part dominates here, so its NUFFT error (~3e-6 of its size
+    at w = 8: the truncated kernel jumps by zeta/sinh(zeta) ~ 2e-6 at the
+    support edge) is not masked by a large local term."""
     B = _B()
     f = W.three_line_pairs(N_l=16)
-    p = params(f, M=32, Q=2, precision=B.BS_FP64)
-    v = gpu_velocity(f, p)
     g = geom(f, 4, 2)
-    m = oracle.components_matched(g, f.L, KAPPA, A_CORE, DELTA, p.alpha, p.rc, (p.M[0] - 1) // 2)
-    assert rms_rel(v, m["total"]) < 1e-6
+    p16 = params(f, M=32, Q=2, w=16, sigma=2.0, precision=B.BS_FP64)
+    v16 = gpu_velocity(f, p16)
+    m = oracle.components_matched(g, f.L, KAPPA, A_CORE, DELTA, p16.alpha, p16.rc, (p16.M[0] - 1) // 2)
+    assert rms_rel(v16, m["total"]) < 1e-10
+    p = params(f, M=32, Q=2, w=8, precision=B.BS_FP64)
+    v = gpu_velocity(f, p)
     vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
     eps_v, _ = B.bs_error_estimate(p, g.lp.sum())
     vrms = np.sqrt(np.mean(np.sum(vr ** 2, axis=1)))
