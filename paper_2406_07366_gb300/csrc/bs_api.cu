@@ -83,16 +83,31 @@ void gauss_legendre(int n, double* x, double* w)
     }
 }
 
-// Smallest m >= n, m % 8 == 0, m = 2^a 3^b 5^c 7^d.
+// Smallest m >= n with m % 8 == 0 and m = 2^a 3^b (the lengths the
+// library's transforms handle).
 int fft_friendly(int n)
 {
     for (int m = std::max(n, 8);; ++m) {
         if (m % 8) continue;
         int r = m;
-        for (int p : { 2, 3, 5, 7 })
+        for (int p : { 2, 3 })
             while (r % p == 0) r /= p;
         if (r == 1) return m;
     }
+}
+
+// Radices of a length-n transform: the factors 3 first, then 8s, then a 4 or a 2.
+FftPlan make_plan(int n)
+{
+    FftPlan pl;
+    pl.n = n;
+    pl.nr = 0;
+    int r = n;
+    while (r % 3 == 0) { pl.r[pl.nr++] = 3; r /= 3; }
+    while (r % 8 == 0) { pl.r[pl.nr++] = 8; r /= 8; }
+    if (r == 4) { pl.r[pl.nr++] = 4; r = 1; }
+    if (r == 2) { pl.r[pl.nr++] = 2; r = 1; }
+    return pl;
 }
 
 // Normalised backwards Kaiser-Bessel kernel psi(z) = sinh(zeta s)/(s sinh zeta).
@@ -132,6 +147,10 @@ struct Derived {
     int nc[3], m;
     long long ncells;
     double hc[3];
+    // pruned-FFT pipeline
+    FftPlan plan[3];
+    int tx, ty, nbx, nby, ncols, colcap;  // z-column blocks; records per source at most
+    int mcy, mcx, yc;                     // chunk sizes of the y, x and inverse-z passes
 };
 
 int derive(const bs_params* p, Derived* d)
@@ -188,6 +207,24 @@ int derive(const bs_params* p, Derived* d)
         d->m -= 1;
     }
     if (d->ncells > (1LL << 28)) return fail(BS_ERR_ARG, "too many short-range cells (rc too small)");
+    // pruned-FFT pipeline shapes (shared memory per CTA kept near 100 KB)
+    const size_t rb = p->precision == BS_FP64 ? 8 : 4;
+    for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c]);
+    int txy = (int)(100000 / (6 * (size_t)d->ng[2] * rb));
+    txy = txy >= 8 ? 8 : (txy >= 4 ? 4 : 2);
+    d->ty = std::min(4, txy);
+    d->tx = txy / d->ty;
+    d->nbx = d->ng[0] / d->tx;
+    d->nby = d->ng[1] / d->ty;
+    d->ncols = d->nbx * d->nby;
+    d->colcap = ((p->nufft_w - 1) / d->tx + 2) * ((p->nufft_w - 1) / d->ty + 2);
+    const size_t cb = 2 * rb;
+    int mcy = (int)(64000 / (2 * (size_t)(d->ng[1] + 1) * cb));
+    d->mcy = std::max(1, std::min(16, mcy));
+    const int lines_x = (p->flags & BS_WANT_PSI) ? 6 : 3;
+    int mcx = (int)(100000 / (2 * (size_t)lines_x * (d->ng[0] + 1) * cb));
+    d->mcx = std::max(1, std::min(16, mcx));
+    d->yc = 8;
     return BS_OK;
 }
 
@@ -278,10 +315,30 @@ int alloc_grids(bs_ctx* c)
     const size_t csz = (size_t)d.ng[0] * d.ng[1] * d.nh;
     TRY(dalloc(c, c->alloc_g, &c->w.grid, 3 * rsz * sizeof(T)));
     TRY(dalloc(c, c->alloc_g, &c->w.spec, 3 * csz * 2 * sizeof(T)));
-    if (c->p.flags & BS_WANT_PSI) TRY(dalloc(c, c->alloc_g, &c->w.spec_psi, 3 * csz * 2 * sizeof(T)));
+    if ((c->p.flags & BS_WANT_PSI) && (c->p.flags & BS_FFT_CUFFT))
+        TRY(dalloc(c, c->alloc_g, &c->w.spec_psi, 3 * csz * 2 * sizeof(T)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.tile_cnt, sizeof(int) * (size_t)(d.ntiles + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.tile_cur, sizeof(int) * (size_t)(d.ntiles + 1)));
-    TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp2, sizeof(int) * (size_t)scan_blocks(d.ntiles)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp2,
+               sizeof(int) * (size_t)std::max(scan_blocks(d.ntiles), scan_blocks(d.ncols))));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.col_cnt, sizeof(int) * (size_t)(d.ncols + 1)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.col_cur, sizeof(int) * (size_t)(d.ncols + 1)));
+    {
+        const size_t f2n = 3 * (size_t)d.ng[0] * (2 * d.K[1] + 1) * (d.K[2] + 1);
+        TRY(dalloc(c, c->alloc_g, &c->w.f2, f2n * 2 * sizeof(T)));
+        if (c->p.flags & BS_WANT_PSI) TRY(dalloc(c, c->alloc_g, &c->w.f2psi, f2n * 2 * sizeof(T)));
+        const int ntw = d.ng[0] + d.ng[1] + d.ng[2];
+        std::vector<T> tw(2 * (size_t)ntw);
+        int o = 0;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int j = 0; j < d.ng[ax]; ++j, ++o) {
+                const double ph = -2.0 * kPi * j / d.ng[ax];
+                tw[2 * o] = (T)cos(ph);
+                tw[2 * o + 1] = (T)sin(ph);
+            }
+        TRY(dalloc(c, c->alloc_g, &c->w.tw, sizeof(T) * tw.size()));
+        CUDA_TRY(cudaMemcpy(c->w.tw, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice));
+    }
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cnt, sizeof(int) * (size_t)(d.ncells + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cur, sizeof(int) * (size_t)(d.ncells + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp, sizeof(int) * (size_t)scan_blocks((int)d.ncells)));
@@ -301,7 +358,8 @@ int alloc_grids(bs_ctx* c)
     }
     TRY(dalloc(c, c->alloc_g, &c->w.ktab, sizeof(T) * ntab));
     CUDA_TRY(cudaMemcpy(c->w.ktab, tab.data(), sizeof(T) * ntab, cudaMemcpyHostToDevice));
-    return make_plans<T>(c);
+    if (c->p.flags & BS_FFT_CUFFT) return make_plans<T>(c);
+    return BS_OK;
 }
 
 template <typename T>
@@ -333,6 +391,7 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.lr_rec, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, &w.lr_sorted, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, (void**)&w.lr_key, sizeof(int) * NQ));
+    TRY(dalloc(c, L, &w.col_rec, sizeof(LrRec<T>) * NQ * (size_t)c->d.colcap));
     TRY(dalloc(c, L, (void**)&w.nodes_in, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.vel_out, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.psi_out, sizeof(double) * 3 * N));
@@ -459,33 +518,89 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     CE(cudaEventRecord(c->ev_join, ss));
 
     // long range on the main stream
-    CE(launch_sort_lr<T>(w, (int)c->NQ, d.ntiles, s));
-    rec(c, 4, s);
-    SpreadP SP;
-    for (int k = 0; k < 3; ++k) {
-        SP.ng[k] = d.ng[k];
-        SP.tile[k] = d.tile[k];
-        SP.ntile[k] = d.ntile[k];
+    if (p.flags & BS_FFT_CUFFT) {
+        CE(launch_sort_lr<T>(w, (int)c->NQ, d.ntiles, s));
+        rec(c, 4, s);
+        SpreadP SP;
+        for (int k = 0; k < 3; ++k) {
+            SP.ng[k] = d.ng[k];
+            SP.tile[k] = d.tile[k];
+            SP.ntile[k] = d.ntile[k];
+        }
+        SP.w = p.nufft_w;
+        SP.zeta = d.zeta;
+        CE(launch_spread<T>(SP, w, d.ntiles, s));
+        rec(c, 5, s);
+        TRY(fft_fwd<T>(c, s));
+        rec(c, 6, s);
+        KspaceP K;
+        for (int k = 0; k < 3; ++k) {
+            K.ng[k] = d.ng[k];
+            K.K[k] = d.K[k];
+            K.kk[k] = 2.0 * kPi / p.L[k];
+        }
+        K.nh = d.nh;
+        K.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
+        K.want_psi = want_psi ? 1 : 0;
+        CE(launch_kspace<T>(K, w, s));
+        rec(c, 7, s);
+        TRY(fft_inv<T>(c, w.spec, s));
+        rec(c, 8, s);
+    } else {
+        ColP CP;
+        CP.tx = d.tx;
+        CP.ty = d.ty;
+        CP.nbx = d.nbx;
+        CP.nby = d.nby;
+        CP.ncols = d.ncols;
+        CP.w = p.nufft_w;
+        CE(launch_col_sort<T>(CP, w, (int)c->NQ, s));
+        rec(c, 4, s);
+        SpZP SZ;
+        for (int k = 0; k < 3; ++k) {
+            SZ.ng[k] = d.ng[k];
+            SZ.K[k] = d.K[k];
+        }
+        SZ.tx = d.tx;
+        SZ.ty = d.ty;
+        SZ.nbx = d.nbx;
+        SZ.nby = d.nby;
+        SZ.w = p.nufft_w;
+        SZ.zeta = d.zeta;
+        SZ.plan2 = d.plan[2];
+        CE(launch_spread_zfft<T>(SZ, w, s));
+        rec(c, 5, s);
+        FftYP YP;
+        for (int k = 0; k < 3; ++k) {
+            YP.ng[k] = d.ng[k];
+            YP.K[k] = d.K[k];
+        }
+        YP.mc = d.mcy;
+        YP.plan1 = d.plan[1];
+        CE(launch_fft_y<T>(YP, w, w.f2, -1, s));
+        rec(c, 6, s);
+        FftXP XP;
+        for (int k = 0; k < 3; ++k) {
+            XP.ng[k] = d.ng[k];
+            XP.K[k] = d.K[k];
+            XP.kk[k] = 2.0 * kPi / p.L[k];
+        }
+        XP.mc = d.mcx;
+        XP.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
+        XP.plan0 = d.plan[0];
+        CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
+        rec(c, 7, s);
+        CE(launch_fft_y<T>(YP, w, w.f2, +1, s));
+        FftZP ZP;
+        for (int k = 0; k < 3; ++k) {
+            ZP.ng[k] = d.ng[k];
+            ZP.K[k] = d.K[k];
+        }
+        ZP.yc = d.yc;
+        ZP.plan2 = d.plan[2];
+        CE(launch_fft_z_c2r<T>(ZP, w, s));
+        rec(c, 8, s);
     }
-    SP.w = p.nufft_w;
-    SP.zeta = d.zeta;
-    CE(launch_spread<T>(SP, w, d.ntiles, s));
-    rec(c, 5, s);
-    TRY(fft_fwd<T>(c, s));
-    rec(c, 6, s);
-    KspaceP K;
-    for (int k = 0; k < 3; ++k) {
-        K.ng[k] = d.ng[k];
-        K.K[k] = d.K[k];
-        K.kk[k] = 2.0 * kPi / p.L[k];
-    }
-    K.nh = d.nh;
-    K.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
-    K.want_psi = want_psi ? 1 : 0;
-    CE(launch_kspace<T>(K, w, s));
-    rec(c, 7, s);
-    TRY(fft_inv<T>(c, w.spec, s));
-    rec(c, 8, s);
     CE(cudaStreamWaitEvent(s, c->ev_join, 0));
     rec(c, 9, s);
 
@@ -506,7 +621,26 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         CE(launch_interp<T>(I, nodes, w, w.grid, 0, vel, nullptr, s));
     }
     if (want_psi) {
-        TRY(fft_inv<T>(c, w.spec_psi, s));
+        if (p.flags & BS_FFT_CUFFT) {
+            TRY(fft_inv<T>(c, w.spec_psi, s));
+        } else {
+            FftYP YP;
+            for (int k = 0; k < 3; ++k) {
+                YP.ng[k] = d.ng[k];
+                YP.K[k] = d.K[k];
+            }
+            YP.mc = d.mcy;
+            YP.plan1 = d.plan[1];
+            CE(launch_fft_y<T>(YP, w, w.f2psi, +1, s));
+            FftZP ZP;
+            for (int k = 0; k < 3; ++k) {
+                ZP.ng[k] = d.ng[k];
+                ZP.K[k] = d.K[k];
+            }
+            ZP.yc = d.yc;
+            ZP.plan2 = d.plan[2];
+            CE(launch_fft_z_c2r<T>(ZP, w, s));
+        }
         if (psi_parts) {
             CE(launch_interp<T>(I, nodes, w, w.grid, 2, nullptr, psi_parts + 2 * N3, s));
             CE(launch_to_double<T>(w.psr, psi_parts + N3, (int)N3, s));
@@ -692,6 +826,8 @@ int bs_set_filaments(bs_ctx* c, int nfil, const int64_t* offsets, const int32_t*
     }
     c->nfil = nfil;
     c->N = N;
+    c->w.nmax_fil = 0;
+    for (int l = 0; l < nfil; ++l) c->w.nmax_fil = std::max(c->w.nmax_fil, (int)(off[l + 1] - off[l]));
     c->NQ = N * c->p.quad_Q;
     c->have_fil = false;
     int rc = (c->p.precision == BS_FP64) ? alloc_filaments<double>(c, off, fil_of, prev, shift)

@@ -12,6 +12,7 @@ namespace bsw {
 constexpr int kMaxQ = 8;
 constexpr int kMaxW = 16;
 constexpr int kThreads = 256;
+constexpr size_t kSplineSmemMax = 96 * 1024;  // warp-per-filament spline fit up to this smem
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 // Device status bits (bs_status).
@@ -105,6 +106,50 @@ struct KspaceP {
     int want_psi;
 };
 
+// Radix sequence of one 1-D transform of length n (product of r[0..nr)).
+struct FftPlan {
+    int n;
+    int nr;
+    int r[16];
+};
+
+// Column binning of the spread records (blocks of tx x ty full z-columns).
+struct ColP {
+    int tx, ty, nbx, nby, ncols, w;
+};
+
+struct SpZP {
+    int ng[3];
+    int K[3];
+    int tx, ty, nbx, nby;
+    int w;
+    double zeta;
+    FftPlan plan2;
+};
+
+struct FftYP {
+    int ng[3];
+    int K[3];
+    int mc;
+    FftPlan plan1;
+};
+
+struct FftXP {
+    int ng[3];
+    int K[3];
+    int mc;
+    double kk[3];
+    double scale;
+    FftPlan plan0;
+};
+
+struct FftZP {
+    int ng[3];
+    int K[3];
+    int yc;
+    FftPlan plan2;
+};
+
 struct InterpP {
     int N;
     int ng[3];
@@ -130,6 +175,7 @@ struct Work {
     void* cpr = nullptr;    // N Thomas scratch
     void* zz = nullptr;     // N Sherman-Morrison vector
     void* Tper = nullptr;   // nfil
+    int nmax_fil = 0;       // longest filament
     // node outputs
     double* vls = nullptr;  // N x 3  v_local - v_self
     double* pls = nullptr;  // N x 3  psi_local - psi_self
@@ -156,6 +202,13 @@ struct Work {
     void* spec_psi = nullptr; // 3 x ... (psi)
     void* ktab = nullptr;     // per-axis k-space tables
     void* fft_work = nullptr;
+    // pruned-FFT pipeline
+    void* tw = nullptr;       // twiddles e^{-2 pi i j / n_d}, n0 + n1 + n2 complex
+    void* f2 = nullptr;       // 3 x n0 x (2K1+1) x (K2+1) complex
+    void* f2psi = nullptr;
+    void* col_rec = nullptr;  // duplicated spread records, by z-column block
+    int* col_cnt = nullptr;   // ncols + 1
+    int* col_cur = nullptr;
     // host staging for bs_compute_host
     double* nodes_in = nullptr;
     double* vel_out = nullptr;
@@ -185,6 +238,19 @@ cudaError_t launch_kspace(const KspaceP& P, const Work& w, cudaStream_t s);
 template <typename T>
 cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, const void* grid, int what,
                           double* out, double* part_long, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s);
+template <typename T>
+size_t spread_zfft_smem(const SpZP& P);
 
 template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);

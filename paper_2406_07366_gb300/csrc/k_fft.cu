@@ -1,0 +1,648 @@
+// Long-range pipeline on a pruned 3-D FFT (Sec. 3.3, Appendix A).
+//
+// Only the modes |m_d| <= K_d of the spread grid are needed (Sec. 3.3: the
+// k-space pass zeroes every other mode), so the three axes are transformed
+// one at a time and each pass writes only what the next one reads:
+//
+//   A  spread + z real FFT (fused): one CTA owns Tx x Ty full z-columns of
+//      the grid in shared memory, spreads every point whose support reaches
+//      them, transforms the 3 Tx Ty real z-lines and writes modes 0..K2.
+//      F1[c][x][y][mz]
+//   B  y FFT of F1, writes |m_y| <= K1.                F2[c][x][my][mz]
+//   C  x FFT of F2, the k-space pass (deconvolution, Gaussian filter, curl,
+//      1/k^2, truncation, k = 0), inverse x FFT, back into F2 (and F2psi).
+//   D  inverse y FFT (zero-padded) into F1.
+//   E  inverse z real FFT (zero-padded) into the real grid for the
+//      interpolation.
+//
+// The 1-D transforms are Stockham autosort passes of radix 2, 3, 4, 8 over
+// lines held in shared memory (lengths 2^a 3^b), unnormalised, with the
+// forward sign e^{-2 pi i jk/n}.  Twiddles e^{-2 pi i j/n} come from a table
+// computed on the host in float64.  Two real lines are transformed as one
+// complex line and separated afterwards.
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bsw {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) { C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; }
+// multiply by sign * i
+template <typename C>
+__device__ __forceinline__ C cmuli(C a, int sign) { C r; r.x = -sign * a.y; r.y = sign * a.x; return r; }
+
+// In-register DFT of size R with exponent sign (+1 or -1).
+template <typename T, int R>
+__device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
+{
+    using C = typename Cx<T>::t;
+    if (R == 2) {
+        const C a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    } else if (R == 3) {
+        const T h = (T)0.86602540378443864676 * (T)sign;  // sin(2 pi / 3) with the sign
+        const C s = cadd(x[1], x[2]);
+        const C d = csub(x[1], x[2]);
+        C t;
+        t.x = x[0].x - (T)0.5 * s.x;
+        t.y = x[0].y - (T)0.5 * s.y;
+        C u;  // i h d
+        u.x = -h * d.y;
+        u.y = h * d.x;
+        x[0] = cadd(x[0], s);
+        x[1] = cadd(t, u);
+        x[2] = csub(t, u);
+    } else if (R == 4) {
+        const C a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+        const C c = cadd(x[1], x[3]), d = cmuli(csub(x[1], x[3]), sign);
+        x[0] = cadd(a, c);
+        x[2] = csub(a, c);
+        x[1] = cadd(b, d);
+        x[3] = csub(b, d);
+    } else if (R == 8) {
+        C e[4] = { x[0], x[2], x[4], x[6] };
+        C o[4] = { x[1], x[3], x[5], x[7] };
+        dft<T, 4>(e, sign);
+        dft<T, 4>(o, sign);
+        const T r2 = (T)0.70710678118654752440;
+        // w8^m = e^{sign 2 pi i m / 8}
+        C w1;
+        w1.x = r2;
+        w1.y = (T)sign * r2;
+        C w3;
+        w3.x = -r2;
+        w3.y = (T)sign * r2;
+        o[1] = cmul(o[1], w1);
+        o[2] = cmuli(o[2], sign);
+        o[3] = cmul(o[3], w3);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            x[m] = cadd(e[m], o[m]);
+            x[m + 4] = csub(e[m], o[m]);
+        }
+    }
+}
+
+// One Stockham pass of radix R over nlines lines (line stride ls) of length
+// n; p = product of the radices already applied.  Twiddles tw[j] =
+// e^{-2 pi i j / n}; sign -1 forward, +1 inverse.
+template <typename T, int R>
+__device__ __forceinline__ void fft_pass(const typename Cx<T>::t* __restrict__ in, typename Cx<T>::t* __restrict__ out,
+                                         int nlines, int ls, int n, int p, const typename Cx<T>::t* __restrict__ tw,
+                                         int sign)
+{
+    using C = typename Cx<T>::t;
+    const int nr = n / R;
+    const int tot = nlines * nr;
+    const int tstep = n / (p * R);
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int line = idx / nr;
+        const int i = idx - line * nr;
+        const int k = i % p;
+        const C* src = in + line * ls;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = src[i + q * nr];
+        if (p > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C w = tw[q * k * tstep];
+                if (sign > 0) w.y = -w.y;
+                x[q] = cmul(x[q], w);
+            }
+        }
+        dft<T, R>(x, sign);
+        C* dst = out + line * ls + (i - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[q * p] = x[q];
+    }
+}
+
+// All passes of one length-n transform on nlines lines; a and b are two
+// buffers of nlines * ls complex values, the data starts in a.  Returns the
+// buffer holding the result.
+template <typename T>
+__device__ typename Cx<T>::t* fft_lines(typename Cx<T>::t* a, typename Cx<T>::t* b, int nlines, int ls,
+                                        const FftPlan& pl, const typename Cx<T>::t* __restrict__ tw, int sign)
+{
+    using C = typename Cx<T>::t;
+    C* in = a;
+    C* out = b;
+    int p = 1;
+    for (int s = 0; s < pl.nr; ++s) {
+        const int R = pl.r[s];
+        if (R == 8) fft_pass<T, 8>(in, out, nlines, ls, pl.n, p, tw, sign);
+        else if (R == 4) fft_pass<T, 4>(in, out, nlines, ls, pl.n, p, tw, sign);
+        else if (R == 3) fft_pass<T, 3>(in, out, nlines, ls, pl.n, p, tw, sign);
+        else fft_pass<T, 2>(in, out, nlines, ls, pl.n, p, tw, sign);
+        __syncthreads();
+        C* t = in;
+        in = out;
+        out = t;
+        p *= R;
+    }
+    return in;
+}
+
+template <typename T>
+__device__ __forceinline__ T kb_val(T z, T zeta, T inorm)
+{
+    T s2 = (T)1 - z * z;
+    s2 = s2 > (T)0 ? s2 : (T)0;
+    const T s = sqrt(s2);
+    const T num = (s > (T)1e-6) ? -expm1((T)-2 * zeta * s) / s : (T)2 * zeta;
+    return exp(zeta * (s - (T)1)) * num * inorm;
+}
+
+// ---------------------------------------------------------------------------
+// Binning of the spread records by z-column block, each point copied into
+// every block its support reaches (with the offset of its support relative
+// to that block), so that a block reads only points that touch it.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void col_range(int ib, int H, int Tb, int& b0, int& b1)
+{
+    const int lo = ib - H + 1, hi = ib + H;
+    b0 = lo >= 0 ? lo / Tb : -((-lo + Tb - 1) / Tb);
+    b1 = hi / Tb;
+}
+
+template <typename T>
+__global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int base = rec[i].base;
+    const int ib0 = base & 1023, ib1 = (base >> 10) & 1023;
+    int x0, x1, y0, y1;
+    col_range<T>(ib0, P.w / 2, P.tx, x0, x1);
+    col_range<T>(ib1, P.w / 2, P.ty, y0, y1);
+    for (int by = y0; by <= y1; ++by) {
+        const int wy = ((by % P.nby) + P.nby) % P.nby;
+        for (int bx = x0; bx <= x1; ++bx) {
+            const int wx = ((bx % P.nbx) + P.nbx) % P.nbx;
+            atomicAdd(&cnt[wx + P.nbx * wy], 1);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cur,
+                              LrRec<T>* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    LrRec<T> R = rec[i];
+    const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
+    const int H = P.w / 2;
+    int x0, x1, y0, y1;
+    col_range<T>(ib0, H, P.tx, x0, x1);
+    col_range<T>(ib1, H, P.ty, y0, y1);
+    for (int by = y0; by <= y1; ++by) {
+        const int wy = ((by % P.nby) + P.nby) % P.nby;
+        const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block
+        for (int bx = x0; bx <= x1; ++bx) {
+            const int wx = ((bx % P.nbx) + P.nbx) % P.nbx;
+            const int r0 = ib0 - H + 1 - bx * P.tx;
+            LrRec<T> D = R;
+            D.base = (r0 + 128) | ((r1 + 128) << 8) | (ib2 << 16);
+            const int p = atomicAdd(&cur[wx + P.nbx * wy], 1);
+            out[p] = D;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A: spread + z real FFT.
+// smem: real accumulator 3 Tx Ty lines of stride n2+1 (reused as one FFT
+// buffer), a complex buffer of 3 Tx Ty / 2 lines of n2, per-warp kernel
+// tables.
+// ---------------------------------------------------------------------------
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
+                                                          const LrRec<T>* __restrict__ recs,
+                                                          const typename Cx<T>::t* __restrict__ tw2,
+                                                          typename Cx<T>::t* __restrict__ F1)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Tx = P.tx, Ty = P.ty, n2 = P.ng[2];
+    const int nreal = 3 * Tx * Ty;
+    const int LS = n2 + 1;
+    T* acc = reinterpret_cast<T*>(smem_raw);
+    const size_t abytes = (((size_t)nreal * LS * sizeof(T)) + 15) & ~(size_t)15;
+    C* cb = reinterpret_cast<C*>(smem_raw + abytes);
+    const int ncl = nreal / 2;
+    T* ktab = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(cb) + (size_t)ncl * n2 * sizeof(C));
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int bx = blockIdx.x % P.nbx, by = blockIdx.x / P.nbx;
+    for (int i = tid; i < nreal * LS; i += blockDim.x) acc[i] = (T)0;
+    __syncthreads();
+
+    // spread: one warp per record, lanes over (support row, z)
+    const T zeta = (T)P.zeta;
+    const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+    constexpr int H = W / 2;
+    T* kw = ktab + wid * 3 * W;
+    const int s0 = cstart[blockIdx.x], s1 = cstart[blockIdx.x + 1];
+    const int plane = Tx * Ty * LS;  // component stride in acc
+    for (int k = s0 + wid; k < s1; k += nw) {
+        const LrRec<T> R = recs[k];
+        const int r0 = (R.base & 255) - 128, r1 = ((R.base >> 8) & 255) - 128, ib2 = (R.base >> 16) & 1023;
+        const int a0 = max(r0, 0), e0 = min(r0 + W - 1, Tx - 1);
+        const int a1 = max(r1, 0), e1 = min(r1 + W - 1, Ty - 1);
+        const T f0 = R.f[0], f1 = R.f[1], f2 = R.f[2];
+        const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
+        __syncwarp();
+        for (int i = lane; i < 3 * W; i += 32) {
+            const int d = i / W, t = i - d * W;
+            const T f = d == 0 ? f0 : (d == 1 ? f1 : f2);
+            kw[i] = kb_val((f + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        }
+        __syncwarp();
+        const int n0 = e0 - a0 + 1, n1 = e1 - a1 + 1;
+        const int rows_per = 32 / W;
+        const int rsub = lane / W, c2 = lane - rsub * W;
+        if (rsub < rows_per) {
+            int z = ib2 - H + 1 + c2;
+            z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
+            const T wz = kw[2 * W + c2];
+            const int nrows = n0 * n1;
+            for (int r = rsub; r < nrows; r += rows_per) {
+                const int c0 = r / n1, c1 = r - c0 * n1;
+                const int x0 = a0 + c0, x1 = a1 + c1;
+                const T wv = kw[x0 - r0] * kw[W + x1 - r1] * wz;
+                const int cell = (x0 * Ty + x1) * LS + z;
+                atomicAdd(&acc[cell], wv * q0);
+                atomicAdd(&acc[plane + cell], wv * q1);
+                atomicAdd(&acc[2 * plane + cell], wv * q2);
+            }
+        }
+    }
+    __syncthreads();
+    // pack real lines 2l, 2l+1 into complex line l
+    for (int i = tid; i < ncl * n2; i += blockDim.x) {
+        const int l = i / n2, z = i - l * n2;
+        C v;
+        v.x = acc[(2 * l) * LS + z];
+        v.y = acc[(2 * l + 1) * LS + z];
+        cb[l * n2 + z] = v;
+    }
+    __syncthreads();
+    C* res = fft_lines<T>(cb, reinterpret_cast<C*>(acc), ncl, n2, P.plan2, tw2, -1);
+    // separate the two real transforms and write modes 0..K2
+    const int K2 = P.K[2];
+    const int nk = K2 + 1;
+    for (int i = tid; i < nreal * nk; i += blockDim.x) {
+        const int rl = i / nk, mz = i - rl * nk;
+        const int l = rl >> 1;
+        const C zk = res[l * n2 + mz];
+        const C zn = res[l * n2 + (mz == 0 ? 0 : n2 - mz)];
+        C o;
+        if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
+            o.x = (T)0.5 * (zk.x + zn.x);
+            o.y = (T)0.5 * (zk.y - zn.y);
+        } else {              // B_k = (Z_k - conj Z_{n-k}) / (2i)
+            o.x = (T)0.5 * (zk.y + zn.y);
+            o.y = (T)0.5 * (zn.x - zk.x);
+        }
+        const int c = rl / (Tx * Ty), rem = rl - c * Tx * Ty;
+        const int lx = rem / Ty, ly = rem - lx * Ty;
+        const int x = bx * Tx + lx, y = by * Ty + ly;
+        F1[(((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk + mz] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// B / D: transforms along y.  One CTA per (c, x, chunk of MC z-modes).
+// forward: F1[c][x][y][mz] -> F2[c][x][my'][mz], my' = my + K1, |my| <= K1
+// inverse: F2 -> F1 (zero-padded to n1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* __restrict__ F1,
+                                                    typename Cx<T>::t* __restrict__ F2,
+                                                    const typename Cx<T>::t* __restrict__ tw1, int sign)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = P.ng[1], K1 = P.K[1], nk = P.K[2] + 1, MC = P.mc;
+    const int LS = n1 + 1;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + MC * LS;
+    const int nch = (nk + MC - 1) / MC;
+    const int ch = blockIdx.x % nch;
+    const int cx = blockIdx.x / nch;  // c * n0 + x
+    const int mz0 = ch * MC;
+    const int mcount = min(MC, nk - mz0);
+    const int ny2 = 2 * K1 + 1;
+    C zero;
+    zero.x = 0;
+    zero.y = 0;
+    if (sign < 0) {
+        for (int i = threadIdx.x; i < n1 * MC; i += blockDim.x) {
+            const int y = i / MC, l = i - y * MC;
+            a[l * LS + y] = (l < mcount) ? F1[((size_t)cx * n1 + y) * nk + mz0 + l] : zero;
+        }
+    } else {
+        for (int i = threadIdx.x; i < n1 * MC; i += blockDim.x) {
+            const int y = i / MC, l = i - y * MC;
+            const int my = y <= n1 / 2 ? y : y - n1;  // frequency held at index y
+            C v = zero;
+            if (l < mcount && my >= -K1 && my <= K1) v = F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l];
+            a[l * LS + y] = v;
+        }
+    }
+    __syncthreads();
+    C* res = fft_lines<T>(a, b, MC, LS, P.plan1, tw1, sign);
+    if (sign < 0) {
+        for (int i = threadIdx.x; i < ny2 * MC; i += blockDim.x) {
+            const int myp = i / MC, l = i - myp * MC;
+            if (l >= mcount) continue;
+            const int my = myp - K1;
+            const int y = my < 0 ? my + n1 : my;
+            F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] = res[l * LS + y];
+        }
+    } else {
+        for (int i = threadIdx.x; i < n1 * MC; i += blockDim.x) {
+            const int y = i / MC, l = i - y * MC;
+            if (l >= mcount) continue;
+            F1[((size_t)cx * n1 + y) * nk + mz0 + l] = res[l * LS + y];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// C: x forward FFT + k-space pass + x inverse FFT, in place on F2.
+// One CTA per (my', chunk of MC z-modes); the 3 components together (the
+// curl couples them).  tabs: e^{-k_d^2/4alpha^2} / F_d(m)^2 per axis.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
+                                                           typename Cx<T>::t* __restrict__ F2psi,
+                                                           const typename Cx<T>::t* __restrict__ tw0,
+                                                           const T* __restrict__ tab0, const T* __restrict__ tab1,
+                                                           const T* __restrict__ tab2)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n0 = P.ng[0], K0 = P.K[0], K1 = P.K[1], nk = P.K[2] + 1, MC = P.mc;
+    const int ny2 = 2 * K1 + 1;
+    const int LS = n0 + 1;
+    const int want_psi = F2psi != nullptr;
+    const int nl = (want_psi ? 6 : 3) * MC;  // lines: [comp][mz]; psi lines follow
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + nl * LS;
+    const int nch = (nk + MC - 1) / MC;
+    const int ch = blockIdx.x % nch;
+    const int myp = blockIdx.x / nch;
+    const int mz0 = ch * MC;
+    const int mcount = min(MC, nk - mz0);
+    C zero;
+    zero.x = 0;
+    zero.y = 0;
+    // load: line (c, l) position x <- F2[c][x][myp][mz0 + l]
+    for (int i = threadIdx.x; i < 3 * n0 * MC; i += blockDim.x) {
+        const int l = i % MC;
+        const int cx = i / MC;  // c * n0 + x
+        const int c = cx / n0, x = cx - c * n0;
+        a[(c * MC + l) * LS + x] = (l < mcount) ? F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] : zero;
+    }
+    __syncthreads();
+    C* res = fft_lines<T>(a, b, 3 * MC, LS, P.plan0, tw0, -1);
+    C* other = (res == a) ? b : a;
+    // k-space pass: mode (mx, my, mz) for every (l, x-index)
+    const int my = myp - K1;
+    const int amy = my < 0 ? -my : my;
+    for (int i = threadIdx.x; i < MC * n0; i += blockDim.x) {
+        const int l = i / n0, xi = i - l * n0;
+        const int mx = xi <= n0 / 2 ? xi : xi - n0;
+        const int amx = mx < 0 ? -mx : mx;
+        const int mz = mz0 + l;
+        C w0 = res[(0 * MC + l) * LS + xi], w1 = res[(1 * MC + l) * LS + xi], w2 = res[(2 * MC + l) * LS + xi];
+        if (l >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
+            w0 = zero;
+            w1 = zero;
+            w2 = zero;
+            res[(0 * MC + l) * LS + xi] = zero;
+            res[(1 * MC + l) * LS + xi] = zero;
+            res[(2 * MC + l) * LS + xi] = zero;
+            if (want_psi) {
+                res[(3 * MC + l) * LS + xi] = zero;
+                res[(4 * MC + l) * LS + xi] = zero;
+                res[(5 * MC + l) * LS + xi] = zero;
+            }
+            continue;
+        }
+        const T k0 = (T)(P.kk[0] * mx), k1 = (T)(P.kk[1] * my), k2 = (T)(P.kk[2] * mz);
+        const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
+        const T mult = (T)P.scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
+        w0.x *= mult; w0.y *= mult;
+        w1.x *= mult; w1.y *= mult;
+        w2.x *= mult; w2.y *= mult;
+        // i k x w
+        const T cr0 = k1 * w2.x - k2 * w1.x, ci0 = k1 * w2.y - k2 * w1.y;
+        const T cr1 = k2 * w0.x - k0 * w2.x, ci1 = k2 * w0.y - k0 * w2.y;
+        const T cr2 = k0 * w1.x - k1 * w0.x, ci2 = k0 * w1.y - k1 * w0.y;
+        C o;
+        o.x = -ci0; o.y = cr0; res[(0 * MC + l) * LS + xi] = o;
+        o.x = -ci1; o.y = cr1; res[(1 * MC + l) * LS + xi] = o;
+        o.x = -ci2; o.y = cr2; res[(2 * MC + l) * LS + xi] = o;
+        if (want_psi) {
+            res[(3 * MC + l) * LS + xi] = w0;
+            res[(4 * MC + l) * LS + xi] = w1;
+            res[(5 * MC + l) * LS + xi] = w2;
+        }
+    }
+    __syncthreads();
+    C* out = fft_lines<T>(res, other, nl, LS, P.plan0, tw0, +1);
+    for (int i = threadIdx.x; i < 3 * n0 * MC; i += blockDim.x) {
+        const int l = i % MC;
+        if (l >= mcount) continue;
+        const int cx = i / MC;
+        const int c = cx / n0, x = cx - c * n0;
+        const size_t g = ((size_t)cx * ny2 + myp) * nk + mz0 + l;
+        F2[g] = out[(c * MC + l) * LS + x];
+        if (want_psi) F2psi[g] = out[((3 + c) * MC + l) * LS + x];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// E: inverse z real FFT.  One CTA per (c, x, chunk of YC y-lines); two real
+// lines per complex transform.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft_z_c2r(FftZP P, const typename Cx<T>::t* __restrict__ F1,
+                                                        const typename Cx<T>::t* __restrict__ tw2,
+                                                        T* __restrict__ grid)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = P.ng[1], n2 = P.ng[2], nk = P.K[2] + 1, YC = P.yc;
+    const int ncl = YC / 2;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + ncl * n2;
+    const int nch = n1 / YC;
+    const int ch = blockIdx.x % nch;
+    const int cx = blockIdx.x / nch;  // c * n0 + x
+    const int y0 = ch * YC;
+    C zero;
+    zero.x = 0;
+    zero.y = 0;
+    for (int i = threadIdx.x; i < ncl * n2; i += blockDim.x) a[i] = zero;
+    __syncthreads();
+    // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k), k = 0..K2
+    for (int i = threadIdx.x; i < ncl * nk; i += blockDim.x) {
+        const int l = i / nk, k = i - l * nk;
+        const C A = F1[((size_t)cx * n1 + y0 + 2 * l) * nk + k];
+        const C Bv = F1[((size_t)cx * n1 + y0 + 2 * l + 1) * nk + k];
+        C z;
+        if (k == 0) {
+            z.x = A.x;
+            z.y = Bv.x;
+            a[l * n2] = z;
+        } else {
+            z.x = A.x - Bv.y;
+            z.y = A.y + Bv.x;
+            a[l * n2 + k] = z;
+            z.x = A.x + Bv.y;
+            z.y = -A.y + Bv.x;
+            a[l * n2 + n2 - k] = z;
+        }
+    }
+    __syncthreads();
+    const C* res = fft_lines<T>(a, b, ncl, n2, P.plan2, tw2, +1);
+    const size_t gsz = (size_t)P.ng[0] * n1 * n2;
+    const int c = cx / P.ng[0], x = cx - c * P.ng[0];
+    T* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
+    for (int i = threadIdx.x; i < YC * n2; i += blockDim.x) {
+        const int yl = i / n2, z = i - yl * n2;
+        const C v = res[(yl >> 1) * n2 + z];
+        gout[(size_t)yl * n2 + z] = (yl & 1) ? v.y : v.x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(w.col_cnt, 0, sizeof(int) * (size_t)(P.ncols + 1), s);
+    if (e != cudaSuccess) return e;
+    if (NQ > 0) k_col_count<T><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(P, (const LrRec<T>*)w.lr_rec, NQ,
+                                                                                  w.col_cnt);
+    e = scan_exclusive(w.col_cnt, P.ncols, w.scan_tmp2, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(w.col_cur, w.col_cnt, sizeof(int) * (size_t)P.ncols, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (NQ > 0)
+        k_col_scatter<T><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(P, (const LrRec<T>*)w.lr_rec, NQ,
+                                                                             w.col_cur, (LrRec<T>*)w.col_rec);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t spread_zfft_smem(const SpZP& P)
+{
+    using C = typename Cx<T>::t;
+    const int nreal = 3 * P.tx * P.ty;
+    const size_t abytes = (((size_t)nreal * (P.ng[2] + 1) * sizeof(T)) + 15) & ~(size_t)15;
+    return abytes + (size_t)(nreal / 2) * P.ng[2] * sizeof(C) + (kThreads / 32) * 3 * (size_t)P.w * sizeof(T);
+}
+
+template <typename T, int W>
+static cudaError_t spz_w(const SpZP& P, const Work& w, cudaStream_t s)
+{
+    using C = typename Cx<T>::t;
+    const size_t sm = spread_zfft_smem<T>(P);
+    cudaError_t e = cudaFuncSetAttribute(k_spread_zfft<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_spread_zfft<T, W><<<P.nbx * P.nby, kThreads, sm, s>>>(P, w.col_cnt, (const LrRec<T>*)w.col_rec,
+                                                             (const C*)w.tw + P.ng[0] + P.ng[1], (C*)w.spec);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s)
+{
+    switch (P.w) {
+    case 2: return spz_w<T, 2>(P, w, s);
+    case 4: return spz_w<T, 4>(P, w, s);
+    case 6: return spz_w<T, 6>(P, w, s);
+    case 8: return spz_w<T, 8>(P, w, s);
+    case 10: return spz_w<T, 10>(P, w, s);
+    case 12: return spz_w<T, 12>(P, w, s);
+    case 14: return spz_w<T, 14>(P, w, s);
+    case 16: return spz_w<T, 16>(P, w, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s)
+{
+    using C = typename Cx<T>::t;
+    const size_t sm = 2 * (size_t)P.mc * (P.ng[1] + 1) * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nk = P.K[2] + 1;
+    const int nch = (nk + P.mc - 1) / P.mc;
+    k_fft_y<T><<<3 * P.ng[0] * nch, kThreads, sm, s>>>(P, (C*)w.spec, (C*)f2, (const C*)w.tw + P.ng[0], sign);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s)
+{
+    using C = typename Cx<T>::t;
+    const int nl = (want_psi ? 6 : 3) * P.mc;
+    const size_t sm = 2 * (size_t)nl * (P.ng[0] + 1) * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_x_kspace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nk = P.K[2] + 1;
+    const int nch = (nk + P.mc - 1) / P.mc;
+    const T* tab0 = (const T*)w.ktab;
+    const T* tab1 = tab0 + (P.K[0] + 1);
+    const T* tab2 = tab1 + (P.K[1] + 1);
+    k_fft_x_kspace<T><<<(2 * P.K[1] + 1) * nch, kThreads, sm, s>>>(P, (C*)w.f2, want_psi ? (C*)w.f2psi : nullptr,
+                                                                    (const C*)w.tw, tab0, tab1, tab2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s)
+{
+    using C = typename Cx<T>::t;
+    const size_t sm = 2 * (size_t)(P.yc / 2) * P.ng[2] * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_fft_z_c2r<T><<<3 * P.ng[0] * (P.ng[1] / P.yc), kThreads, sm, s>>>(P, (const C*)w.spec,
+                                                                         (const C*)w.tw + P.ng[0] + P.ng[1],
+                                                                         (T*)w.grid);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaStream_t);
+template cudaError_t launch_col_sort<double>(const ColP&, const Work&, int, cudaStream_t);
+template cudaError_t launch_spread_zfft<float>(const SpZP&, const Work&, cudaStream_t);
+template cudaError_t launch_spread_zfft<double>(const SpZP&, const Work&, cudaStream_t);
+template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, cudaStream_t);
+template cudaError_t launch_fft_y<double>(const FftYP&, const Work&, void*, int, cudaStream_t);
+template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool, cudaStream_t);
+template cudaError_t launch_fft_x_kspace<double>(const FftXP&, const Work&, bool, cudaStream_t);
+template cudaError_t launch_fft_z_c2r<float>(const FftZP&, const Work&, cudaStream_t);
+template cudaError_t launch_fft_z_c2r<double>(const FftZP&, const Work&, cudaStream_t);
+template size_t spread_zfft_smem<float>(const SpZP&);
+template size_t spread_zfft_smem<double>(const SpZP&);
+
+}  // namespace bsw

@@ -174,6 +174,114 @@ __global__ void k_spline(const double* __restrict__ nodes, const int64_t* __rest
     }
 }
 
+// The same fit with one warp per filament, staged in shared memory: the
+// lanes compute chords, increments and right-hand sides in parallel; lanes
+// 0..3 then run the four sequential Thomas sweeps (x, y, z and the
+// Sherman-Morrison vector) out of shared memory; all lanes apply the
+// correction and write the moments.  smem: 9 * nmax values of T.
+template <typename T>
+__global__ void k_spline_warp(const double* __restrict__ nodes, const int64_t* __restrict__ off,
+                              const double* __restrict__ shift, int nfil, int nmax, T* __restrict__ hseg,
+                              T* __restrict__ dp, T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ Tper)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* sh_h = reinterpret_cast<T*>(sm_raw);  // n
+    T* sh_dp = sh_h + nmax;                   // 3 n
+    T* sh_r = sh_dp + 3 * nmax;               // 4 n: right-hand sides, then solutions
+    T* sh_cp = sh_r + 4 * nmax;               // n: modified super-diagonal
+    const int f = blockIdx.x;
+    if (f >= nfil) return;
+    const int lane = threadIdx.x;
+    const int64_t o = off[f];
+    const int n = (int)(off[f + 1] - o);
+    const double s0 = shift[3 * f], s1 = shift[3 * f + 1], s2 = shift[3 * f + 2];
+
+    double tpart = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const double* a = nodes + 3 * (o + j);
+        const double* b = nodes + 3 * (j + 1 < n ? o + j + 1 : o);
+        const double w0 = (j + 1 < n) ? 0.0 : s0, w1 = (j + 1 < n) ? 0.0 : s1, w2 = (j + 1 < n) ? 0.0 : s2;
+        const double d0 = b[0] + w0 - a[0], d1 = b[1] + w1 - a[1], d2 = b[2] + w2 - a[2];
+        const double h = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        tpart += h;
+        sh_h[j] = (T)h;
+        hseg[o + j] = (T)h;
+        ds[3 * (o + j) + 0] = (T)d0;
+        ds[3 * (o + j) + 1] = (T)d1;
+        ds[3 * (o + j) + 2] = (T)d2;
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) tpart += __shfl_xor_sync(0xffffffffu, tpart, k);
+    const double Tsum = tpart;
+    if (lane == 0) Tper[f] = (T)Tsum;
+    const double invT = 1.0 / Tsum;
+    for (int j = lane; j < n; j += 32) {
+        const double* a = nodes + 3 * (o + j);
+        const double* b = nodes + 3 * (j + 1 < n ? o + j + 1 : o);
+        const double w0 = (j + 1 < n) ? 0.0 : s0, w1 = (j + 1 < n) ? 0.0 : s1, w2 = (j + 1 < n) ? 0.0 : s2;
+        const double h = sqrt((b[0] + w0 - a[0]) * (b[0] + w0 - a[0]) + (b[1] + w1 - a[1]) * (b[1] + w1 - a[1]) +
+                              (b[2] + w2 - a[2]) * (b[2] + w2 - a[2]));
+        const T p0 = (T)(b[0] + w0 - a[0] - s0 * h * invT);
+        const T p1 = (T)(b[1] + w1 - a[1] - s1 * h * invT);
+        const T p2 = (T)(b[2] + w2 - a[2] - s2 * h * invT);
+        sh_dp[j] = p0;
+        sh_dp[nmax + j] = p1;
+        sh_dp[2 * nmax + j] = p2;
+        dp[3 * (o + j) + 0] = p0;
+        dp[3 * (o + j) + 1] = p1;
+        dp[3 * (o + j) + 2] = p2;
+    }
+    __syncwarp();
+    // right-hand sides 6 (dp_j / h_j - dp_{j-1} / h_{j-1}) and the vector u
+    const T hl = sh_h[n - 1];
+    const T gamma = -(T)2 * (hl + sh_h[0]);
+    for (int j = lane; j < n; j += 32) {
+        const int jm = j == 0 ? n - 1 : j - 1;
+        const T hj = sh_h[j], hm = sh_h[jm];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            sh_r[c * nmax + j] = (T)6 * (sh_dp[c * nmax + j] / hj - sh_dp[c * nmax + jm] / hm);
+        sh_r[3 * nmax + j] = (j == 0) ? gamma : ((j == n - 1) ? hl : (T)0);
+    }
+    __syncwarp();
+    if (lane < 4) {
+        T* r = sh_r + lane * nmax;
+        const T a0 = hl, cn = hl;
+        T cprev = 0, dprev = 0, hm = hl;
+        for (int j = 0; j < n; ++j) {
+            const T hj = sh_h[j];
+            const T a = (j == 0) ? (T)0 : hm;
+            T bb = (T)2 * (hm + hj);
+            if (j == 0) bb -= gamma;
+            if (j == n - 1) bb -= a0 * cn / gamma;
+            const T c = (j == n - 1) ? (T)0 : hj;
+            const T im = (T)1 / (bb - a * cprev);
+            cprev = c * im;
+            dprev = (r[j] - a * dprev) * im;
+            if (lane == 0) sh_cp[j] = cprev;
+            r[j] = dprev;
+            hm = hj;
+        }
+        __syncwarp(0xfu);
+        T x = r[n - 1];
+        for (int j = n - 2; j >= 0; --j) {
+            x = r[j] - sh_cp[j] * x;
+            r[j] = x;
+        }
+    }
+    __syncwarp();
+    const T vfac = hl / gamma;
+    const T* z = sh_r + 3 * nmax;
+    const T den = (T)1 + z[0] + vfac * z[n - 1];
+    T fc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fc[c] = (sh_r[c * nmax] + vfac * sh_r[c * nmax + n - 1]) / den;
+    for (int j = lane; j < n; j += 32) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Mm[3 * (o + j) + c] = sh_r[c * nmax + j] - fc[c] * z[j];
+    }
+}
+
 // Wrap x into [0, L); non-finite input maps to 0 and raises the flag.
 __device__ __forceinline__ double wrap_box(double x, double L, bool& bad)
 {
@@ -425,6 +533,17 @@ template <typename T>
 cudaError_t launch_spline(const double* nodes, const Work& w, int nfil, cudaStream_t s)
 {
     if (nfil <= 0) return cudaSuccess;
+    const size_t sm = 9 * (size_t)w.nmax_fil * sizeof(T);
+    if (sm <= kSplineSmemMax) {
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_spline_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        k_spline_warp<T><<<nfil, 32, sm, s>>>(nodes, w.off, w.shift, nfil, w.nmax_fil, (T*)w.hseg, (T*)w.dp,
+                                               (T*)w.ds, (T*)w.Mm, (T*)w.Tper);
+        return cudaGetLastError();
+    }
+    // filaments too long for shared memory: one thread per filament, in global memory
     const int tb = 64;
     k_spline<T><<<(nfil + tb - 1) / tb, tb, 0, s>>>(nodes, w.off, w.shift, nfil, (T*)w.hseg, (T*)w.dp, (T*)w.ds,
                                                     (T*)w.Mm, (T*)w.cpr, (T*)w.zz, (T*)w.Tper);

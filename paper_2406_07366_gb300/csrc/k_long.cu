@@ -37,75 +37,104 @@ __global__ void __launch_bounds__(kThreads) k_spread(SpreadP P, const int* __res
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T0 = P.tile[0], T1 = P.tile[1], T2 = P.tile[2];
-    const int tsz = T0 * T1 * T2;
+    const int T2P = T2 + 1;  // padded row: lanes on different rows hit different banks
+    const int tsz = T0 * T1 * T2P;
     T* acc = reinterpret_cast<T*>(smem_raw);
     T* ktab = acc + 3 * tsz;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    int* bstart = reinterpret_cast<int*>(ktab + nw * 3 * W);  // 27 bin starts
+    int* bpre = bstart + 27;                                  // 28 prefix counts
+    int* bwrap = bpre + 28;                                   // 27 x 3 image shifts (in grid points)
     const int b = blockIdx.x;
     const int nt0 = P.ntile[0], nt1 = P.ntile[1], nt2 = P.ntile[2];
     const int t0 = b % nt0, t1 = (b / nt0) % nt1, t2 = b / (nt0 * nt1);
     const int O0 = t0 * T0, O1 = t1 * T1, O2 = t2 * T2;
     for (int i = tid; i < 3 * tsz; i += blockDim.x) acc[i] = (T)0;
+    // the 27 neighbouring tile bins (periodic), with the image shift of each
+    int cnt = 0;
+    if (tid < 27) {
+        const int d0 = tid % 3 - 1, d1 = (tid / 3) % 3 - 1, d2 = tid / 9 - 1;
+        int u0 = t0 + d0, u1 = t1 + d1, u2 = t2 + d2, s0 = 0, s1 = 0, s2 = 0;
+        if (u0 < 0) { u0 += nt0; s0 = -P.ng[0]; } else if (u0 >= nt0) { u0 -= nt0; s0 = P.ng[0]; }
+        if (u1 < 0) { u1 += nt1; s1 = -P.ng[1]; } else if (u1 >= nt1) { u1 -= nt1; s1 = P.ng[1]; }
+        if (u2 < 0) { u2 += nt2; s2 = -P.ng[2]; } else if (u2 >= nt2) { u2 -= nt2; s2 = P.ng[2]; }
+        const int nb = u0 + nt0 * (u1 + nt1 * u2);
+        const int a = tstart[nb];
+        cnt = tstart[nb + 1] - a;
+        bstart[tid] = a;
+        bwrap[3 * tid + 0] = s0;
+        bwrap[3 * tid + 1] = s1;
+        bwrap[3 * tid + 2] = s2;
+    }
+    if (wid == 0) {  // exclusive prefix of the 27 counts
+        int v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < 27) bpre[lane + 1] = v;
+        if (lane == 0) bpre[0] = 0;
+    }
     __syncthreads();
 
     const T zeta = (T)P.zeta;
     const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
     T* kw = ktab + wid * 3 * W;
     constexpr int H = W / 2;
-    for (int d2 = -1; d2 <= 1; ++d2) {
-        int u2 = t2 + d2, w2 = 0;
-        if (u2 < 0) { u2 += nt2; w2 = -1; } else if (u2 >= nt2) { u2 -= nt2; w2 = 1; }
-        for (int d1 = -1; d1 <= 1; ++d1) {
-            int u1 = t1 + d1, w1 = 0;
-            if (u1 < 0) { u1 += nt1; w1 = -1; } else if (u1 >= nt1) { u1 -= nt1; w1 = 1; }
-            for (int d0 = -1; d0 <= 1; ++d0) {
-                int u0 = t0 + d0, w0 = 0;
-                if (u0 < 0) { u0 += nt0; w0 = -1; } else if (u0 >= nt0) { u0 -= nt0; w0 = 1; }
-                const int nb = u0 + nt0 * (u1 + nt1 * u2);
-                const int s0 = tstart[nb], s1 = tstart[nb + 1];
-                for (int k = s0 + wid; k < s1; k += nw) {
-                    const LrRec<T> R = pts[k];
-                    const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
-                    // first support cell relative to the tile origin (unwrapped image)
-                    const int r0 = ib0 + w0 * P.ng[0] - O0 - H + 1;
-                    const int r1 = ib1 + w1 * P.ng[1] - O1 - H + 1;
-                    const int r2 = ib2 + w2 * P.ng[2] - O2 - H + 1;
-                    const int a0 = max(r0, 0), e0 = min(r0 + W - 1, T0 - 1);
-                    const int a1 = max(r1, 0), e1 = min(r1 + W - 1, T1 - 1);
-                    const int a2 = max(r2, 0), e2 = min(r2 + W - 1, T2 - 1);
-                    if (a0 > e0 || a1 > e1 || a2 > e2) continue;  // warp-uniform
-                    __syncwarp();
-                    for (int i = lane; i < 3 * W; i += 32) {
-                        const int d = i / W, t = i - d * W;
-                        const T z = (R.f[d] + (T)(H - 1 - t)) * ((T)2 / (T)W);
-                        kw[i] = kb_eval(z, zeta, inorm);
-                    }
-                    __syncwarp();
-                    const int n0 = e0 - a0 + 1, n1 = e1 - a1 + 1, n2 = e2 - a2 + 1;
-                    const int tot = n0 * n1 * n2;
-                    for (int e = lane; e < tot; e += 32) {
-                        const int c2 = e % n2;
-                        const int rest = e / n2;
-                        const int c1 = rest % n1, c0 = rest / n1;
-                        const int x0 = a0 + c0, x1 = a1 + c1, x2 = a2 + c2;
-                        const T wv = kw[x0 - r0] * kw[W + x1 - r1] * kw[2 * W + x2 - r2];
-                        const int cell = (x0 * T1 + x1) * T2 + x2;
-                        atomicAdd(&acc[cell], wv * R.q[0]);
-                        atomicAdd(&acc[tsz + cell], wv * R.q[1]);
-                        atomicAdd(&acc[2 * tsz + cell], wv * R.q[2]);
-                    }
-                }
+    const int total = bpre[27];
+    const int my_pre = (lane < 28) ? bpre[lane] : 0x7fffffff;
+    for (int k = wid; k < total; k += nw) {
+        // bin of entry k: the number of prefixes <= k, minus one
+        const unsigned m = __ballot_sync(0xffffffffu, lane < 28 && my_pre <= k);
+        const int bin = __popc(m) - 1;
+        const LrRec<T> R = pts[bstart[bin] + (k - bpre[bin])];
+        const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
+        const int r0 = ib0 + bwrap[3 * bin + 0] - O0 - H + 1;
+        const int r1 = ib1 + bwrap[3 * bin + 1] - O1 - H + 1;
+        const int r2 = ib2 + bwrap[3 * bin + 2] - O2 - H + 1;
+        const int a0 = max(r0, 0), e0 = min(r0 + W - 1, T0 - 1);
+        const int a1 = max(r1, 0), e1 = min(r1 + W - 1, T1 - 1);
+        const int a2 = max(r2, 0), e2 = min(r2 + W - 1, T2 - 1);
+        if (a0 > e0 || a1 > e1 || a2 > e2) continue;  // warp-uniform
+        const T f0 = R.f[0], f1 = R.f[1], f2 = R.f[2];
+        const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
+        __syncwarp();
+        for (int i = lane; i < 3 * W; i += 32) {
+            const int d = i / W, t = i - d * W;
+            const T f = d == 0 ? f0 : (d == 1 ? f1 : f2);
+            kw[i] = kb_eval((f + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        }
+        __syncwarp();
+        // lanes over (row, z): rows = (x, y) pairs of the support box
+        const int n0 = e0 - a0 + 1, n1 = e1 - a1 + 1, n2 = e2 - a2 + 1;
+        const int rows_per = 32 / n2;
+        const int rsub = lane / n2, c2 = lane - rsub * n2;
+        if (rsub < rows_per) {
+            const int x2 = a2 + c2;
+            const T wz = kw[2 * W + x2 - r2];
+            const int nrows = n0 * n1;
+            for (int r = rsub; r < nrows; r += rows_per) {
+                const int c0 = r / n1, c1 = r - c0 * n1;
+                const int x0 = a0 + c0, x1 = a1 + c1;
+                const T wv = kw[x0 - r0] * kw[W + x1 - r1] * wz;
+                const int cell = (x0 * T1 + x1) * T2P + x2;
+                atomicAdd(&acc[cell], wv * q0);
+                atomicAdd(&acc[tsz + cell], wv * q1);
+                atomicAdd(&acc[2 * tsz + cell], wv * q2);
             }
         }
     }
     __syncthreads();
     const size_t gsz = (size_t)P.ng[0] * P.ng[1] * P.ng[2];
-    for (int i = tid; i < tsz; i += blockDim.x) {
+    const int tcount = T0 * T1 * T2;
+    for (int i = tid; i < tcount; i += blockDim.x) {
         const int x2 = i % T2, x1 = (i / T2) % T1, x0 = i / (T1 * T2);
+        const int si = (x0 * T1 + x1) * T2P + x2;
         const size_t gi = ((size_t)(O0 + x0) * P.ng[1] + (O1 + x1)) * P.ng[2] + (O2 + x2);
-        grid[gi] = acc[i];
-        grid[gsz + gi] = acc[tsz + i];
-        grid[2 * gsz + gi] = acc[2 * tsz + i];
+        grid[gi] = acc[si];
+        grid[gsz + gi] = acc[tsz + si];
+        grid[2 * gsz + gi] = acc[2 * tsz + si];
     }
 }
 
@@ -174,7 +203,9 @@ __global__ void k_kspace(KspaceP P, typename Cplx<T>::t* __restrict__ spec, type
 
 // Type-2 interpolation at the nodes, plus the epilogue sum
 //   out = add_d (float64: local - self) + add_t (short range, T) + interp.
-// part (optional) receives the interpolated long-range part alone.
+// part (optional) receives the interpolated long-range part alone.  The
+// weights of the last two axes live in registers (static indices); those of
+// the first axis are computed in the outer loop.
 template <typename T, int W>
 __global__ void __launch_bounds__(128) k_interp(InterpP P, const double* __restrict__ nodes, const T* __restrict__ grid,
                                                 const double* __restrict__ add_d, const T* __restrict__ add_t,
@@ -185,8 +216,8 @@ __global__ void __launch_bounds__(128) k_interp(InterpP P, const double* __restr
     constexpr int H = W / 2;
     const T zeta = (T)P.zeta;
     const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
-    T kv[3][W];
-    int ix[3][W];
+    int ib[3];
+    T fr[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double x = nodes[3 * j + d];
@@ -195,30 +226,39 @@ __global__ void __launch_bounds__(128) k_interp(InterpP P, const double* __restr
         if (xw >= P.L[d]) xw -= P.L[d];
         if (xw < 0.0) xw = 0.0;
         const double g = xw / P.hg[d];
-        int ib = (int)floor(g);
-        ib = ib < 0 ? 0 : (ib >= P.ng[d] ? P.ng[d] - 1 : ib);
-        double fr = g - (double)ib;
-        fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
-        const T f = (T)fr;
+        int k = (int)floor(g);
+        k = k < 0 ? 0 : (k >= P.ng[d] ? P.ng[d] - 1 : k);
+        double f = g - (double)k;
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        ib[d] = k;
+        fr[d] = (T)f;
+    }
+    T ky[W], kz[W];
+    int iy[W], iz[W];
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-            kv[d][t] = kb_eval((f + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-            int gi = ib - H + 1 + t;
-            gi = gi < 0 ? gi + P.ng[d] : (gi >= P.ng[d] ? gi - P.ng[d] : gi);
-            ix[d][t] = gi;
-        }
+    for (int t = 0; t < W; ++t) {
+        ky[t] = kb_eval((fr[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        kz[t] = kb_eval((fr[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        int gy = ib[1] - H + 1 + t, gz = ib[2] - H + 1 + t;
+        iy[t] = gy < 0 ? gy + P.ng[1] : (gy >= P.ng[1] ? gy - P.ng[1] : gy);
+        iz[t] = gz < 0 ? gz + P.ng[2] : (gz >= P.ng[2] ? gz - P.ng[2] : gz);
     }
     const size_t gsz = (size_t)P.ng[0] * P.ng[1] * P.ng[2];
     T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll 1
     for (int p = 0; p < W; ++p) {
+        const T kx = kb_eval((fr[0] + (T)(H - 1 - p)) * ((T)2 / (T)W), zeta, inorm);
+        int gx = ib[0] - H + 1 + p;
+        gx = gx < 0 ? gx + P.ng[0] : (gx >= P.ng[0] ? gx - P.ng[0] : gx);
+        const size_t plane = (size_t)gx * P.ng[1];
+#pragma unroll
         for (int q = 0; q < W; ++q) {
-            const T wpq = kv[0][p] * kv[1][q];
-            const size_t row = ((size_t)ix[0][p] * P.ng[1] + ix[1][q]) * P.ng[2];
+            const T wpq = kx * ky[q];
+            const size_t row = (plane + iy[q]) * P.ng[2];
 #pragma unroll
             for (int r = 0; r < W; ++r) {
-                const size_t gi = row + ix[2][r];
-                const T wv = wpq * kv[2][r];
+                const size_t gi = row + iz[r];
+                const T wv = wpq * kz[r];
                 a0 += wv * grid[gi];
                 a1 += wv * grid[gsz + gi];
                 a2 += wv * grid[2 * gsz + gi];
@@ -257,7 +297,8 @@ __global__ void k_to_double(const T* __restrict__ in, double* __restrict__ out, 
 template <typename T>
 static size_t spread_smem(const SpreadP& P)
 {
-    return sizeof(T) * (3 * (size_t)P.tile[0] * P.tile[1] * P.tile[2] + (kThreads / 32) * 3 * (size_t)P.w);
+    return sizeof(T) * (3 * (size_t)P.tile[0] * P.tile[1] * (P.tile[2] + 1) + (kThreads / 32) * 3 * (size_t)P.w) +
+           sizeof(int) * (27 + 28 + 81);
 }
 
 template <typename T, int W>

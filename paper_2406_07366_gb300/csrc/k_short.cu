@@ -66,22 +66,23 @@ __global__ void __launch_bounds__(128) k_short(ShortP P, const SrTgt<T>* __restr
             const int yc = fully ? iy : imod(cy - m + iy, nc1);
             const T dyc = (T)cdiff(yc, cy, nc1) * h1;
             const int row = (zc * nc1 + yc) * nc0;
-            // one or two contiguous x-ranges
-            int xa[2], xb[2], nr;
+            // one or two contiguous x-ranges [xa0, xb0], [xa1, xb1]
+            int xa0, xb0, xa1 = 0, xb1 = -1;
             if (fullx) {
-                xa[0] = 0; xb[0] = nc0 - 1; nr = 1;
+                xa0 = 0; xb0 = nc0 - 1;
             } else {
                 const int lo = cx - m, hi = cx + m;
                 if (lo < 0) {
-                    xa[0] = lo + nc0; xb[0] = nc0 - 1; xa[1] = 0; xb[1] = hi; nr = 2;
+                    xa0 = lo + nc0; xb0 = nc0 - 1; xa1 = 0; xb1 = hi;
                 } else if (hi >= nc0) {
-                    xa[0] = lo; xb[0] = nc0 - 1; xa[1] = 0; xb[1] = hi - nc0; nr = 2;
+                    xa0 = lo; xb0 = nc0 - 1; xa1 = 0; xb1 = hi - nc0;
                 } else {
-                    xa[0] = lo; xb[0] = hi; nr = 1;
+                    xa0 = lo; xb0 = hi;
                 }
             }
+            const int nr = (xb1 >= xa1) ? 2 : 1;
             for (int r = 0; r < nr; ++r) {
-                const int s0 = start[row + xa[r]], s1 = start[row + xb[r] + 1];
+                const int s0 = start[row + (r ? xa1 : xa0)], s1 = start[row + (r ? xb1 : xb0) + 1];
                 for (int k = s0; k < s1; ++k) {
                     const SrRec<T> S = src[k];
                     if (S.seg == j || S.seg == jp) continue;  // C_0 of the node (Eq. BS_on_vortex)

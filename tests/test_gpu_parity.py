@@ -97,6 +97,22 @@ def test_quadrature_points_and_charges(case, prec):
     assert np.all(qX >= 0) and np.all(qX < f.L[None, :])
 
 
+def test_long_filament_spline_fallback():
+    """A filament too long for the shared-memory spline fit (1500 nodes in
+    float64) takes the global-memory path; its quadrature must match too."""
+    B = _B()
+    f = W.ring(R=1.1, N=1500)
+    p = params(f, M=32, Q=2, precision=B.BS_FP64)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    qX, qq = bs.quadrature(torch.from_numpy(f.nodes).cuda())
+    torch.cuda.synchronize()
+    qX, qq = qX.cpu().numpy(), qq.cpu().numpy()
+    bs.close()
+    g = geom(f, 4, 2)
+    assert np.abs(_min_image(qX - g.qX, f.L)).max() < 1e-12 * np.abs(f.nodes).max()
+    assert np.abs(qq - g.qq).max() < 1e-11 * np.abs(g.qq).max()
+
+
 def _ragged():
     """Filaments of very different sizes, including the minimum N_l = 4."""
     parts = [W.ring(R=0.9, N=4, center=[1.0, 2.0, 3.0]), W.ring(R=0.5, N=5, center=[4.0, 1.0, 2.0], axis=0),
@@ -133,6 +149,25 @@ def test_parts_fp64_match_oracle(case, nufft):
         assert err < tol, (name, err)
         errp = np.abs(pp[i] - m["psi_" + name]).max() / pscale
         assert errp < tol, ("psi_" + name, errp)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["ellipses", "tangle"])
+def test_pruned_fft_equals_full_cufft(case, prec):
+    """The library's pruned per-axis transforms and the full cuFFT R2C/C2R
+    path compute the same long-range part (and psi) up to rounding."""
+    B = _B()
+    f = W.ellipses(nfil=10, N_l=32, seed=4) if case == "ellipses" else W.fourier_tangle(200, 40, seed=8,
+                                                                                          amp=2 * math.pi / 50)
+    pr = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
+    outs = []
+    for extra in (0, B.BS_FFT_CUFFT):
+        p = params(f, M=48, Q=2, w=8, precision=pr, flags=B.BS_WANT_PSI | extra)
+        outs.append(gpu_parts(f, p, want_psi=True))
+    (va, pa), (vb, pb) = outs
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.abs(va[2] - vb[2]).max() < tol * np.abs(vb[2]).max()
+    assert np.abs(pa[2] - pb[2]).max() < tol * np.abs(pb[2]).max()
 
 
 def test_parts_mixed_match_oracle():
