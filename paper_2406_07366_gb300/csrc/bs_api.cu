@@ -96,6 +96,17 @@ int fft_friendly(int n)
     }
 }
 
+// Line stride (in complex elements) of nl lines of length n in shared memory:
+// with the line-fastest butterfly order, a group of `slots` threads (one
+// shared-memory wavefront: 16 float2 or 8 double2) spans nl lines x slots/nl
+// positions, which fall in distinct banks when stride = slots/nl (mod slots);
+// for nl >= slots an odd stride suffices.
+int line_stride(int n, int nl, int slots)
+{
+    const int target = nl >= slots ? 1 : (slots % nl == 0 ? slots / nl : 1);
+    return n + (((target - n) % slots) + slots) % slots;
+}
+
 // Radices of a length-n transform: the factors 3 first, then 8s, then a 4 or a 2.
 FftPlan make_plan(int n)
 {
@@ -107,6 +118,13 @@ FftPlan make_plan(int n)
     while (r % 8 == 0) { pl.r[pl.nr++] = 8; r /= 8; }
     if (r == 4) { pl.r[pl.nr++] = 4; r = 1; }
     if (r == 2) { pl.r[pl.nr++] = 2; r = 1; }
+    int L = n;
+    for (int s = 0; s < pl.nr; ++s) {
+        pl.st[s] = L / pl.r[s];
+        pl.tws[s] = n / L;
+        pl.sd[s] = make_fastdiv((unsigned)pl.st[s]);
+        L = pl.st[s];
+    }
     return pl;
 }
 
@@ -150,7 +168,8 @@ struct Derived {
     // pruned-FFT pipeline
     FftPlan plan[3];
     int tx, ty, nbx, nby, ncols, colcap;  // z-column blocks; records per source at most
-    int mcy, mcx, yc;                     // chunk sizes of the y, x and inverse-z passes
+    int lmcy, lmcx, yc;                   // log2 chunk sizes of the y and x passes; inverse-z chunk
+    int lsz;                              // padded stride of the real z-lines of the spread
 };
 
 int derive(const bs_params* p, Derived* d)
@@ -207,24 +226,28 @@ int derive(const bs_params* p, Derived* d)
         d->m -= 1;
     }
     if (d->ncells > (1LL << 28)) return fail(BS_ERR_ARG, "too many short-range cells (rc too small)");
-    // pruned-FFT pipeline shapes (shared memory per CTA kept near 100 KB)
+    // pruned-FFT pipeline shapes: single-buffer in-place transforms, shared
+    // memory per CTA near 50 KB (4-5 CTAs per SM)
     const size_t rb = p->precision == BS_FP64 ? 8 : 4;
+    const size_t cb = 2 * rb;
     for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c]);
-    int txy = (int)(100000 / (6 * (size_t)d->ng[2] * rb));
-    txy = txy >= 8 ? 8 : (txy >= 4 ? 4 : 2);
+    int txy = (int)(50000 / (1.5 * (d->ng[2] + 1) * cb));
+    txy = txy >= 16 ? 16 : (txy >= 8 ? 8 : (txy >= 4 ? 4 : 2));
     d->ty = std::min(4, txy);
     d->tx = txy / d->ty;
     d->nbx = d->ng[0] / d->tx;
     d->nby = d->ng[1] / d->ty;
     d->ncols = d->nbx * d->nby;
     d->colcap = ((p->nufft_w - 1) / d->tx + 2) * ((p->nufft_w - 1) / d->ty + 2);
-    const size_t cb = 2 * rb;
-    int mcy = (int)(64000 / (2 * (size_t)(d->ng[1] + 1) * cb));
-    d->mcy = std::max(1, std::min(16, mcy));
+    const size_t mcy = 50000 / ((size_t)(d->ng[1] + 1) * cb);
+    d->lmcy = 0;
+    while (d->lmcy < 4 && ((size_t)2 << d->lmcy) <= mcy) ++d->lmcy;
     const int lines_x = (p->flags & BS_WANT_PSI) ? 6 : 3;
-    int mcx = (int)(100000 / (2 * (size_t)lines_x * (d->ng[0] + 1) * cb));
-    d->mcx = std::max(1, std::min(16, mcx));
-    d->yc = 8;
+    const size_t mcx = 50000 / ((size_t)lines_x * (d->ng[0] + 1) * cb);
+    d->lmcx = 0;
+    while (d->lmcx < 4 && ((size_t)2 << d->lmcx) <= mcx) ++d->lmcx;
+    d->yc = (d->ng[1] % 16 == 0) ? 16 : 8;
+    d->lsz = d->ng[2] + 1;
     return BS_OK;
 }
 
@@ -566,8 +589,17 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         SZ.nbx = d.nbx;
         SZ.nby = d.nby;
         SZ.w = p.nufft_w;
+        SZ.cls = line_stride(d.ng[2], 3 * d.tx * d.ty / 2, 128 / (2 * (int)sizeof(T)));
+        SZ.ls = d.lsz;
+        while (SZ.ls < SZ.cls) SZ.ls += 32;  // the real region also holds the complex lines
         SZ.zeta = d.zeta;
         SZ.plan2 = d.plan[2];
+        SZ.d_nbx = make_fastdiv((unsigned)d.nbx);
+        SZ.d_n2 = make_fastdiv((unsigned)d.ng[2]);
+        SZ.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
+        SZ.d_txy = make_fastdiv((unsigned)(d.tx * d.ty));
+        SZ.d_ty = make_fastdiv((unsigned)d.ty);
+        SZ.d_ncl = make_fastdiv((unsigned)(3 * d.tx * d.ty / 2));
         CE(launch_spread_zfft<T>(SZ, w, s));
         rec(c, 5, s);
         FftYP YP;
@@ -575,8 +607,11 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             YP.ng[k] = d.ng[k];
             YP.K[k] = d.K[k];
         }
-        YP.mc = d.mcy;
+        YP.lmc = d.lmcy;
+        YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
         YP.plan1 = d.plan[1];
+        YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
+        YP.d_lines = make_fastdiv(1u << d.lmcy);
         CE(launch_fft_y<T>(YP, w, w.f2, -1, s));
         rec(c, 6, s);
         FftXP XP;
@@ -585,9 +620,14 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             XP.K[k] = d.K[k];
             XP.kk[k] = 2.0 * kPi / p.L[k];
         }
-        XP.mc = d.mcx;
+        XP.lmc = d.lmcx;
+        XP.ls = line_stride(d.ng[0], 3 << d.lmcx, 128 / (2 * (int)sizeof(T)));
         XP.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
         XP.plan0 = d.plan[0];
+        XP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcx) - 1) >> d.lmcx));
+        XP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
+        XP.d_lines = make_fastdiv(3u << d.lmcx);
+        XP.d_lines_psi = make_fastdiv(6u << d.lmcx);
         CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
         rec(c, 7, s);
         CE(launch_fft_y<T>(YP, w, w.f2, +1, s));
@@ -597,7 +637,13 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             ZP.K[k] = d.K[k];
         }
         ZP.yc = d.yc;
+        ZP.cls = line_stride(d.ng[2], d.yc / 2, 128 / (2 * (int)sizeof(T)));
         ZP.plan2 = d.plan[2];
+        ZP.d_nch = make_fastdiv((unsigned)(d.ng[1] / d.yc));
+        ZP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
+        ZP.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
+        ZP.d_n2 = make_fastdiv((unsigned)d.ng[2]);
+        ZP.d_ncl = make_fastdiv((unsigned)(d.yc / 2));
         CE(launch_fft_z_c2r<T>(ZP, w, s));
         rec(c, 8, s);
     }
@@ -629,8 +675,11 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
                 YP.ng[k] = d.ng[k];
                 YP.K[k] = d.K[k];
             }
-            YP.mc = d.mcy;
+            YP.lmc = d.lmcy;
+            YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
             YP.plan1 = d.plan[1];
+            YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
+            YP.d_lines = make_fastdiv(1u << d.lmcy);
             CE(launch_fft_y<T>(YP, w, w.f2psi, +1, s));
             FftZP ZP;
             for (int k = 0; k < 3; ++k) {
@@ -638,7 +687,13 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
                 ZP.K[k] = d.K[k];
             }
             ZP.yc = d.yc;
+            ZP.cls = line_stride(d.ng[2], d.yc / 2, 128 / (2 * (int)sizeof(T)));
             ZP.plan2 = d.plan[2];
+            ZP.d_nch = make_fastdiv((unsigned)(d.ng[1] / d.yc));
+            ZP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
+            ZP.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
+            ZP.d_n2 = make_fastdiv((unsigned)d.ng[2]);
+            ZP.d_ncl = make_fastdiv((unsigned)(d.yc / 2));
             CE(launch_fft_z_c2r<T>(ZP, w, s));
         }
         if (psi_parts) {

@@ -106,11 +106,51 @@ struct KspaceP {
     int want_psi;
 };
 
-// Radix sequence of one 1-D transform of length n (product of r[0..nr)).
+// Exact unsigned division by a run-time constant d for 0 <= x < 2^31
+// (Granlund & Montgomery): q = umulhi(x, m) >> s, or x >> s for powers of 2.
+struct FastDiv {
+    unsigned d, m;
+    int s;
+    int pow2;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    FastDiv f;
+    f.d = d;
+    int l = 0;
+    while ((1ull << l) < d) ++l;  // ceil(log2 d)
+    if ((d & (d - 1)) == 0) {
+        f.m = 0;
+        f.s = l;
+        f.pow2 = 1;
+    } else {
+        f.m = (unsigned)((1ull << (31 + l)) / d + 1);
+        f.s = l - 1;
+        f.pow2 = 0;
+    }
+    return f;
+}
+
+__device__ __forceinline__ int fdiv(int x, const FastDiv& f)
+{
+    return f.pow2 ? (int)((unsigned)x >> f.s) : (int)(__umulhi((unsigned)x, f.m) >> f.s);
+}
+
+// Radix sequence of one in-place 1-D transform of length n = r[0] ... r[nr-1].
+// Pass s works on spans L_s = st[s] r[s] with butterfly stride st[s] =
+// n / (r[0] ... r[s]); tws[s] = n / L_s is its twiddle step; sd[s] divides by
+// st[s].  Decimation in frequency runs the passes forward and leaves
+// frequency k at position rev(k) = sum_s d_s st[s] (k = d_0 + r[0] d_1 +
+// r[0] r[1] d_2 + ...); decimation in time runs them backward and takes its
+// input at those positions.
 struct FftPlan {
     int n;
     int nr;
     int r[16];
+    int st[16];
+    int tws[16];
+    FastDiv sd[16];
 };
 
 // Column binning of the spread records (blocks of tx x ty full z-columns).
@@ -123,31 +163,40 @@ struct SpZP {
     int K[3];
     int tx, ty, nbx, nby;
     int w;
+    int ls;             // padded stride of the real z-lines in shared memory
+    int cls;            // complex line stride of the z FFT buffers
     double zeta;
     FftPlan plan2;
+    FastDiv d_nbx, d_n2, d_nk, d_txy, d_ty, d_ncl;
 };
 
 struct FftYP {
     int ng[3];
     int K[3];
-    int mc;
+    int lmc;            // log2 of the chunk of z-modes per CTA
+    int ls;             // line stride in shared memory
     FftPlan plan1;
+    FastDiv d_nch, d_lines;
 };
 
 struct FftXP {
     int ng[3];
     int K[3];
-    int mc;
+    int lmc;            // log2 of the chunk of z-modes per CTA
+    int ls;             // line stride in shared memory
     double kk[3];
     double scale;
     FftPlan plan0;
+    FastDiv d_nch, d_n0, d_lines, d_lines_psi;
 };
 
 struct FftZP {
     int ng[3];
     int K[3];
     int yc;
+    int cls;            // complex line stride in shared memory
     FftPlan plan2;
+    FastDiv d_nch, d_n0, d_nk, d_n2, d_ncl;
 };
 
 struct InterpP {

@@ -15,16 +15,21 @@
 //   E  inverse z real FFT (zero-padded) into the real grid for the
 //      interpolation.
 //
-// The 1-D transforms are Stockham autosort passes of radix 2, 3, 4, 8 over
-// lines held in shared memory (lengths 2^a 3^b), unnormalised, with the
-// forward sign e^{-2 pi i jk/n}.  Twiddles e^{-2 pi i j/n} come from a table
-// computed on the host in float64.  Two real lines are transformed as one
-// complex line and separated afterwards.
+// The 1-D transforms run in place on lines held in shared memory (lengths
+// 2^a 3^b; radix 8, 4, 3, 2), unnormalised, forward sign e^{-2 pi i jk/n}:
+// forward transforms by decimation in frequency (natural order in, frequency
+// k out at position rev(k)), inverse transforms by decimation in time
+// (frequency k in at rev(k), natural order out).  Consumers index rev(k)
+// directly, so no reordering pass is needed, and one buffer per line set
+// suffices.  Twiddles e^{-2 pi i j/n} come from a table computed on the host
+// in float64.  Two real lines are transformed as one complex line.
 #include <math.h>
 
 #include "bs_internal.cuh"
 
 namespace bsw {
+
+constexpr int kSpzChunk = 128;  // spread records staged in shared memory at a time
 
 template <typename T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
@@ -93,65 +98,94 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
     }
 }
 
-// One Stockham pass of radix R over nlines lines (line stride ls) of length
-// n; p = product of the radices already applied.  Twiddles tw[j] =
-// e^{-2 pi i j / n}; sign -1 forward, +1 inverse.
-template <typename T, int R>
-__device__ __forceinline__ void fft_pass(const typename Cx<T>::t* __restrict__ in, typename Cx<T>::t* __restrict__ out,
-                                         int nlines, int ls, int n, int p, const typename Cx<T>::t* __restrict__ tw,
-                                         int sign)
+// One in-place pass of radix R over nlines lines (stride ls) of length n:
+// span L = st R, butterfly (b, j) on elements b L + j + q st.
+//   dif: DFT_R, then multiply output m by w_L^{j m};
+//   dit: multiply input q by w_L^{j q}, then DFT_R.
+// Butterflies are numbered line-fastest, so consecutive threads touch
+// different lines at the same offset (distinct banks, one twiddle address).
+template <typename T, int R, bool DIF>
+__device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, int nlines, const FastDiv& dl, int ls,
+                                         int n, int st, const FastDiv& sd, int tws,
+                                         const typename Cx<T>::t* __restrict__ tw, int sign)
 {
     using C = typename Cx<T>::t;
-    const int nr = n / R;
-    const int tot = nlines * nr;
-    const int tstep = n / (p * R);
+    const int nb = n / R;
+    const int tot = nlines * nb;
+    const int L = st * R;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-        const int line = idx / nr;
-        const int i = idx - line * nr;
-        const int k = i % p;
-        const C* src = in + line * ls;
+        const int i = fdiv(idx, dl);
+        const int line = idx - i * nlines;
+        const int b = fdiv(i, sd);
+        const int j = i - b * st;
+        C* p = buf + line * ls + b * L + j;
         C x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = src[i + q * nr];
-        if (p > 1) {
+        for (int q = 0; q < R; ++q) x[q] = p[q * st];
+        if (!DIF && j > 0) {
 #pragma unroll
             for (int q = 1; q < R; ++q) {
-                C w = tw[q * k * tstep];
+                C w = tw[j * q * tws];
                 if (sign > 0) w.y = -w.y;
                 x[q] = cmul(x[q], w);
             }
         }
         dft<T, R>(x, sign);
-        C* dst = out + line * ls + (i - k) * R + k;
+        if (DIF && j > 0) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) dst[q * p] = x[q];
+            for (int q = 1; q < R; ++q) {
+                C w = tw[j * q * tws];
+                if (sign > 0) w.y = -w.y;
+                x[q] = cmul(x[q], w);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) p[q * st] = x[q];
     }
 }
 
-// All passes of one length-n transform on nlines lines; a and b are two
-// buffers of nlines * ls complex values, the data starts in a.  Returns the
-// buffer holding the result.
-template <typename T>
-__device__ typename Cx<T>::t* fft_lines(typename Cx<T>::t* a, typename Cx<T>::t* b, int nlines, int ls,
-                                        const FftPlan& pl, const typename Cx<T>::t* __restrict__ tw, int sign)
+template <typename T, bool DIF>
+__device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls,
+                                          const FftPlan& pl, int s, const typename Cx<T>::t* __restrict__ tw,
+                                          int sign)
 {
-    using C = typename Cx<T>::t;
-    C* in = a;
-    C* out = b;
-    int p = 1;
+    const int R = pl.r[s];
+    if (R == 8) fft_pass<T, 8, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
+    else if (R == 4) fft_pass<T, 4, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
+    else if (R == 3) fft_pass<T, 3, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
+    else fft_pass<T, 2, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
+    __syncthreads();
+}
+
+// Forward transform (decimation in frequency), natural order in, frequency
+// k left at position rev(k).
+template <typename T>
+__device__ void fft_fwd_dif(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
+                            const typename Cx<T>::t* __restrict__ tw)
+{
+    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true>(buf, nlines, dl, ls, pl, s, tw, -1);
+}
+
+// Inverse transform (decimation in time), frequency k taken at position
+// rev(k), natural order out.
+template <typename T>
+__device__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
+                            const typename Cx<T>::t* __restrict__ tw)
+{
+    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false>(buf, nlines, dl, ls, pl, s, tw, +1);
+}
+
+// Position of frequency index k (0 <= k < n) after a forward transform.
+__device__ __forceinline__ int rev_pos(int k, const FftPlan& pl)
+{
+    int p = 0;
     for (int s = 0; s < pl.nr; ++s) {
         const int R = pl.r[s];
-        if (R == 8) fft_pass<T, 8>(in, out, nlines, ls, pl.n, p, tw, sign);
-        else if (R == 4) fft_pass<T, 4>(in, out, nlines, ls, pl.n, p, tw, sign);
-        else if (R == 3) fft_pass<T, 3>(in, out, nlines, ls, pl.n, p, tw, sign);
-        else fft_pass<T, 2>(in, out, nlines, ls, pl.n, p, tw, sign);
-        __syncthreads();
-        C* t = in;
-        in = out;
-        out = t;
-        p *= R;
+        const int q = (R == 3) ? k / 3 : (k >> (R == 8 ? 3 : (R == 4 ? 2 : 1)));
+        p += (k - q * R) * pl.st[s];
+        k = q;
     }
-    return in;
+    return p;
 }
 
 template <typename T>
@@ -169,7 +203,6 @@ __device__ __forceinline__ T kb_val(T z, T zeta, T inorm)
 // every block its support reaches (with the offset of its support relative
 // to that block), so that a block reads only points that touch it.
 // ---------------------------------------------------------------------------
-template <typename T>
 __device__ __forceinline__ void col_range(int ib, int H, int Tb, int& b0, int& b1)
 {
     const int lo = ib - H + 1, hi = ib + H;
@@ -185,8 +218,8 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
     const int base = rec[i].base;
     const int ib0 = base & 1023, ib1 = (base >> 10) & 1023;
     int x0, x1, y0, y1;
-    col_range<T>(ib0, P.w / 2, P.tx, x0, x1);
-    col_range<T>(ib1, P.w / 2, P.ty, y0, y1);
+    col_range(ib0, P.w / 2, P.tx, x0, x1);
+    col_range(ib1, P.w / 2, P.ty, y0, y1);
     for (int by = y0; by <= y1; ++by) {
         const int wy = ((by % P.nby) + P.nby) % P.nby;
         for (int bx = x0; bx <= x1; ++bx) {
@@ -206,8 +239,8 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
     const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
     const int H = P.w / 2;
     int x0, x1, y0, y1;
-    col_range<T>(ib0, H, P.tx, x0, x1);
-    col_range<T>(ib1, H, P.ty, y0, y1);
+    col_range(ib0, H, P.tx, x0, x1);
+    col_range(ib1, H, P.ty, y0, y1);
     for (int by = y0; by <= y1; ++by) {
         const int wy = ((by % P.nby) + P.nby) % P.nby;
         const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block
@@ -224,9 +257,12 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
 
 // ---------------------------------------------------------------------------
 // A: spread + z real FFT.
-// smem: real accumulator 3 Tx Ty lines of stride n2+1 (reused as one FFT
-// buffer), a complex buffer of 3 Tx Ty / 2 lines of n2, per-warp kernel
-// tables.
+// The 3 Tx Ty real z-lines are accumulated directly as complex lines (real
+// line 2l in .x, 2l+1 in .y of complex line l, stride cls), transformed in
+// place, and separated while writing modes 0..K2.  Records are staged in
+// shared memory a chunk at a time and dealt to the warps round-robin; a
+// warp's lanes always hold distinct cells and shared atomic adds resolve two
+// warps meeting on a cell.
 // ---------------------------------------------------------------------------
 template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
@@ -237,77 +273,79 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Tx = P.tx, Ty = P.ty, n2 = P.ng[2];
-    const int nreal = 3 * Tx * Ty;
-    const int LS = n2 + 1;
-    T* acc = reinterpret_cast<T*>(smem_raw);
-    const size_t abytes = (((size_t)nreal * LS * sizeof(T)) + 15) & ~(size_t)15;
-    C* cb = reinterpret_cast<C*>(smem_raw + abytes);
+    const int txy = Tx * Ty;
+    const int nreal = 3 * txy;
     const int ncl = nreal / 2;
-    T* ktab = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(cb) + (size_t)ncl * n2 * sizeof(C));
+    const int CS = P.cls;
+    C* cb = reinterpret_cast<C*>(smem_raw);
+    T* accf = reinterpret_cast<T*>(cb);  // real line rl, position z at float ((rl>>1) CS + z) 2 + (rl&1)
+    LrRec<T>* srec = reinterpret_cast<LrRec<T>*>(cb + (size_t)ncl * CS);
+    T* ktab = reinterpret_cast<T*>(srec + kSpzChunk);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const int bx = blockIdx.x % P.nbx, by = blockIdx.x / P.nbx;
-    for (int i = tid; i < nreal * LS; i += blockDim.x) acc[i] = (T)0;
-    __syncthreads();
+    const int by = fdiv(blockIdx.x, P.d_nbx);
+    const int bx = blockIdx.x - by * P.nbx;
+    C zero;
+    zero.x = 0;
+    zero.y = 0;
+    for (int i = tid; i < ncl * CS; i += blockDim.x) cb[i] = zero;
 
-    // spread: one warp per record, lanes over (support row, z)
     const T zeta = (T)P.zeta;
     const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
     constexpr int H = W / 2;
     T* kw = ktab + wid * 3 * W;
     const int s0 = cstart[blockIdx.x], s1 = cstart[blockIdx.x + 1];
-    const int plane = Tx * Ty * LS;  // component stride in acc
-    for (int k = s0 + wid; k < s1; k += nw) {
-        const LrRec<T> R = recs[k];
-        const int r0 = (R.base & 255) - 128, r1 = ((R.base >> 8) & 255) - 128, ib2 = (R.base >> 16) & 1023;
-        const int a0 = max(r0, 0), e0 = min(r0 + W - 1, Tx - 1);
-        const int a1 = max(r1, 0), e1 = min(r1 + W - 1, Ty - 1);
-        const T f0 = R.f[0], f1 = R.f[1], f2 = R.f[2];
-        const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
-        __syncwarp();
-        for (int i = lane; i < 3 * W; i += 32) {
-            const int d = i / W, t = i - d * W;
-            const T f = d == 0 ? f0 : (d == 1 ? f1 : f2);
-            kw[i] = kb_val((f + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-        }
-        __syncwarp();
-        const int n0 = e0 - a0 + 1, n1 = e1 - a1 + 1;
-        const int rows_per = 32 / W;
-        const int rsub = lane / W, c2 = lane - rsub * W;
-        if (rsub < rows_per) {
-            int z = ib2 - H + 1 + c2;
-            z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
-            const T wz = kw[2 * W + c2];
-            const int nrows = n0 * n1;
-            for (int r = rsub; r < nrows; r += rows_per) {
-                const int c0 = r / n1, c1 = r - c0 * n1;
-                const int x0 = a0 + c0, x1 = a1 + c1;
-                const T wv = kw[x0 - r0] * kw[W + x1 - r1] * wz;
-                const int cell = (x0 * Ty + x1) * LS + z;
-                atomicAdd(&acc[cell], wv * q0);
-                atomicAdd(&acc[plane + cell], wv * q1);
-                atomicAdd(&acc[2 * plane + cell], wv * q2);
+    const int rows_per = 32 / W;
+    const int rsub = lane / W, t = lane - rsub * W;  // this lane: support row group and z offset
+    for (int c0r = s0; c0r < s1; c0r += kSpzChunk) {
+        const int nch = min(kSpzChunk, s1 - c0r);
+        __syncthreads();
+        for (int i = tid; i < nch; i += blockDim.x) srec[i] = recs[c0r + i];
+        __syncthreads();
+        for (int kk = wid; kk < nch; kk += nw) {
+            const LrRec<T> R = srec[kk];
+            const int ib2 = (R.base >> 16) & 1023;
+            const int r0 = (R.base & 255) - 128, r1 = ((R.base >> 8) & 255) - 128;
+            const int a0 = max(r0, 0), e0 = min(r0 + W - 1, Tx - 1);
+            const int a1 = max(r1, 0), e1 = min(r1 + W - 1, Ty - 1);
+            const T f0 = R.f[0], f1 = R.f[1], f2 = R.f[2];
+            const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
+            __syncwarp();
+            for (int i = lane; i < 3 * W; i += 32) {
+                const int d = i / W, tt = i - d * W;
+                const T f = d == 0 ? f0 : (d == 1 ? f1 : f2);
+                kw[i] = kb_val((f + (T)(H - 1 - tt)) * ((T)2 / (T)W), zeta, inorm);
+            }
+            __syncwarp();
+            if (rsub < rows_per) {
+                int z = ib2 - H + 1 + t;
+                z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
+                const T wz = kw[2 * W + t];
+                const int n1 = e1 - a1 + 1;
+                const int nrows = (e0 - a0 + 1) * n1;
+                for (int r = rsub; r < nrows; r += rows_per) {
+                    const int c0 = r / n1, c1 = r - c0 * n1;
+                    const int x0 = a0 + c0, x1 = a1 + c1;
+                    const T wv = kw[x0 - r0] * kw[W + x1 - r1] * wz;
+                    const int rl = x0 * Ty + x1;  // real line of component 0
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int rlc = rl + c * txy;
+                        const T qc = c == 0 ? q0 : (c == 1 ? q1 : q2);
+                        atomicAdd(&accf[((rlc >> 1) * CS + z) * 2 + (rlc & 1)], wv * qc);
+                    }
+                }
             }
         }
     }
     __syncthreads();
-    // pack real lines 2l, 2l+1 into complex line l
-    for (int i = tid; i < ncl * n2; i += blockDim.x) {
-        const int l = i / n2, z = i - l * n2;
-        C v;
-        v.x = acc[(2 * l) * LS + z];
-        v.y = acc[(2 * l + 1) * LS + z];
-        cb[l * n2 + z] = v;
-    }
-    __syncthreads();
-    C* res = fft_lines<T>(cb, reinterpret_cast<C*>(acc), ncl, n2, P.plan2, tw2, -1);
+    fft_fwd_dif<T>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
     // separate the two real transforms and write modes 0..K2
-    const int K2 = P.K[2];
-    const int nk = K2 + 1;
+    const int nk = P.K[2] + 1;
     for (int i = tid; i < nreal * nk; i += blockDim.x) {
-        const int rl = i / nk, mz = i - rl * nk;
+        const int rl = fdiv(i, P.d_nk), mz = i - rl * nk;
         const int l = rl >> 1;
-        const C zk = res[l * n2 + mz];
-        const C zn = res[l * n2 + (mz == 0 ? 0 : n2 - mz)];
+        const C zk = cb[l * CS + rev_pos(mz, P.plan2)];
+        const C zn = cb[l * CS + rev_pos(mz == 0 ? 0 : n2 - mz, P.plan2)];
         C o;
         if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
             o.x = (T)0.5 * (zk.x + zn.x);
@@ -316,15 +354,15 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
             o.x = (T)0.5 * (zk.y + zn.y);
             o.y = (T)0.5 * (zn.x - zk.x);
         }
-        const int c = rl / (Tx * Ty), rem = rl - c * Tx * Ty;
-        const int lx = rem / Ty, ly = rem - lx * Ty;
+        const int c = fdiv(rl, P.d_txy), rem = rl - c * txy;
+        const int lx = fdiv(rem, P.d_ty), ly = rem - lx * Ty;
         const int x = bx * Tx + lx, y = by * Ty + ly;
         F1[(((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk + mz] = o;
     }
 }
 
 // ---------------------------------------------------------------------------
-// B / D: transforms along y.  One CTA per (c, x, chunk of MC z-modes).
+// B / D: transforms along y.  One CTA per (c, x, chunk of 2^lmc z-modes).
 // forward: F1[c][x][y][mz] -> F2[c][x][my'][mz], my' = my + K1, |my| <= K1
 // inverse: F2 -> F1 (zero-padded to n1)
 // ---------------------------------------------------------------------------
@@ -335,55 +373,53 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* 
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n1 = P.ng[1], K1 = P.K[1], nk = P.K[2] + 1, MC = P.mc;
-    const int LS = n1 + 1;
+    const int n1 = P.ng[1], K1 = P.K[1], nk = P.K[2] + 1;
+    const int lmc = P.lmc, MC = 1 << lmc;
+    const int LS = P.ls;
     C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + MC * LS;
-    const int nch = (nk + MC - 1) / MC;
-    const int ch = blockIdx.x % nch;
-    const int cx = blockIdx.x / nch;  // c * n0 + x
-    const int mz0 = ch * MC;
+    const int nch = (nk + MC - 1) >> lmc;
+    const int cx = fdiv(blockIdx.x, P.d_nch);  // c * n0 + x
+    const int ch = blockIdx.x - cx * nch;
+    const int mz0 = ch << lmc;
     const int mcount = min(MC, nk - mz0);
     const int ny2 = 2 * K1 + 1;
     C zero;
     zero.x = 0;
     zero.y = 0;
     if (sign < 0) {
-        for (int i = threadIdx.x; i < n1 * MC; i += blockDim.x) {
-            const int y = i / MC, l = i - y * MC;
+        for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
+            const int y = i >> lmc, l = i & (MC - 1);
             a[l * LS + y] = (l < mcount) ? F1[((size_t)cx * n1 + y) * nk + mz0 + l] : zero;
         }
-    } else {
-        for (int i = threadIdx.x; i < n1 * MC; i += blockDim.x) {
-            const int y = i / MC, l = i - y * MC;
-            const int my = y <= n1 / 2 ? y : y - n1;  // frequency held at index y
-            C v = zero;
-            if (l < mcount && my >= -K1 && my <= K1) v = F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l];
-            a[l * LS + y] = v;
-        }
-    }
-    __syncthreads();
-    C* res = fft_lines<T>(a, b, MC, LS, P.plan1, tw1, sign);
-    if (sign < 0) {
-        for (int i = threadIdx.x; i < ny2 * MC; i += blockDim.x) {
-            const int myp = i / MC, l = i - myp * MC;
+        __syncthreads();
+        fft_fwd_dif<T>(a, MC, P.d_lines, LS, P.plan1, tw1);
+        for (int i = threadIdx.x; i < (ny2 << lmc); i += blockDim.x) {
+            const int myp = i >> lmc, l = i & (MC - 1);
             if (l >= mcount) continue;
             const int my = myp - K1;
-            const int y = my < 0 ? my + n1 : my;
-            F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] = res[l * LS + y];
+            F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] = a[l * LS + rev_pos(my < 0 ? my + n1 : my, P.plan1)];
         }
     } else {
-        for (int i = threadIdx.x; i < n1 * MC; i += blockDim.x) {
-            const int y = i / MC, l = i - y * MC;
+        for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
+            const int y = i >> lmc, l = i & (MC - 1);  // y: frequency index
+            const int my = y <= n1 / 2 ? y : y - n1;
+            C v = zero;
+            if (l < mcount && my >= -K1 && my <= K1) v = F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l];
+            a[l * LS + rev_pos(y, P.plan1)] = v;
+        }
+        __syncthreads();
+        fft_inv_dit<T>(a, MC, P.d_lines, LS, P.plan1, tw1);
+        for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
+            const int y = i >> lmc, l = i & (MC - 1);
             if (l >= mcount) continue;
-            F1[((size_t)cx * n1 + y) * nk + mz0 + l] = res[l * LS + y];
+            F1[((size_t)cx * n1 + y) * nk + mz0 + l] = a[l * LS + y];
         }
     }
 }
 
 // ---------------------------------------------------------------------------
 // C: x forward FFT + k-space pass + x inverse FFT, in place on F2.
-// One CTA per (my', chunk of MC z-modes); the 3 components together (the
+// One CTA per (my', chunk of 2^lmc z-modes); the 3 components together (the
 // curl couples them).  tabs: e^{-k_d^2/4alpha^2} / F_d(m)^2 per axis.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -395,54 +431,52 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n0 = P.ng[0], K0 = P.K[0], K1 = P.K[1], nk = P.K[2] + 1, MC = P.mc;
+    const int n0 = P.ng[0], K0 = P.K[0], K1 = P.K[1], nk = P.K[2] + 1;
+    const int lmc = P.lmc, MC = 1 << lmc;
     const int ny2 = 2 * K1 + 1;
-    const int LS = n0 + 1;
+    const int LS = P.ls;
     const int want_psi = F2psi != nullptr;
-    const int nl = (want_psi ? 6 : 3) * MC;  // lines: [comp][mz]; psi lines follow
-    C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + nl * LS;
-    const int nch = (nk + MC - 1) / MC;
-    const int ch = blockIdx.x % nch;
-    const int myp = blockIdx.x / nch;
-    const int mz0 = ch * MC;
+    C* a = reinterpret_cast<C*>(smem_raw);  // lines [comp][mz], psi lines follow
+    const int nch = (nk + MC - 1) >> lmc;
+    const int myp = fdiv(blockIdx.x, P.d_nch);
+    const int ch = blockIdx.x - myp * nch;
+    const int mz0 = ch << lmc;
     const int mcount = min(MC, nk - mz0);
     C zero;
     zero.x = 0;
     zero.y = 0;
-    // load: line (c, l) position x <- F2[c][x][myp][mz0 + l]
-    for (int i = threadIdx.x; i < 3 * n0 * MC; i += blockDim.x) {
-        const int l = i % MC;
-        const int cx = i / MC;  // c * n0 + x
-        const int c = cx / n0, x = cx - c * n0;
-        a[(c * MC + l) * LS + x] = (l < mcount) ? F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] : zero;
+    for (int i = threadIdx.x; i < ((3 * n0) << lmc); i += blockDim.x) {
+        const int l = i & (MC - 1);
+        const int cx = i >> lmc;  // c * n0 + x
+        const int c = fdiv(cx, P.d_n0), x = cx - c * n0;
+        a[((c << lmc) + l) * LS + x] = (l < mcount) ? F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] : zero;
     }
     __syncthreads();
-    C* res = fft_lines<T>(a, b, 3 * MC, LS, P.plan0, tw0, -1);
-    C* other = (res == a) ? b : a;
-    // k-space pass: mode (mx, my, mz) for every (l, x-index)
+    fft_fwd_dif<T>(a, 3 * MC, P.d_lines, LS, P.plan0, tw0);
+    // k-space pass: frequency (mx, my, mz) sits at position rev(xi) of line (c, l)
     const int my = myp - K1;
     const int amy = my < 0 ? -my : my;
-    for (int i = threadIdx.x; i < MC * n0; i += blockDim.x) {
-        const int l = i / n0, xi = i - l * n0;
+    for (int i = threadIdx.x; i < (n0 << lmc); i += blockDim.x) {
+        const int l = i & (MC - 1), xi = i >> lmc;
         const int mx = xi <= n0 / 2 ? xi : xi - n0;
         const int amx = mx < 0 ? -mx : mx;
         const int mz = mz0 + l;
-        C w0 = res[(0 * MC + l) * LS + xi], w1 = res[(1 * MC + l) * LS + xi], w2 = res[(2 * MC + l) * LS + xi];
+        const int pos = rev_pos(xi, P.plan0);
+        C* r0 = a + ((0 * MC + l) * LS + pos);
+        C* r1 = a + ((1 * MC + l) * LS + pos);
+        C* r2 = a + ((2 * MC + l) * LS + pos);
         if (l >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
-            w0 = zero;
-            w1 = zero;
-            w2 = zero;
-            res[(0 * MC + l) * LS + xi] = zero;
-            res[(1 * MC + l) * LS + xi] = zero;
-            res[(2 * MC + l) * LS + xi] = zero;
+            *r0 = zero;
+            *r1 = zero;
+            *r2 = zero;
             if (want_psi) {
-                res[(3 * MC + l) * LS + xi] = zero;
-                res[(4 * MC + l) * LS + xi] = zero;
-                res[(5 * MC + l) * LS + xi] = zero;
+                a[(3 * MC + l) * LS + pos] = zero;
+                a[(4 * MC + l) * LS + pos] = zero;
+                a[(5 * MC + l) * LS + pos] = zero;
             }
             continue;
         }
+        C w0 = *r0, w1 = *r1, w2 = *r2;
         const T k0 = (T)(P.kk[0] * mx), k1 = (T)(P.kk[1] * my), k2 = (T)(P.kk[2] * mz);
         const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
         const T mult = (T)P.scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
@@ -454,25 +488,25 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
         const T cr1 = k2 * w0.x - k0 * w2.x, ci1 = k2 * w0.y - k0 * w2.y;
         const T cr2 = k0 * w1.x - k1 * w0.x, ci2 = k0 * w1.y - k1 * w0.y;
         C o;
-        o.x = -ci0; o.y = cr0; res[(0 * MC + l) * LS + xi] = o;
-        o.x = -ci1; o.y = cr1; res[(1 * MC + l) * LS + xi] = o;
-        o.x = -ci2; o.y = cr2; res[(2 * MC + l) * LS + xi] = o;
+        o.x = -ci0; o.y = cr0; *r0 = o;
+        o.x = -ci1; o.y = cr1; *r1 = o;
+        o.x = -ci2; o.y = cr2; *r2 = o;
         if (want_psi) {
-            res[(3 * MC + l) * LS + xi] = w0;
-            res[(4 * MC + l) * LS + xi] = w1;
-            res[(5 * MC + l) * LS + xi] = w2;
+            a[(3 * MC + l) * LS + pos] = w0;
+            a[(4 * MC + l) * LS + pos] = w1;
+            a[(5 * MC + l) * LS + pos] = w2;
         }
     }
     __syncthreads();
-    C* out = fft_lines<T>(res, other, nl, LS, P.plan0, tw0, +1);
-    for (int i = threadIdx.x; i < 3 * n0 * MC; i += blockDim.x) {
-        const int l = i % MC;
+    fft_inv_dit<T>(a, (want_psi ? 6 : 3) * MC, want_psi ? P.d_lines_psi : P.d_lines, LS, P.plan0, tw0);
+    for (int i = threadIdx.x; i < ((3 * n0) << lmc); i += blockDim.x) {
+        const int l = i & (MC - 1);
         if (l >= mcount) continue;
-        const int cx = i / MC;
-        const int c = cx / n0, x = cx - c * n0;
+        const int cx = i >> lmc;
+        const int c = fdiv(cx, P.d_n0), x = cx - c * n0;
         const size_t g = ((size_t)cx * ny2 + myp) * nk + mz0 + l;
-        F2[g] = out[(c * MC + l) * LS + x];
-        if (want_psi) F2psi[g] = out[((3 + c) * MC + l) * LS + x];
+        F2[g] = a[((c << lmc) + l) * LS + x];
+        if (want_psi) F2psi[g] = a[(((3 + c) << lmc) + l) * LS + x];
     }
 }
 
@@ -489,44 +523,44 @@ __global__ void __launch_bounds__(kThreads) k_fft_z_c2r(FftZP P, const typename 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.ng[1], n2 = P.ng[2], nk = P.K[2] + 1, YC = P.yc;
     const int ncl = YC / 2;
+    const int CS = P.cls;
     C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + ncl * n2;
     const int nch = n1 / YC;
-    const int ch = blockIdx.x % nch;
-    const int cx = blockIdx.x / nch;  // c * n0 + x
+    const int cx = fdiv(blockIdx.x, P.d_nch);  // c * n0 + x
+    const int ch = blockIdx.x - cx * nch;
     const int y0 = ch * YC;
     C zero;
     zero.x = 0;
     zero.y = 0;
-    for (int i = threadIdx.x; i < ncl * n2; i += blockDim.x) a[i] = zero;
+    for (int i = threadIdx.x; i < ncl * CS; i += blockDim.x) a[i] = zero;
     __syncthreads();
-    // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k), k = 0..K2
+    // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k), k = 0..K2, at rev positions
     for (int i = threadIdx.x; i < ncl * nk; i += blockDim.x) {
-        const int l = i / nk, k = i - l * nk;
+        const int l = fdiv(i, P.d_nk), k = i - l * nk;
         const C A = F1[((size_t)cx * n1 + y0 + 2 * l) * nk + k];
         const C Bv = F1[((size_t)cx * n1 + y0 + 2 * l + 1) * nk + k];
         C z;
         if (k == 0) {
             z.x = A.x;
             z.y = Bv.x;
-            a[l * n2] = z;
+            a[l * CS] = z;
         } else {
             z.x = A.x - Bv.y;
             z.y = A.y + Bv.x;
-            a[l * n2 + k] = z;
+            a[l * CS + rev_pos(k, P.plan2)] = z;
             z.x = A.x + Bv.y;
             z.y = -A.y + Bv.x;
-            a[l * n2 + n2 - k] = z;
+            a[l * CS + rev_pos(n2 - k, P.plan2)] = z;
         }
     }
     __syncthreads();
-    const C* res = fft_lines<T>(a, b, ncl, n2, P.plan2, tw2, +1);
+    fft_inv_dit<T>(a, ncl, P.d_ncl, CS, P.plan2, tw2);
     const size_t gsz = (size_t)P.ng[0] * n1 * n2;
-    const int c = cx / P.ng[0], x = cx - c * P.ng[0];
+    const int c = fdiv(cx, P.d_n0), x = cx - c * P.ng[0];
     T* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
     for (int i = threadIdx.x; i < YC * n2; i += blockDim.x) {
-        const int yl = i / n2, z = i - yl * n2;
-        const C v = res[(yl >> 1) * n2 + z];
+        const int yl = fdiv(i, P.d_n2), z = i - yl * n2;
+        const C v = a[(yl >> 1) * CS + z];
         gout[(size_t)yl * n2 + z] = (yl & 1) ? v.y : v.x;
     }
 }
@@ -555,9 +589,9 @@ template <typename T>
 size_t spread_zfft_smem(const SpZP& P)
 {
     using C = typename Cx<T>::t;
-    const int nreal = 3 * P.tx * P.ty;
-    const size_t abytes = (((size_t)nreal * (P.ng[2] + 1) * sizeof(T)) + 15) & ~(size_t)15;
-    return abytes + (size_t)(nreal / 2) * P.ng[2] * sizeof(C) + (kThreads / 32) * 3 * (size_t)P.w * sizeof(T);
+    const int ncl = 3 * P.tx * P.ty / 2;
+    return (size_t)ncl * P.cls * sizeof(C) + kSpzChunk * sizeof(LrRec<T>) +
+           (kThreads / 32) * 3 * (size_t)P.w * sizeof(T);
 }
 
 template <typename T, int W>
@@ -592,11 +626,12 @@ template <typename T>
 cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s)
 {
     using C = typename Cx<T>::t;
-    const size_t sm = 2 * (size_t)P.mc * (P.ng[1] + 1) * sizeof(C);
+    const int MC = 1 << P.lmc;
+    const size_t sm = (size_t)MC * P.ls * sizeof(C);
     cudaError_t e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nk = P.K[2] + 1;
-    const int nch = (nk + P.mc - 1) / P.mc;
+    const int nch = (nk + MC - 1) / MC;
     k_fft_y<T><<<3 * P.ng[0] * nch, kThreads, sm, s>>>(P, (C*)w.spec, (C*)f2, (const C*)w.tw + P.ng[0], sign);
     return cudaGetLastError();
 }
@@ -605,12 +640,13 @@ template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s)
 {
     using C = typename Cx<T>::t;
-    const int nl = (want_psi ? 6 : 3) * P.mc;
-    const size_t sm = 2 * (size_t)nl * (P.ng[0] + 1) * sizeof(C);
+    const int MC = 1 << P.lmc;
+    const int nl = (want_psi ? 6 : 3) * MC;
+    const size_t sm = (size_t)nl * P.ls * sizeof(C);
     cudaError_t e = cudaFuncSetAttribute(k_fft_x_kspace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nk = P.K[2] + 1;
-    const int nch = (nk + P.mc - 1) / P.mc;
+    const int nch = (nk + MC - 1) / MC;
     const T* tab0 = (const T*)w.ktab;
     const T* tab1 = tab0 + (P.K[0] + 1);
     const T* tab2 = tab1 + (P.K[1] + 1);
@@ -623,7 +659,7 @@ template <typename T>
 cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s)
 {
     using C = typename Cx<T>::t;
-    const size_t sm = 2 * (size_t)(P.yc / 2) * P.ng[2] * sizeof(C);
+    const size_t sm = (size_t)(P.yc / 2) * P.cls * sizeof(C);
     cudaError_t e = cudaFuncSetAttribute(k_fft_z_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_fft_z_c2r<T><<<3 * P.ng[0] * (P.ng[1] / P.yc), kThreads, sm, s>>>(P, (const C*)w.spec,

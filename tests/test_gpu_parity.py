@@ -224,11 +224,13 @@ def test_total_fp64_high_accuracy_is_implementation_parity():
 @pytest.mark.parametrize("case", ["ring64", "ellipses40"])
 def test_total_mixed_configs(case):
     """Mixed precision on the ring (64 nodes, M = 32) and the 40-ellipse set
-    (2560 nodes, Q = 3, M = 64): rms error <= 1e-5 against the converged sum."""
+    (2560 nodes, Q = 3, M = 64): rms error <= 1e-5 against the converged sum.
+    w = 8 keeps the NUFFT error (~1e-5 of the total at w = 6 on the ring,
+    Appendix A) below the float32 budget being checked here."""
     B = _B()
     spec = W.WORKLOADS[case]
     f = spec["gen"]()
-    p = params(f, M=spec["M"], Q=spec["Q"], w=6, sigma=1.5, precision=B.BS_MIXED)
+    p = params(f, M=spec["M"], Q=spec["Q"], w=8, sigma=1.5, precision=B.BS_MIXED)
     v = gpu_velocity(f, p)
     g = geom(f, 4, spec["Q"])
     vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
