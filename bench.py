@@ -35,13 +35,13 @@ import numpy as np  # noqa: E402
 METRIC = "filament nodes/s per Biot–Savart eval at 1e-6 rel. err; FP32/batched vs FP64"
 UNIT = "nodes/s"
 L2_FLUSH_BYTES = 512 << 20
-KERNELS_PER_STEP = 16  # spline, nodes, 2 x (count, 3 scan, scatter), short, spread, k-space, interp
+KERNELS_PER_STEP = 19  # spline, nodes, 2 x (count, 3 scan, scatter), short, spread+z FFT, y FFT, x FFT+k-space, inverse y, inverse z, interp
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="tangle1e5")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -69,8 +69,11 @@ class Clocks:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            t0 = time.time()  # the sampler is up once its first line is written
+            while time.time() - t0 < 5 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -117,12 +120,13 @@ def make_params(B, spec, f, precision, flags=0):
                          M=spec["M"], Q=spec["Q"], w=w, sigma=spec["sigma"], precision=precision, flags=flags)
 
 
-def spread_bytes(p, ng, NQ, real_bytes):
-    """Algorithmic bytes of one spread launch: write three real grids, read the
-    binned records once (32 B float / 64 B double) and the bin offsets."""
+def spread_zfft_bytes(p, ng, K, NQ, real_bytes):
+    """Algorithmic bytes of one fused spread + z-transform launch: read every
+    spread record once (32 B float / 64 B double) and write the retained
+    z-modes 0..K_z of the three components, complex, for every (x, y) grid
+    column."""
     rec = 32 if real_bytes == 4 else 64
-    ntiles = (ng[0] // 8) * (ng[1] // 8) * (ng[2] // (32 if ng[2] % 32 == 0 else (16 if ng[2] % 16 == 0 else 8)))
-    return 3 * real_bytes * ng[0] * ng[1] * ng[2] + rec * NQ + 4 * (ntiles + 1)
+    return rec * NQ + 3 * ng[0] * ng[1] * (K[2] + 1) * 2 * real_bytes
 
 
 def ncu_traffic(kernel, workload, source):
@@ -187,7 +191,8 @@ def run_ours(args, rank, world, dist):
     spec, f = workload(args.workload)
     prec = B.BS_MIXED if args.precision == "mixed" else B.BS_FP64
     p = make_params(B, spec, f, prec, flags=B.BS_TIMING)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)  # non-default: the evaluation is replayed as a CUDA graph
+    torch.cuda.set_stream(stream)
     bs = B.BiotSavart(p, f.offsets, f.closing, stream=stream)
     nodes = torch.from_numpy(f.nodes).to(dev)
     vel = torch.empty_like(nodes)
@@ -197,6 +202,32 @@ def run_ours(args, rank, world, dist):
         bs.velocity(nodes, vel)
     bs.status()
     torch.cuda.synchronize()
+    # direct calls (no graph), for reference
+    ed0, ed1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    direct = []
+    for _ in range(5):
+        flush.zero_()
+        ed0.record(stream)
+        bs.velocity(nodes, vel)
+        ed1.record(stream)
+        torch.cuda.synchronize()
+        direct.append(ed0.elapsed_time(ed1))
+    # the same evaluation replayed from a CUDA graph (context without stage events)
+    bsg = B.BiotSavart(make_params(B, spec, f, prec), f.offsets, f.closing, stream=stream)
+    velg = torch.empty_like(nodes)
+    bsg.capture(nodes, velg)
+    for _ in range(3):
+        bsg.launch()
+    torch.cuda.synchronize()
+    graph_ms = []
+    for _ in range(10):
+        flush.zero_()
+        ed0.record(stream)
+        bsg.launch()
+        ed1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms.append(ed0.elapsed_time(ed1))
+    bsg.close()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -208,7 +239,7 @@ def run_ours(args, rank, world, dist):
     for k in range(args.steps):
         flush.zero_()  # L2 flush between steps, outside the timed events
         ev[k][0].record(stream)
-        bs.velocity(nodes, vel)
+        bs.velocity(nodes, vel)  # one full evaluation (bs_compute)
         ev[k][1].record(stream)
         stages.append(bs.stage_times())  # synchronises the streams
     torch.cuda.synchronize()
@@ -228,7 +259,8 @@ def run_ours(args, rank, world, dist):
     ng, _ = B.bs_nufft_setup(p, want_table=False)
     real_bytes = 4 if prec == B.BS_MIXED else 8
     NQ = f.N * spec["Q"]
-    sb = spread_bytes(p, ng, NQ, real_bytes)
+    Kd = [(p.M[i] - 1) // 2 for i in range(3)]
+    sb = spread_zfft_bytes(p, ng, Kd, NQ, real_bytes)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -309,11 +341,11 @@ def run_ours(args, rank, world, dist):
                        if prec == B.BS_MIXED else "f64",
                        "N": f.N, "nfil": f.nfil, "M": spec["M"], "n_g": ng, "Q": spec["Q"], "w": p.nufft_w,
                        "sigma": spec["sigma"], "beta": spec["beta"], "alpha": p.alpha, "rc": p.rc,
-                       "l2": "512 MiB L2 flush between timed steps (outside the events); grids 1.4 GB > L2",
+                       "l2": "512 MiB L2 flush between timed steps (outside the events)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "kernel": "k_spread", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": ncu_traffic("k_spread", args.workload, "paper_2406_07366_gb300/csrc/k_long.cu")
+            "roofline": {"bound": "hbm", "kernel": "k_spread_zfft", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic("k_spread_zfft", args.workload, "paper_2406_07366_gb300/csrc/k_fft.cu")
                          if prec == B.BS_MIXED else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
                          "algorithmic_bytes": sb, "ms": stage_mean["spread"]},
@@ -322,6 +354,7 @@ def run_ours(args, rank, world, dist):
                     "d2h_bytes_per_step": int(f.N * 24), "ms_per_step": e2e_s * 1e3,
                     "api": "bs_compute_host (pinned host buffers)"},
             "gpu_launches": launches,
+            "ms_per_step_graph_replay": statistics.median(graph_ms),
             "clocks": clk,
             "stages_ms": stage_mean,
             "fp64_form": fp64,

@@ -174,6 +174,22 @@ int bs_compute(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
 int bs_compute_host(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
 
 /*
+ * Kinetic energy per unit mass (Sec. 2.4, Eq. kinetic_energy_streamfunction,
+ * E = kappa/(2V) oint psi . ds), with the velocity and streamfunction of
+ * the same evaluation.  The long-range part is the float64 Fourier
+ * reduction (1/2) sum_{k != 0} e^{-k^2/4 alpha^2} |omega_k|^2 / k^2 over the
+ * resolved modes; the rest (psi_local + psi^(n) - psi^(f)_self at the nodes,
+ * dotted with the tau-derivative of the curve) is interpolated by the same
+ * periodic cubic spline and integrated exactly along each filament.
+ *   nodes  (device) N x 3
+ *   vel    (device) N x 3 output, or NULL
+ *   psi    (device) N x 3 output, or NULL
+ *   energy (host)   scalar output
+ * Needs BS_WANT_PSI; synchronises the stream.  Filaments up to 5120 nodes.
+ */
+int bs_compute_energy(bs_ctx* ctx, const double* nodes, double* vel, double* psi, double* energy);
+
+/*
  * The four parts of Eq. ewald_velocity_splitting separately, for parity
  * tests: parts (device) 4 x N x 3 = [v_local, v^(n), v^(f), v^(f)_self];
  * psi_parts (device) the same for the streamfunction, or NULL.
@@ -187,6 +203,19 @@ int bs_compute_parts(bs_ctx* ctx, const double* nodes, double* parts, double* ps
  * positions wrapped into [0, L).  Refits the splines; allocates nothing.
  */
 int bs_get_quadrature(bs_ctx* ctx, const double* nodes, double* qX, double* qq);
+
+/*
+ * Capture one bs_compute(ctx, nodes, vel, psi) into a CUDA graph bound to
+ * these device buffers (both branches of the evaluation become graph
+ * branches), replacing any previous graph; bs_graph_launch replays it on
+ * the context stream.  Needs a non-default stream (bs_create /
+ * bs_set_stream).  A later bs_set_filaments drops the graph.  The buffers
+ * must stay valid while the graph is used; their contents are read at
+ * replay time.  Errors: BS_ERR_ARG, BS_ERR_STATE (replay without capture),
+ * BS_ERR_CUDA.
+ */
+int bs_graph_capture(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
+int bs_graph_launch(bs_ctx* ctx);
 
 /* Synchronise the stream and return the device status word as a status
  * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY); clears it. */

@@ -79,6 +79,10 @@ def _load():
         lib.or_fourier_coefs.restype = None
         lib.or_fourier_eval.argtypes = [ctypes.c_long, _i64p, _dp, _dp, ctypes.c_double, _ip, _dp, _dp, _dp]
         lib.or_fourier_eval.restype = None
+        lib.or_energy_fourier.argtypes = [_dp, _ip, _dp, ctypes.c_double]
+        lib.or_energy_fourier.restype = ctypes.c_double
+        lib.or_energy_line.argtypes = [ctypes.c_long, _i64p, _dp, _dp, ctypes.c_int, _dp]
+        lib.or_energy_line.restype = ctypes.c_double
         lib.or_self.argtypes = [ctypes.c_long, _i64p, _dp, _i64p, _i64p, _dp, ctypes.c_int, _dp, _dp,
                                 ctypes.c_double, ctypes.c_double, _dp, _dp]
         lib.or_self.restype = None
@@ -277,6 +281,32 @@ def _fsum_rows(parts, signs):
         idx = it.multi_index
         x[...] = math.fsum(s * p[idx] for p, s in zip(parts, signs))
     return out
+
+
+def energy(g: Geometry, L, kappa, a, delta, alpha, rc, K, all_images=False, order=4):
+    """Kinetic energy E = kappa/(2V) oint psi . ds (Eq. kinetic_energy_streamfunction):
+    the long-range part as the Fourier reduction (1/2) sum_{k!=0} e^{-k^2/4alpha^2}
+    |omega_k|^2/k^2 over the mode cube K, plus kappa/(2V) times the line integral
+    of the spline interpolant of (psi_local + psi^(n) - psi^(f)_self) . sdot.
+    all_images selects the converged short range (27 images, no cut-off)."""
+    L = np.asarray(L, dtype=np.float64)
+    Kv = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (3,)))
+    om = fourier_coefs(g, L, kappa, Kv)
+    ef = float(_load().or_energy_fourier(_p(om), _p(Kv, _ip), _p(L), alpha))
+    _, pl = local(g, kappa, a, delta)
+    _, ps = short_range(g, L, kappa, alpha, rc, all_images=all_images)
+    _, px = self_term(g, kappa, alpha)
+    rest = np.ascontiguousarray(pl + ps - px)
+    line = float(_load().or_energy_line(g.offsets.size - 1, _p(g.offsets, _i64p), _p(g.nodes), _p(g.shift),
+                                        int(order), _p(rest)))
+    V = float(np.prod(L))
+    return ef + kappa / (2 * V) * line
+
+
+def energy_converged(g: Geometry, L, kappa, a, delta, beta_o=6.0, alpha_scale=1.0):
+    """The energy with the oracle's own converged split (27 images, mode cube K_o)."""
+    alpha, K = converged_params(L, beta_o, alpha_scale)
+    return energy(g, L, kappa, a, delta, alpha, 0.0, K, all_images=True)
 
 
 def converged_params(L, beta_o=6.0, alpha_scale=1.0):

@@ -697,6 +697,79 @@ void or_self(long ntgt, const int64_t* tgt, const double* nodes, const int64_t* 
 }
 
 /*
+ * Kinetic energy (Sec. 2.4, Eq. kinetic_energy_streamfunction,
+ * E = kappa/(2V) oint psi . ds), split as in the Ewald decomposition:
+ *   long range: kappa/(2V) sum_q q . psi^(f)(s_q) = (1/2) sum_{k != 0}
+ *               e^{-k^2/4 alpha^2} |omega_k|^2 / k^2   (or_energy_fourier,
+ *               over the full cube of omega from or_fourier_coefs);
+ *   the rest:   psi_local + psi^(n) - psi^(f)_self known at the nodes, f_j =
+ *               psi_j . sdot(tau_j) interpolated by the same periodic spline
+ *               in tau and integrated over each filament with Gauss-Legendre
+ *               (or_energy_line returns sum over filaments of int f dtau).
+ */
+double or_energy_fourier(const double* om, const int* K, const double* L, double alpha)
+{
+    const long n0 = 2 * K[0] + 1, n1 = 2 * K[1] + 1, n2 = 2 * K[2] + 1;
+    const long nm = n0 * n1 * n2;
+    double kk[3] = { 2.0 * OR_PI / L[0], 2.0 * OR_PI / L[1], 2.0 * OR_PI / L[2] };
+    csum acc = { 0, 0 };
+    for (long mi = 0; mi < nm; mi++) {
+        long m0 = mi / (n1 * n2) - K[0], m1 = (mi / n2) % n1 - K[1], m2 = mi % n2 - K[2];
+        double k0 = kk[0] * m0, k1 = kk[1] * m1, k2 = kk[2] * m2;
+        double k2s = k0 * k0 + k1 * k1 + k2 * k2;
+        if (k2s == 0.0) continue;
+        double w2 = 0.0;
+        for (int c = 0; c < 6; c++) w2 += om[6 * mi + c] * om[6 * mi + c];
+        cs_add(&acc, 0.5 * exp(-k2s / (4.0 * alpha * alpha)) * w2 / k2s);
+    }
+    return cs_get(&acc);
+}
+
+double or_energy_line(long nfil, const int64_t* off, const double* nodes, const double* shift, int k,
+                      const double* psi_nodes)
+{
+    double h[8], w[8];
+    or_gauss_legendre(4, h, w);
+    csum tot = { 0, 0 };
+    for (long f = 0; f < nfil; f++) {
+        long n = off[f + 1] - off[f];
+        const double* s = nodes + 3 * off[f];
+        const double* sh = shift + 3 * f;
+        double* tau = (double*)malloc((size_t)n * sizeof(double));
+        double* d = (double*)malloc((size_t)(n * 3) * sizeof(double));
+        double* fv = (double*)malloc((size_t)(n * 3) * sizeof(double));
+        double* fc = (double*)malloc((size_t)(n * 3) * sizeof(double));
+        double T;
+        fit_filament(n, s, sh, k, tau, &T, d);
+        kseq K = { tau, n, T };
+        /* f_j = psi_j . sdot(tau_j); carried in the first of three columns */
+        for (long j = 0; j < n; j++) {
+            double d1[3];
+            spline_eval(&K, k, d, j, tau[j], 1, d1);
+            for (int c = 0; c < 3; c++) d1[c] += sh[c] / T;
+            const double* ps = psi_nodes + 3 * (off[f] + j);
+            fv[3 * j] = ps[0] * d1[0] + ps[1] * d1[1] + ps[2] * d1[2];
+            fv[3 * j + 1] = 0.0;
+            fv[3 * j + 2] = 0.0;
+        }
+        spline_fit(&K, k, fv, fc);
+        for (long j = 0; j < n; j++) {
+            double dtau = (j < n - 1 ? tau[j + 1] : T) - tau[j];
+            for (int i = 0; i < 4; i++) {
+                double v[3];
+                spline_eval(&K, k, fc, j, tau[j] + h[i] * dtau, 0, v);
+                cs_add(&tot, w[i] * dtau * v[0]);
+            }
+        }
+        free(tau);
+        free(d);
+        free(fv);
+        free(fc);
+    }
+    return cs_get(&tot);
+}
+
+/*
  * Naive open-space Biot-Savart sum (Eq. BS_on_vortex with no periodic
  * images, the alpha = 0 reading of Sec. 3.2): every quadrature point except
  * those of the two unwrapped segments adjacent to the node.

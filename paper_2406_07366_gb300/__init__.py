@@ -33,7 +33,7 @@ STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", 
 EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_create", "bs_set_stream",
            "bs_set_filaments", "bs_compute", "bs_compute_host", "bs_compute_parts", "bs_get_quadrature",
            "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error",
-           "bs_short_range_static"]
+           "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy"]
 
 
 class bs_params(ctypes.Structure):
@@ -79,6 +79,9 @@ def _load():
         "bs_workspace_bytes": ([vp, P(ctypes.c_longlong)], ctypes.c_int),
         "bs_destroy": ([vp], None),
         "bs_last_error": ([], ctypes.c_char_p),
+        "bs_graph_capture": ([vp, vp, vp, vp], ctypes.c_int),
+        "bs_compute_energy": ([vp, vp, vp, vp, P(ctypes.c_double)], ctypes.c_int),
+        "bs_graph_launch": ([vp], ctypes.c_int),
         "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
@@ -184,6 +187,20 @@ def bs_get_quadrature(ctx, nodes, qX, qq):
     _check(lib().bs_get_quadrature(ctx, _ptr(nodes), _ptr(qX), _ptr(qq)))
 
 
+def bs_compute_energy(ctx, nodes, vel=None, psi=None):
+    e = ctypes.c_double()
+    _check(lib().bs_compute_energy(ctx, _ptr(nodes), _ptr(vel), _ptr(psi), ctypes.byref(e)))
+    return e.value
+
+
+def bs_graph_capture(ctx, nodes, vel, psi=None):
+    _check(lib().bs_graph_capture(ctx, _ptr(nodes), _ptr(vel), _ptr(psi)))
+
+
+def bs_graph_launch(ctx):
+    _check(lib().bs_graph_launch(ctx))
+
+
 def bs_status(ctx):
     return _check(lib().bs_status(ctx))
 
@@ -264,6 +281,17 @@ class BiotSavart:
         pp = self.torch.empty((4, self.N, 3), dtype=self.torch.float64, device="cuda") if want_psi else None
         bs_compute_parts(self.ctx, nodes, parts, pp)
         return (parts, pp) if want_psi else parts
+
+    def energy(self, nodes, vel=None, psi=None):
+        """Kinetic energy (and optionally velocity / streamfunction) of one evaluation."""
+        return bs_compute_energy(self.ctx, nodes, vel, psi)
+
+    def capture(self, nodes, vel, psi=None):
+        """Capture one evaluation into a CUDA graph (replay with launch())."""
+        bs_graph_capture(self.ctx, nodes, vel, psi)
+
+    def launch(self):
+        bs_graph_launch(self.ctx)
 
     def quadrature(self, nodes):
         Q = self.params.quad_Q

@@ -273,6 +273,8 @@ struct bs_ctx {
     long long bytes = 0;
     std::vector<std::pair<void*, size_t>> alloc_n, alloc_g;
     int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
 };
 
 namespace {
@@ -366,6 +368,7 @@ int alloc_grids(bs_ctx* c)
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cur, sizeof(int) * (size_t)(d.ncells + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp, sizeof(int) * (size_t)scan_blocks((int)d.ncells)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.status, sizeof(int)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.energy_acc, 2 * sizeof(double)));
     CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
     // k-space tables e^{-k_d^2 / 4 alpha^2} / F_d(m)^2, m = 0..K_d
     const int ntab = d.K[0] + d.K[1] + d.K[2] + 3;
@@ -497,15 +500,17 @@ int fft_inv(bs_ctx* c, void* spec, cudaStream_t s)
 // are recorded on the stream each stage runs on (the two branches stay
 // concurrent); stage i spans events [kStageBeg[i], kStageEnd[i]].
 template <typename T>
-int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts, double* psi_parts)
+int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts, double* psi_parts,
+        bool want_energy = false)
 {
     const bs_params& p = c->p;
     const Derived& d = c->d;
     const Work& w = c->w;
     cudaStream_t s = c->stream;
     const size_t N3 = (size_t)c->N * 3;
-    const bool want_psi = (psi != nullptr) || (psi_parts != nullptr);
+    const bool want_psi = (psi != nullptr) || (psi_parts != nullptr) || want_energy;
     c->timed = (p.flags & BS_TIMING) != 0;
+    if (want_energy) CE(cudaMemsetAsync(w.energy_acc, 0, 2 * sizeof(double), s));
 
     GeomP G;
     fill_geom(c, G);
@@ -565,6 +570,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         K.nh = d.nh;
         K.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
         K.want_psi = want_psi ? 1 : 0;
+        K.energy = want_energy ? w.energy_acc : nullptr;
         CE(launch_kspace<T>(K, w, s));
         rec(c, 7, s);
         TRY(fft_inv<T>(c, w.spec, s));
@@ -628,6 +634,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         XP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
         XP.d_lines = make_fastdiv(3u << d.lmcx);
         XP.d_lines_psi = make_fastdiv(6u << d.lmcx);
+        XP.energy = want_energy ? w.energy_acc : nullptr;
         CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
         rec(c, 7, s);
         CE(launch_fft_y<T>(YP, w, w.f2, +1, s));
@@ -649,6 +656,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     }
     CE(cudaStreamWaitEvent(s, c->ev_join, 0));
     rec(c, 9, s);
+    if (want_energy) CE(launch_energy_line<T>(nodes, w, c->nfil, w.nmax_fil, s));
 
     InterpP I;
     I.N = (int)c->N;
@@ -867,6 +875,14 @@ int bs_set_filaments(bs_ctx* c, int nfil, const int64_t* offsets, const int32_t*
     if (N * c->p.quad_Q > (1LL << 31) - 1) return fail(BS_ERR_ARG, "too many quadrature points");
     CUDA_TRY(cudaSetDevice(c->device));
     CUDA_TRY(cudaDeviceSynchronize());
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
     free_list(c, c->alloc_n);  // drop the buffers of a previous topology
     c->w.off = nullptr;
     std::vector<int> fil_of((size_t)N), prev((size_t)N);
@@ -930,6 +946,29 @@ int bs_compute_parts(bs_ctx* c, const double* nodes, double* parts, double* psi_
                                      : run<float>(c, nodes, nullptr, nullptr, parts, psi_parts);
 }
 
+int bs_compute_energy(bs_ctx* c, const double* nodes, double* vel, double* psi, double* energy)
+{
+    TRY(check_ctx(c));
+    if (!energy) return fail(BS_ERR_ARG, "null energy");
+    *energy = 0.0;
+    if (c->N == 0) return BS_OK;
+    if (!nodes) return fail(BS_ERR_ARG, "null nodes");
+    if (!(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "the energy needs a context created with BS_WANT_PSI");
+    if (5 * (size_t)c->w.nmax_fil * sizeof(double) > 200 * 1024)
+        return fail(BS_ERR_ARG, "filament too long for the energy integral (%d nodes > 5120)", c->w.nmax_fil);
+    double* v = vel ? vel : c->w.vel_out;
+    double* ps = psi ? psi : c->w.psi_out;
+    int rc = c->p.precision == BS_FP64 ? run<double>(c, nodes, v, ps, nullptr, nullptr, true)
+                                       : run<float>(c, nodes, v, ps, nullptr, nullptr, true);
+    if (rc != BS_OK) return rc;
+    double acc[2];
+    CUDA_TRY(cudaMemcpyAsync(acc, c->w.energy_acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double V = c->p.L[0] * c->p.L[1] * c->p.L[2];
+    *energy = acc[0] + c->p.kappa / (2.0 * V) * acc[1];
+    return BS_OK;
+}
+
 int bs_get_quadrature(bs_ctx* c, const double* nodes, double* qX, double* qq)
 {
     TRY(check_ctx(c));
@@ -944,6 +983,45 @@ int bs_get_quadrature(bs_ctx* c, const double* nodes, double* qX, double* qq)
         CE(launch_spline<float>(nodes, c->w, c->nfil, c->stream));
         CE(launch_export_quadrature<float>(G, nodes, c->w, qX, qq, c->stream));
     }
+    return BS_OK;
+}
+
+int bs_graph_capture(bs_ctx* c, const double* nodes, double* vel, double* psi)
+{
+    TRY(check_ctx(c));
+    if (!c->stream) return fail(BS_ERR_ARG, "graph capture needs a non-default stream");
+    if (!nodes || !vel) return fail(BS_ERR_ARG, "null nodes or vel");
+    if (psi && !(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "psi requested without BS_WANT_PSI");
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (c->N == 0) return BS_OK;
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = c->p.precision == BS_FP64 ? run<double>(c, nodes, vel, psi, nullptr, nullptr)
+                                       : run<float>(c, nodes, vel, psi, nullptr, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc != BS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(BS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    c->graph = g;
+    CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    return BS_OK;
+}
+
+int bs_graph_launch(bs_ctx* c)
+{
+    TRY(check_ctx(c));
+    if (c->N == 0) return BS_OK;
+    if (!c->gexec) return fail(BS_ERR_STATE, "no captured graph (call bs_graph_capture first)");
+    CUDA_TRY(cudaGraphLaunch(c->gexec, c->stream));
     return BS_OK;
 }
 
@@ -996,6 +1074,8 @@ void bs_destroy(bs_ctx* c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->side) cudaStreamSynchronize(c->side);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     if (c->plans) {
         if (c->plan_fwd) cufftDestroy(c->plan_fwd);
         if (c->plan_inv) cufftDestroy(c->plan_inv);

@@ -104,6 +104,7 @@ struct KspaceP {
     double kk[3];       // 2 pi / L
     double scale;       // kappa / V
     int want_psi;
+    double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
 };
 
 // Exact unsigned division by a run-time constant d for 0 <= x < 2^31
@@ -188,6 +189,7 @@ struct FftXP {
     double scale;
     FftPlan plan0;
     FastDiv d_nch, d_n0, d_lines, d_lines_psi;
+    double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
 };
 
 struct FftZP {
@@ -263,6 +265,7 @@ struct Work {
     double* vel_out = nullptr;
     double* psi_out = nullptr;
     int* status = nullptr;
+    double* energy_acc = nullptr;  // [0] Fourier part, [1] line integral
 };
 
 // Launchers (explicit instantiations for float and double live in the .cu files).
@@ -300,6 +303,9 @@ template <typename T>
 cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s);
 template <typename T>
 size_t spread_zfft_smem(const SpZP& P);
+
+template <typename T>
+cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);

@@ -456,6 +456,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
     // k-space pass: frequency (mx, my, mz) sits at position rev(xi) of line (c, l)
     const int my = myp - K1;
     const int amy = my < 0 ? -my : my;
+    double esum = 0.0;  // energy of this thread's modes (float64 reduction)
     for (int i = threadIdx.x; i < (n0 << lmc); i += blockDim.x) {
         const int l = i & (MC - 1), xi = i >> lmc;
         const int mx = xi <= n0 / 2 ? xi : xi - n0;
@@ -480,6 +481,13 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
         const T k0 = (T)(P.kk[0] * mx), k1 = (T)(P.kk[1] * my), k2 = (T)(P.kk[2] * mz);
         const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
         const T mult = (T)P.scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
+        if (P.energy) {
+            // (1/2) e^{-k^2/4a^2} |omega|^2 / k^2 = (kappa/V) mult |F|^2 / 2; the
+            // half spectrum holds the pair (k, -k) once when mz > 0
+            const double f2 = (double)w0.x * w0.x + (double)w0.y * w0.y + (double)w1.x * w1.x +
+                              (double)w1.y * w1.y + (double)w2.x * w2.x + (double)w2.y * w2.y;
+            esum += (mz > 0 ? 1.0 : 0.5) * P.scale * (double)mult * f2;
+        }
         w0.x *= mult; w0.y *= mult;
         w1.x *= mult; w1.y *= mult;
         w2.x *= mult; w2.y *= mult;
@@ -496,6 +504,11 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
             a[(4 * MC + l) * LS + pos] = w1;
             a[(5 * MC + l) * LS + pos] = w2;
         }
+    }
+    if (P.energy) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        if ((threadIdx.x & 31) == 0 && esum != 0.0) atomicAdd(P.energy, esum);
     }
     __syncthreads();
     fft_inv_dit<T>(a, (want_psi ? 6 : 3) * MC, want_psi ? P.d_lines_psi : P.d_lines, LS, P.plan0, tw0);

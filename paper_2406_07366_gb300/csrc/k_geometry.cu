@@ -499,6 +499,119 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     if (flags) atomicOr(status, flags);
 }
 
+// Energy line integral (Sec. 2.4, Eq. kinetic_energy_streamfunction): per
+// filament, f_j = (psi_local + psi^(n) - psi^(f)_self)(s_j) . sdot(tau_j) at
+// the nodes, interpolated by the periodic cubic spline with the same knots
+// (float64 moments m_j from the cyclic tridiagonal system), integrated exactly:
+// int f dtau = sum_j [h_j (f_j + f_{j+1}) / 2 - h_j^3 (m_j + m_{j+1}) / 24].
+// One warp per filament; smem 5 * nmax doubles; the sum over filaments is
+// added to *acc.
+template <typename T>
+__global__ void k_energy_line(const int64_t* __restrict__ off, const double* __restrict__ shift, int nfil, int nmax,
+                              const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ Mm,
+                              const T* __restrict__ Tper, const double* __restrict__ pls, const T* __restrict__ psr,
+                              double* __restrict__ acc)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double* sh_h = reinterpret_cast<double*>(sm_raw);
+    double* sh_f = sh_h + nmax;   // values f_j
+    double* sh_r = sh_f + nmax;   // right-hand side, then moments
+    double* sh_z = sh_r + nmax;   // Sherman-Morrison vector
+    double* sh_c = sh_z + nmax;   // modified super-diagonal
+    const int f = blockIdx.x;
+    if (f >= nfil) return;
+    const int lane = threadIdx.x;
+    const int64_t o = off[f];
+    const int n = (int)(off[f + 1] - o);
+    const double Tp = (double)Tper[f];
+    const double dr0 = shift[3 * f] / Tp, dr1 = shift[3 * f + 1] / Tp, dr2 = shift[3 * f + 2] / Tp;
+    for (int j = lane; j < n; j += 32) {
+        const int jn = (j + 1 < n) ? j + 1 : 0;
+        const double h = (double)hseg[o + j];
+        sh_h[j] = h;
+        double fj = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double Mj = (double)Mm[3 * (o + j) + c], Mn = (double)Mm[3 * (o + jn) + c];
+            const double drc = c == 0 ? dr0 : (c == 1 ? dr1 : dr2);
+            const double sdot = (double)dp[3 * (o + j) + c] / h - h * (2.0 * Mj + Mn) / 6.0 + drc;
+            const double psi = pls[3 * (o + j) + c] + (double)psr[3 * (o + j) + c];
+            fj += psi * sdot;
+        }
+        sh_f[j] = fj;
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+        const int jm = j == 0 ? n - 1 : j - 1, jn = (j + 1 < n) ? j + 1 : 0;
+        sh_r[j] = 6.0 * ((sh_f[jn] - sh_f[j]) / sh_h[j] - (sh_f[j] - sh_f[jm]) / sh_h[jm]);
+        sh_z[j] = 0.0;
+    }
+    __syncwarp();
+    const double hl = sh_h[n - 1];
+    const double gamma = -2.0 * (hl + sh_h[0]);
+    if (lane == 0) {
+        sh_z[0] = gamma;
+        sh_z[n - 1] = hl;
+    }
+    __syncwarp();
+    if (lane < 2) {  // lane 0: the right-hand side, lane 1: the Sherman-Morrison vector
+        double* r = lane == 0 ? sh_r : sh_z;
+        double cprev = 0, dprev = 0, hm = hl;
+        for (int j = 0; j < n; ++j) {
+            const double hj = sh_h[j];
+            const double a = (j == 0) ? 0.0 : hm;
+            double bb = 2.0 * (hm + hj);
+            if (j == 0) bb -= gamma;
+            if (j == n - 1) bb -= hl * hl / gamma;
+            const double c = (j == n - 1) ? 0.0 : hj;
+            const double im = 1.0 / (bb - a * cprev);
+            cprev = c * im;
+            dprev = (r[j] - a * dprev) * im;
+            if (lane == 0) sh_c[j] = cprev;
+            r[j] = dprev;
+            hm = hj;
+        }
+        __syncwarp(0x3u);
+        double x = r[n - 1];
+        for (int j = n - 2; j >= 0; --j) {
+            x = r[j] - sh_c[j] * x;
+            r[j] = x;
+        }
+    }
+    __syncwarp();
+    const double vfac = hl / gamma;
+    const double fac = (sh_r[0] + vfac * sh_r[n - 1]) / (1.0 + sh_z[0] + vfac * sh_z[n - 1]);
+    double part = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const int jn = (j + 1 < n) ? j + 1 : 0;
+        const double mj = sh_r[j] - fac * sh_z[j], mn = sh_r[jn] - fac * sh_z[jn];
+        const double h = sh_h[j];
+        part += 0.5 * h * (sh_f[j] + sh_f[jn]) - h * h * h * (mj + mn) / 24.0;
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) part += __shfl_xor_sync(0xffffffffu, part, k);
+    if (lane == 0) atomicAdd(acc, part);
+}
+
+template <typename T>
+cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s)
+{
+    (void)nodes;
+    if (nfil <= 0) return cudaSuccess;
+    const size_t sm = 5 * (size_t)nmax * sizeof(double);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_energy_line<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_energy_line<T><<<nfil, 32, sm, s>>>(w.off, w.shift, nfil, nmax, (const T*)w.hseg, (const T*)w.dp,
+                                          (const T*)w.Mm, (const T*)w.Tper, w.pls, (const T*)w.psr,
+                                          w.energy_acc + 1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_energy_line<float>(const double*, const Work&, int, int, cudaStream_t);
+template cudaError_t launch_energy_line<double>(const double*, const Work&, int, int, cudaStream_t);
+
 // Quadrature export for bs_get_quadrature (float64, wrapped positions).
 template <typename T>
 __global__ void k_export_quad(GeomP P, const double* __restrict__ nodes, const int* __restrict__ fil_of,

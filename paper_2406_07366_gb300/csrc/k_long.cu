@@ -155,6 +155,7 @@ __global__ void k_kspace(KspaceP P, typename Cplx<T>::t* __restrict__ spec, type
     using C = typename Cplx<T>::t;
     const long long n1h = (long long)P.ng[1] * P.nh;
     const long long tot = (long long)P.ng[0] * n1h;
+    double esum = 0.0;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
          idx += (long long)gridDim.x * blockDim.x) {
         const int i2 = (int)(idx % P.nh);
@@ -182,6 +183,11 @@ __global__ void k_kspace(KspaceP P, typename Cplx<T>::t* __restrict__ spec, type
         const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
         const T mult = (T)P.scale * tab0[a0] * tab1[a1] * tab2[m2] / ksq;
         const C f0 = spec[idx], f1 = spec[tot + idx], f2 = spec[2 * tot + idx];
+        if (P.energy) {
+            const double a2 = (double)f0.x * f0.x + (double)f0.y * f0.y + (double)f1.x * f1.x +
+                              (double)f1.y * f1.y + (double)f2.x * f2.x + (double)f2.y * f2.y;
+            esum += (m2 > 0 ? 1.0 : 0.5) * P.scale * (double)mult * a2;
+        }
         const T w0r = f0.x * mult, w0i = f0.y * mult;
         const T w1r = f1.x * mult, w1i = f1.y * mult;
         const T w2r = f2.x * mult, w2i = f2.y * mult;
@@ -198,6 +204,11 @@ __global__ void k_kspace(KspaceP P, typename Cplx<T>::t* __restrict__ spec, type
             o.x = w1r; o.y = w1i; spsi[tot + idx] = o;
             o.x = w2r; o.y = w2i; spsi[2 * tot + idx] = o;
         }
+    }
+    if (P.energy) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        if ((threadIdx.x & 31) == 0 && esum != 0.0) atomicAdd(P.energy, esum);
     }
 }
 

@@ -449,6 +449,59 @@ def test_stage_times_are_recorded():
     assert set(t) == set(B.STAGES) and all(x >= 0 for x in t.values())
 
 
+@pytest.mark.parametrize("path", ["pruned", "cufft"])
+def test_energy_matches_oracle(path):
+    """Energy (Eq. kinetic_energy_streamfunction, float64 Fourier reduction +
+    spline line integral): at w = 16, sigma = 2 the GPU equals the oracle's
+    energy at the same split to 1e-10; at beta = 3.5, w = 8 it is within 1e-6
+    of the oracle's energy at that split, the mixed form within 1e-5.  (The
+    split energy itself moves by a few 1e-6 with alpha on this coarse curve:
+    the line integral of the interpolated psi and the quadrature sum behind
+    the Fourier part discretise the curve differently.)"""
+    B = _B()
+    f = W.ellipses(nfil=6, N_l=24, seed=9)
+    g = geom(f, 4, 2)
+    extra = B.BS_FFT_CUFFT if path == "cufft" else 0
+    p = params(f, M=32, Q=2, w=16, sigma=2.0, precision=B.BS_FP64, flags=B.BS_WANT_PSI | extra)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    E = bs.energy(torch.from_numpy(f.nodes).cuda())
+    bs.close()
+    Em = oracle.energy(g, f.L, KAPPA, A_CORE, DELTA, p.alpha, p.rc, (p.M[0] - 1) // 2)
+    assert abs(E - Em) < 1e-10 * abs(Em), (E, Em)
+    for prec, w, tol in ((B.BS_FP64, 8, 1e-6), (B.BS_MIXED, 8, 1e-5)):
+        p = params(f, M=32, Q=2, w=w, precision=prec, flags=B.BS_WANT_PSI | extra)
+        bs = B.BiotSavart(p, f.offsets, f.closing)
+        E = bs.energy(torch.from_numpy(f.nodes).cuda())
+        bs.close()
+        Em = oracle.energy(g, f.L, KAPPA, A_CORE, DELTA, p.alpha, p.rc, (p.M[0] - 1) // 2)
+        assert abs(E - Em) < tol * abs(Em), (prec, E, Em)
+
+
+def test_graph_replay_equals_direct_call():
+    """The CUDA-graph replay of one evaluation gives the direct call's result,
+    and follows new node positions written into the bound buffer."""
+    B = _B()
+    f = W.ellipses(nfil=8, N_l=32, seed=12)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = params(f, M=32, Q=2, precision=B.BS_FP64)
+        bs = B.BiotSavart(p, f.offsets, f.closing, stream=s)
+        nodes = torch.from_numpy(f.nodes).cuda()
+        ref = bs.velocity(nodes).clone()
+        vg = torch.empty_like(ref)
+        bs.capture(nodes, vg)
+        bs.launch()
+        s.synchronize()
+        assert (vg - ref).abs().max().item() < 1e-13 * ref.abs().max().item()
+        nodes.add_(0.01)
+        ref2 = bs.velocity(nodes).clone()
+        bs.launch()
+        s.synchronize()
+        assert (vg - ref2).abs().max().item() < 1e-13 * ref2.abs().max().item()
+        bs.status()
+        bs.close()
+
+
 def test_repeated_calls_agree():
     B = _B()
     f = W.ellipses(nfil=8, N_l=32, seed=8)

@@ -269,3 +269,31 @@ def test_truncation_error_within_paper_estimate():
     eps_v = KAPPA * (Lt / (np.sqrt(np.pi) * alpha * V) + (1 / beta) * np.sqrt(Lt / (8 * np.pi * V))) * np.exp(-beta ** 2)
     assert err < eps_v, (err, eps_v)
     assert err > eps_v / 100  # the estimate is not wildly loose either
+
+
+def test_ring_energy_converges_to_closed_form():
+    """Eq. vortex_ring_energy: E V = kappa^2 R/2 [ln(8R/a) - (Delta + 1)] for an
+    isolated ring; the periodic, discretised energy approaches it as N and L
+    grow (the paper prints no tolerance: convergence only)."""
+    k = GOLD["kelvin_ring"]
+    errs = []
+    for N, L in ((32, 2 * np.pi), (64, 4 * np.pi), (128, 8 * np.pi)):
+        f = W.ring(R=k["R"], N=N, L=L)
+        g = _geom(f, 4, 3)
+        E = oracle.energy_converged(g, f.L, k["kappa"], k["a"], k["delta"])
+        errs.append(abs(E * L ** 3 - k["E_times_V"]) / k["E_times_V"])
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 2e-5, errs
+
+
+def test_energy_depends_on_alpha_only_through_interpolation():
+    """The long-range energy is the exact Fourier reduction while the other
+    parts are interpolated from the nodes, so the total moves with alpha only
+    by the interpolation error, which vanishes as the nodes get denser."""
+    d = []
+    for N in (24, 48, 96):
+        f = W.ring(R=1.0, N=N)
+        g = _geom(f, 4, 2)
+        e1 = oracle.energy_converged(g, f.L, KAPPA, A_CORE, DELTA)
+        e2 = oracle.energy_converged(g, f.L, KAPPA, A_CORE, DELTA, alpha_scale=1.5)
+        d.append(abs(e1 - e2) / abs(e1))
+    assert d[0] > d[1] > d[2] and d[2] < 1e-8, d
