@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16, help="oracle targets timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-batched-form", action="store_true")
     return ap.parse_args()
 
 
@@ -118,6 +119,40 @@ def make_params(B, spec, f, precision, flags=0):
     w = spec["w"] if precision == B.BS_MIXED else max(spec["w"], 8)
     return B.make_params(f.L, kappa=spec["kappa"], a=spec["a"], delta=spec["delta"], beta=spec["beta"],
                          M=spec["M"], Q=spec["Q"], w=w, sigma=spec["sigma"], precision=precision, flags=flags)
+
+
+def run_batched_form(B, dev, stream, flush, steps):
+    """The batched form: 64 independent Fourier tangles with node counts
+    log-uniform in [10^3, 10^5] (100 nodes per filament), grids matched to
+    k_max (alpha = C_beta N^(1/3)/L, M in [32, 128]), mixed precision, the
+    whole batch replayed from one CUDA graph per evaluation."""
+    import torch
+    from paper_2406_07366_gb300 import workloads as W
+    fs = W.tangle_batch(nconf=64, seed=5)
+    params = [B.tangle_params(f.N, f.L, beta=3.5, M_min=32, M_max=128, Q=2, w=6, sigma=1.5,
+                              precision=B.BS_MIXED) for f in fs]
+    bt = B.BiotSavartBatch(params, fs, stream=stream)
+    nodes = torch.from_numpy(np.concatenate([f.nodes for f in fs])).to(dev)
+    vel = torch.empty_like(nodes)
+    for _ in range(3):
+        bt.velocity(nodes, vel)
+    bt.status()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        bt.velocity(nodes, vel)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    bt.status()
+    bt.close()
+    t = statistics.mean(ms)
+    Ms = sorted(p.M[0] for p in params)
+    return {"value": bt.N / (t * 1e-3), "ms_per_step": t, "steps": steps, "nconf": len(fs), "N_total": bt.N,
+            "N_range": [min(f.N for f in fs), max(f.N for f in fs)], "M_range": [Ms[0], Ms[-1]],
+            "issue": "one CUDA graph per evaluation, members on 8 concurrent streams"}
 
 
 def spread_zfft_bytes(p, ng, K, NQ, real_bytes):
@@ -284,6 +319,10 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    batched = None
+    if not args.no_batched_form and world == 1:
+        batched = run_batched_form(B, dev, stream, flush, min(args.steps, 20))
+
     # the float64 form on the same workload, for the FP32-vs-FP64 comparison
     fp64 = None
     if not args.no_fp64_form and prec == B.BS_MIXED:
@@ -358,6 +397,7 @@ def run_ours(args, rank, world, dist):
             "clocks": clk,
             "stages_ms": stage_mean,
             "fp64_form": fp64,
+            "batched_form": batched,
             "accuracy": accuracy,
         }
     bs.close()

@@ -217,6 +217,39 @@ int bs_get_quadrature(bs_ctx* ctx, const double* nodes, double* qX, double* qq);
 int bs_graph_capture(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
 int bs_graph_launch(bs_ctx* ctx);
 
+/*
+ * Batches of independent configurations (the paper evaluates one
+ * configuration at a time; a batch evaluates many of the Sec. 5 problems,
+ * each with its own parameters and grid, in one call).
+ *
+ * bs_batch_create: nconf members, params[i] for member i (host array,
+ * copied; BS_TIMING is ignored).  stream: cudaStream_t the batch runs on;
+ * with a non-default stream bs_batch_compute captures the whole batch into
+ * one CUDA graph on its first call (again whenever the node or velocity
+ * pointer changes, or after bs_batch_set) and replays it, members running
+ * concurrently on an internal pool of up to 8 streams; with the legacy
+ * default stream (NULL) the members are issued directly.
+ * bs_batch_set: filaments of member i, as bs_set_filaments.
+ * bs_batch_node_offsets: offsets[0..nconf] (host) of each member's nodes in
+ * the concatenated node array.
+ * bs_batch_compute: nodes (device, N_total x 3 float64, members back to
+ * back in index order) -> vel (device, same layout).  Asynchronous.
+ * bs_batch_status: synchronise and return the first member status that is
+ * not BS_OK (clears all).  bs_batch_member: the member's context, owned by
+ * the batch (for bs_compute_parts, bs_compute_energy ...; do not destroy it,
+ * and do not change its stream).
+ * Errors: BS_ERR_ARG, BS_ERR_STATE (a member without filaments), the codes
+ * of bs_create / bs_set_filaments, BS_ERR_CUDA.
+ */
+typedef struct bs_batch bs_batch;
+int bs_batch_create(bs_batch** out, int nconf, const bs_params* params, void* stream);
+int bs_batch_set(bs_batch* b, int i, int nfil, const int64_t* offsets, const int32_t* closing);
+int bs_batch_node_offsets(bs_batch* b, int64_t* offsets);
+int bs_batch_compute(bs_batch* b, const double* nodes, double* vel);
+int bs_batch_status(bs_batch* b);
+int bs_batch_member(bs_batch* b, int i, bs_ctx** member);
+void bs_batch_destroy(bs_batch* b);
+
 /* Synchronise the stream and return the device status word as a status
  * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY); clears it. */
 int bs_status(bs_ctx* ctx);

@@ -33,7 +33,9 @@ STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", 
 EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_create", "bs_set_stream",
            "bs_set_filaments", "bs_compute", "bs_compute_host", "bs_compute_parts", "bs_get_quadrature",
            "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error",
-           "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy"]
+           "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
+           "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
+           "bs_batch_member", "bs_batch_destroy"]
 
 
 class bs_params(ctypes.Structure):
@@ -82,6 +84,13 @@ def _load():
         "bs_graph_capture": ([vp, vp, vp, vp], ctypes.c_int),
         "bs_compute_energy": ([vp, vp, vp, vp, P(ctypes.c_double)], ctypes.c_int),
         "bs_graph_launch": ([vp], ctypes.c_int),
+        "bs_batch_create": ([P(vp), ctypes.c_int, P(bs_params), vp], ctypes.c_int),
+        "bs_batch_set": ([vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32)], ctypes.c_int),
+        "bs_batch_node_offsets": ([vp, P(ctypes.c_int64)], ctypes.c_int),
+        "bs_batch_compute": ([vp, vp, vp], ctypes.c_int),
+        "bs_batch_status": ([vp], ctypes.c_int),
+        "bs_batch_member": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
+        "bs_batch_destroy": ([vp], None),
         "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
@@ -205,6 +214,45 @@ def bs_status(ctx):
     return _check(lib().bs_status(ctx))
 
 
+def bs_batch_create(params, stream=None):
+    arr = (bs_params * len(params))(*params)
+    b = ctypes.c_void_p()
+    _check(lib().bs_batch_create(ctypes.byref(b), len(params), arr, stream))
+    return b
+
+
+def bs_batch_set(b, i, offsets, closing=None):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nfil = off.size - 1
+    cl = None if closing is None else np.ascontiguousarray(closing, dtype=np.int32).reshape(nfil, 3)
+    _check(lib().bs_batch_set(b, i, nfil, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+
+def bs_batch_node_offsets(b, nconf):
+    off = np.zeros(nconf + 1, dtype=np.int64)
+    _check(lib().bs_batch_node_offsets(b, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return off
+
+
+def bs_batch_compute(b, nodes, vel):
+    _check(lib().bs_batch_compute(b, _ptr(nodes), _ptr(vel)))
+
+
+def bs_batch_status(b):
+    return _check(lib().bs_batch_status(b))
+
+
+def bs_batch_member(b, i):
+    c = ctypes.c_void_p()
+    _check(lib().bs_batch_member(b, i, ctypes.byref(c)))
+    return c
+
+
+def bs_batch_destroy(b):
+    lib().bs_batch_destroy(b)
+
+
 def bs_stage_times(ctx):
     ms = (ctypes.c_float * 16)()
     n = ctypes.c_int()
@@ -250,6 +298,56 @@ def make_params(L, kappa=1.0, a=1e-6, delta=0.25, beta=3.5, M=32, Q=2, order=4, 
     elif rc is not None:
         p.rc = rc
     return p
+
+
+def tangle_params(N, L, beta=3.5, M_min=32, M_max=128, **kw) -> bs_params:
+    """Parameters of one member of a batch of tangles: alpha = C_beta N^(1/3) / L
+    (Eq. alpha_optimal_performance, Table tab:performance), M the smallest odd
+    count with k_max >= 2 beta alpha, clamped to [M_min, M_max], then alpha
+    re-derived from k_max (so the accuracy coefficient stays beta)."""
+    M = bs_params_from_beta(beta, L, M=0, N=int(N)).M[0]
+    M = int(min(max(M, M_min), M_max))
+    return make_params(L, beta=beta, M=M, **kw)
+
+
+class BiotSavartBatch:
+    """Independent configurations evaluated together (one CUDA graph per call
+    pattern); node and velocity tensors hold the members back to back."""
+
+    def __init__(self, params, filaments, stream=None):
+        import torch
+        self.torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.params = list(params)
+        self.b = bs_batch_create(self.params, ctypes.c_void_p(stream.cuda_stream))
+        for i, f in enumerate(filaments):
+            bs_batch_set(self.b, i, f.offsets, f.closing)
+        self.offsets = bs_batch_node_offsets(self.b, len(self.params))
+        self.N = int(self.offsets[-1])
+
+    def velocity(self, nodes, vel=None):
+        vel = self.torch.empty((self.N, 3), dtype=self.torch.float64, device="cuda") if vel is None else vel
+        bs_batch_compute(self.b, nodes, vel)
+        return vel
+
+    def member(self, i):
+        return bs_batch_member(self.b, i)
+
+    def status(self):
+        return bs_batch_status(self.b)
+
+    def close(self):
+        if self.b:
+            bs_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BiotSavart:

@@ -128,6 +128,19 @@ FftPlan make_plan(int n)
     return pl;
 }
 
+// Position of frequency index k (0 <= k < n) after the forward (decimation
+// in frequency) transform of plan pl: the mixed-radix digits of k, least
+// significant first in the order of the passes, weighted by the pass strides.
+int rev_pos_host(int k, const FftPlan& pl)
+{
+    int p = 0;
+    for (int s = 0; s < pl.nr; ++s) {
+        p += (k % pl.r[s]) * pl.st[s];
+        k /= pl.r[s];
+    }
+    return p;
+}
+
 // Normalised backwards Kaiser-Bessel kernel psi(z) = sinh(zeta s)/(s sinh zeta).
 double kb_host(double z, double zeta)
 {
@@ -363,6 +376,12 @@ int alloc_grids(bs_ctx* c)
             }
         TRY(dalloc(c, c->alloc_g, &c->w.tw, sizeof(T) * tw.size()));
         CUDA_TRY(cudaMemcpy(c->w.tw, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice));
+        std::vector<int> rev(ntw);
+        o = 0;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int k = 0; k < d.ng[ax]; ++k) rev[o++] = rev_pos_host(k, d.plan[ax]);
+        TRY(dalloc(c, c->alloc_g, (void**)&c->w.rev, sizeof(int) * rev.size()));
+        CUDA_TRY(cudaMemcpy(c->w.rev, rev.data(), sizeof(int) * rev.size(), cudaMemcpyHostToDevice));
     }
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cnt, sizeof(int) * (size_t)(d.ncells + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cur, sizeof(int) * (size_t)(d.ncells + 1)));
@@ -600,6 +619,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         while (SZ.ls < SZ.cls) SZ.ls += 32;  // the real region also holds the complex lines
         SZ.zeta = d.zeta;
         SZ.plan2 = d.plan[2];
+        SZ.rev = w.rev + d.ng[0] + d.ng[1];
         SZ.d_nbx = make_fastdiv((unsigned)d.nbx);
         SZ.d_n2 = make_fastdiv((unsigned)d.ng[2]);
         SZ.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
@@ -616,6 +636,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         YP.lmc = d.lmcy;
         YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
         YP.plan1 = d.plan[1];
+            YP.rev = w.rev + d.ng[0];
         YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
         YP.d_lines = make_fastdiv(1u << d.lmcy);
         CE(launch_fft_y<T>(YP, w, w.f2, -1, s));
@@ -630,6 +651,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         XP.ls = line_stride(d.ng[0], 3 << d.lmcx, 128 / (2 * (int)sizeof(T)));
         XP.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
         XP.plan0 = d.plan[0];
+        XP.rev = w.rev;
         XP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcx) - 1) >> d.lmcx));
         XP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
         XP.d_lines = make_fastdiv(3u << d.lmcx);
@@ -646,6 +668,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         ZP.yc = d.yc;
         ZP.cls = line_stride(d.ng[2], d.yc / 2, 128 / (2 * (int)sizeof(T)));
         ZP.plan2 = d.plan[2];
+            ZP.rev = w.rev + d.ng[0] + d.ng[1];
         ZP.d_nch = make_fastdiv((unsigned)(d.ng[1] / d.yc));
         ZP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
         ZP.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
@@ -686,6 +709,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             YP.lmc = d.lmcy;
             YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
             YP.plan1 = d.plan[1];
+            YP.rev = w.rev + d.ng[0];
             YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
             YP.d_lines = make_fastdiv(1u << d.lmcy);
             CE(launch_fft_y<T>(YP, w, w.f2psi, +1, s));
@@ -697,6 +721,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             ZP.yc = d.yc;
             ZP.cls = line_stride(d.ng[2], d.yc / 2, 128 / (2 * (int)sizeof(T)));
             ZP.plan2 = d.plan[2];
+            ZP.rev = w.rev + d.ng[0] + d.ng[1];
             ZP.d_nch = make_fastdiv((unsigned)(d.ng[1] / d.yc));
             ZP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
             ZP.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
@@ -1088,6 +1113,192 @@ void bs_destroy(bs_ctx* c)
         if (c->ev_t[i]) cudaEventDestroy(c->ev_t[i]);
     if (c->side) cudaStreamDestroy(c->side);
     delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent configurations.  Member i is a full context with
+// its own grid sizes; the members' evaluations are issued on a pool of
+// streams (largest members first, round-robin) and captured together into
+// one CUDA graph, so small members run concurrently and the whole batch
+// costs one graph launch.
+// ---------------------------------------------------------------------------
+struct bs_batch {
+    int nconf = 0;
+    std::vector<bs_ctx*> ctx;
+    std::vector<int64_t> node_off;  // nconf + 1, member i owns nodes [node_off[i], node_off[i+1])
+    std::vector<int> order;         // issue order, largest member first
+    cudaStream_t stream = nullptr;  // caller's stream
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> ev_done;
+    cudaEvent_t ev_start = nullptr;
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double* g_nodes = nullptr;
+    double* g_vel = nullptr;
+};
+
+namespace {
+
+void batch_drop_graph(bs_batch* b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->g_nodes = nullptr;
+    b->g_vel = nullptr;
+}
+
+// Issue every member's evaluation on the pool, joined back to b->stream.
+int batch_issue(bs_batch* b, const double* nodes, double* vel)
+{
+    CUDA_TRY(cudaEventRecord(b->ev_start, b->stream));
+    for (cudaStream_t s : b->pool) CUDA_TRY(cudaStreamWaitEvent(s, b->ev_start, 0));
+    for (int i : b->order) {
+        bs_ctx* c = b->ctx[i];
+        if (c->N == 0) continue;
+        const size_t o = 3 * (size_t)b->node_off[i];
+        const int rc = c->p.precision == BS_FP64 ? run<double>(c, nodes + o, vel + o, nullptr, nullptr, nullptr)
+                                                 : run<float>(c, nodes + o, vel + o, nullptr, nullptr, nullptr);
+        if (rc != BS_OK) return rc;
+    }
+    for (size_t k = 0; k < b->pool.size(); ++k) {
+        CUDA_TRY(cudaEventRecord(b->ev_done[k], b->pool[k]));
+        CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_done[k], 0));
+    }
+    return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bs_batch_destroy(bs_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    for (cudaStream_t s : b->pool) cudaStreamSynchronize(s);
+    batch_drop_graph(b);
+    for (bs_ctx* c : b->ctx) bs_destroy(c);
+    for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
+    delete b;
+}
+
+int bs_batch_create(bs_batch** out, int nconf, const bs_params* params, void* stream)
+{
+    if (!out || !params || nconf <= 0) return fail(BS_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    bs_batch* b = new bs_batch();
+    b->nconf = nconf;
+    b->stream = (cudaStream_t)stream;
+    b->node_off.assign(nconf + 1, 0);
+    cudaError_t e = cudaGetDevice(&b->device);
+    const int ns = std::min(nconf, 8);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->pool.push_back(s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->ev_done.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        const int rc = fail(BS_ERR_CUDA, "CUDA set-up failed: %s", cudaGetErrorString(e));
+        bs_batch_destroy(b);
+        return rc;
+    }
+    for (int i = 0; i < nconf; ++i) {
+        bs_params p = params[i];
+        p.flags &= ~BS_TIMING;  // stage events cannot be read back from a graph
+        bs_ctx* c = nullptr;
+        const int rc = bs_create(&c, &p, nullptr);
+        if (rc != BS_OK) {
+            std::string msg = g_err;
+            bs_batch_destroy(b);
+            fail(rc, "batch member %d: %s", i, msg.c_str());
+            return rc;
+        }
+        b->ctx.push_back(c);
+    }
+    *out = b;
+    return BS_OK;
+}
+
+int bs_batch_set(bs_batch* b, int i, int nfil, const int64_t* offsets, const int32_t* closing)
+{
+    if (!b || i < 0 || i >= b->nconf) return fail(BS_ERR_ARG, "bad batch or member index");
+    batch_drop_graph(b);
+    const int rc = bs_set_filaments(b->ctx[i], nfil, offsets, closing);
+    if (rc != BS_OK) return rc;
+    for (int k = 0; k < b->nconf; ++k) b->node_off[k + 1] = b->node_off[k] + b->ctx[k]->N;
+    b->order.resize(b->nconf);
+    for (int k = 0; k < b->nconf; ++k) b->order[k] = k;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [b](int x, int y) { return b->ctx[x]->N > b->ctx[y]->N; });
+    for (size_t r = 0; r < b->order.size(); ++r) b->ctx[b->order[r]]->stream = b->pool[r % b->pool.size()];
+    return BS_OK;
+}
+
+int bs_batch_node_offsets(bs_batch* b, int64_t* offsets)
+{
+    if (!b || !offsets) return fail(BS_ERR_ARG, "null argument");
+    for (int k = 0; k <= b->nconf; ++k) offsets[k] = b->node_off[k];
+    return BS_OK;
+}
+
+int bs_batch_compute(bs_batch* b, const double* nodes, double* vel)
+{
+    if (!b) return fail(BS_ERR_ARG, "null batch");
+    for (int i = 0; i < b->nconf; ++i)
+        if (!b->ctx[i]->have_fil) return fail(BS_ERR_STATE, "batch member %d has no filaments", i);
+    if (b->node_off[b->nconf] == 0) return BS_OK;
+    if (!nodes || !vel) return fail(BS_ERR_ARG, "null nodes or vel");
+    CUDA_TRY(cudaSetDevice(b->device));
+    if (!b->stream) return batch_issue(b, nodes, vel);  // the legacy stream cannot be captured
+    if (!b->gexec || b->g_nodes != nodes || b->g_vel != vel) {
+        batch_drop_graph(b);
+        CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = batch_issue(b, nodes, vel);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (rc != BS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        b->graph = g;
+        CUDA_TRY(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+        b->g_nodes = nodes;
+        b->g_vel = vel;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+    return BS_OK;
+}
+
+int bs_batch_status(bs_batch* b)
+{
+    if (!b) return fail(BS_ERR_ARG, "null batch");
+    CUDA_TRY(cudaSetDevice(b->device));
+    if (b->stream) CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int first = BS_OK;
+    for (int i = 0; i < b->nconf; ++i) {
+        const int rc = bs_status(b->ctx[i]);
+        if (rc != BS_OK && first == BS_OK) first = rc;
+    }
+    return first;
+}
+
+int bs_batch_member(bs_batch* b, int i, bs_ctx** member)
+{
+    if (!b || !member || i < 0 || i >= b->nconf) return fail(BS_ERR_ARG, "bad batch or member index");
+    *member = b->ctx[i];
+    return BS_OK;
 }
 
 }  // extern "C"

@@ -168,6 +168,7 @@ struct SpZP {
     int cls;            // complex line stride of the z FFT buffers
     double zeta;
     FftPlan plan2;
+    const int* rev;  // position of frequency k after the forward transform, k < n
     FastDiv d_nbx, d_n2, d_nk, d_txy, d_ty, d_ncl;
 };
 
@@ -177,6 +178,7 @@ struct FftYP {
     int lmc;            // log2 of the chunk of z-modes per CTA
     int ls;             // line stride in shared memory
     FftPlan plan1;
+    const int* rev;
     FastDiv d_nch, d_lines;
 };
 
@@ -188,6 +190,7 @@ struct FftXP {
     double kk[3];
     double scale;
     FftPlan plan0;
+    const int* rev;
     FastDiv d_nch, d_n0, d_lines, d_lines_psi;
     double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
 };
@@ -198,6 +201,7 @@ struct FftZP {
     int yc;
     int cls;            // complex line stride in shared memory
     FftPlan plan2;
+    const int* rev;  // position of frequency k after the forward transform, k < n
     FastDiv d_nch, d_n0, d_nk, d_n2, d_ncl;
 };
 
@@ -252,6 +256,7 @@ struct Work {
     void* spec = nullptr;     // 3 x ng0 ng1 nh complex
     void* spec_psi = nullptr; // 3 x ... (psi)
     void* ktab = nullptr;     // per-axis k-space tables
+    int* rev = nullptr;       // per-axis positions of frequency k after the forward transform (n0 + n1 + n2)
     void* fft_work = nullptr;
     // pruned-FFT pipeline
     void* tw = nullptr;       // twiddles e^{-2 pi i j / n_d}, n0 + n1 + n2 complex

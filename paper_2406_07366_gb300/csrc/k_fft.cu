@@ -175,19 +175,6 @@ __device__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& d
     for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false>(buf, nlines, dl, ls, pl, s, tw, +1);
 }
 
-// Position of frequency index k (0 <= k < n) after a forward transform.
-__device__ __forceinline__ int rev_pos(int k, const FftPlan& pl)
-{
-    int p = 0;
-    for (int s = 0; s < pl.nr; ++s) {
-        const int R = pl.r[s];
-        const int q = (R == 3) ? k / 3 : (k >> (R == 8 ? 3 : (R == 4 ? 2 : 1)));
-        p += (k - q * R) * pl.st[s];
-        k = q;
-    }
-    return p;
-}
-
 template <typename T>
 __device__ __forceinline__ T kb_val(T z, T zeta, T inorm)
 {
@@ -344,8 +331,8 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
     for (int i = tid; i < nreal * nk; i += blockDim.x) {
         const int rl = fdiv(i, P.d_nk), mz = i - rl * nk;
         const int l = rl >> 1;
-        const C zk = cb[l * CS + rev_pos(mz, P.plan2)];
-        const C zn = cb[l * CS + rev_pos(mz == 0 ? 0 : n2 - mz, P.plan2)];
+        const C zk = cb[l * CS + P.rev[mz]];
+        const C zn = cb[l * CS + P.rev[mz == 0 ? 0 : n2 - mz]];
         C o;
         if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
             o.x = (T)0.5 * (zk.x + zn.x);
@@ -397,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* 
             const int myp = i >> lmc, l = i & (MC - 1);
             if (l >= mcount) continue;
             const int my = myp - K1;
-            F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] = a[l * LS + rev_pos(my < 0 ? my + n1 : my, P.plan1)];
+            F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] = a[l * LS + P.rev[my < 0 ? my + n1 : my]];
         }
     } else {
         for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
@@ -405,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* 
             const int my = y <= n1 / 2 ? y : y - n1;
             C v = zero;
             if (l < mcount && my >= -K1 && my <= K1) v = F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l];
-            a[l * LS + rev_pos(y, P.plan1)] = v;
+            a[l * LS + P.rev[y]] = v;
         }
         __syncthreads();
         fft_inv_dit<T>(a, MC, P.d_lines, LS, P.plan1, tw1);
@@ -462,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
         const int mx = xi <= n0 / 2 ? xi : xi - n0;
         const int amx = mx < 0 ? -mx : mx;
         const int mz = mz0 + l;
-        const int pos = rev_pos(xi, P.plan0);
+        const int pos = P.rev[xi];
         C* r0 = a + ((0 * MC + l) * LS + pos);
         C* r1 = a + ((1 * MC + l) * LS + pos);
         C* r2 = a + ((2 * MC + l) * LS + pos);
@@ -560,10 +547,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_z_c2r(FftZP P, const typename 
         } else {
             z.x = A.x - Bv.y;
             z.y = A.y + Bv.x;
-            a[l * CS + rev_pos(k, P.plan2)] = z;
+            a[l * CS + P.rev[k]] = z;
             z.x = A.x + Bv.y;
             z.y = -A.y + Bv.x;
-            a[l * CS + rev_pos(n2 - k, P.plan2)] = z;
+            a[l * CS + P.rev[n2 - k]] = z;
         }
     }
     __syncthreads();

@@ -156,3 +156,19 @@ def test_create_fails_cleanly_without_a_device(B):
     with pytest.raises(B.BSError) as e:
         B.bs_create(p)
     assert e.value.code == B.BS_ERR_CUDA
+
+
+def test_tangle_params_clamp_modes(B):
+    """Batch members: alpha from C_beta N^(1/3) (Eq. alpha_optimal_performance),
+    M clamped to [32, 128], alpha re-derived so that r_c alpha = beta."""
+    L = [2 * math.pi] * 3
+    small = B.tangle_params(200, L)
+    big = B.tangle_params(100000, L)
+    assert small.M[0] == 32 and big.M[0] == 128
+    assert B.bs_params_from_beta(3.5, L, M=0, N=200).M[0] < 32
+    mid = B.tangle_params(10000, L)
+    free = B.bs_params_from_beta(3.5, L, M=0, N=10000)
+    assert 32 <= mid.M[0] <= 128 and mid.M[0] == free.M[0]
+    for p in (small, mid, big):
+        assert p.alpha * p.rc == pytest.approx(3.5, rel=1e-14)
+        assert p.alpha == pytest.approx(((p.M[0] - 1) // 2) / (2 * 3.5), rel=1e-14)

@@ -1,0 +1,126 @@
+"""Batches of independent configurations (``-m gpu``).
+
+Each member of a batch is evaluated by the same pipeline as a single
+context; the batch only changes how the members are issued (one CUDA graph,
+members on concurrent streams).  So every member must reproduce the result
+of its own single context, and, through that, the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_07366_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KAPPA, A_CORE, DELTA = 1.0, 1e-6, 0.25
+
+
+def _B():
+    import paper_2406_07366_gb300 as B
+    return B
+
+
+def _members(seed=31):
+    """Five members of different sizes, shapes and grids."""
+    fs = [W.fourier_tangle(nfil=n, N_l=N_l, seed=seed + k, amp=2 * math.pi / 48)
+          for k, (n, N_l) in enumerate([(30, 40), (6, 24), (80, 32), (12, 64)])]
+    fs.append(W.ellipses(nfil=9, N_l=32, seed=seed + 7))
+    return fs
+
+
+def _run_batch(B, params, fs, stream):
+    with torch.cuda.stream(stream):
+        bt = B.BiotSavartBatch(params, fs, stream=stream)
+        nodes = torch.from_numpy(np.concatenate([f.nodes for f in fs])).cuda()
+        vel = bt.velocity(nodes)
+        bt.status()
+    return bt, nodes, vel
+
+
+def _single(B, p, f):
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    v = bs.velocity(torch.from_numpy(f.nodes).cuda()).clone()
+    bs.status()
+    bs.close()
+    return v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_members_equal_single_contexts(prec):
+    B = _B()
+    fs = _members()
+    P = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
+    params = [B.tangle_params(f.N, f.L, M_min=24, M_max=48, Q=2, w=8 if prec == "fp64" else 6, precision=P)
+              for f in fs]
+    assert len({p.M[0] for p in params}) > 1  # the members have different grids
+    s = torch.cuda.Stream()
+    bt, nodes, vel = _run_batch(B, params, fs, s)
+    off = bt.offsets
+    assert list(np.diff(off)) == [f.N for f in fs]
+    tol = 1e-12 if prec == "fp64" else 1e-6  # float atomics reorder the mixed sums
+    for i, (p, f) in enumerate(zip(params, fs)):
+        ref = _single(B, p, f)
+        got = vel[off[i]:off[i + 1]]
+        err = (got - ref).abs().max().item() / ref.abs().max().item()
+        assert err < tol, (i, err)
+    bt.close()
+
+
+def test_batch_replay_follows_new_positions_and_matches_oracle():
+    """The captured batch reads the node buffer at replay time; after
+    deforming the curves in place, each member matches the oracle's
+    converged velocity at the method's beta = 3.5 accuracy."""
+    B = _B()
+    fs = _members(seed=41)[:3]
+    params = [B.tangle_params(f.N, f.L, M_min=32, M_max=48, Q=2, w=8, precision=B.BS_FP64) for f in fs]
+    s = torch.cuda.Stream()
+    bt, nodes, vel = _run_batch(B, params, fs, s)
+    moved = [f.nodes + 0.02 * np.sin(3.0 * f.nodes[:, [1, 2, 0]]) for f in fs]
+    with torch.cuda.stream(s):
+        nodes.copy_(torch.from_numpy(np.concatenate(moved)))
+        bt.velocity(nodes, vel)
+        bt.status()
+    off = bt.offsets
+    for i, f in enumerate(fs):
+        g = oracle.geometry(moved[i], f.offsets, f.closing, f.L, 4, 2)
+        vo, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
+        d = vel[off[i]:off[i + 1]].cpu().numpy() - vo
+        rms = math.sqrt(np.mean(np.sum(d ** 2, 1)) / np.mean(np.sum(vo ** 2, 1)))
+        assert rms < 1e-5, (i, rms)
+    bt.close()
+
+
+def test_batch_on_legacy_stream_issues_directly():
+    """With the legacy default stream there is no graph; the result is the same."""
+    B = _B()
+    fs = _members(seed=51)[:2]
+    params = [B.tangle_params(f.N, f.L, M_min=24, M_max=32, Q=2, w=8, precision=B.BS_FP64) for f in fs]
+    bt = B.BiotSavartBatch(params, fs, stream=torch.cuda.default_stream())
+    nodes = torch.from_numpy(np.concatenate([f.nodes for f in fs])).cuda()
+    vel = bt.velocity(nodes)
+    bt.status()
+    off = bt.offsets
+    for i, (p, f) in enumerate(zip(params, fs)):
+        ref = _single(B, p, f)
+        assert (vel[off[i]:off[i + 1]] - ref).abs().max().item() < 1e-12 * ref.abs().max().item()
+    bt.close()
+
+
+def test_batch_member_without_filaments_is_an_error():
+    B = _B()
+    f = W.ellipses(nfil=3, N_l=16, seed=3)
+    p = B.make_params(f.L, M=24, Q=2, precision=B.BS_FP64)
+    b = B.bs_batch_create([p, p], torch.cuda.current_stream().cuda_stream)
+    try:
+        B.bs_batch_set(b, 0, f.offsets, f.closing)
+        nodes = torch.from_numpy(f.nodes).cuda()
+        vel = torch.empty_like(nodes)
+        with pytest.raises(B.BSError) as e:
+            B.bs_batch_compute(b, nodes, vel)
+        assert e.value.code == B.BS_ERR_STATE
+    finally:
+        B.bs_batch_destroy(b)
