@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-batched-form", action="store_true")
+    ap.add_argument("--no-large-form", action="store_true")
+    ap.add_argument("--rk4-steps", type=int, default=100, help="RK4 steps of the large tangle")
     return ap.parse_args()
 
 
@@ -153,6 +155,70 @@ def run_batched_form(B, dev, stream, flush, steps):
     return {"value": bt.N / (t * 1e-3), "ms_per_step": t, "steps": steps, "nconf": len(fs), "N_total": bt.N,
             "N_range": [min(f.N for f in fs), max(f.N for f in fs)], "M_range": [Ms[0], Ms[-1]],
             "issue": "one CUDA graph per evaluation, members on 8 concurrent streams"}
+
+
+def polygon_impulse(nodes, offsets, kappa=1.0):
+    """(kappa/2) sum over the closed polygons of s_j x s_{j+1} (host diagnostic)."""
+    x = nodes.reshape(-1, 3)
+    nxt = np.arange(x.shape[0]) + 1
+    nxt[offsets[1:] - 1] = offsets[:-1]
+    return 0.5 * kappa * np.cross(x, x[nxt]).sum(axis=0)
+
+
+def run_large_form(B, dev, stream, flush, steps, rk_steps):
+    """Large tangle: 20000 filaments x 200 nodes (4e6 nodes), M = 512, mixed
+    precision; one evaluation replayed from its CUDA graph, then rk_steps RK4
+    steps (Sec. 5.2, dt = Kelvin-wave period at the smallest node spacing)
+    replayed from the captured step, with the energy and impulse drift."""
+    import torch
+    spec, f = workload("tangle4e6")
+    p = make_params(B, spec, f, B.BS_MIXED, flags=B.BS_WANT_PSI)
+    bs = B.BiotSavart(p, f.offsets, f.closing, stream=stream)
+    nodes = torch.from_numpy(f.nodes).to(dev)
+    vel = torch.empty_like(nodes)
+    bs.capture(nodes, vel)
+    for _ in range(2):
+        bs.launch()
+    bs.status()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        bs.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.mean(ms)
+    out = {"workload": "tangle4e6: 20000 closed filaments x 200 nodes, N=4e6, M=512^3 modes, beta=3.5",
+           "value": f.N / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "steps": steps, "n_g": B.bs_nufft_setup(
+               p, want_table=False)[0], "mode": "CUDA graph replay"}
+    if rk_steps > 0:
+        seg = []
+        x = f.nodes
+        for l in range(f.nfil):
+            s = x[f.offsets[l]:f.offsets[l + 1]]
+            seg.append(np.linalg.norm(np.roll(s, -1, axis=0) - s, axis=1).min())
+        dt = B.kelvin_wave_period(min(seg), spec["kappa"], spec["a"], spec["delta"])
+        E0 = bs.energy(nodes)
+        P0 = polygon_impulse(nodes.cpu().numpy(), f.offsets, spec["kappa"])
+        bs.rk4_capture(nodes, dt)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bs.rk4_launch(rk_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rk_ms = e0.elapsed_time(e1)
+        bs.status()
+        E1 = bs.energy(nodes)
+        P1 = polygon_impulse(nodes.cpu().numpy(), f.offsets, spec["kappa"])
+        out["rk4"] = {"steps": rk_steps, "dt": dt, "ms": rk_ms, "ms_per_step": rk_ms / rk_steps,
+                      "evaluations_per_s": 4 * rk_steps / (rk_ms * 1e-3),
+                      "energy_rel_drift": (E1 - E0) / E0,
+                      "impulse_rel_drift": float(np.linalg.norm(P1 - P0) / np.linalg.norm(P0)),
+                      "max_node_displacement": float(np.abs(nodes.cpu().numpy() - f.nodes).max())}
+    bs.close()
+    return out
 
 
 def spread_zfft_bytes(p, ng, K, NQ, real_bytes):
@@ -319,6 +385,10 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    large = None
+    if not args.no_large_form and world == 1:
+        large = run_large_form(B, dev, stream, flush, 5, args.rk4_steps)
+
     batched = None
     if not args.no_batched_form and world == 1:
         batched = run_batched_form(B, dev, stream, flush, min(args.steps, 20))
@@ -398,6 +468,7 @@ def run_ours(args, rank, world, dist):
             "stages_ms": stage_mean,
             "fp64_form": fp64,
             "batched_form": batched,
+            "large_form": large,
             "accuracy": accuracy,
         }
     bs.close()

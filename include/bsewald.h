@@ -218,6 +218,25 @@ int bs_graph_capture(bs_ctx* ctx, const double* nodes, double* vel, double* psi)
 int bs_graph_launch(bs_ctx* ctx);
 
 /*
+ * Time stepping (Sec. 5.2): nodes advance by ds/dt = v(s) with the classical
+ * fourth-order Runge-Kutta scheme; every stage refits the spline, because
+ * every evaluation does.  nodes (device, N x 3 float64) are read and
+ * overwritten in place.
+ * bs_rk4_step: one step of size dt, issued directly on the context stream.
+ * bs_rk4_capture: capture one step, bound to this node buffer, into a CUDA
+ * graph (non-default stream needed; replaces a previous capture; dropped by
+ * bs_set_filaments); bs_rk4_launch replays it nsteps times.
+ * The first call allocates the RK4 workspace (15 N doubles).  dt is fixed at
+ * capture; the paper's stable choice is the Kelvin-wave period at the
+ * smallest node spacing.  Geometry faults surface through bs_status.
+ * Errors: BS_ERR_ARG (dt <= 0 or not finite, null nodes, default stream for
+ * capture), BS_ERR_STATE (launch without capture), BS_ERR_OOM, BS_ERR_CUDA.
+ */
+int bs_rk4_step(bs_ctx* ctx, double* nodes, double dt);
+int bs_rk4_capture(bs_ctx* ctx, double* nodes, double dt);
+int bs_rk4_launch(bs_ctx* ctx, int nsteps);
+
+/*
  * Batches of independent configurations (the paper evaluates one
  * configuration at a time; a batch evaluates many of the Sec. 5 problems,
  * each with its own parameters and grid, in one call).

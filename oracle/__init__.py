@@ -348,3 +348,31 @@ def components_matched(g: Geometry, L, kappa, a, delta, alpha, rc, K, targets=No
     return dict(local=vl, short=vs, long=vf, self=vx, psi_local=pl, psi_short=ps, psi_long=pf, psi_self=px,
                 total=_fsum_rows([vl, vs, vf, vx], [1, 1, 1, -1]),
                 psi_total=_fsum_rows([pl, ps, pf, px], [1, 1, 1, -1]))
+
+
+def rk4_converged(nodes, offsets, closing, L, kappa, a, delta, dt, nsteps, order=4, Q=2):
+    """Node positions after nsteps classical RK4 steps of ds/dt = v(s)
+    (Sec. 5.2), each stage velocity the oracle's converged one (the spline
+    refitted at every stage)."""
+    x = np.array(nodes, dtype=np.float64, copy=True)
+
+    def v(y):
+        g = geometry(y, offsets, closing, L, order, Q)
+        return velocity_converged(g, L, kappa, a, delta)[0]
+
+    for _ in range(nsteps):
+        k1 = v(x)
+        k2 = v(x + 0.5 * dt * k1)
+        k3 = v(x + 0.5 * dt * k2)
+        k4 = v(x + dt * k3)
+        x = x + dt / 6.0 * (k1 + 2.0 * (k2 + k3) + k4)
+    return x
+
+
+def polygon_impulse(nodes, offsets, kappa):
+    """Impulse (kappa/2) oint s x ds of the closed polygons through the nodes."""
+    P = np.zeros(3)
+    for l in range(offsets.size - 1):
+        s = nodes[offsets[l]:offsets[l + 1]]
+        P += 0.5 * kappa * np.cross(s, np.roll(s, -1, axis=0)).sum(axis=0)
+    return P

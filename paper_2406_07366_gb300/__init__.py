@@ -13,6 +13,7 @@ integrals over spatial curves in periodic domains", arXiv:2406.07366.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -35,7 +36,7 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error",
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
-           "bs_batch_member", "bs_batch_destroy"]
+           "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch"]
 
 
 class bs_params(ctypes.Structure):
@@ -91,6 +92,9 @@ def _load():
         "bs_batch_status": ([vp], ctypes.c_int),
         "bs_batch_member": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
         "bs_batch_destroy": ([vp], None),
+        "bs_rk4_step": ([vp, vp, ctypes.c_double], ctypes.c_int),
+        "bs_rk4_capture": ([vp, vp, ctypes.c_double], ctypes.c_int),
+        "bs_rk4_launch": ([vp, ctypes.c_int], ctypes.c_int),
         "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
@@ -212,6 +216,27 @@ def bs_graph_launch(ctx):
 
 def bs_status(ctx):
     return _check(lib().bs_status(ctx))
+
+
+def bs_rk4_step(ctx, nodes, dt):
+    _check(lib().bs_rk4_step(ctx, _ptr(nodes), float(dt)))
+
+
+def bs_rk4_capture(ctx, nodes, dt):
+    _check(lib().bs_rk4_capture(ctx, _ptr(nodes), float(dt)))
+
+
+def bs_rk4_launch(ctx, nsteps):
+    _check(lib().bs_rk4_launch(ctx, int(nsteps)))
+
+
+def kelvin_wave_period(lam, kappa=1.0, a=1e-6, delta=0.25):
+    """Period of a Kelvin wave of wavelength lam on a straight vortex
+    (Sec. 5.2): T = (2 lam^2 / kappa) / [ln(lam / (pi a)) + 1/2 - (delta + gamma)],
+    gamma the Euler-Mascheroni constant.  The paper's stable RK4 step is
+    T at the smallest node spacing."""
+    gamma = 0.57721566490153286061
+    return 2.0 * lam * lam / kappa / (math.log(lam / (math.pi * a)) + 0.5 - (delta + gamma))
 
 
 def bs_batch_create(params, stream=None):
@@ -390,6 +415,17 @@ class BiotSavart:
 
     def launch(self):
         bs_graph_launch(self.ctx)
+
+    def rk4_step(self, nodes, dt):
+        """One RK4 step of the nodes in place."""
+        bs_rk4_step(self.ctx, nodes, dt)
+
+    def rk4_capture(self, nodes, dt):
+        """Capture one in-place RK4 step into a CUDA graph (replay with rk4_launch)."""
+        bs_rk4_capture(self.ctx, nodes, dt)
+
+    def rk4_launch(self, nsteps):
+        bs_rk4_launch(self.ctx, nsteps)
 
     def quadrature(self, nodes):
         Q = self.params.quad_Q

@@ -288,6 +288,9 @@ struct bs_ctx {
     int device = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    double* rk = nullptr;  // RK4 workspace: k1..k4 and the stage positions, 5 x N x 3
+    cudaGraph_t rk_graph = nullptr;
+    cudaGraphExec_t rk_exec = nullptr;
 };
 
 namespace {
@@ -748,6 +751,43 @@ int check_ctx(bs_ctx* c)
     return BS_OK;
 }
 
+
+void rk4_drop_graph(bs_ctx* c)
+{
+    if (c->rk_exec) cudaGraphExecDestroy(c->rk_exec);
+    if (c->rk_graph) cudaGraphDestroy(c->rk_graph);
+    c->rk_exec = nullptr;
+    c->rk_graph = nullptr;
+}
+
+int rk4_alloc(bs_ctx* c)
+{
+    if (!c->rk) TRY(dalloc(c, c->alloc_n, (void**)&c->rk, sizeof(double) * 15 * (size_t)c->N));
+    return BS_OK;
+}
+
+// One RK4 step of the nodes in place: four evaluations on the stage
+// positions, then the weighted update (Sec. 5.2).
+int rk4_issue(bs_ctx* c, double* nodes, double dt)
+{
+    const long long n3 = 3 * (long long)c->N;
+    double* k[4] = { c->rk, c->rk + n3, c->rk + 2 * n3, c->rk + 3 * n3 };
+    double* xs = c->rk + 4 * n3;
+    const double cs[3] = { 0.5 * dt, 0.5 * dt, dt };
+    const double* x = nodes;
+    for (int st = 0; st < 4; ++st) {
+        const int rc = c->p.precision == BS_FP64 ? run<double>(c, x, k[st], nullptr, nullptr, nullptr)
+                                                 : run<float>(c, x, k[st], nullptr, nullptr, nullptr);
+        if (rc != BS_OK) return rc;
+        if (st < 3) {
+            CE(launch_rk4_stage(nodes, k[st], cs[st], xs, n3, c->stream));
+            x = xs;
+        }
+    }
+    CE(launch_rk4_final(nodes, k[0], k[1], k[2], k[3], dt, n3, c->stream));
+    return BS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -908,8 +948,10 @@ int bs_set_filaments(bs_ctx* c, int nfil, const int64_t* offsets, const int32_t*
         cudaGraphDestroy(c->graph);
         c->graph = nullptr;
     }
+    rk4_drop_graph(c);
     free_list(c, c->alloc_n);  // drop the buffers of a previous topology
     c->w.off = nullptr;
+    c->rk = nullptr;
     std::vector<int> fil_of((size_t)N), prev((size_t)N);
     std::vector<double> shift(3 * (size_t)nfil, 0.0);
     for (int l = 0; l < nfil; ++l) {
@@ -1050,6 +1092,49 @@ int bs_graph_launch(bs_ctx* c)
     return BS_OK;
 }
 
+int bs_rk4_step(bs_ctx* c, double* nodes, double dt)
+{
+    TRY(check_ctx(c));
+    if (c->N == 0) return BS_OK;
+    if (!nodes) return fail(BS_ERR_ARG, "null nodes");
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(BS_ERR_ARG, "dt must be positive and finite");
+    TRY(rk4_alloc(c));
+    return rk4_issue(c, nodes, dt);
+}
+
+int bs_rk4_capture(bs_ctx* c, double* nodes, double dt)
+{
+    TRY(check_ctx(c));
+    if (!c->stream) return fail(BS_ERR_ARG, "graph capture needs a non-default stream");
+    if (!nodes) return fail(BS_ERR_ARG, "null nodes");
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(BS_ERR_ARG, "dt must be positive and finite");
+    rk4_drop_graph(c);
+    if (c->N == 0) return BS_OK;
+    TRY(rk4_alloc(c));
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = rk4_issue(c, nodes, dt);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc != BS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(BS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    c->rk_graph = g;
+    CUDA_TRY(cudaGraphInstantiate(&c->rk_exec, c->rk_graph, 0));
+    return BS_OK;
+}
+
+int bs_rk4_launch(bs_ctx* c, int nsteps)
+{
+    TRY(check_ctx(c));
+    if (nsteps < 0) return fail(BS_ERR_ARG, "negative step count");
+    if (c->N == 0 || nsteps == 0) return BS_OK;
+    if (!c->rk_exec) return fail(BS_ERR_STATE, "no captured RK4 step (call bs_rk4_capture first)");
+    for (int i = 0; i < nsteps; ++i) CUDA_TRY(cudaGraphLaunch(c->rk_exec, c->stream));
+    return BS_OK;
+}
+
 int bs_status(bs_ctx* c)
 {
     if (!c) return fail(BS_ERR_ARG, "null context");
@@ -1101,6 +1186,7 @@ void bs_destroy(bs_ctx* c)
     if (c->side) cudaStreamSynchronize(c->side);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    rk4_drop_graph(c);
     if (c->plans) {
         if (c->plan_fwd) cufftDestroy(c->plan_fwd);
         if (c->plan_inv) cufftDestroy(c->plan_inv);

@@ -316,6 +316,10 @@ template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);
 
 // Set the thread-local message returned by bs_last_error.
+cudaError_t launch_rk4_stage(const double* x0, const double* k, double c, double* out, long long n, cudaStream_t s);
+cudaError_t launch_rk4_final(double* x, const double* k1, const double* k2, const double* k3, const double* k4,
+                             double h, long long n, cudaStream_t s);
+
 void set_last_error(const char* msg);
 
 // Exclusive scan of n ints in place (cnt[n] receives the total); tmp holds

@@ -295,6 +295,23 @@ def test_tangle1e5_fp64_sampled():
     assert rms_rel(v[tg], vr) < 2e-6
 
 
+def test_tangle4e6_mixed_sampled():
+    """Large tangle, 20000 filaments x 200 nodes (4e6 nodes, 8e6 sources),
+    M = 512 (768^3 spread grid), mixed precision: 8 sampled nodes against the
+    converged oracle summing over all sources, plus every velocity finite."""
+    B = _B()
+    spec = W.WORKLOADS["tangle4e6"]
+    f = spec["gen"]()
+    p = params(f, M=spec["M"], Q=spec["Q"], w=spec["w"], sigma=spec["sigma"], precision=B.BS_MIXED)
+    v = gpu_velocity(f, p)
+    assert np.all(np.isfinite(v))
+    rng = np.random.default_rng(4)
+    tg = np.sort(rng.choice(f.N, 8, replace=False))
+    g = geom(f, 4, spec["Q"])
+    vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA, targets=tg)
+    assert rms_rel(v[tg], vr) < 1e-5
+
+
 # ------------------------------------------------------------------ edge cases
 def test_antiparallel_lines_zero_velocity():
     B = _B()

@@ -297,3 +297,37 @@ def test_energy_depends_on_alpha_only_through_interpolation():
         e2 = oracle.energy_converged(g, f.L, KAPPA, A_CORE, DELTA, alpha_scale=1.5)
         d.append(abs(e1 - e2) / abs(e1))
     assert d[0] > d[1] > d[2] and d[2] < 1e-8, d
+
+
+def test_rk4_energy_and_impulse_drift_shrink_with_resolution():
+    """Sec. 5.2: the filament energy and impulse are invariants of the
+    continuous motion, so their drift over a fixed time under RK4 with the
+    Kelvin-wave step comes only from the discretisation and must shrink as
+    the curves are refined (leapfrogging ellipses, N_l = 32 -> 64, same
+    physical time).  A wrong sign or a dropped term in any velocity part
+    breaks the conservation at every resolution."""
+    import paper_2406_07366_gb300 as B
+    drifts = []
+    T = None
+    for N_l in (32, 64):
+        f = W.leapfrog_ellipses(N_l=N_l)
+        dmin = min(np.linalg.norm(np.diff(f.nodes[f.offsets[l]:f.offsets[l + 1]], axis=0, append=f.nodes[
+            f.offsets[l]:f.offsets[l] + 1]), axis=1).min() for l in range(f.nfil))
+        dt = B.kelvin_wave_period(dmin, KAPPA, A_CORE, DELTA)
+        if T is None:
+            T = 10 * dt
+        n = int(round(T / dt))
+        dt = T / n
+        x1 = oracle.rk4_converged(f.nodes, f.offsets, f.closing, f.L, KAPPA, A_CORE, DELTA, dt, n)
+        e0 = oracle.energy_converged(oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 4, 2), f.L, KAPPA,
+                                     A_CORE, DELTA)
+        e1 = oracle.energy_converged(oracle.geometry(x1, f.offsets, f.closing, f.L, 4, 2), f.L, KAPPA,
+                                     A_CORE, DELTA)
+        p0 = oracle.polygon_impulse(f.nodes, f.offsets, KAPPA)
+        p1 = oracle.polygon_impulse(x1, f.offsets, KAPPA)
+        drifts.append((abs(e1 - e0) / abs(e0), np.linalg.norm(p1 - p0) / np.linalg.norm(p0)))
+        # the pair moves: the time span is not trivially short
+        assert np.abs(x1 - f.nodes).max() > 1e-3
+    (e32, p32), (e64, p64) = drifts
+    assert e32 < 1e-4 and p32 < 2e-5
+    assert e64 < e32 / 2.5 and p64 < p32 / 2.5
