@@ -107,17 +107,36 @@ int line_stride(int n, int nl, int slots)
     return n + (((target - n) % slots) + slots) % slots;
 }
 
-// Radices of a length-n transform: the factors 3 first, then 8s, then a 4 or a 2.
-FftPlan make_plan(int n)
+// Radices of a length-n transform: the fewest in-register passes, each of a
+// size the kernels implement (up to maxr), and among those the most even
+// split (largest smallest factor), largest factor first.
+void plan_search(int n, int maxr, int start, std::vector<int>& cur, std::vector<int>& best)
+{
+    static const int kRadices[] = { 32, 24, 16, 12, 9, 8, 6, 4, 3, 2 };
+    if (n == 1) {
+        if (best.empty() || cur.size() < best.size() ||
+            (cur.size() == best.size() && cur.back() > best.back()))
+            best = cur;
+        return;
+    }
+    if (!best.empty() && cur.size() + 1 > best.size()) return;
+    for (int i = start; i < 10; ++i) {
+        const int r = kRadices[i];
+        if (r > maxr || n % r) continue;
+        cur.push_back(r);
+        plan_search(n / r, maxr, i, cur, best);
+        cur.pop_back();
+    }
+}
+
+FftPlan make_plan(int n, int maxr)
 {
     FftPlan pl;
     pl.n = n;
-    pl.nr = 0;
-    int r = n;
-    while (r % 3 == 0) { pl.r[pl.nr++] = 3; r /= 3; }
-    while (r % 8 == 0) { pl.r[pl.nr++] = 8; r /= 8; }
-    if (r == 4) { pl.r[pl.nr++] = 4; r = 1; }
-    if (r == 2) { pl.r[pl.nr++] = 2; r = 1; }
+    std::vector<int> cur, best;
+    plan_search(n, maxr, 0, cur, best);
+    pl.nr = (int)best.size();
+    for (int s = 0; s < pl.nr; ++s) pl.r[s] = best[s];
     int L = n;
     for (int s = 0; s < pl.nr; ++s) {
         pl.st[s] = L / pl.r[s];
@@ -243,7 +262,7 @@ int derive(const bs_params* p, Derived* d)
     // memory per CTA near 50 KB (4-5 CTAs per SM)
     const size_t rb = p->precision == BS_FP64 ? 8 : 4;
     const size_t cb = 2 * rb;
-    for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c]);
+    for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c], 8);
     int txy = (int)(50000 / (1.5 * (d->ng[2] + 1) * cb));
     txy = txy >= 16 ? 16 : (txy >= 8 ? 8 : (txy >= 4 ? 4 : 2));
     d->ty = std::min(4, txy);
@@ -439,7 +458,7 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.lr_rec, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, &w.lr_sorted, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, (void**)&w.lr_key, sizeof(int) * NQ));
-    TRY(dalloc(c, L, &w.col_rec, sizeof(LrRec<T>) * NQ * (size_t)c->d.colcap));
+    TRY(dalloc(c, L, &w.col_rec, col_rec_bytes<T>(c->p.nufft_w) * NQ * (size_t)c->d.colcap));
     TRY(dalloc(c, L, (void**)&w.nodes_in, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.vel_out, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.psi_out, sizeof(double) * 3 * N));
@@ -605,6 +624,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         CP.nby = d.nby;
         CP.ncols = d.ncols;
         CP.w = p.nufft_w;
+        CP.zeta = d.zeta;
         CE(launch_col_sort<T>(CP, w, (int)c->NQ, s));
         rec(c, 4, s);
         SpZP SZ;
@@ -887,6 +907,7 @@ int bs_create(bs_ctx** out, const bs_params* p, void* stream)
         return rc;
     }
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = set_fft_constants();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);

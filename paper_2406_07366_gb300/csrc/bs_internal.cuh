@@ -43,6 +43,19 @@ template <typename T> struct __align__(16) SrTgt {
 
 // Long-range source: fractional grid position, charge, packed base index
 // (10 bits per axis).
+// Spread record of one point copied into one block of Tx x Ty z-columns
+// (Tx, Ty <= 4): the support start relative to the block (base: r0 + 128 |
+// (r1 + 128) << 8 | z index << 16), the charge, and the kernel weights
+// already evaluated: wx[lx] / wy[ly] for the block's local columns (zero
+// outside the support), wz[t] for the W support points along z.
+template <typename T, int W> struct __align__(16) SpRec {
+    int base;
+    T q[3];
+    T wx[4];
+    T wy[4];
+    T wz[W];
+};
+
 template <typename T> struct LrRec;
 template <> struct __align__(16) LrRec<float> {
     float f[3];
@@ -157,6 +170,7 @@ struct FftPlan {
 // Column binning of the spread records (blocks of tx x ty full z-columns).
 struct ColP {
     int tx, ty, nbx, nby, ncols, w;
+    double zeta;  // kernel shape parameter
 };
 
 struct SpZP {
@@ -300,6 +314,9 @@ template <typename T>
 cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s);
+template <typename T>
+size_t col_rec_bytes(int w);
+cudaError_t set_fft_constants();
 template <typename T>
 cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s);
 template <typename T>

@@ -25,6 +25,8 @@
 // in float64.  Two real lines are transformed as one complex line.
 #include <math.h>
 
+#include <mutex>
+
 #include "bs_internal.cuh"
 
 namespace bsw {
@@ -45,16 +47,46 @@ __device__ __forceinline__ C cmul(C a, C b) { C r; r.x = a.x * b.x - a.y * b.y; 
 template <typename C>
 __device__ __forceinline__ C cmuli(C a, int sign) { C r; r.x = -sign * a.y; r.y = sign * a.x; return r; }
 
-// In-register DFT of size R with exponent sign (+1 or -1).
+// e^{-2 pi i m / R} for the composite in-register sizes R in {6, 9, 12, 16,
+// 24, 32}, m = 0..R-1, written once per device from float64 values
+// (set_fft_constants).  Indices are compile-time constants after unrolling,
+// so the factors come straight from the constant bank.
+constexpr int kTwOff6 = 0, kTwOff9 = 6, kTwOff12 = 15, kTwOff16 = 27, kTwOff24 = 43, kTwOff32 = 67, kTwCount = 99;
+__constant__ float2 c_twf[kTwCount];
+__constant__ double2 c_twd[kTwCount];
+
+template <int R> struct TwOff;
+template <> struct TwOff<6> { static constexpr int v = kTwOff6; };
+template <> struct TwOff<9> { static constexpr int v = kTwOff9; };
+template <> struct TwOff<12> { static constexpr int v = kTwOff12; };
+template <> struct TwOff<16> { static constexpr int v = kTwOff16; };
+template <> struct TwOff<24> { static constexpr int v = kTwOff24; };
+template <> struct TwOff<32> { static constexpr int v = kTwOff32; };
+
+template <typename T> __device__ __forceinline__ typename Cx<T>::t ctw(int i);
+template <> __device__ __forceinline__ float2 ctw<float>(int i) { return c_twf[i]; }
+template <> __device__ __forceinline__ double2 ctw<double>(int i) { return c_twd[i]; }
+
+// Factor R = A * B of a composite size: A the leading base radix.
+template <int R> struct Split;
+template <> struct Split<6> { static constexpr int A = 3, B = 2; };
+template <> struct Split<9> { static constexpr int A = 3, B = 3; };
+template <> struct Split<12> { static constexpr int A = 4, B = 3; };
+template <> struct Split<16> { static constexpr int A = 4, B = 4; };
+template <> struct Split<24> { static constexpr int A = 8, B = 3; };
+template <> struct Split<32> { static constexpr int A = 8, B = 4; };
+
+// In-register DFT of size R with exponent sign (+1 or -1):
+// x[k] <- sum_n x[n] e^{sign 2 pi i n k / R}, natural order in and out.
 template <typename T, int R>
 __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
 {
     using C = typename Cx<T>::t;
-    if (R == 2) {
+    if constexpr (R == 2) {
         const C a = x[0], b = x[1];
         x[0] = cadd(a, b);
         x[1] = csub(a, b);
-    } else if (R == 3) {
+    } else if constexpr (R == 3) {
         const T h = (T)0.86602540378443864676 * (T)sign;  // sin(2 pi / 3) with the sign
         const C s = cadd(x[1], x[2]);
         const C d = csub(x[1], x[2]);
@@ -67,14 +99,14 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
         x[0] = cadd(x[0], s);
         x[1] = cadd(t, u);
         x[2] = csub(t, u);
-    } else if (R == 4) {
+    } else if constexpr (R == 4) {
         const C a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
         const C c = cadd(x[1], x[3]), d = cmuli(csub(x[1], x[3]), sign);
         x[0] = cadd(a, c);
         x[2] = csub(a, c);
         x[1] = cadd(b, d);
         x[3] = csub(b, d);
-    } else if (R == 8) {
+    } else if constexpr (R == 8) {
         C e[4] = { x[0], x[2], x[4], x[6] };
         C o[4] = { x[1], x[3], x[5], x[7] };
         dft<T, 4>(e, sign);
@@ -94,6 +126,47 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
         for (int m = 0; m < 4; ++m) {
             x[m] = cadd(e[m], o[m]);
             x[m + 4] = csub(e[m], o[m]);
+        }
+    } else {
+        // n = a B + b, k = k1 + A k2:
+        // X[k1 + A k2] = sum_b w_B^{b k2} [ w_R^{b k1} sum_a x[a B + b] w_A^{a k1} ]
+        constexpr int A = Split<R>::A, B = Split<R>::B;
+        C y[R];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            C t[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) t[a] = x[a * B + b];
+            dft<T, A>(t, sign);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) {
+                C v = t[k1];
+                const int m = (b * k1) % R;
+                if (m != 0) {
+                    if (4 * m == R) {
+                        v = cmuli(v, sign);
+                    } else if (2 * m == R) {
+                        v.x = -v.x;
+                        v.y = -v.y;
+                    } else if (4 * m == 3 * R) {
+                        v = cmuli(v, -sign);
+                    } else {
+                        C w = ctw<T>(TwOff<R>::v + m);  // e^{-2 pi i m / R}
+                        if (sign > 0) w.y = -w.y;
+                        v = cmul(v, w);
+                    }
+                }
+                y[k1 * B + b] = v;
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+            C t[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) t[b] = y[k1 * B + b];
+            dft<T, B>(t, sign);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) x[k1 + A * k2] = t[k2];
         }
     }
 }
@@ -144,36 +217,48 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
     }
 }
 
-template <typename T, bool DIF>
+template <typename T, bool DIF, int RM>
 __device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls,
                                           const FftPlan& pl, int s, const typename Cx<T>::t* __restrict__ tw,
                                           int sign)
 {
     const int R = pl.r[s];
-    if (R == 8) fft_pass<T, 8, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
-    else if (R == 4) fft_pass<T, 4, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
-    else if (R == 3) fft_pass<T, 3, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
-    else fft_pass<T, 2, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign);
+#define BSW_PASS(RR) fft_pass<T, RR, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign)
+    // only the radices up to RM are compiled into this kernel (register budget)
+    switch (R) {
+    case 32: if constexpr (RM >= 32) BSW_PASS(32); break;
+    case 24: if constexpr (RM >= 24) BSW_PASS(24); break;
+    case 16: if constexpr (RM >= 16) BSW_PASS(16); break;
+    case 12: if constexpr (RM >= 12) BSW_PASS(12); break;
+    case 9: if constexpr (RM >= 9) BSW_PASS(9); break;
+    case 8: BSW_PASS(8); break;
+    case 6: BSW_PASS(6); break;
+    case 4: BSW_PASS(4); break;
+    case 3: BSW_PASS(3); break;
+    default: BSW_PASS(2); break;
+    }
+#undef BSW_PASS
     __syncthreads();
 }
 
 // Forward transform (decimation in frequency), natural order in, frequency
 // k left at position rev(k).
-template <typename T>
+template <typename T, int RM>
 __device__ void fft_fwd_dif(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
-    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true>(buf, nlines, dl, ls, pl, s, tw, -1);
+    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true, RM>(buf, nlines, dl, ls, pl, s, tw, -1);
 }
 
 // Inverse transform (decimation in time), frequency k taken at position
 // rev(k), natural order out.
-template <typename T>
+template <typename T, int RM>
 __device__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
-    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false>(buf, nlines, dl, ls, pl, s, tw, +1);
+    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false, RM>(buf, nlines, dl, ls, pl, s, tw, +1);
 }
+
 
 template <typename T>
 __device__ __forceinline__ T kb_val(T z, T zeta, T inorm)
@@ -216,25 +301,55 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
     }
 }
 
-template <typename T>
+// One thread per point: the 3 W kernel weights are evaluated once, then the
+// point is written into every block its support reaches, with the x and y
+// weights of that block's local columns picked out (zero outside the support).
+template <typename T, int W>
 __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cur,
-                              LrRec<T>* __restrict__ out)
+                              SpRec<T, W>* __restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    LrRec<T> R = rec[i];
+    const LrRec<T> R = rec[i];
     const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
-    const int H = P.w / 2;
+    constexpr int H = W / 2;
+    const T zeta = (T)P.zeta;
+    const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+    // weight of support point t along axis d: psi((f_d + H - 1 - t) / (W / 2))
+    T kx[W], ky[W];
+    SpRec<T, W> D;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        kx[t] = kb_val((R.f[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        ky[t] = kb_val((R.f[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        D.wz[t] = kb_val((R.f[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+    }
+    D.q[0] = R.q[0];
+    D.q[1] = R.q[1];
+    D.q[2] = R.q[2];
     int x0, x1, y0, y1;
     col_range(ib0, H, P.tx, x0, x1);
     col_range(ib1, H, P.ty, y0, y1);
     for (int by = y0; by <= y1; ++by) {
         const int wy = ((by % P.nby) + P.nby) % P.nby;
         const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block
+#pragma unroll
+        for (int ly = 0; ly < 4; ++ly) {
+            T v = (T)0;
+#pragma unroll
+            for (int t = 0; t < W; ++t) v = (t + r1 == ly) ? ky[t] : v;
+            D.wy[ly] = v;
+        }
         for (int bx = x0; bx <= x1; ++bx) {
             const int wx = ((bx % P.nbx) + P.nbx) % P.nbx;
             const int r0 = ib0 - H + 1 - bx * P.tx;
-            LrRec<T> D = R;
+#pragma unroll
+            for (int lx = 0; lx < 4; ++lx) {
+                T v = (T)0;
+#pragma unroll
+                for (int t = 0; t < W; ++t) v = (t + r0 == lx) ? kx[t] : v;
+                D.wx[lx] = v;
+            }
             D.base = (r0 + 128) | ((r1 + 128) << 8) | (ib2 << 16);
             const int p = atomicAdd(&cur[wx + P.nbx * wy], 1);
             out[p] = D;
@@ -246,14 +361,15 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
 // A: spread + z real FFT.
 // The 3 Tx Ty real z-lines are accumulated directly as complex lines (real
 // line 2l in .x, 2l+1 in .y of complex line l, stride cls), transformed in
-// place, and separated while writing modes 0..K2.  Records are staged in
-// shared memory a chunk at a time and dealt to the warps round-robin; a
-// warp's lanes always hold distinct cells and shared atomic adds resolve two
-// warps meeting on a cell.
+// place, and separated while writing modes 0..K2.  Records (weights already
+// evaluated) are staged in shared memory a chunk at a time and dealt to the
+// warps round-robin.  A lane owns one (local y column, z support point) slot
+// and walks the block's x columns, so a warp's lanes always hold distinct
+// cells; shared atomic adds resolve two warps meeting on a cell.
 // ---------------------------------------------------------------------------
-template <typename T, int W>
-__global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
-                                                          const LrRec<T>* __restrict__ recs,
+template <typename T, int W, int RM>
+__global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
+                                                          const SpRec<T, W>* __restrict__ recs,
                                                           const typename Cx<T>::t* __restrict__ tw2,
                                                           typename Cx<T>::t* __restrict__ F1)
 {
@@ -266,8 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
     const int CS = P.cls;
     C* cb = reinterpret_cast<C*>(smem_raw);
     T* accf = reinterpret_cast<T*>(cb);  // real line rl, position z at float ((rl>>1) CS + z) 2 + (rl&1)
-    LrRec<T>* srec = reinterpret_cast<LrRec<T>*>(cb + (size_t)ncl * CS);
-    T* ktab = reinterpret_cast<T*>(srec + kSpzChunk);
+    SpRec<T, W>* srec = reinterpret_cast<SpRec<T, W>*>(cb + (size_t)ncl * CS);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int by = fdiv(blockIdx.x, P.d_nbx);
     const int bx = blockIdx.x - by * P.nbx;
@@ -276,44 +391,37 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
     zero.y = 0;
     for (int i = tid; i < ncl * CS; i += blockDim.x) cb[i] = zero;
 
-    const T zeta = (T)P.zeta;
-    const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
     constexpr int H = W / 2;
-    T* kw = ktab + wid * 3 * W;
     const int s0 = cstart[blockIdx.x], s1 = cstart[blockIdx.x + 1];
-    const int rows_per = 32 / W;
-    const int rsub = lane / W, t = lane - rsub * W;  // this lane: support row group and z offset
+    const int nslot = Ty * W;
     for (int c0r = s0; c0r < s1; c0r += kSpzChunk) {
         const int nch = min(kSpzChunk, s1 - c0r);
         __syncthreads();
-        for (int i = tid; i < nch; i += blockDim.x) srec[i] = recs[c0r + i];
+        {
+            // copy the chunk as 16-byte words
+            constexpr int kWords = (int)(sizeof(SpRec<T, W>) / 16);
+            const int4* src = reinterpret_cast<const int4*>(recs + c0r);
+            int4* dst = reinterpret_cast<int4*>(srec);
+            for (int i = tid; i < nch * kWords; i += blockDim.x) dst[i] = src[i];
+        }
         __syncthreads();
         for (int kk = wid; kk < nch; kk += nw) {
-            const LrRec<T> R = srec[kk];
-            const int ib2 = (R.base >> 16) & 1023;
-            const int r0 = (R.base & 255) - 128, r1 = ((R.base >> 8) & 255) - 128;
+            const SpRec<T, W>& R = srec[kk];
+            const int base = R.base;
+            const int ib2 = (base >> 16) & 1023;
+            const int r0 = (base & 255) - 128, r1 = ((base >> 8) & 255) - 128;
             const int a0 = max(r0, 0), e0 = min(r0 + W - 1, Tx - 1);
             const int a1 = max(r1, 0), e1 = min(r1 + W - 1, Ty - 1);
-            const T f0 = R.f[0], f1 = R.f[1], f2 = R.f[2];
             const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
-            __syncwarp();
-            for (int i = lane; i < 3 * W; i += 32) {
-                const int d = i / W, tt = i - d * W;
-                const T f = d == 0 ? f0 : (d == 1 ? f1 : f2);
-                kw[i] = kb_val((f + (T)(H - 1 - tt)) * ((T)2 / (T)W), zeta, inorm);
-            }
-            __syncwarp();
-            if (rsub < rows_per) {
+            for (int sl = lane; sl < nslot; sl += 32) {
+                const int ly = sl / W, t = sl - ly * W;
+                if (ly < a1 || ly > e1) continue;
                 int z = ib2 - H + 1 + t;
                 z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
-                const T wz = kw[2 * W + t];
-                const int n1 = e1 - a1 + 1;
-                const int nrows = (e0 - a0 + 1) * n1;
-                for (int r = rsub; r < nrows; r += rows_per) {
-                    const int c0 = r / n1, c1 = r - c0 * n1;
-                    const int x0 = a0 + c0, x1 = a1 + c1;
-                    const T wv = kw[x0 - r0] * kw[W + x1 - r1] * wz;
-                    const int rl = x0 * Ty + x1;  // real line of component 0
+                const T wyz = R.wy[ly] * R.wz[t];
+                for (int lx = a0; lx <= e0; ++lx) {
+                    const T wv = R.wx[lx] * wyz;
+                    const int rl = lx * Ty + ly;  // real line of component 0
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const int rlc = rl + c * txy;
@@ -325,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
         }
     }
     __syncthreads();
-    fft_fwd_dif<T>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
+    fft_fwd_dif<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
     // separate the two real transforms and write modes 0..K2
     const int nk = P.K[2] + 1;
     for (int i = tid; i < nreal * nk; i += blockDim.x) {
@@ -353,8 +461,8 @@ __global__ void __launch_bounds__(kThreads) k_spread_zfft(SpZP P, const int* __r
 // forward: F1[c][x][y][mz] -> F2[c][x][my'][mz], my' = my + K1, |my| <= K1
 // inverse: F2 -> F1 (zero-padded to n1)
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* __restrict__ F1,
+template <typename T, int RM>
+__global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::t* __restrict__ F1,
                                                     typename Cx<T>::t* __restrict__ F2,
                                                     const typename Cx<T>::t* __restrict__ tw1, int sign)
 {
@@ -379,7 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* 
             a[l * LS + y] = (l < mcount) ? F1[((size_t)cx * n1 + y) * nk + mz0 + l] : zero;
         }
         __syncthreads();
-        fft_fwd_dif<T>(a, MC, P.d_lines, LS, P.plan1, tw1);
+        fft_fwd_dif<T, RM>(a, MC, P.d_lines, LS, P.plan1, tw1);
         for (int i = threadIdx.x; i < (ny2 << lmc); i += blockDim.x) {
             const int myp = i >> lmc, l = i & (MC - 1);
             if (l >= mcount) continue;
@@ -395,7 +503,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* 
             a[l * LS + P.rev[y]] = v;
         }
         __syncthreads();
-        fft_inv_dit<T>(a, MC, P.d_lines, LS, P.plan1, tw1);
+        fft_inv_dit<T, RM>(a, MC, P.d_lines, LS, P.plan1, tw1);
         for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
             const int y = i >> lmc, l = i & (MC - 1);
             if (l >= mcount) continue;
@@ -409,8 +517,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(FftYP P, typename Cx<T>::t* 
 // One CTA per (my', chunk of 2^lmc z-modes); the 3 components together (the
 // curl couples them).  tabs: e^{-k_d^2/4alpha^2} / F_d(m)^2 per axis.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
+template <typename T, int RM>
+__global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
                                                            typename Cx<T>::t* __restrict__ F2psi,
                                                            const typename Cx<T>::t* __restrict__ tw0,
                                                            const T* __restrict__ tab0, const T* __restrict__ tab1,
@@ -439,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
         a[((c << lmc) + l) * LS + x] = (l < mcount) ? F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] : zero;
     }
     __syncthreads();
-    fft_fwd_dif<T>(a, 3 * MC, P.d_lines, LS, P.plan0, tw0);
+    fft_fwd_dif<T, RM>(a, 3 * MC, P.d_lines, LS, P.plan0, tw0);
     // k-space pass: frequency (mx, my, mz) sits at position rev(xi) of line (c, l)
     const int my = myp - K1;
     const int amy = my < 0 ? -my : my;
@@ -498,7 +606,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
         if ((threadIdx.x & 31) == 0 && esum != 0.0) atomicAdd(P.energy, esum);
     }
     __syncthreads();
-    fft_inv_dit<T>(a, (want_psi ? 6 : 3) * MC, want_psi ? P.d_lines_psi : P.d_lines, LS, P.plan0, tw0);
+    fft_inv_dit<T, RM>(a, (want_psi ? 6 : 3) * MC, want_psi ? P.d_lines_psi : P.d_lines, LS, P.plan0, tw0);
     for (int i = threadIdx.x; i < ((3 * n0) << lmc); i += blockDim.x) {
         const int l = i & (MC - 1);
         if (l >= mcount) continue;
@@ -514,8 +622,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_kspace(FftXP P, typename Cx<
 // E: inverse z real FFT.  One CTA per (c, x, chunk of YC y-lines); two real
 // lines per complex transform.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fft_z_c2r(FftZP P, const typename Cx<T>::t* __restrict__ F1,
+template <typename T, int RM>
+__global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typename Cx<T>::t* __restrict__ F1,
                                                         const typename Cx<T>::t* __restrict__ tw2,
                                                         T* __restrict__ grid)
 {
@@ -554,7 +662,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_z_c2r(FftZP P, const typename 
         }
     }
     __syncthreads();
-    fft_inv_dit<T>(a, ncl, P.d_ncl, CS, P.plan2, tw2);
+    fft_inv_dit<T, RM>(a, ncl, P.d_ncl, CS, P.plan2, tw2);
     const size_t gsz = (size_t)P.ng[0] * n1 * n2;
     const int c = fdiv(cx, P.d_n0), x = cx - c * P.ng[0];
     T* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
@@ -569,6 +677,46 @@ __global__ void __launch_bounds__(kThreads) k_fft_z_c2r(FftZP P, const typename 
 // host launchers
 // ---------------------------------------------------------------------------
 template <typename T>
+size_t col_rec_bytes(int w)
+{
+    switch (w) {
+    case 2: return sizeof(SpRec<T, 2>);
+    case 4: return sizeof(SpRec<T, 4>);
+    case 6: return sizeof(SpRec<T, 6>);
+    case 8: return sizeof(SpRec<T, 8>);
+    case 10: return sizeof(SpRec<T, 10>);
+    case 12: return sizeof(SpRec<T, 12>);
+    case 14: return sizeof(SpRec<T, 14>);
+    case 16: return sizeof(SpRec<T, 16>);
+    default: return 0;
+    }
+}
+
+template <typename T, int W>
+static cudaError_t col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s)
+{
+    k_col_scatter<T, W><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(P, (const LrRec<T>*)w.lr_rec, NQ,
+                                                                           w.col_cur, (SpRec<T, W>*)w.col_rec);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s)
+{
+    switch (P.w) {
+    case 2: return col_scatter_w<T, 2>(P, w, NQ, s);
+    case 4: return col_scatter_w<T, 4>(P, w, NQ, s);
+    case 6: return col_scatter_w<T, 6>(P, w, NQ, s);
+    case 8: return col_scatter_w<T, 8>(P, w, NQ, s);
+    case 10: return col_scatter_w<T, 10>(P, w, NQ, s);
+    case 12: return col_scatter_w<T, 12>(P, w, NQ, s);
+    case 14: return col_scatter_w<T, 14>(P, w, NQ, s);
+    case 16: return col_scatter_w<T, 16>(P, w, NQ, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
 cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(w.col_cnt, 0, sizeof(int) * (size_t)(P.ncols + 1), s);
@@ -580,9 +728,8 @@ cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s
     e = cudaMemcpyAsync(w.col_cur, w.col_cnt, sizeof(int) * (size_t)P.ncols, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     if (NQ > 0)
-        k_col_scatter<T><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(P, (const LrRec<T>*)w.lr_rec, NQ,
-                                                                             w.col_cur, (LrRec<T>*)w.col_rec);
-    return cudaGetLastError();
+        e = launch_col_scatter_w<T>(P, w, NQ, s);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -590,20 +737,51 @@ size_t spread_zfft_smem(const SpZP& P)
 {
     using C = typename Cx<T>::t;
     const int ncl = 3 * P.tx * P.ty / 2;
-    return (size_t)ncl * P.cls * sizeof(C) + kSpzChunk * sizeof(LrRec<T>) +
-           (kThreads / 32) * 3 * (size_t)P.w * sizeof(T);
+    return (size_t)ncl * P.cls * sizeof(C) + kSpzChunk * col_rec_bytes<T>(P.w);
 }
+
+// Register-budget class of a plan: the largest radix it uses, rounded up to
+// a compiled set.  Only radices up to 8 (with the composite 6) are compiled:
+// measured on the 384-point lines of the 1e5-node tangle, two passes of
+// radix 24 x 16 at 128 registers (two CTAs per SM) ran 30 % slower than three
+// passes of 8 x 8 x 6 at 64 registers (five CTAs per SM, shared-memory bound).
+static int plan_rm(const FftPlan& pl)
+{
+    int m = 2;
+    for (int s = 0; s < pl.nr; ++s) m = pl.r[s] > m ? pl.r[s] : m;
+    return m <= 8 ? 8 : (m <= 16 ? 16 : (m <= 24 ? 24 : 32));
+}
+
+// Calls f.run<RM>() with the plan's register class.
+template <typename T, typename F>
+static cudaError_t by_rm(const FftPlan& pl, F&& f)
+{
+    return plan_rm(pl) == 8 ? f.template run<8>() : cudaErrorInvalidValue;
+}
+
+template <typename T, int W>
+struct SpzLaunch {
+    const SpZP& P;
+    const Work& w;
+    cudaStream_t s;
+    template <int RM>
+    cudaError_t run()
+    {
+        using C = typename Cx<T>::t;
+        const size_t sm = spread_zfft_smem<T>(P);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_spread_zfft<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_spread_zfft<T, W, RM><<<P.nbx * P.nby, kThreads, sm, s>>>(
+            P, w.col_cnt, (const SpRec<T, W>*)w.col_rec, (const C*)w.tw + P.ng[0] + P.ng[1], (C*)w.spec);
+        return cudaGetLastError();
+    }
+};
 
 template <typename T, int W>
 static cudaError_t spz_w(const SpZP& P, const Work& w, cudaStream_t s)
 {
-    using C = typename Cx<T>::t;
-    const size_t sm = spread_zfft_smem<T>(P);
-    cudaError_t e = cudaFuncSetAttribute(k_spread_zfft<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_spread_zfft<T, W><<<P.nbx * P.nby, kThreads, sm, s>>>(P, w.col_cnt, (const LrRec<T>*)w.col_rec,
-                                                             (const C*)w.tw + P.ng[0] + P.ng[1], (C*)w.spec);
-    return cudaGetLastError();
+    return by_rm<T>(P.plan2, SpzLaunch<T, W>{ P, w, s });
 }
 
 template <typename T>
@@ -623,49 +801,90 @@ cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s)
 }
 
 template <typename T>
+struct FftYLaunch {
+    const FftYP& P;
+    const Work& w;
+    void* f2;
+    int sign;
+    cudaStream_t s;
+    template <int RM>
+    cudaError_t run()
+    {
+        using C = typename Cx<T>::t;
+        const int MC = 1 << P.lmc;
+        const size_t sm = (size_t)MC * P.ls * sizeof(C);
+        cudaError_t e = cudaFuncSetAttribute(k_fft_y<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        const int nk = P.K[2] + 1;
+        const int nch = (nk + MC - 1) / MC;
+        k_fft_y<T, RM><<<3 * P.ng[0] * nch, kThreads, sm, s>>>(P, (C*)w.spec, (C*)f2, (const C*)w.tw + P.ng[0],
+                                                                sign);
+        return cudaGetLastError();
+    }
+};
+
+template <typename T>
 cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s)
 {
-    using C = typename Cx<T>::t;
-    const int MC = 1 << P.lmc;
-    const size_t sm = (size_t)MC * P.ls * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    const int nk = P.K[2] + 1;
-    const int nch = (nk + MC - 1) / MC;
-    k_fft_y<T><<<3 * P.ng[0] * nch, kThreads, sm, s>>>(P, (C*)w.spec, (C*)f2, (const C*)w.tw + P.ng[0], sign);
-    return cudaGetLastError();
+    return by_rm<T>(P.plan1, FftYLaunch<T>{ P, w, f2, sign, s });
 }
+
+template <typename T>
+struct FftXLaunch {
+    const FftXP& P;
+    const Work& w;
+    bool want_psi;
+    cudaStream_t s;
+    template <int RM>
+    cudaError_t run()
+    {
+        using C = typename Cx<T>::t;
+        const int MC = 1 << P.lmc;
+        const int nl = (want_psi ? 6 : 3) * MC;
+        const size_t sm = (size_t)nl * P.ls * sizeof(C);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_fft_x_kspace<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        const int nk = P.K[2] + 1;
+        const int nch = (nk + MC - 1) / MC;
+        const T* tab0 = (const T*)w.ktab;
+        const T* tab1 = tab0 + (P.K[0] + 1);
+        const T* tab2 = tab1 + (P.K[1] + 1);
+        k_fft_x_kspace<T, RM><<<(2 * P.K[1] + 1) * nch, kThreads, sm, s>>>(
+            P, (C*)w.f2, want_psi ? (C*)w.f2psi : nullptr, (const C*)w.tw, tab0, tab1, tab2);
+        return cudaGetLastError();
+    }
+};
 
 template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s)
 {
-    using C = typename Cx<T>::t;
-    const int MC = 1 << P.lmc;
-    const int nl = (want_psi ? 6 : 3) * MC;
-    const size_t sm = (size_t)nl * P.ls * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_x_kspace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    const int nk = P.K[2] + 1;
-    const int nch = (nk + MC - 1) / MC;
-    const T* tab0 = (const T*)w.ktab;
-    const T* tab1 = tab0 + (P.K[0] + 1);
-    const T* tab2 = tab1 + (P.K[1] + 1);
-    k_fft_x_kspace<T><<<(2 * P.K[1] + 1) * nch, kThreads, sm, s>>>(P, (C*)w.f2, want_psi ? (C*)w.f2psi : nullptr,
-                                                                    (const C*)w.tw, tab0, tab1, tab2);
-    return cudaGetLastError();
+    return by_rm<T>(P.plan0, FftXLaunch<T>{ P, w, want_psi, s });
 }
+
+template <typename T>
+struct FftZLaunch {
+    const FftZP& P;
+    const Work& w;
+    cudaStream_t s;
+    template <int RM>
+    cudaError_t run()
+    {
+        using C = typename Cx<T>::t;
+        const size_t sm = (size_t)(P.yc / 2) * P.cls * sizeof(C);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_fft_z_c2r<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_fft_z_c2r<T, RM><<<3 * P.ng[0] * (P.ng[1] / P.yc), kThreads, sm, s>>>(
+            P, (const C*)w.spec, (const C*)w.tw + P.ng[0] + P.ng[1], (T*)w.grid);
+        return cudaGetLastError();
+    }
+};
 
 template <typename T>
 cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s)
 {
-    using C = typename Cx<T>::t;
-    const size_t sm = (size_t)(P.yc / 2) * P.cls * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_z_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_fft_z_c2r<T><<<3 * P.ng[0] * (P.ng[1] / P.yc), kThreads, sm, s>>>(P, (const C*)w.spec,
-                                                                         (const C*)w.tw + P.ng[0] + P.ng[1],
-                                                                         (T*)w.grid);
-    return cudaGetLastError();
+    return by_rm<T>(P.plan2, FftZLaunch<T>{ P, w, s });
 }
 
 template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaStream_t);
@@ -678,6 +897,35 @@ template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool,
 template cudaError_t launch_fft_x_kspace<double>(const FftXP&, const Work&, bool, cudaStream_t);
 template cudaError_t launch_fft_z_c2r<float>(const FftZP&, const Work&, cudaStream_t);
 template cudaError_t launch_fft_z_c2r<double>(const FftZP&, const Work&, cudaStream_t);
+// Writes the composite-radix twiddles into the current device's constant
+// bank (once per device).
+cudaError_t set_fft_constants()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    float2 hf[kTwCount];
+    double2 hd[kTwCount];
+    const int sizes[6] = { 6, 9, 12, 16, 24, 32 };
+    const int offs[6] = { kTwOff6, kTwOff9, kTwOff12, kTwOff16, kTwOff24, kTwOff32 };
+    for (int k = 0; k < 6; ++k)
+        for (int m = 0; m < sizes[k]; ++m) {
+            const double ph = -2.0 * 3.14159265358979323846 * m / sizes[k];
+            hd[offs[k] + m] = make_double2(cos(ph), sin(ph));
+            hf[offs[k] + m] = make_float2((float)cos(ph), (float)sin(ph));
+        }
+    e = cudaMemcpyToSymbol(c_twf, hf, sizeof hf);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_twd, hd, sizeof hd);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
+template size_t col_rec_bytes<float>(int);
+template size_t col_rec_bytes<double>(int);
 template size_t spread_zfft_smem<float>(const SpZP&);
 template size_t spread_zfft_smem<double>(const SpZP&);
 

@@ -75,13 +75,14 @@ def test_rk4_trajectory_matches_oracle(prec):
 
 
 def test_rk4_ring_translates_rigidly():
-    """Config-1 ring: the exact motion is a rigid translation along the axis
-    at the Kelvin speed (Eq. vortex_ring_velocity), which RK4 integrates
-    exactly.  The mean displacement over n steps matches n dt times the
-    oracle's velocity to the method's beta = 3.5 accuracy; per node, and for
-    the radius and the energy, the only departures are the method's own
-    velocity error at beta = 3.5 (its cubic mode truncation and the grid
-    break the ring's symmetry: speeds differ across nodes by ~3e-5)."""
+    """Config-1 ring: it travels along its axis at about the Kelvin speed
+    (Eq. vortex_ring_velocity).  The periodic images form a cubic lattice, so
+    the ring keeps only a four-fold symmetry and its node speeds differ by
+    ~3e-5 (in the oracle as on the GPU): the motion is a translation up to
+    that slow deformation.  The mean displacement over n steps matches n dt
+    times the oracle's mean velocity to the method's beta = 3.5 accuracy;
+    per node, and for the radius and the energy, the departures stay at the
+    size of that deformation."""
     B = _B()
     f = W.ring(N=64)
     p = B.make_params(f.L, M=32, Q=2, w=8, precision=B.BS_FP64, flags=B.BS_WANT_PSI)
@@ -102,7 +103,8 @@ def test_rk4_ring_translates_rigidly():
     g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 4, 2)
     vo, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
     vz = vo[:, 2].mean()
-    assert np.abs(vo[:, 2] - vz).max() < 1e-12 * abs(vz)  # the oracle keeps the symmetry
+    # the oracle keeps the four-fold symmetry of the ring in the cubic lattice
+    assert np.abs(vo[:, 2] - np.roll(vo[:, 2], 16)).max() < 1e-12 * abs(vz)
     dist = n * dt * abs(vz)
     assert dist > 0.05  # about 40% of a grid cell
     disp = got - f.nodes
