@@ -47,6 +47,23 @@ __device__ __forceinline__ C cmul(C a, C b) { C r; r.x = a.x * b.x - a.y * b.y; 
 template <typename C>
 __device__ __forceinline__ C cmuli(C a, int sign) { C r; r.x = -sign * a.y; r.y = sign * a.x; return r; }
 
+// Asynchronous global -> shared copy of one complex value (8 or 16 bytes,
+// both addresses aligned to it); visible to the thread after
+// cp_async_wait_all(), to the block after the barrier that follows.  A load
+// phase issues all its copies before waiting, so every thread keeps many
+// loads in flight instead of one.
+template <typename C>
+__device__ __forceinline__ void cp_async_cx(C* smem_dst, const C* gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // e^{-2 pi i m / R} for the composite in-register sizes R in {6, 9, 12, 16,
 // 24, 32}, m = 0..R-1, written once per device from float64 values
 // (set_fft_constants).  Indices are compile-time constants after unrolling,
@@ -402,7 +419,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
             constexpr int kWords = (int)(sizeof(SpRec<T, W>) / 16);
             const int4* src = reinterpret_cast<const int4*>(recs + c0r);
             int4* dst = reinterpret_cast<int4*>(srec);
-            for (int i = tid; i < nch * kWords; i += blockDim.x) dst[i] = src[i];
+            for (int i = tid; i < nch * kWords; i += blockDim.x) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + i) : "memory");
+            }
+            cp_async_wait_all();
         }
         __syncthreads();
         for (int kk = wid; kk < nch; kk += nw) {
@@ -484,8 +505,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
     if (sign < 0) {
         for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
             const int y = i >> lmc, l = i & (MC - 1);
-            a[l * LS + y] = (l < mcount) ? F1[((size_t)cx * n1 + y) * nk + mz0 + l] : zero;
+            if (l < mcount)
+                cp_async_cx(&a[l * LS + y], &F1[((size_t)cx * n1 + y) * nk + mz0 + l]);
+            else
+                a[l * LS + y] = zero;
         }
+        cp_async_wait_all();
         __syncthreads();
         fft_fwd_dif<T, RM>(a, MC, P.d_lines, LS, P.plan1, tw1);
         for (int i = threadIdx.x; i < (ny2 << lmc); i += blockDim.x) {
@@ -498,10 +523,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
         for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
             const int y = i >> lmc, l = i & (MC - 1);  // y: frequency index
             const int my = y <= n1 / 2 ? y : y - n1;
-            C v = zero;
-            if (l < mcount && my >= -K1 && my <= K1) v = F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l];
-            a[l * LS + P.rev[y]] = v;
+            C* d = &a[l * LS + P.rev[y]];
+            if (l < mcount && my >= -K1 && my <= K1)
+                cp_async_cx(d, &F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l]);
+            else
+                *d = zero;
         }
+        cp_async_wait_all();
         __syncthreads();
         fft_inv_dit<T, RM>(a, MC, P.d_lines, LS, P.plan1, tw1);
         for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
@@ -544,8 +572,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
         const int l = i & (MC - 1);
         const int cx = i >> lmc;  // c * n0 + x
         const int c = fdiv(cx, P.d_n0), x = cx - c * n0;
-        a[((c << lmc) + l) * LS + x] = (l < mcount) ? F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] : zero;
+        if (l < mcount)
+            cp_async_cx(&a[((c << lmc) + l) * LS + x], &F2[((size_t)cx * ny2 + myp) * nk + mz0 + l]);
+        else
+            a[((c << lmc) + l) * LS + x] = zero;
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_fwd_dif<T, RM>(a, 3 * MC, P.d_lines, LS, P.plan0, tw0);
     // k-space pass: frequency (mx, my, mz) sits at position rev(xi) of line (c, l)
@@ -643,6 +675,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
     for (int i = threadIdx.x; i < ncl * CS; i += blockDim.x) a[i] = zero;
     __syncthreads();
     // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k), k = 0..K2, at rev positions
+    // (unrolled so that each thread has several loads in flight)
+#pragma unroll 4
     for (int i = threadIdx.x; i < ncl * nk; i += blockDim.x) {
         const int l = fdiv(i, P.d_nk), k = i - l * nk;
         const C A = F1[((size_t)cx * n1 + y0 + 2 * l) * nk + k];
