@@ -6,7 +6,7 @@
 //
 // Sources are binned in cells of edge >= r_c/m (m = 3 in Sec. 5.3) and
 // sorted by cell with x fastest, so the 2m+1 cells of a row along x form one
-// contiguous range of the sorted array (two when the row wraps).  One thread
+// contiguous range of the sorted array (two when the row wraps).  One warp
 // per node walks the (2m+1)^2 rows around its cell.  Positions are cell
 // index + offset from the cell origin: the separation is
 // (integer cell difference) * h + (offset difference), which keeps T
@@ -35,13 +35,20 @@ __device__ __forceinline__ int cdiff(int a, int b, int n)
 template <typename T>
 __device__ __forceinline__ T erfc_t(T x) { return erfc(x); }
 
+// One warp per target node.  The lanes first list the source ranges of the
+// (2m+1)^2 neighbour rows (32 rows at a time; a row wrapping around the box
+// gives two ranges), prefix-sum their lengths, then stride through the
+// flattened candidate list, so every lane has work however short the rows
+// are.  Each lane finds the row of its candidate by a binary search over the
+// lanes' inclusive sums.  The per-lane partial sums are reduced at the end.
 template <typename T>
-__global__ void __launch_bounds__(128) k_short(ShortP P, const SrTgt<T>* __restrict__ tgt, const int* __restrict__ prev,
+__global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restrict__ tgt, const int* __restrict__ prev,
                                                const int* __restrict__ start, const SrRec<T>* __restrict__ src,
                                                T* __restrict__ vsr, T* __restrict__ psr)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.N) return;
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (j >= P.N) return;  // whole warps exit together
     const SrTgt<T> t = tgt[j];
     const int jp = prev[j];
     const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
@@ -57,71 +64,119 @@ __global__ void __launch_bounds__(128) k_short(ShortP P, const SrTgt<T>* __restr
     // neighbour ranges per axis: all cells when 2m+1 >= n
     const bool fullx = (2 * m + 1 >= nc0), fully = (2 * m + 1 >= nc1), fullz = (2 * m + 1 >= nc2);
     const int ny = fully ? nc1 : 2 * m + 1, nz = fullz ? nc2 : 2 * m + 1;
+    const int nrows = ny * nz;
+    // x-ranges of every row: one or two contiguous runs [xa0, xb0], [xa1, xb1]
+    int xa0, xb0, xa1 = 0, xb1 = -1;
+    if (fullx) {
+        xa0 = 0;
+        xb0 = nc0 - 1;
+    } else {
+        const int lo = cx - m, hi = cx + m;
+        if (lo < 0) {
+            xa0 = lo + nc0; xb0 = nc0 - 1; xa1 = 0; xb1 = hi;
+        } else if (hi >= nc0) {
+            xa0 = lo; xb0 = nc0 - 1; xa1 = 0; xb1 = hi - nc0;
+        } else {
+            xa0 = lo; xb0 = hi;
+        }
+    }
 
     T v0 = 0, v1 = 0, v2 = 0, p0 = 0, p1 = 0, p2 = 0;
-    for (int iz = 0; iz < nz; ++iz) {
-        const int zc = fullz ? iz : imod(cz - m + iz, nc2);
-        const T dzc = (T)cdiff(zc, cz, nc2) * h2;
-        for (int iy = 0; iy < ny; ++iy) {
+    for (int rb = 0; rb < nrows; rb += 32) {
+        // this lane's row
+        const int r = rb + lane;
+        int s0 = 0, n0 = 0, s1 = 0, n1r = 0, dyi = 0, dzi = 0;
+        if (r < nrows) {
+            const int iz = r / ny, iy = r - iz * ny;
+            const int zc = fullz ? iz : imod(cz - m + iz, nc2);
             const int yc = fully ? iy : imod(cy - m + iy, nc1);
-            const T dyc = (T)cdiff(yc, cy, nc1) * h1;
+            dzi = cdiff(zc, cz, nc2);
+            dyi = cdiff(yc, cy, nc1);
             const int row = (zc * nc1 + yc) * nc0;
-            // one or two contiguous x-ranges [xa0, xb0], [xa1, xb1]
-            int xa0, xb0, xa1 = 0, xb1 = -1;
-            if (fullx) {
-                xa0 = 0; xb0 = nc0 - 1;
-            } else {
-                const int lo = cx - m, hi = cx + m;
-                if (lo < 0) {
-                    xa0 = lo + nc0; xb0 = nc0 - 1; xa1 = 0; xb1 = hi;
-                } else if (hi >= nc0) {
-                    xa0 = lo; xb0 = nc0 - 1; xa1 = 0; xb1 = hi - nc0;
-                } else {
-                    xa0 = lo; xb0 = hi;
-                }
+            s0 = start[row + xa0];
+            n0 = start[row + xb0 + 1] - s0;
+            if (xb1 >= xa1) {
+                s1 = start[row + xa1];
+                n1r = start[row + xb1 + 1] - s1;
             }
-            const int nr = (xb1 >= xa1) ? 2 : 1;
-            for (int r = 0; r < nr; ++r) {
-                const int s0 = start[row + (r ? xa1 : xa0)], s1 = start[row + (r ? xb1 : xb0) + 1];
-                for (int k = s0; k < s1; ++k) {
-                    const SrRec<T> S = src[k];
-                    if (S.seg == j || S.seg == jp) continue;  // C_0 of the node (Eq. BS_on_vortex)
-                    T rx = (T)cdiff(S.cx, cx, nc0) * h0 + (S.o[0] - t.o[0]);
-                    T ry = dyc + (S.o[1] - t.o[1]);
-                    T rz = dzc + (S.o[2] - t.o[2]);
-                    // exact minimum image when a cell difference sits at n/2
-                    rx = rx > (T)0.5 * L0 ? rx - L0 : (rx < (T)-0.5 * L0 ? rx + L0 : rx);
-                    ry = ry > (T)0.5 * L1 ? ry - L1 : (ry < (T)-0.5 * L1 ? ry + L1 : ry);
-                    rz = rz > (T)0.5 * L2 ? rz - L2 : (rz < (T)-0.5 * L2 ? rz + L2 : rz);
-                    const T r2 = rx * rx + ry * ry + rz * rz;
-                    if (r2 >= rc2 || r2 == (T)0) continue;
-                    const T rr = sqrt(r2);
-                    const T x = alpha * rr;
-                    const T ec = erfc_t(x);
-                    const T g = ec + two_over_sqrtpi * x * exp(-x * x);
-                    const T ir = (T)1 / rr;
-                    const T fv = g * ir * ir * ir;
-                    v0 += fv * (ry * S.q[2] - rz * S.q[1]);
-                    v1 += fv * (rz * S.q[0] - rx * S.q[2]);
-                    v2 += fv * (rx * S.q[1] - ry * S.q[0]);
-                    if (P.want_psi) {
-                        const T fp = ec * ir;
-                        p0 += fp * S.q[0];
-                        p1 += fp * S.q[1];
-                        p2 += fp * S.q[2];
-                    }
-                }
+        }
+        // inclusive prefix sum of the lanes' candidate counts
+        int inc = n0 + n1r;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        for (int cb = 0; cb < total; cb += 32) {  // warp-uniform trip count: every shuffle has all lanes
+            const int c = cb + lane;
+            // owner lane: the first lane whose inclusive sum exceeds c
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int probe = __shfl_sync(0xffffffffu, inc, lo + step - 1);
+                if (probe <= c) lo += step;
+            }
+            lo = lo > 31 ? 31 : lo;
+            const int own_inc = __shfl_sync(0xffffffffu, inc, lo);
+            const int own_n0 = __shfl_sync(0xffffffffu, n0, lo);
+            const int own_n1 = __shfl_sync(0xffffffffu, n1r, lo);
+            const int own_s0 = __shfl_sync(0xffffffffu, s0, lo);
+            const int own_s1 = __shfl_sync(0xffffffffu, s1, lo);
+            const int own_dy = __shfl_sync(0xffffffffu, dyi, lo);
+            const int own_dz = __shfl_sync(0xffffffffu, dzi, lo);
+            if (c >= total) continue;
+            const int local = c - (own_inc - own_n0 - own_n1);
+            const int k = local < own_n0 ? own_s0 + local : own_s1 + (local - own_n0);
+            const SrRec<T> S = src[k];
+            if (S.seg == j || S.seg == jp) continue;  // C_0 of the node (Eq. BS_on_vortex)
+            T rx = (T)cdiff(S.cx, cx, nc0) * h0 + (S.o[0] - t.o[0]);
+            T ry = (T)own_dy * h1 + (S.o[1] - t.o[1]);
+            T rz = (T)own_dz * h2 + (S.o[2] - t.o[2]);
+            // exact minimum image when a cell difference sits at n/2
+            rx = rx > (T)0.5 * L0 ? rx - L0 : (rx < (T)-0.5 * L0 ? rx + L0 : rx);
+            ry = ry > (T)0.5 * L1 ? ry - L1 : (ry < (T)-0.5 * L1 ? ry + L1 : ry);
+            rz = rz > (T)0.5 * L2 ? rz - L2 : (rz < (T)-0.5 * L2 ? rz + L2 : rz);
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 >= rc2 || r2 == (T)0) continue;
+            const T rr = sqrt(r2);
+            const T x = alpha * rr;
+            const T ec = erfc_t(x);
+            const T g = ec + two_over_sqrtpi * x * exp(-x * x);
+            const T ir = (T)1 / rr;
+            const T fv = g * ir * ir * ir;
+            v0 += fv * (ry * S.q[2] - rz * S.q[1]);
+            v1 += fv * (rz * S.q[0] - rx * S.q[2]);
+            v2 += fv * (rx * S.q[1] - ry * S.q[0]);
+            if (P.want_psi) {
+                const T fp = ec * ir;
+                p0 += fp * S.q[0];
+                p1 += fp * S.q[1];
+                p2 += fp * S.q[2];
             }
         }
     }
-    const T pref = (T)P.pref;
-    vsr[3 * j + 0] = pref * v0;
-    vsr[3 * j + 1] = pref * v1;
-    vsr[3 * j + 2] = pref * v2;
-    if (P.want_psi) {
-        psr[3 * j + 0] = pref * p0;
-        psr[3 * j + 1] = pref * p1;
-        psr[3 * j + 2] = pref * p2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        if (P.want_psi) {
+            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+            p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+        }
+    }
+    if (lane == 0) {
+        const T pref = (T)P.pref;
+        vsr[3 * j + 0] = pref * v0;
+        vsr[3 * j + 1] = pref * v1;
+        vsr[3 * j + 2] = pref * v2;
+        if (P.want_psi) {
+            psr[3 * j + 0] = pref * p0;
+            psr[3 * j + 1] = pref * p1;
+            psr[3 * j + 2] = pref * p2;
+        }
     }
 }
 
@@ -129,8 +184,9 @@ template <typename T>
 cudaError_t launch_short(const ShortP& P, const Work& w, cudaStream_t s)
 {
     if (P.N <= 0) return cudaSuccess;
-    const int tb = 128;
-    k_short<T><<<(P.N + tb - 1) / tb, tb, 0, s>>>(P, (const SrTgt<T>*)w.tgt, w.prev, w.cell_cnt,
+    const int tb = 256;  // 8 targets per block, one warp each
+    const long long threads = 32LL * P.N;
+    k_short<T><<<(unsigned)((threads + tb - 1) / tb), tb, 0, s>>>(P, (const SrTgt<T>*)w.tgt, w.prev, w.cell_cnt,
                                                    (const SrRec<T>*)w.sr_sorted, (T*)w.vsr, (T*)w.psr);
     return cudaGetLastError();
 }
