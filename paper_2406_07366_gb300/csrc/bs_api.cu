@@ -278,7 +278,9 @@ int derive(const bs_params* p, Derived* d)
     const size_t mcx = 50000 / ((size_t)lines_x * (d->ng[0] + 1) * cb);
     d->lmcx = 0;
     while (d->lmcx < 4 && ((size_t)2 << d->lmcx) <= mcx) ++d->lmcx;
-    d->yc = (d->ng[1] % 16 == 0) ? 16 : 8;
+    // inverse z: 2 yc real lines per CTA as yc/2 complex ones; 16 complex
+    // lines at an odd stride keep every transform pass free of bank conflicts
+    d->yc = (rb == 4 && d->ng[1] % 32 == 0) ? 32 : ((d->ng[1] % 16 == 0) ? 16 : 8);
     d->lsz = d->ng[2] + 1;
     return BS_OK;
 }

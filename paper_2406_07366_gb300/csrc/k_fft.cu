@@ -201,11 +201,26 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
 {
     using C = typename Cx<T>::t;
     const int nb = n / R;
-    const int tot = nlines * nb;
+    // Shared memory serves 8-byte elements a half-warp (16 lanes) and 16-byte
+    // ones a quarter-warp (8 lanes) at a time.  A line count between half of
+    // that group and the group that does not divide it (12 of 16, 6 of 8) is
+    // numbered as a full group with the extra lines idle: then each group
+    // covers G lines at one offset, which an odd line stride spreads over all
+    // banks.
+    constexpr int G = sizeof(C) == 8 ? 16 : 8;
+    const bool pad = nlines < G && (G % nlines) != 0 && 2 * nlines > G;
+    const int tot = (pad ? G : nlines) * nb;
     const int L = st * R;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-        const int i = fdiv(idx, dl);
-        const int line = idx - i * nlines;
+        int i, line;
+        if (pad) {
+            i = idx / G;
+            line = idx & (G - 1);
+            if (line >= nlines) continue;
+        } else {
+            i = fdiv(idx, dl);
+            line = idx - i * nlines;
+        }
         const int b = fdiv(i, sd);
         const int j = i - b * st;
         C* p = buf + line * ls + b * L + j;
@@ -455,25 +470,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
     }
     __syncthreads();
     fft_fwd_dif<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
-    // separate the two real transforms and write modes 0..K2
+    // separate the two real transforms and write modes 0..K2.  A thread takes
+    // 8 consecutive modes of one line: with the lanes on consecutive groups,
+    // the digit-reversed positions of one instruction fall in distinct banks.
     const int nk = P.K[2] + 1;
-    for (int i = tid; i < nreal * nk; i += blockDim.x) {
-        const int rl = fdiv(i, P.d_nk), mz = i - rl * nk;
+    const int nq = (nk + 7) >> 3;
+    for (int i = tid; i < nreal * nq; i += blockDim.x) {
+        const int rl = i / nq, q = i - rl * nq;
         const int l = rl >> 1;
-        const C zk = cb[l * CS + P.rev[mz]];
-        const C zn = cb[l * CS + P.rev[mz == 0 ? 0 : n2 - mz]];
-        C o;
-        if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
-            o.x = (T)0.5 * (zk.x + zn.x);
-            o.y = (T)0.5 * (zk.y - zn.y);
-        } else {              // B_k = (Z_k - conj Z_{n-k}) / (2i)
-            o.x = (T)0.5 * (zk.y + zn.y);
-            o.y = (T)0.5 * (zn.x - zk.x);
-        }
         const int c = fdiv(rl, P.d_txy), rem = rl - c * txy;
         const int lx = fdiv(rem, P.d_ty), ly = rem - lx * Ty;
         const int x = bx * Tx + lx, y = by * Ty + ly;
-        F1[(((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk + mz] = o;
+        C* dst = F1 + (((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int mz = 8 * q + d;
+            if (mz >= nk) break;
+            const C zk = cb[l * CS + P.rev[mz]];
+            const C zn = cb[l * CS + P.rev[mz == 0 ? 0 : n2 - mz]];
+            C o;
+            if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
+                o.x = (T)0.5 * (zk.x + zn.x);
+                o.y = (T)0.5 * (zk.y - zn.y);
+            } else {              // B_k = (Z_k - conj Z_{n-k}) / (2i)
+                o.x = (T)0.5 * (zk.y + zn.y);
+                o.y = (T)0.5 * (zn.x - zk.x);
+            }
+            dst[mz] = o;
+        }
     }
 }
 
@@ -568,6 +592,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
     C zero;
     zero.x = 0;
     zero.y = 0;
+    // the MC modes of one (c, x) are adjacent in F2: lanes on them first, so a
+    // warp reads whole 32-byte sectors
     for (int i = threadIdx.x; i < ((3 * n0) << lmc); i += blockDim.x) {
         const int l = i & (MC - 1);
         const int cx = i >> lmc;  // c * n0 + x
@@ -584,52 +610,59 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
     const int my = myp - K1;
     const int amy = my < 0 ? -my : my;
     double esum = 0.0;  // energy of this thread's modes (float64 reduction)
-    for (int i = threadIdx.x; i < (n0 << lmc); i += blockDim.x) {
-        const int l = i & (MC - 1), xi = i >> lmc;
-        const int mx = xi <= n0 / 2 ? xi : xi - n0;
-        const int amx = mx < 0 ? -mx : mx;
+    // a thread takes 8 consecutive x frequencies of one line, the lanes on
+    // consecutive groups (distinct banks at the digit-reversed positions)
+    const int nq = n0 >> 3;
+    for (int i = threadIdx.x; i < nq * MC; i += blockDim.x) {
+        const int l = i / nq, q = i - l * nq;
         const int mz = mz0 + l;
-        const int pos = P.rev[xi];
-        C* r0 = a + ((0 * MC + l) * LS + pos);
-        C* r1 = a + ((1 * MC + l) * LS + pos);
-        C* r2 = a + ((2 * MC + l) * LS + pos);
-        if (l >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
-            *r0 = zero;
-            *r1 = zero;
-            *r2 = zero;
-            if (want_psi) {
-                a[(3 * MC + l) * LS + pos] = zero;
-                a[(4 * MC + l) * LS + pos] = zero;
-                a[(5 * MC + l) * LS + pos] = zero;
+#pragma unroll 2
+        for (int d = 0; d < 8; ++d) {
+            const int xi = 8 * q + d;
+            const int mx = xi <= n0 / 2 ? xi : xi - n0;
+            const int amx = mx < 0 ? -mx : mx;
+            const int pos = P.rev[xi];
+            C* r0 = a + ((0 * MC + l) * LS + pos);
+            C* r1 = a + ((1 * MC + l) * LS + pos);
+            C* r2 = a + ((2 * MC + l) * LS + pos);
+            if (l >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
+                *r0 = zero;
+                *r1 = zero;
+                *r2 = zero;
+                if (want_psi) {
+                    a[(3 * MC + l) * LS + pos] = zero;
+                    a[(4 * MC + l) * LS + pos] = zero;
+                    a[(5 * MC + l) * LS + pos] = zero;
+                }
+                continue;
             }
-            continue;
-        }
-        C w0 = *r0, w1 = *r1, w2 = *r2;
-        const T k0 = (T)(P.kk[0] * mx), k1 = (T)(P.kk[1] * my), k2 = (T)(P.kk[2] * mz);
-        const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
-        const T mult = (T)P.scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
-        if (P.energy) {
-            // (1/2) e^{-k^2/4a^2} |omega|^2 / k^2 = (kappa/V) mult |F|^2 / 2; the
-            // half spectrum holds the pair (k, -k) once when mz > 0
-            const double f2 = (double)w0.x * w0.x + (double)w0.y * w0.y + (double)w1.x * w1.x +
-                              (double)w1.y * w1.y + (double)w2.x * w2.x + (double)w2.y * w2.y;
-            esum += (mz > 0 ? 1.0 : 0.5) * P.scale * (double)mult * f2;
-        }
-        w0.x *= mult; w0.y *= mult;
-        w1.x *= mult; w1.y *= mult;
-        w2.x *= mult; w2.y *= mult;
-        // i k x w
-        const T cr0 = k1 * w2.x - k2 * w1.x, ci0 = k1 * w2.y - k2 * w1.y;
-        const T cr1 = k2 * w0.x - k0 * w2.x, ci1 = k2 * w0.y - k0 * w2.y;
-        const T cr2 = k0 * w1.x - k1 * w0.x, ci2 = k0 * w1.y - k1 * w0.y;
-        C o;
-        o.x = -ci0; o.y = cr0; *r0 = o;
-        o.x = -ci1; o.y = cr1; *r1 = o;
-        o.x = -ci2; o.y = cr2; *r2 = o;
-        if (want_psi) {
-            a[(3 * MC + l) * LS + pos] = w0;
-            a[(4 * MC + l) * LS + pos] = w1;
-            a[(5 * MC + l) * LS + pos] = w2;
+            C w0 = *r0, w1 = *r1, w2 = *r2;
+            const T k0 = (T)(P.kk[0] * mx), k1 = (T)(P.kk[1] * my), k2 = (T)(P.kk[2] * mz);
+            const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
+            const T mult = (T)P.scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
+            if (P.energy) {
+                // (1/2) e^{-k^2/4a^2} |omega|^2 / k^2 = (kappa/V) mult |F|^2 / 2; the
+                // half spectrum holds the pair (k, -k) once when mz > 0
+                const double f2 = (double)w0.x * w0.x + (double)w0.y * w0.y + (double)w1.x * w1.x +
+                                  (double)w1.y * w1.y + (double)w2.x * w2.x + (double)w2.y * w2.y;
+                esum += (mz > 0 ? 1.0 : 0.5) * P.scale * (double)mult * f2;
+            }
+            w0.x *= mult; w0.y *= mult;
+            w1.x *= mult; w1.y *= mult;
+            w2.x *= mult; w2.y *= mult;
+            // i k x w
+            const T cr0 = k1 * w2.x - k2 * w1.x, ci0 = k1 * w2.y - k2 * w1.y;
+            const T cr1 = k2 * w0.x - k0 * w2.x, ci1 = k2 * w0.y - k0 * w2.y;
+            const T cr2 = k0 * w1.x - k1 * w0.x, ci2 = k0 * w1.y - k1 * w0.y;
+            C o;
+            o.x = -ci0; o.y = cr0; *r0 = o;
+            o.x = -ci1; o.y = cr1; *r1 = o;
+            o.x = -ci2; o.y = cr2; *r2 = o;
+            if (want_psi) {
+                a[(3 * MC + l) * LS + pos] = w0;
+                a[(4 * MC + l) * LS + pos] = w1;
+                a[(5 * MC + l) * LS + pos] = w2;
+            }
         }
     }
     if (P.energy) {
@@ -674,25 +707,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
     zero.y = 0;
     for (int i = threadIdx.x; i < ncl * CS; i += blockDim.x) a[i] = zero;
     __syncthreads();
-    // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k), k = 0..K2, at rev positions
-    // (unrolled so that each thread has several loads in flight)
-#pragma unroll 4
-    for (int i = threadIdx.x; i < ncl * nk; i += blockDim.x) {
-        const int l = fdiv(i, P.d_nk), k = i - l * nk;
-        const C A = F1[((size_t)cx * n1 + y0 + 2 * l) * nk + k];
-        const C Bv = F1[((size_t)cx * n1 + y0 + 2 * l + 1) * nk + k];
-        C z;
-        if (k == 0) {
-            z.x = A.x;
-            z.y = Bv.x;
-            a[l * CS] = z;
-        } else {
-            z.x = A.x - Bv.y;
-            z.y = A.y + Bv.x;
-            a[l * CS + P.rev[k]] = z;
-            z.x = A.x + Bv.y;
-            z.y = -A.y + Bv.x;
-            a[l * CS + P.rev[n2 - k]] = z;
+    // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k), k = 0..K2, at rev
+    // positions; a thread takes 8 consecutive k of one line pair (distinct
+    // banks per instruction, 16 loads in flight)
+    const int nq = (nk + 7) >> 3;
+    for (int i = threadIdx.x; i < ncl * nq; i += blockDim.x) {
+        const int l = i / nq, q = i - l * nq;
+        const C* rowA = F1 + ((size_t)cx * n1 + y0 + 2 * l) * nk;
+        const C* rowB = rowA + nk;
+        C A[8], Bv[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int k = 8 * q + d;
+            if (k < nk) {
+                A[d] = rowA[k];
+                Bv[d] = rowB[k];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int k = 8 * q + d;
+            if (k >= nk) break;
+            C z;
+            if (k == 0) {
+                z.x = A[d].x;
+                z.y = Bv[d].x;
+                a[l * CS] = z;
+            } else {
+                z.x = A[d].x - Bv[d].y;
+                z.y = A[d].y + Bv[d].x;
+                a[l * CS + P.rev[k]] = z;
+                z.x = A[d].x + Bv[d].y;
+                z.y = -A[d].y + Bv[d].x;
+                a[l * CS + P.rev[n2 - k]] = z;
+            }
         }
     }
     __syncthreads();
