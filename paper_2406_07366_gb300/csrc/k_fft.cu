@@ -93,11 +93,13 @@ template <> struct Split<16> { static constexpr int A = 4, B = 4; };
 template <> struct Split<24> { static constexpr int A = 8, B = 3; };
 template <> struct Split<32> { static constexpr int A = 8, B = 4; };
 
-// In-register DFT of size R with exponent sign (+1 or -1):
-// x[k] <- sum_n x[n] e^{sign 2 pi i n k / R}, natural order in and out.
-template <typename T, int R>
-__device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
+// In-register DFT of size R with exponent sign S (+1 or -1, a compile-time
+// constant so that every sign folds into the constants):
+// x[k] <- sum_n x[n] e^{S 2 pi i n k / R}, natural order in and out.
+template <typename T, int R, int S>
+__device__ __forceinline__ void dft(typename Cx<T>::t* x)
 {
+    constexpr int sign = S;
     using C = typename Cx<T>::t;
     if constexpr (R == 2) {
         const C a = x[0], b = x[1];
@@ -126,8 +128,8 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
     } else if constexpr (R == 8) {
         C e[4] = { x[0], x[2], x[4], x[6] };
         C o[4] = { x[1], x[3], x[5], x[7] };
-        dft<T, 4>(e, sign);
-        dft<T, 4>(o, sign);
+        dft<T, 4, S>(e);
+        dft<T, 4, S>(o);
         const T r2 = (T)0.70710678118654752440;
         // w8^m = e^{sign 2 pi i m / 8}
         C w1;
@@ -154,7 +156,7 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
             C t[A];
 #pragma unroll
             for (int a = 0; a < A; ++a) t[a] = x[a * B + b];
-            dft<T, A>(t, sign);
+            dft<T, A, S>(t);
 #pragma unroll
             for (int k1 = 0; k1 < A; ++k1) {
                 C v = t[k1];
@@ -169,7 +171,7 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
                         v = cmuli(v, -sign);
                     } else {
                         C w = ctw<T>(TwOff<R>::v + m);  // e^{-2 pi i m / R}
-                        if (sign > 0) w.y = -w.y;
+                        if constexpr (S > 0) w.y = -w.y;
                         v = cmul(v, w);
                     }
                 }
@@ -181,7 +183,7 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
             C t[B];
 #pragma unroll
             for (int b = 0; b < B; ++b) t[b] = y[k1 * B + b];
-            dft<T, B>(t, sign);
+            dft<T, B, S>(t);
 #pragma unroll
             for (int k2 = 0; k2 < B; ++k2) x[k1 + A * k2] = t[k2];
         }
@@ -197,8 +199,9 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x, int sign)
 template <typename T, int R, bool DIF>
 __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, int nlines, const FastDiv& dl, int ls,
                                          int n, int st, const FastDiv& sd, int tws,
-                                         const typename Cx<T>::t* __restrict__ tw, int sign)
+                                         const typename Cx<T>::t* __restrict__ tw)
 {
+    constexpr int S = DIF ? -1 : 1;  // forward transforms by DIF, inverse by DIT
     using C = typename Cx<T>::t;
     const int nb = n / R;
     // Shared memory serves 8-byte elements a half-warp (16 lanes) and 16-byte
@@ -231,16 +234,16 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
 #pragma unroll
             for (int q = 1; q < R; ++q) {
                 C w = tw[j * q * tws];
-                if (sign > 0) w.y = -w.y;
+                if constexpr (S > 0) w.y = -w.y;
                 x[q] = cmul(x[q], w);
             }
         }
-        dft<T, R>(x, sign);
+        dft<T, R, S>(x);
         if (DIF && j > 0) {
 #pragma unroll
             for (int q = 1; q < R; ++q) {
                 C w = tw[j * q * tws];
-                if (sign > 0) w.y = -w.y;
+                if constexpr (S > 0) w.y = -w.y;
                 x[q] = cmul(x[q], w);
             }
         }
@@ -251,11 +254,10 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
 
 template <typename T, bool DIF, int RM>
 __device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls,
-                                          const FftPlan& pl, int s, const typename Cx<T>::t* __restrict__ tw,
-                                          int sign)
+                                          const FftPlan& pl, int s, const typename Cx<T>::t* __restrict__ tw)
 {
     const int R = pl.r[s];
-#define BSW_PASS(RR) fft_pass<T, RR, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw, sign)
+#define BSW_PASS(RR) fft_pass<T, RR, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw)
     // only the radices up to RM are compiled into this kernel (register budget)
     switch (R) {
     case 32: if constexpr (RM >= 32) BSW_PASS(32); break;
@@ -276,19 +278,19 @@ __device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, co
 // Forward transform (decimation in frequency), natural order in, frequency
 // k left at position rev(k).
 template <typename T, int RM>
-__device__ void fft_fwd_dif(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
+__device__ __forceinline__ void fft_fwd_dif(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
-    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true, RM>(buf, nlines, dl, ls, pl, s, tw, -1);
+    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true, RM>(buf, nlines, dl, ls, pl, s, tw);
 }
 
 // Inverse transform (decimation in time), frequency k taken at position
 // rev(k), natural order out.
 template <typename T, int RM>
-__device__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
+__device__ __forceinline__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
-    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false, RM>(buf, nlines, dl, ls, pl, s, tw, +1);
+    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false, RM>(buf, nlines, dl, ls, pl, s, tw);
 }
 
 
