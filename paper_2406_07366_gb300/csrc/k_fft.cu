@@ -196,6 +196,32 @@ __device__ __forceinline__ void dft(typename Cx<T>::t* x)
 //   dit: multiply input q by w_L^{j q}, then DFT_R.
 // Butterflies are numbered line-fastest, so consecutive threads touch
 // different lines at the same offset (distinct banks, one twiddle address).
+// x[q] *= w^q, q = 1..R-1, w = e^{S 2 pi i m / n} taken from the float64-
+// computed table tw[m] = e^{-2 pi i m / n}.  Only w and w^4 are read; the
+// other powers are products of at most three table values (w^2 = w w,
+// w^3 = w^2 w, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3), which keeps the
+// rounding within a few units in the last place.
+template <typename T, int R, int S>
+__device__ __forceinline__ void apply_twiddles(typename Cx<T>::t* x, const typename Cx<T>::t* __restrict__ tw, int m)
+{
+    using C = typename Cx<T>::t;
+    C w[R];
+    w[1] = tw[m];
+    if constexpr (S > 0) w[1].y = -w[1].y;
+    if constexpr (R > 2) w[2] = cmul(w[1], w[1]);
+    if constexpr (R > 3) w[3] = cmul(w[2], w[1]);
+    if constexpr (R > 4) {
+        w[4] = tw[4 * m];
+        if constexpr (S > 0) w[4].y = -w[4].y;
+    }
+    if constexpr (R > 5) w[5] = cmul(w[4], w[1]);
+    if constexpr (R > 6) w[6] = cmul(w[4], w[2]);
+    if constexpr (R > 7) w[7] = cmul(w[4], w[3]);
+    static_assert(R <= 8, "twiddle powers are built for radices up to 8");
+#pragma unroll
+    for (int q = 1; q < R; ++q) x[q] = cmul(x[q], w[q]);
+}
+
 template <typename T, int R, bool DIF>
 __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, int nlines, const FastDiv& dl, int ls,
                                          int n, int st, const FastDiv& sd, int tws,
@@ -230,23 +256,9 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
         C x[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = p[q * st];
-        if (!DIF && j > 0) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) {
-                C w = tw[j * q * tws];
-                if constexpr (S > 0) w.y = -w.y;
-                x[q] = cmul(x[q], w);
-            }
-        }
+        if (!DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * tws);
         dft<T, R, S>(x);
-        if (DIF && j > 0) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) {
-                C w = tw[j * q * tws];
-                if constexpr (S > 0) w.y = -w.y;
-                x[q] = cmul(x[q], w);
-            }
-        }
+        if (DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * tws);
 #pragma unroll
         for (int q = 0; q < R; ++q) p[q * st] = x[q];
     }
@@ -528,40 +540,49 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
     C zero;
     zero.x = 0;
     zero.y = 0;
+    // MC divides the block: every thread keeps one mode l and walks the lines'
+    // positions with a fixed step, so the global addresses advance by a
+    // pointer increment instead of a 64-bit index product per element.
+    const int l = threadIdx.x & (MC - 1);
+    const int r0 = threadIdx.x >> lmc, rstep = blockDim.x >> lmc;
+    const bool live = l < mcount;
+    C* const al = a + l * LS;
     if (sign < 0) {
-        for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
-            const int y = i >> lmc, l = i & (MC - 1);
-            if (l < mcount)
-                cp_async_cx(&a[l * LS + y], &F1[((size_t)cx * n1 + y) * nk + mz0 + l]);
+        const C* src = F1 + ((size_t)cx * n1 + r0) * nk + mz0 + l;
+        const size_t sstep = (size_t)rstep * nk;
+        for (int y = r0; y < n1; y += rstep, src += sstep) {
+            if (live)
+                cp_async_cx(&al[y], src);
             else
-                a[l * LS + y] = zero;
+                al[y] = zero;
         }
         cp_async_wait_all();
         __syncthreads();
         fft_fwd_dif<T, RM>(a, MC, P.d_lines, LS, P.plan1, tw1);
-        for (int i = threadIdx.x; i < (ny2 << lmc); i += blockDim.x) {
-            const int myp = i >> lmc, l = i & (MC - 1);
-            if (l >= mcount) continue;
-            const int my = myp - K1;
-            F2[((size_t)cx * ny2 + myp) * nk + mz0 + l] = a[l * LS + P.rev[my < 0 ? my + n1 : my]];
+        if (live) {
+            C* dst = F2 + ((size_t)cx * ny2 + r0) * nk + mz0 + l;
+            for (int myp = r0; myp < ny2; myp += rstep, dst += sstep) {
+                const int my = myp - K1;
+                *dst = al[P.rev[my < 0 ? my + n1 : my]];
+            }
         }
     } else {
-        for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
-            const int y = i >> lmc, l = i & (MC - 1);  // y: frequency index
+        const C* src = F2 + ((size_t)cx * ny2) * nk + mz0 + l;
+        for (int y = r0; y < n1; y += rstep) {  // y: frequency index
             const int my = y <= n1 / 2 ? y : y - n1;
-            C* d = &a[l * LS + P.rev[y]];
-            if (l < mcount && my >= -K1 && my <= K1)
-                cp_async_cx(d, &F2[((size_t)cx * ny2 + (my + K1)) * nk + mz0 + l]);
+            C* d = &al[P.rev[y]];
+            if (live && my >= -K1 && my <= K1)
+                cp_async_cx(d, src + (size_t)(my + K1) * nk);
             else
                 *d = zero;
         }
         cp_async_wait_all();
         __syncthreads();
         fft_inv_dit<T, RM>(a, MC, P.d_lines, LS, P.plan1, tw1);
-        for (int i = threadIdx.x; i < (n1 << lmc); i += blockDim.x) {
-            const int y = i >> lmc, l = i & (MC - 1);
-            if (l >= mcount) continue;
-            F1[((size_t)cx * n1 + y) * nk + mz0 + l] = a[l * LS + y];
+        if (live) {
+            C* dst = F1 + ((size_t)cx * n1 + r0) * nk + mz0 + l;
+            const size_t dstep = (size_t)rstep * nk;
+            for (int y = r0; y < n1; y += rstep, dst += dstep) *dst = al[y];
         }
     }
 }
@@ -595,15 +616,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
     zero.x = 0;
     zero.y = 0;
     // the MC modes of one (c, x) are adjacent in F2: lanes on them first, so a
-    // warp reads whole 32-byte sectors
-    for (int i = threadIdx.x; i < ((3 * n0) << lmc); i += blockDim.x) {
-        const int l = i & (MC - 1);
-        const int cx = i >> lmc;  // c * n0 + x
-        const int c = fdiv(cx, P.d_n0), x = cx - c * n0;
-        if (l < mcount)
-            cp_async_cx(&a[((c << lmc) + l) * LS + x], &F2[((size_t)cx * ny2 + myp) * nk + mz0 + l]);
-        else
-            a[((c << lmc) + l) * LS + x] = zero;
+    // warp reads whole 32-byte sectors.  MC divides the block, so a thread
+    // keeps its mode l and steps x by a fixed amount (pointer increments).
+    const int l = threadIdx.x & (MC - 1);
+    const int x0 = threadIdx.x >> lmc, xstep = blockDim.x >> lmc;
+    const bool live = l < mcount;
+    const size_t gstep = (size_t)xstep * ny2 * nk;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        C* const al = a + ((c << lmc) + l) * LS;
+        const C* src = F2 + (((size_t)c * n0 + x0) * ny2 + myp) * nk + mz0 + l;
+        for (int x = x0; x < n0; x += xstep, src += gstep) {
+            if (live)
+                cp_async_cx(&al[x], src);
+            else
+                al[x] = zero;
+        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -615,33 +643,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
     // a thread takes 8 consecutive x frequencies of one line, the lanes on
     // consecutive groups (distinct banks at the digit-reversed positions)
     const int nq = n0 >> 3;
+    const T kk0 = (T)P.kk[0], kk1 = (T)P.kk[1], kk2 = (T)P.kk[2];  // 2 pi / L_d
+    const T scale = (T)P.scale;
     for (int i = threadIdx.x; i < nq * MC; i += blockDim.x) {
-        const int l = i / nq, q = i - l * nq;
-        const int mz = mz0 + l;
+        const int lk = i / nq, q = i - lk * nq;
+        const int mz = mz0 + lk;
 #pragma unroll 2
         for (int d = 0; d < 8; ++d) {
             const int xi = 8 * q + d;
             const int mx = xi <= n0 / 2 ? xi : xi - n0;
             const int amx = mx < 0 ? -mx : mx;
             const int pos = P.rev[xi];
-            C* r0 = a + ((0 * MC + l) * LS + pos);
-            C* r1 = a + ((1 * MC + l) * LS + pos);
-            C* r2 = a + ((2 * MC + l) * LS + pos);
-            if (l >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
+            C* r0 = a + ((0 * MC + lk) * LS + pos);
+            C* r1 = a + ((1 * MC + lk) * LS + pos);
+            C* r2 = a + ((2 * MC + lk) * LS + pos);
+            if (lk >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
                 *r0 = zero;
                 *r1 = zero;
                 *r2 = zero;
                 if (want_psi) {
-                    a[(3 * MC + l) * LS + pos] = zero;
-                    a[(4 * MC + l) * LS + pos] = zero;
-                    a[(5 * MC + l) * LS + pos] = zero;
+                    a[(3 * MC + lk) * LS + pos] = zero;
+                    a[(4 * MC + lk) * LS + pos] = zero;
+                    a[(5 * MC + lk) * LS + pos] = zero;
                 }
                 continue;
             }
             C w0 = *r0, w1 = *r1, w2 = *r2;
-            const T k0 = (T)(P.kk[0] * mx), k1 = (T)(P.kk[1] * my), k2 = (T)(P.kk[2] * mz);
+            const T k0 = kk0 * (T)mx, k1 = kk1 * (T)my, k2 = kk2 * (T)mz;
             const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
-            const T mult = (T)P.scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
+            const T mult = scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
             if (P.energy) {
                 // (1/2) e^{-k^2/4a^2} |omega|^2 / k^2 = (kappa/V) mult |F|^2 / 2; the
                 // half spectrum holds the pair (k, -k) once when mz > 0
@@ -661,9 +691,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
             o.x = -ci1; o.y = cr1; *r1 = o;
             o.x = -ci2; o.y = cr2; *r2 = o;
             if (want_psi) {
-                a[(3 * MC + l) * LS + pos] = w0;
-                a[(4 * MC + l) * LS + pos] = w1;
-                a[(5 * MC + l) * LS + pos] = w2;
+                a[(3 * MC + lk) * LS + pos] = w0;
+                a[(4 * MC + lk) * LS + pos] = w1;
+                a[(5 * MC + lk) * LS + pos] = w2;
             }
         }
     }
@@ -674,14 +704,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
     }
     __syncthreads();
     fft_inv_dit<T, RM>(a, (want_psi ? 6 : 3) * MC, want_psi ? P.d_lines_psi : P.d_lines, LS, P.plan0, tw0);
-    for (int i = threadIdx.x; i < ((3 * n0) << lmc); i += blockDim.x) {
-        const int l = i & (MC - 1);
-        if (l >= mcount) continue;
-        const int cx = i >> lmc;
-        const int c = fdiv(cx, P.d_n0), x = cx - c * n0;
-        const size_t g = ((size_t)cx * ny2 + myp) * nk + mz0 + l;
-        F2[g] = a[((c << lmc) + l) * LS + x];
-        if (want_psi) F2psi[g] = a[(((3 + c) << lmc) + l) * LS + x];
+    if (live) {
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            const C* al = a + ((c << lmc) + l) * LS;
+            const C* ap = a + (((3 + c) << lmc) + l) * LS;
+            const size_t g0 = (((size_t)c * n0 + x0) * ny2 + myp) * nk + mz0 + l;
+            C* dst = F2 + g0;
+            C* dpsi = want_psi ? F2psi + g0 : nullptr;
+            for (int x = x0; x < n0; x += xstep, dst += gstep) {
+                *dst = al[x];
+                if (want_psi) {
+                    *dpsi = ap[x];
+                    dpsi += gstep;
+                }
+            }
+        }
     }
 }
 
@@ -750,10 +788,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
     const size_t gsz = (size_t)P.ng[0] * n1 * n2;
     const int c = fdiv(cx, P.d_n0), x = cx - c * P.ng[0];
     T* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
+    // the CTA's YC rows of n2 reals are contiguous in the grid
     for (int i = threadIdx.x; i < YC * n2; i += blockDim.x) {
         const int yl = fdiv(i, P.d_n2), z = i - yl * n2;
         const C v = a[(yl >> 1) * CS + z];
-        gout[(size_t)yl * n2 + z] = (yl & 1) ? v.y : v.x;
+        gout[i] = (yl & 1) ? v.y : v.x;
     }
 }
 
