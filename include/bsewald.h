@@ -269,6 +269,28 @@ int bs_batch_status(bs_batch* b);
 int bs_batch_member(bs_batch* b, int i, bs_ctx** member);
 void bs_batch_destroy(bs_batch* b);
 
+/*
+ * bs_autotune_alpha -- pick the Ewald parameter by timing (Sec. 5.3 sets
+ * alpha = C_beta N^(1/3) / L with C_beta fitted to CPU timings; the balance
+ * of the short- and long-range costs differs on a GPU).  The accuracy
+ * coefficient beta = base->alpha * base->rc is kept.  For each candidate
+ * cbeta[i]: alpha = cbeta[i] N^(1/3) / min L (at least 2 beta / min L, so
+ * rc <= L/2), M the smallest odd count with k_max >= 2 beta alpha, alpha then
+ * re-derived from k_max and rc = beta / alpha; every other field comes from
+ * *base.  Each candidate context evaluates the filaments (offsets, closing
+ * as bs_set_filaments; nodes on the device, N x 3) once to warm up and then
+ * reps times on an internal stream, timed with CUDA events.
+ *   best   (host) the fastest candidate's parameters
+ *   ms_out (host, ncand, or NULL) mean milliseconds per evaluation, -1 for
+ *          candidates not reached after an error
+ * Allocates and frees one context at a time (and an N x 3 scratch); run it
+ * before other work on the device, not inside a stream capture.  Errors:
+ * BS_ERR_ARG, the codes of bs_create / bs_set_filaments / bs_compute,
+ * BS_ERR_CUDA.
+ */
+int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t* offsets, const int32_t* closing,
+                      const double* nodes, int ncand, const double* cbeta, int reps, bs_params* best, float* ms_out);
+
 /* Synchronise the stream and return the device status word as a status
  * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY); clears it. */
 int bs_status(bs_ctx* ctx);

@@ -36,7 +36,8 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error",
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
-           "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch"]
+           "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
+           "bs_autotune_alpha"]
 
 
 class bs_params(ctypes.Structure):
@@ -95,6 +96,8 @@ def _load():
         "bs_rk4_step": ([vp, vp, ctypes.c_double], ctypes.c_int),
         "bs_rk4_capture": ([vp, vp, ctypes.c_double], ctypes.c_int),
         "bs_rk4_launch": ([vp, ctypes.c_int], ctypes.c_int),
+        "bs_autotune_alpha": ([P(bs_params), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32), vp, ctypes.c_int,
+                               P(ctypes.c_double), ctypes.c_int, P(bs_params), P(ctypes.c_float)], ctypes.c_int),
         "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
@@ -228,6 +231,21 @@ def bs_rk4_capture(ctx, nodes, dt):
 
 def bs_rk4_launch(ctx, nsteps):
     _check(lib().bs_rk4_launch(ctx, int(nsteps)))
+
+
+def bs_autotune_alpha(base, offsets, closing, nodes, cbeta, reps=3):
+    """Time each candidate C_beta on these filaments; returns (best params, ms list)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nfil = off.size - 1
+    cl = None if closing is None else np.ascontiguousarray(closing, dtype=np.int32).reshape(nfil, 3)
+    cb = np.ascontiguousarray(cbeta, dtype=np.float64)
+    ms = np.zeros(cb.size, dtype=np.float32)
+    best = bs_params()
+    _check(lib().bs_autotune_alpha(ctypes.byref(base), nfil, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  _ptr(nodes), cb.size, cb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  int(reps), ctypes.byref(best), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return best, [float(x) for x in ms]
 
 
 def kelvin_wave_period(lam, kappa=1.0, a=1e-6, delta=0.25):

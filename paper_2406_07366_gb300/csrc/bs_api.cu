@@ -502,6 +502,11 @@ void fill_geom(const bs_ctx* c, GeomP& G)
     G.alpha = p.alpha;
     G.w = p.nufft_w;
     G.seg_max = 0.25 * std::min(p.L[0], std::min(p.L[1], p.L[2]));
+    for (int k = 0; k < 3; ++k) {
+        G.iL[k] = 1.0 / p.L[k];
+        G.ihc[k] = 1.0 / d.hc[k];
+        G.ihg[k] = 1.0 / d.hg[k];
+    }
     G.want_psi = (p.flags & BS_WANT_PSI) ? 1 : 0;
 }
 
@@ -712,6 +717,8 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         I.ng[k] = d.ng[k];
         I.hg[k] = d.hg[k];
         I.L[k] = p.L[k];
+        I.iL[k] = 1.0 / p.L[k];
+        I.ihg[k] = 1.0 / d.hg[k];
     }
     I.w = p.nufft_w;
     I.zeta = d.zeta;
@@ -1411,3 +1418,79 @@ int bs_batch_member(bs_batch* b, int i, bs_ctx** member)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Choice of the Ewald parameter by measurement (Sec. 5.3 picks alpha =
+// C_beta N^(1/3) / L from CPU timings; the balance between the short- and
+// long-range parts differs on this GPU, so it is measured here).
+// ---------------------------------------------------------------------------
+extern "C" int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t* offsets, const int32_t* closing,
+                                 const double* nodes, int ncand, const double* cbeta, int reps, bs_params* best,
+                                 float* ms_out)
+{
+    if (!base || !cbeta || !best || !nodes || ncand <= 0 || reps <= 0 || nfil <= 0 || !offsets)
+        return fail(BS_ERR_ARG, "bad autotune arguments");
+    const double beta = base->alpha * base->rc;
+    if (!(beta > 0)) return fail(BS_ERR_ARG, "base parameters need alpha * rc = beta > 0");
+    const double Lmin = std::min(base->L[0], std::min(base->L[1], base->L[2]));
+    const long long N = offsets[nfil];
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    double* vel = nullptr;
+    if (ce == cudaSuccess) ce = cudaMalloc(&vel, sizeof(double) * 3 * (size_t)N);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamDestroy(s);
+        return fail(BS_ERR_CUDA, "autotune set-up failed: %s", cudaGetErrorString(ce));
+    }
+    int rc = BS_OK, nbest = -1;
+    float tbest = 0.0f;
+    for (int i = 0; i < ncand && rc == BS_OK; ++i) {
+        if (ms_out) ms_out[i] = -1.0f;
+        // alpha from the candidate C_beta, M the smallest odd count with
+        // k_max >= 2 beta alpha, then alpha re-derived from k_max
+        double alpha = cbeta[i] * cbrt((double)N) / Lmin;
+        alpha = std::max(alpha, 2.0 * beta / Lmin);  // rc <= L/2
+        const int K = (int)ceil(beta * alpha * Lmin / kPi);
+        bs_params p;
+        if ((rc = bs_params_from_beta(beta, base->L, 2 * K + 1, 0, &p)) != BS_OK) break;
+        bs_params q = *base;
+        q.alpha = p.alpha;
+        q.rc = p.rc;
+        for (int c = 0; c < 3; ++c) q.M[c] = p.M[c];
+        q.flags &= ~BS_TIMING;
+        bs_ctx* c = nullptr;
+        if ((rc = bs_create(&c, &q, s)) != BS_OK) break;
+        rc = bs_set_filaments(c, nfil, offsets, closing);
+        float t = 0.0f;
+        for (int r = 0; r < reps + 1 && rc == BS_OK; ++r) {  // the first call warms up
+            if (r == 1) cudaEventRecord(e0, s);
+            rc = bs_compute(c, nodes, vel, nullptr);
+        }
+        if (rc == BS_OK) {
+            cudaEventRecord(e1, s);
+            ce = cudaEventSynchronize(e1);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            if (ce != cudaSuccess) rc = fail(BS_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
+        }
+        if (rc == BS_OK) rc = bs_status(c);
+        bs_destroy(c);
+        if (rc != BS_OK) break;
+        t /= (float)reps;
+        if (ms_out) ms_out[i] = t;
+        if (nbest < 0 || t < tbest) {
+            nbest = i;
+            tbest = t;
+            *best = q;
+        }
+    }
+    cudaFree(vel);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    return rc;
+}

@@ -87,6 +87,7 @@ struct GeomP {
     int tile[3];        // spread tile edge
     int ntile[3];
     double seg_max;     // longest allowed segment chord (min L / 4)
+    double iL[3], ihc[3], ihg[3];  // reciprocals of L, hc, hg (binning multiplies: float64 division is slow here)
     int want_psi;
 };
 
@@ -224,6 +225,7 @@ struct InterpP {
     int ng[3];
     double hg[3];
     double L[3];
+    double iL[3], ihg[3];  // reciprocals of L and hg
     int w;
     double zeta;
     int want_psi;

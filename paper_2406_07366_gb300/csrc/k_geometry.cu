@@ -282,14 +282,14 @@ __global__ void k_spline_warp(const double* __restrict__ nodes, const int64_t* _
     }
 }
 
-// Wrap x into [0, L); non-finite input maps to 0 and raises the flag.
-__device__ __forceinline__ double wrap_box(double x, double L, bool& bad)
+// Wrap x into [0, L) (iL = 1/L); non-finite input maps to 0 and raises the flag.
+__device__ __forceinline__ double wrap_box(double x, double L, double iL, bool& bad)
 {
     if (!isfinite(x)) {
         bad = true;
         return 0.0;
     }
-    double y = x - L * floor(x / L);
+    double y = x - L * floor(x * iL);
     if (y >= L) y -= L;
     if (y < 0.0) y = 0.0;
     return y;
@@ -383,7 +383,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         bool b2 = false;
         double xw[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xw[c] = wrap_box(sj[c] + (double)del[c], P.L[c], b2);
+        for (int c = 0; c < 3; ++c) xw[c] = wrap_box(sj[c] + (double)del[c], P.L[c], P.iL[c], b2);
         if (b2) {
             bad = true;
             q[0] = q[1] = q[2] = 0;
@@ -394,7 +394,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         int ci[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            int k = (int)(xw[c] / P.hc[c]);
+            int k = (int)(xw[c] * P.ihc[c]);
             k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
             ci[c] = k;
             R.o[c] = (T)(xw[c] - k * P.hc[c]);
@@ -409,7 +409,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         int ib[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double g = xw[c] / P.hg[c];
+            const double g = xw[c] * P.ihg[c];
             int k = (int)floor(g);
             k = k < 0 ? 0 : (k >= P.ng[c] ? P.ng[c] - 1 : k);
             ib[c] = k;
@@ -485,8 +485,8 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         int ci[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double xw = wrap_box(sj[c], P.L[c], b2);
-            int k = (int)(xw / P.hc[c]);
+            const double xw = wrap_box(sj[c], P.L[c], P.iL[c], b2);
+            int k = (int)(xw * P.ihc[c]);
             k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
             ci[c] = k;
             tg.o[c] = (T)(xw - k * P.hc[c]);
@@ -636,7 +636,7 @@ __global__ void k_export_quad(GeomP P, const double* __restrict__ nodes, const i
         bool b = false;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            qX[3 * p + c] = wrap_box(nodes[3 * j + c] + (double)del[c], P.L[c], b);
+            qX[3 * p + c] = wrap_box(nodes[3 * j + c] + (double)del[c], P.L[c], P.iL[c], b);
             qq[3 * p + c] = (double)(wq * sd[c]);
         }
     }

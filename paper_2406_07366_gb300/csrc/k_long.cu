@@ -233,10 +233,10 @@ __global__ void __launch_bounds__(128) k_interp(InterpP P, const double* __restr
     for (int d = 0; d < 3; ++d) {
         double x = nodes[3 * j + d];
         if (!isfinite(x)) x = 0.0;
-        double xw = x - P.L[d] * floor(x / P.L[d]);
+        double xw = x - P.L[d] * floor(x * P.iL[d]);
         if (xw >= P.L[d]) xw -= P.L[d];
         if (xw < 0.0) xw = 0.0;
-        const double g = xw / P.hg[d];
+        const double g = xw * P.ihg[d];
         int k = (int)floor(g);
         k = k < 0 ? 0 : (k >= P.ng[d] ? P.ng[d] - 1 : k);
         double f = g - (double)k;
