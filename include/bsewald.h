@@ -205,6 +205,22 @@ int bs_compute_parts(bs_ctx* ctx, const double* nodes, double* parts, double* ps
 int bs_get_quadrature(bs_ctx* ctx, const double* nodes, double* qX, double* qq);
 
 /*
+ * bs_energy_spectrum -- kinetic energy spectrum of the filaments' velocity
+ * field on the context's Fourier modes (Eq. def_energy_spectrum):
+ *   E(k_m) = 1/(2 dk) sum over |k| in [k_m - dk/2, k_m + dk/2) of |v_k|^2,
+ *   k_m = m dk, dk = 2 pi / min L, m = 0..nbins-1,
+ * with v_k = i k x omega_k / k^2 from the same spread and forward transforms
+ * as bs_compute (the modes |m_d| <= K_d, k = 0 excluded).  smoothed = 0: the
+ * full (unsmoothed) field's truncated spectrum; smoothed = 1: the long-range
+ * field's, E(k) e^{-k^2 / 2 alpha^2} (Sec. 6, Fig. fig:energy_spectra).
+ *   nodes (device) N x 3; Ek (host) nbins doubles; dk_out (host, or NULL)
+ * Shells past the corner of the mode cube are zero.  Synchronises the
+ * context stream.  Needs the default transform path (BS_ERR_STATE with
+ * BS_FFT_CUFFT).  Errors: BS_ERR_ARG, BS_ERR_STATE, BS_ERR_CUDA.
+ */
+int bs_energy_spectrum(bs_ctx* ctx, const double* nodes, int smoothed, int nbins, double* Ek, double* dk_out);
+
+/*
  * Capture one bs_compute(ctx, nodes, vel, psi) into a CUDA graph bound to
  * these device buffers (both branches of the evaluation become graph
  * branches), replacing any previous graph; bs_graph_launch replays it on

@@ -376,3 +376,31 @@ def polygon_impulse(nodes, offsets, kappa):
         s = nodes[offsets[l]:offsets[l + 1]]
         P += 0.5 * kappa * np.cross(s, np.roll(s, -1, axis=0)).sum(axis=0)
     return P
+
+
+def energy_spectrum(g: Geometry, L, kappa, K, nbins, alpha=None):
+    """Energy spectrum of Eq. def_energy_spectrum: E(k_m) = 1/(2 dk) times the
+    sum of |v_k|^2 over the modes with m - 1/2 <= |k| / dk < m + 1/2,
+    v_k = i k x omega_k / k^2 over the cube |m_d| <= K_d (k = 0 excluded),
+    dk = 2 pi / min L.  With alpha, the long-range field's spectrum
+    (|v_k|^2 e^{-k^2 / 2 alpha^2}).  Returns (k_m, E)."""
+    L = np.asarray(L, dtype=np.float64)
+    Kv = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (3,)))
+    om = fourier_coefs(g, L, kappa, Kv).reshape(2 * Kv[0] + 1, 2 * Kv[1] + 1, 2 * Kv[2] + 1, 3, 2)
+    w = om[..., 0] + 1j * om[..., 1]
+    k = [2 * math.pi / L[d] * np.arange(-Kv[d], Kv[d] + 1) for d in range(3)]
+    kx, ky, kz = np.meshgrid(k[0], k[1], k[2], indexing="ij")
+    kv = np.stack([kx, ky, kz], axis=-1)
+    ksq = kx ** 2 + ky ** 2 + kz ** 2
+    cross = np.cross(kv, w)  # k x omega (complex)
+    v2 = np.sum(np.abs(cross) ** 2, axis=-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v2 = np.where(ksq > 0, v2 / ksq ** 2, 0.0)
+    if alpha is not None:
+        v2 = v2 * np.exp(-ksq / (2 * alpha ** 2))
+    dk = 2 * math.pi / L.min()
+    m = np.floor(np.sqrt(ksq) / dk + 0.5).astype(np.int64)
+    E = np.zeros(int(nbins))
+    sel = (ksq > 0) & (m < nbins)
+    np.add.at(E, m[sel], v2[sel])
+    return dk * np.arange(int(nbins)), E / (2 * dk)

@@ -37,7 +37,7 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
            "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
-           "bs_autotune_alpha"]
+           "bs_autotune_alpha", "bs_energy_spectrum"]
 
 
 class bs_params(ctypes.Structure):
@@ -96,6 +96,8 @@ def _load():
         "bs_rk4_step": ([vp, vp, ctypes.c_double], ctypes.c_int),
         "bs_rk4_capture": ([vp, vp, ctypes.c_double], ctypes.c_int),
         "bs_rk4_launch": ([vp, ctypes.c_int], ctypes.c_int),
+        "bs_energy_spectrum": ([vp, vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)],
+                               ctypes.c_int),
         "bs_autotune_alpha": ([P(bs_params), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32), vp, ctypes.c_int,
                                P(ctypes.c_double), ctypes.c_int, P(bs_params), P(ctypes.c_float)], ctypes.c_int),
         "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -231,6 +233,15 @@ def bs_rk4_capture(ctx, nodes, dt):
 
 def bs_rk4_launch(ctx, nsteps):
     _check(lib().bs_rk4_launch(ctx, int(nsteps)))
+
+
+def bs_energy_spectrum(ctx, nodes, nbins, smoothed=False):
+    """(k_m, E(k_m)) for m = 0..nbins-1 (Eq. def_energy_spectrum)."""
+    Ek = np.zeros(int(nbins), dtype=np.float64)
+    dk = ctypes.c_double()
+    _check(lib().bs_energy_spectrum(ctx, _ptr(nodes), int(bool(smoothed)), int(nbins),
+                                   Ek.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(dk)))
+    return dk.value * np.arange(int(nbins)), Ek
 
 
 def bs_autotune_alpha(base, offsets, closing, nodes, cbeta, reps=3):
@@ -426,6 +437,10 @@ class BiotSavart:
     def energy(self, nodes, vel=None, psi=None):
         """Kinetic energy (and optionally velocity / streamfunction) of one evaluation."""
         return bs_compute_energy(self.ctx, nodes, vel, psi)
+
+    def energy_spectrum(self, nodes, nbins, smoothed=False):
+        """(k, E(k)) on the context's Fourier modes (Eq. def_energy_spectrum)."""
+        return bs_energy_spectrum(self.ctx, nodes, nbins, smoothed)
 
     def capture(self, nodes, vel, psi=None):
         """Capture one evaluation into a CUDA graph (replay with launch())."""

@@ -200,6 +200,7 @@ struct Derived {
     // pruned-FFT pipeline
     FftPlan plan[3];
     int tx, ty, nbx, nby, ncols, colcap;  // z-column blocks; records per source at most
+    int nshell;                            // spectrum shells reaching the mode cube's corner
     int lmcy, lmcx, yc;                   // log2 chunk sizes of the y and x passes; inverse-z chunk
     int lsz;                              // padded stride of the real z-lines of the spread
 };
@@ -271,6 +272,12 @@ int derive(const bs_params* p, Derived* d)
     d->nby = d->ng[1] / d->ty;
     d->ncols = d->nbx * d->nby;
     d->colcap = ((p->nufft_w - 1) / d->tx + 2) * ((p->nufft_w - 1) / d->ty + 2);
+    {
+        const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
+        double r2 = 0.0;  // |k_corner| / dk, dk = 2 pi / min L
+        for (int c = 0; c < 3; ++c) r2 += (d->K[c] * Lmin / p->L[c]) * (d->K[c] * Lmin / p->L[c]);
+        d->nshell = (int)ceil(sqrt(r2)) + 2;
+    }
     const size_t mcy = 50000 / ((size_t)(d->ng[1] + 1) * cb);
     d->lmcy = 0;
     while (d->lmcy < 4 && ((size_t)2 << d->lmcy) <= mcy) ++d->lmcy;
@@ -412,6 +419,7 @@ int alloc_grids(bs_ctx* c)
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp, sizeof(int) * (size_t)scan_blocks((int)d.ncells)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.status, sizeof(int)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.energy_acc, 2 * sizeof(double)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.shell, sizeof(double) * (size_t)d.nshell));
     CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
     // k-space tables e^{-k_d^2 / 4 alpha^2} / F_d(m)^2, m = 0..K_d
     const int ntab = d.K[0] + d.K[1] + d.K[2] + 3;
@@ -549,7 +557,7 @@ int fft_inv(bs_ctx* c, void* spec, cudaStream_t s)
 // concurrent); stage i spans events [kStageBeg[i], kStageEnd[i]].
 template <typename T>
 int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts, double* psi_parts,
-        bool want_energy = false)
+        bool want_energy = false, double* spectrum = nullptr, int smoothed = 0, int nbins = 0)
 {
     const bs_params& p = c->p;
     const Derived& d = c->d;
@@ -570,7 +578,8 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
                        psi_parts ? psi_parts : nullptr, psi_parts ? psi_parts + 3 * N3 : nullptr, s));
     rec(c, 1, s);
 
-    // short range on the side stream
+    // short range on the side stream (not in spectrum mode)
+    if (!spectrum) {
     CE(cudaEventRecord(c->ev_fork, s));
     CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     cudaStream_t ss = c->side;
@@ -592,6 +601,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     CE(launch_short<T>(S, w, ss));
     rec(c, 3, ss);
     CE(cudaEventRecord(c->ev_join, ss));
+    }
 
     // long range on the main stream
     if (p.flags & BS_FFT_CUFFT) {
@@ -687,6 +697,14 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         XP.d_lines = make_fastdiv(3u << d.lmcx);
         XP.d_lines_psi = make_fastdiv(6u << d.lmcx);
         XP.energy = want_energy ? w.energy_acc : nullptr;
+        XP.spectrum = spectrum;
+        XP.nbins = nbins;
+        XP.smoothed = smoothed;
+        XP.dk = 2.0 * kPi / std::min(p.L[0], std::min(p.L[1], p.L[2]));
+        XP.inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
+        if (spectrum) return (int)launch_fft_x_kspace<T>(XP, w, false, s) == (int)cudaSuccess
+                                 ? BS_OK
+                                 : fail(BS_ERR_CUDA, "spectrum kernel launch failed");
         CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
         rec(c, 7, s);
         CE(launch_fft_y<T>(YP, w, w.f2, +1, s));
@@ -1063,6 +1081,31 @@ int bs_compute_energy(bs_ctx* c, const double* nodes, double* vel, double* psi, 
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     const double V = c->p.L[0] * c->p.L[1] * c->p.L[2];
     *energy = acc[0] + c->p.kappa / (2.0 * V) * acc[1];
+    return BS_OK;
+}
+
+int bs_energy_spectrum(bs_ctx* c, const double* nodes, int smoothed, int nbins, double* Ek, double* dk_out)
+{
+    TRY(check_ctx(c));
+    if (!Ek || nbins <= 0) return fail(BS_ERR_ARG, "bad spectrum output");
+    if (c->p.flags & BS_FFT_CUFFT) return fail(BS_ERR_STATE, "the spectrum needs the pruned transform path");
+    const double dk = 2.0 * kPi / std::min(c->p.L[0], std::min(c->p.L[1], c->p.L[2]));
+    if (dk_out) *dk_out = dk;
+    for (int m = 0; m < nbins; ++m) Ek[m] = 0.0;
+    if (c->N == 0) return BS_OK;
+    if (!nodes) return fail(BS_ERR_ARG, "null nodes");
+    // shells beyond the mode cube's corner stay zero
+    const int nb = std::min(nbins, c->d.nshell);
+    double* bins = c->w.shell;
+    CUDA_TRY(cudaMemsetAsync(bins, 0, sizeof(double) * (size_t)nb, c->stream));
+    const int rc = c->p.precision == BS_FP64
+                       ? run<double>(c, nodes, nullptr, nullptr, nullptr, nullptr, false, bins, smoothed, nb)
+                       : run<float>(c, nodes, nullptr, nullptr, nullptr, nullptr, false, bins, smoothed, nb);
+    if (rc != BS_OK) return rc;
+    CUDA_TRY(cudaMemcpyAsync(Ek, bins, sizeof(double) * (size_t)nb, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double sc = c->p.kappa / (c->p.L[0] * c->p.L[1] * c->p.L[2]);
+    for (int m = 0; m < nb; ++m) Ek[m] *= sc * sc / (2.0 * dk);
     return BS_OK;
 }
 

@@ -119,6 +119,15 @@ struct KspaceP {
     double scale;       // kappa / V
     int want_psi;
     double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
+    // Spectrum mode (spectrum non-null): after the forward x transform, add
+    // |k x F_k|^2 e^{s k^2 / 4a^2} prod tab_d / k^4 (s = +1 unsmoothed, -1
+    // smoothed; both halves of the spectrum) to shell round(|k| / dk) of
+    // spectrum[0..nbins), then stop (no k-space pass, no inverse).
+    double* spectrum;
+    int nbins;
+    int smoothed;
+    double dk;
+    double inv4a2;      // 1 / (4 alpha^2)
 };
 
 // Exact unsigned division by a run-time constant d for 0 <= x < 2^31
@@ -208,6 +217,15 @@ struct FftXP {
     const int* rev;
     FastDiv d_nch, d_n0, d_lines, d_lines_psi;
     double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
+    // Spectrum mode (spectrum non-null): after the forward x transform, add
+    // |k x F_k|^2 e^{s k^2 / 4a^2} prod tab_d / k^4 (s = +1 unsmoothed, -1
+    // smoothed; both halves of the spectrum) to shell round(|k| / dk) of
+    // spectrum[0..nbins), then stop (no k-space pass, no inverse).
+    double* spectrum;
+    int nbins;
+    int smoothed;
+    double dk;
+    double inv4a2;      // 1 / (4 alpha^2)
 };
 
 struct FftZP {
@@ -273,6 +291,7 @@ struct Work {
     void* spec_psi = nullptr; // 3 x ... (psi)
     void* ktab = nullptr;     // per-axis k-space tables
     int* rev = nullptr;       // per-axis positions of frequency k after the forward transform (n0 + n1 + n2)
+    double* shell = nullptr;  // energy-spectrum shell sums
     void* fft_work = nullptr;
     // pruned-FFT pipeline
     void* tw = nullptr;       // twiddles e^{-2 pi i j / n_d}, n0 + n1 + n2 complex

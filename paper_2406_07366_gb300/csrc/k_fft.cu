@@ -25,6 +25,7 @@
 // in float64.  Two real lines are transformed as one complex line.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "bs_internal.cuh"
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
 // curl couples them).  tabs: e^{-k_d^2/4alpha^2} / F_d(m)^2 per axis.
 // ---------------------------------------------------------------------------
 template <typename T, int RM>
-__global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
                                                            typename Cx<T>::t* __restrict__ F2psi,
                                                            const typename Cx<T>::t* __restrict__ tw0,
                                                            const T* __restrict__ tab0, const T* __restrict__ tab1,
@@ -639,6 +640,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_x_kspace(FftXP P, typename 
     // k-space pass: frequency (mx, my, mz) sits at position rev(xi) of line (c, l)
     const int my = myp - K1;
     const int amy = my < 0 ? -my : my;
+    if (P.spectrum) {
+        // energy spectrum (Eq. def_energy_spectrum): shell sums in shared memory
+        double* bins = reinterpret_cast<double*>(a + (size_t)3 * MC * LS);
+        for (int i = threadIdx.x; i < P.nbins; i += blockDim.x) bins[i] = 0.0;
+        __syncthreads();
+        const double kk0 = P.kk[0], kk1 = P.kk[1], kk2 = P.kk[2];
+        const double sg = P.smoothed ? -P.inv4a2 : P.inv4a2;
+        for (int i = threadIdx.x; i < (n0 << lmc); i += blockDim.x) {
+            const int lk = i & (MC - 1), xi = i >> lmc;
+            const int mx = xi <= n0 / 2 ? xi : xi - n0;
+            const int amx = mx < 0 ? -mx : mx;
+            const int mz = mz0 + lk;
+            if (lk >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) continue;
+            const int pos = P.rev[xi];
+            const C F0 = a[(0 * MC + lk) * LS + pos], F1 = a[(1 * MC + lk) * LS + pos],
+                    F2v = a[(2 * MC + lk) * LS + pos];
+            const double k0 = kk0 * mx, k1 = kk1 * my, k2 = kk2 * mz;
+            const double ksq = k0 * k0 + k1 * k1 + k2 * k2;
+            // |k x F|^2 = |k x Re F|^2 + |k x Im F|^2
+            const double ar0 = k1 * F2v.x - k2 * F1.x, ar1 = k2 * F0.x - k0 * F2v.x, ar2 = k0 * F1.x - k1 * F0.x;
+            const double ai0 = k1 * F2v.y - k2 * F1.y, ai1 = k2 * F0.y - k0 * F2v.y, ai2 = k0 * F1.y - k1 * F0.y;
+            const double c2 = ar0 * ar0 + ar1 * ar1 + ar2 * ar2 + ai0 * ai0 + ai1 * ai1 + ai2 * ai2;
+            const double tp = (double)tab0[amx] * (double)tab1[amy] * (double)tab2[mz];
+            const double v = (mz > 0 ? 2.0 : 1.0) * c2 * tp * exp(sg * ksq) / (ksq * ksq);
+            const int m = (int)(sqrt(ksq) / P.dk + 0.5);
+            if (m < P.nbins) atomicAdd(&bins[m], v);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < P.nbins; i += blockDim.x)
+            if (bins[i] != 0.0) atomicAdd(&P.spectrum[i], bins[i]);
+        return;
+    }
     double esum = 0.0;  // energy of this thread's modes (float64 reduction)
     // a thread takes 8 consecutive x frequencies of one line, the lanes on
     // consecutive groups (distinct banks at the digit-reversed positions)
@@ -964,7 +997,8 @@ struct FftXLaunch {
         using C = typename Cx<T>::t;
         const int MC = 1 << P.lmc;
         const int nl = (want_psi ? 6 : 3) * MC;
-        const size_t sm = (size_t)nl * P.ls * sizeof(C);
+        size_t sm = (size_t)nl * P.ls * sizeof(C);
+        if (P.spectrum) sm = std::max(sm, (size_t)3 * MC * P.ls * sizeof(C) + sizeof(double) * (size_t)P.nbins);
         cudaError_t e =
             cudaFuncSetAttribute(k_fft_x_kspace<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;

@@ -331,3 +331,24 @@ def test_rk4_energy_and_impulse_drift_shrink_with_resolution():
     (e32, p32), (e64, p64) = drifts
     assert e32 < 1e-4 and p32 < 2e-5
     assert e64 < e32 / 2.5 and p64 < p32 / 2.5
+
+
+def test_energy_spectrum_of_straight_lines_follows_inverse_k():
+    """Sec. 6: at scales below the vortex spacing the spectrum of straight
+    vortices is E(k) = kappa^2 Lv / (4 pi V) k^-1 (Lv the total length).  Two
+    antiparallel z-lines (Lv = 2L); averaged over shells 6..20 the
+    compensated spectrum E(k) k / (kappa^2 Lv / 4 pi V) is 1 within 5 %, and
+    only modes with k_z = 0 carry energy (the field does not vary along z)."""
+    f = W.antiparallel_lines(N_l=32)
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 4, 2)
+    k, E = oracle.energy_spectrum(g, f.L, KAPPA, 24, 30)
+    V = float(np.prod(f.L))
+    pred = KAPPA ** 2 * 2 * f.L[0] / (4 * math.pi * V)
+    ratio = E[6:21] * k[6:21] / pred
+    assert abs(ratio.mean() - 1.0) < 0.05, ratio
+    # no energy at k = 0 and none in modes with k_z != 0: the k_z = 0 plane alone gives it all
+    Kv = 24
+    om = oracle.fourier_coefs(g, f.L, KAPPA, np.array([Kv] * 3, np.int32)).reshape(49, 49, 49, 3, 2)
+    off_plane = np.abs(np.delete(om, Kv, axis=2)).max()
+    assert off_plane < 1e-12 * np.abs(om).max()
+    assert E[0] == 0.0
