@@ -265,6 +265,79 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
     }
 }
 
+// The same pass with the plan and the line count fixed at compile time
+// (every stride, twiddle step and index division becomes a constant).
+template <typename T, int R, bool DIF, int N, int ST, int TWS, int NL>
+__device__ __forceinline__ void fft_pass_c(typename Cx<T>::t* __restrict__ buf, int ls,
+                                           const typename Cx<T>::t* __restrict__ tw)
+{
+    constexpr int S = DIF ? -1 : 1;
+    using C = typename Cx<T>::t;
+    constexpr int G = sizeof(C) == 8 ? 16 : 8;
+    constexpr bool pad = NL < G && (G % NL) != 0 && 2 * NL > G;
+    constexpr int NLV = pad ? G : NL;
+    constexpr int nb = N / R;
+    constexpr int tot = NLV * nb;
+    constexpr int L = ST * R;
+#pragma unroll 1
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int i = idx / NLV;
+        const int line = idx % NLV;
+        if (pad && line >= NL) continue;
+        const int b = i / ST;
+        const int j = i % ST;
+        C* p = buf + line * ls + b * L + j;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = p[q * ST];
+        if (!DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * TWS);
+        dft<T, R, S>(x);
+        if (DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * TWS);
+#pragma unroll
+        for (int q = 0; q < R; ++q) p[q * ST] = x[q];
+    }
+}
+
+// Three-pass transform of plan (R0, R1, R2), N = R0 R1 R2, NL lines.
+template <typename T, bool DIF, int R0, int R1, int R2, int NL>
+__device__ __forceinline__ void fft3_c(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
+{
+    constexpr int N = R0 * R1 * R2;
+    if constexpr (DIF) {
+        fft_pass_c<T, R0, true, N, R1 * R2, 1, NL>(buf, ls, tw);
+        __syncthreads();
+        fft_pass_c<T, R1, true, N, R2, R0, NL>(buf, ls, tw);
+        __syncthreads();
+        fft_pass_c<T, R2, true, N, 1, R0 * R1, NL>(buf, ls, tw);
+        __syncthreads();
+    } else {
+        fft_pass_c<T, R2, false, N, 1, R0 * R1, NL>(buf, ls, tw);
+        __syncthreads();
+        fft_pass_c<T, R1, false, N, R2, R0, NL>(buf, ls, tw);
+        __syncthreads();
+        fft_pass_c<T, R0, false, N, R1 * R2, 1, NL>(buf, ls, tw);
+        __syncthreads();
+    }
+}
+
+// Plans with a compiled form: 384 = 8 x 8 x 6 (float) at 12, 16 or 24 lines.
+template <typename T, bool DIF>
+__device__ __forceinline__ bool fft_const(typename Cx<T>::t* buf, int nlines, int ls, const FftPlan& pl,
+                                          const typename Cx<T>::t* __restrict__ tw)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (pl.n == 384 && pl.nr == 3 && pl.r[0] == 8 && pl.r[1] == 8 && pl.r[2] == 6) {
+            switch (nlines) {
+            case 12: fft3_c<T, DIF, 8, 8, 6, 12>(buf, ls, tw); return true;
+            case 16: fft3_c<T, DIF, 8, 8, 6, 16>(buf, ls, tw); return true;
+            case 24: fft3_c<T, DIF, 8, 8, 6, 24>(buf, ls, tw); return true;
+            default: break;
+            }
+        }
+    }
+    return false;
+}
+
 template <typename T, bool DIF, int RM>
 __device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls,
                                           const FftPlan& pl, int s, const typename Cx<T>::t* __restrict__ tw)
@@ -294,6 +367,7 @@ template <typename T, int RM>
 __device__ __forceinline__ void fft_fwd_dif(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
+    if (fft_const<T, true>(buf, nlines, ls, pl, tw)) return;
     for (int s = 0; s < pl.nr; ++s) fft_stage<T, true, RM>(buf, nlines, dl, ls, pl, s, tw);
 }
 
@@ -303,6 +377,7 @@ template <typename T, int RM>
 __device__ __forceinline__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
+    if (fft_const<T, false>(buf, nlines, ls, pl, tw)) return;
     for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false, RM>(buf, nlines, dl, ls, pl, s, tw);
 }
 
