@@ -298,39 +298,71 @@ __device__ __forceinline__ void fft_pass_c(typename Cx<T>::t* __restrict__ buf, 
     }
 }
 
-// Three-pass transform of plan (R0, R1, R2), N = R0 R1 R2, NL lines.
-template <typename T, bool DIF, int R0, int R1, int R2, int NL>
-__device__ __forceinline__ void fft3_c(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
+// Transform of plan (Rs...) with N = product of the radices and NL lines:
+// forward passes in plan order (stride N / R0 first), inverse in reverse.
+template <typename T, int NL, int N, int ST, int TWS, int R, int... Rest>
+__device__ __forceinline__ void fft_c_fwd(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
 {
-    constexpr int N = R0 * R1 * R2;
-    if constexpr (DIF) {
-        fft_pass_c<T, R0, true, N, R1 * R2, 1, NL>(buf, ls, tw);
-        __syncthreads();
-        fft_pass_c<T, R1, true, N, R2, R0, NL>(buf, ls, tw);
-        __syncthreads();
-        fft_pass_c<T, R2, true, N, 1, R0 * R1, NL>(buf, ls, tw);
-        __syncthreads();
-    } else {
-        fft_pass_c<T, R2, false, N, 1, R0 * R1, NL>(buf, ls, tw);
-        __syncthreads();
-        fft_pass_c<T, R1, false, N, R2, R0, NL>(buf, ls, tw);
-        __syncthreads();
-        fft_pass_c<T, R0, false, N, R1 * R2, 1, NL>(buf, ls, tw);
-        __syncthreads();
-    }
+    fft_pass_c<T, R, true, N, ST / R, TWS, NL>(buf, ls, tw);
+    __syncthreads();
+    if constexpr (sizeof...(Rest) > 0) fft_c_fwd<T, NL, N, ST / R, TWS * R, Rest...>(buf, ls, tw);
 }
 
-// Plans with a compiled form: 384 = 8 x 8 x 6 (float) at 12, 16 or 24 lines.
+template <typename T, int NL, int N, int ST, int TWS, int R, int... Rest>
+__device__ __forceinline__ void fft_c_inv(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
+{
+    if constexpr (sizeof...(Rest) > 0) fft_c_inv<T, NL, N, ST / R, TWS * R, Rest...>(buf, ls, tw);
+    fft_pass_c<T, R, false, N, ST / R, TWS, NL>(buf, ls, tw);
+    __syncthreads();
+}
+
+template <typename T, bool DIF, int NL, int... Rs>
+__device__ __forceinline__ void fft_c(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
+{
+    constexpr int N = (Rs * ...);
+    if constexpr (DIF)
+        fft_c_fwd<T, NL, N, N, 1, Rs...>(buf, ls, tw);
+    else
+        fft_c_inv<T, NL, N, N, 1, Rs...>(buf, ls, tw);
+}
+
+template <int... Rs>
+__device__ __forceinline__ bool plan_is(const FftPlan& pl)
+{
+    constexpr int r[] = { Rs... };
+    if (pl.nr != (int)sizeof...(Rs)) return false;
+#pragma unroll
+    for (int s = 0; s < (int)sizeof...(Rs); ++s)
+        if (pl.r[s] != r[s]) return false;
+    return true;
+}
+
+// Plans with a compiled form (float): 384 = 8 x 8 x 6 at 12, 16 or 24 lines
+// (the 1e5-node tangle), 768 = 8 x 6 x 4 x 4 at 6, 8 or 16 lines (the 4e6-node
+// tangle), 192 = 8 x 6 x 4 at 16 or 24 lines (the largest batch members).
 template <typename T, bool DIF>
 __device__ __forceinline__ bool fft_const(typename Cx<T>::t* buf, int nlines, int ls, const FftPlan& pl,
                                           const typename Cx<T>::t* __restrict__ tw)
 {
     if constexpr (sizeof(T) == 4) {
-        if (pl.n == 384 && pl.nr == 3 && pl.r[0] == 8 && pl.r[1] == 8 && pl.r[2] == 6) {
+        if (plan_is<8, 8, 6>(pl)) {
             switch (nlines) {
-            case 12: fft3_c<T, DIF, 8, 8, 6, 12>(buf, ls, tw); return true;
-            case 16: fft3_c<T, DIF, 8, 8, 6, 16>(buf, ls, tw); return true;
-            case 24: fft3_c<T, DIF, 8, 8, 6, 24>(buf, ls, tw); return true;
+            case 12: fft_c<T, DIF, 12, 8, 8, 6>(buf, ls, tw); return true;
+            case 16: fft_c<T, DIF, 16, 8, 8, 6>(buf, ls, tw); return true;
+            case 24: fft_c<T, DIF, 24, 8, 8, 6>(buf, ls, tw); return true;
+            default: break;
+            }
+        } else if (plan_is<8, 6, 4, 4>(pl)) {
+            switch (nlines) {
+            case 6: fft_c<T, DIF, 6, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 8: fft_c<T, DIF, 8, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 16: fft_c<T, DIF, 16, 8, 6, 4, 4>(buf, ls, tw); return true;
+            default: break;
+            }
+        } else if (plan_is<8, 6, 4>(pl)) {
+            switch (nlines) {
+            case 16: fft_c<T, DIF, 16, 8, 6, 4>(buf, ls, tw); return true;
+            case 24: fft_c<T, DIF, 24, 8, 6, 4>(buf, ls, tw); return true;
             default: break;
             }
         }
