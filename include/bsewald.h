@@ -63,8 +63,11 @@ enum {
 enum {
     BS_WANT_PSI = 1,   /* also produce the streamfunction (Eq. ewald_streamfunction_splitting) */
     BS_TIMING = 2,     /* record per-stage CUDA-event times (bs_stage_times) */
-    BS_FFT_CUFFT = 4   /* long range through full cuFFT R2C/C2R transforms instead of
+    BS_FFT_CUFFT = 4,  /* long range through full cuFFT R2C/C2R transforms instead of
                           the library's pruned per-axis transforms (a cross-check path) */
+    BS_DETERMINISTIC = 8  /* bitwise-reproducible results on a given GPU and build: the binned
+                             sources keep a fixed order and no floating-point sum depends on thread
+                             timing (slower spread); not with BS_FFT_CUFFT (BS_ERR_ARG) */
 };
 
 /*
@@ -83,7 +86,7 @@ enum {
  *   nufft_sigma   oversampling factor sigma > 1 (Appendix A)
  *   nufft_w       spreading width in grid points, even, 2..16 (Appendix A)
  *   precision     BS_FP64 or BS_MIXED
- *   flags         BS_WANT_PSI | BS_TIMING | BS_FFT_CUFFT
+ *   flags         BS_WANT_PSI | BS_TIMING | BS_FFT_CUFFT | BS_DETERMINISTIC
  *   cell_div      cells per cut-off length m (cells of edge >= rc/m); the
  *                 paper uses 3 (Sec. 5.3); 0 selects the library default
  */

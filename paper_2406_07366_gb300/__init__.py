@@ -25,7 +25,7 @@ BS_OK, BS_ERR_ARG, BS_ERR_RC_GT_HALF_L, BS_ERR_NET_VORTICITY, BS_ERR_SPLINE = 0,
 BS_ERR_NONFINITE, BS_ERR_OOM, BS_ERR_CUDA, BS_ERR_CUFFT, BS_ERR_TIMEOUT = 5, 6, 7, 8, 9
 BS_ERR_STATE, BS_ERR_GEOMETRY = 10, 11
 BS_FP64, BS_MIXED = 0, 1
-BS_WANT_PSI, BS_TIMING, BS_FFT_CUFFT = 1, 2, 4
+BS_WANT_PSI, BS_TIMING, BS_FFT_CUFFT, BS_DETERMINISTIC = 1, 2, 4, 8
 
 STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", "kspace", "fft_inv", "interp",
           "total"]

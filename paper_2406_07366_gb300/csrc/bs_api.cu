@@ -214,6 +214,8 @@ int derive(const bs_params* p, Derived* d)
     if (!(p->a > 0) || !isfinite(p->a)) return fail(BS_ERR_ARG, "core radius a must be positive");
     if (!isfinite(p->delta)) return fail(BS_ERR_ARG, "delta must be finite");
     if (!(p->alpha > 0) || !isfinite(p->alpha)) return fail(BS_ERR_ARG, "alpha must be positive");
+    if ((p->flags & BS_DETERMINISTIC) && (p->flags & BS_FFT_CUFFT))
+        return fail(BS_ERR_ARG, "BS_DETERMINISTIC needs the default transform path, not BS_FFT_CUFFT");
     if (!(p->rc > 0) || !isfinite(p->rc)) return fail(BS_ERR_ARG, "rc must be positive");
     if (p->rc > 0.5 * Lmin * (1 + 1e-12))
         return fail(BS_ERR_RC_GT_HALF_L, "rc = %g exceeds min(L)/2 = %g", p->rc, 0.5 * Lmin);
@@ -420,6 +422,11 @@ int alloc_grids(bs_ctx* c)
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.status, sizeof(int)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.energy_acc, 2 * sizeof(double)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.shell, sizeof(double) * (size_t)d.nshell));
+    if (c->p.flags & BS_DETERMINISTIC) {
+        const int mcx = 1 << d.lmcx;
+        c->w.nepart = (2 * d.K[1] + 1) * ((d.K[2] + 1 + mcx - 1) / mcx);
+        TRY(dalloc(c, c->alloc_g, (void**)&c->w.epart, sizeof(double) * (size_t)c->w.nepart));
+    }
     CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
     // k-space tables e^{-k_d^2 / 4 alpha^2} / F_d(m)^2, m = 0..K_d
     const int ntab = d.K[0] + d.K[1] + d.K[2] + 3;
@@ -469,6 +476,13 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.lr_sorted, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, (void**)&w.lr_key, sizeof(int) * NQ));
     TRY(dalloc(c, L, &w.col_rec, col_rec_bytes<T>(c->p.nufft_w) * NQ * (size_t)c->d.colcap));
+    if (c->p.flags & BS_DETERMINISTIC) {
+        TRY(dalloc(c, L, (void**)&w.sr_idx, sizeof(int) * NQ));
+        TRY(dalloc(c, L, &w.sr_sorted2, sizeof(SrRec<T>) * NQ));
+        TRY(dalloc(c, L, (void**)&w.col_idx, sizeof(int) * NQ * (size_t)c->d.colcap));
+        TRY(dalloc(c, L, &w.col_rec2, col_rec_bytes<T>(c->p.nufft_w) * NQ * (size_t)c->d.colcap));
+        TRY(dalloc(c, L, (void**)&w.lpart, sizeof(double) * std::max<size_t>(nf, 1)));
+    }
     TRY(dalloc(c, L, (void**)&w.nodes_in, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.vel_out, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.psi_out, sizeof(double) * 3 * N));
@@ -566,6 +580,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     const size_t N3 = (size_t)c->N * 3;
     const bool want_psi = (psi != nullptr) || (psi_parts != nullptr) || want_energy;
     c->timed = (p.flags & BS_TIMING) != 0;
+    const bool det = (p.flags & BS_DETERMINISTIC) != 0;
     if (want_energy) CE(cudaMemsetAsync(w.energy_acc, 0, 2 * sizeof(double), s));
 
     GeomP G;
@@ -583,7 +598,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     CE(cudaEventRecord(c->ev_fork, s));
     CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     cudaStream_t ss = c->side;
-    CE(launch_sort_sr<T>(w, (int)c->NQ, (int)d.ncells, ss));
+    CE(launch_sort_sr<T>(w, (int)c->NQ, (int)d.ncells, ss, det));
     rec(c, 2, ss);
     ShortP S;
     memset(&S, 0, sizeof S);
@@ -642,9 +657,10 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         CP.ncols = d.ncols;
         CP.w = p.nufft_w;
         CP.zeta = d.zeta;
-        CE(launch_col_sort<T>(CP, w, (int)c->NQ, s));
+        CE(launch_col_sort<T>(CP, w, (int)c->NQ, s, det));
         rec(c, 4, s);
         SpZP SZ;
+        SZ.det = det ? 1 : 0;
         for (int k = 0; k < 3; ++k) {
             SZ.ng[k] = d.ng[k];
             SZ.K[k] = d.K[k];
@@ -682,6 +698,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         CE(launch_fft_y<T>(YP, w, w.f2, -1, s));
         rec(c, 6, s);
         FftXP XP;
+        XP.epart = (want_energy && det) ? w.epart : nullptr;
         for (int k = 0; k < 3; ++k) {
             XP.ng[k] = d.ng[k];
             XP.K[k] = d.K[k];
@@ -727,7 +744,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     }
     CE(cudaStreamWaitEvent(s, c->ev_join, 0));
     rec(c, 9, s);
-    if (want_energy) CE(launch_energy_line<T>(nodes, w, c->nfil, w.nmax_fil, s));
+    if (want_energy) CE(launch_energy_line<T>(nodes, w, c->nfil, w.nmax_fil, s, det));
 
     InterpP I;
     I.N = (int)c->N;
@@ -1077,8 +1094,21 @@ int bs_compute_energy(bs_ctx* c, const double* nodes, double* vel, double* psi, 
                                        : run<float>(c, nodes, v, ps, nullptr, nullptr, true);
     if (rc != BS_OK) return rc;
     double acc[2];
-    CUDA_TRY(cudaMemcpyAsync(acc, c->w.energy_acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->p.flags & BS_DETERMINISTIC) {
+        // partial sums (per k-space CTA, per filament) added in a fixed order
+        std::vector<double> ep((size_t)c->w.nepart), lp((size_t)c->nfil);
+        CUDA_TRY(cudaMemcpyAsync(ep.data(), c->w.epart, sizeof(double) * ep.size(), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaMemcpyAsync(lp.data(), c->w.lpart, sizeof(double) * lp.size(), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        acc[0] = acc[1] = 0.0;
+        for (double v : ep) acc[0] += v;
+        for (double v : lp) acc[1] += v;
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(acc, c->w.energy_acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
     const double V = c->p.L[0] * c->p.L[1] * c->p.L[2];
     *energy = acc[0] + c->p.kappa / (2.0 * V) * acc[1];
     return BS_OK;

@@ -119,6 +119,7 @@ struct KspaceP {
     double scale;       // kappa / V
     int want_psi;
     double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
+    double* epart;      // if non-null (deterministic): the CTA's share written to epart[blockIdx.x]
     // Spectrum mode (spectrum non-null): after the forward x transform, add
     // |k x F_k|^2 e^{s k^2 / 4a^2} prod tab_d / k^4 (s = +1 unsmoothed, -1
     // smoothed; both halves of the spectrum) to shell round(|k| / dk) of
@@ -184,6 +185,7 @@ struct ColP {
 };
 
 struct SpZP {
+    int det;  // deterministic accumulation: each warp owns a z-range and adds in record order
     int ng[3];
     int K[3];
     int tx, ty, nbx, nby;
@@ -217,6 +219,7 @@ struct FftXP {
     const int* rev;
     FastDiv d_nch, d_n0, d_lines, d_lines_psi;
     double* energy;     // if non-null: += (1/2) sum_k e^{-k^2/4a^2} |omega_k|^2 / k^2
+    double* epart;      // if non-null (deterministic): the CTA's share written to epart[blockIdx.x]
     // Spectrum mode (spectrum non-null): after the forward x transform, add
     // |k x F_k|^2 e^{s k^2 / 4a^2} prod tab_d / k^4 (s = +1 unsmoothed, -1
     // smoothed; both halves of the spectrum) to shell round(|k| / dk) of
@@ -292,6 +295,15 @@ struct Work {
     void* ktab = nullptr;     // per-axis k-space tables
     int* rev = nullptr;       // per-axis positions of frequency k after the forward transform (n0 + n1 + n2)
     double* shell = nullptr;  // energy-spectrum shell sums
+    // BS_DETERMINISTIC: the source index of every binned copy (scatter order),
+    // the copies re-ordered by it, and float64 partial sums reduced in order
+    int* sr_idx = nullptr;
+    int* col_idx = nullptr;
+    void* sr_sorted2 = nullptr;
+    void* col_rec2 = nullptr;
+    double* epart = nullptr;  // per-CTA energy partials of the x/k-space kernel
+    double* lpart = nullptr;  // per-filament energy line integrals
+    int nepart = 0;
     void* fft_work = nullptr;
     // pruned-FFT pipeline
     void* tw = nullptr;       // twiddles e^{-2 pi i j / n_d}, n0 + n1 + n2 complex
@@ -318,7 +330,7 @@ template <typename T>
 cudaError_t launch_export_quadrature(const GeomP& P, const double* nodes, const Work& w, double* qX, double* qq,
                                      cudaStream_t s);
 template <typename T>
-cudaError_t launch_sort_sr(const Work& w, int NQ, int ncells, cudaStream_t s);
+cudaError_t launch_sort_sr(const Work& w, int NQ, int ncells, cudaStream_t s, bool det);
 template <typename T>
 cudaError_t launch_sort_lr(const Work& w, int NQ, int ntiles, cudaStream_t s);
 template <typename T>
@@ -332,7 +344,7 @@ cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, 
                           double* out, double* part_long, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s);
+cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s, bool det);
 template <typename T>
 cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s);
 template <typename T>
@@ -348,7 +360,13 @@ template <typename T>
 size_t spread_zfft_smem(const SpZP& P);
 
 template <typename T>
-cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s);
+cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s, bool det);
+// Warp per segment: out[start[s] + rank] = in[i] with rank the position of
+// key[i] among the segment's keys (distinct within a segment).
+template <typename R>
+cudaError_t launch_segsort(const int* start, int nseg, const R* in, const int* key, R* out, cudaStream_t s);
+cudaError_t launch_segsort_bytes(const int* start, int nseg, const void* in, const int* key, void* out,
+                                 size_t rec_bytes, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);

@@ -460,7 +460,7 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
 // weights of that block's local columns picked out (zero outside the support).
 template <typename T, int W>
 __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cur,
-                              SpRec<T, W>* __restrict__ out)
+                              SpRec<T, W>* __restrict__ out, int* __restrict__ idx_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -507,6 +507,7 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
             D.base = (r0 + 128) | ((r1 + 128) << 8) | (ib2 << 16);
             const int p = atomicAdd(&cur[wx + P.nbx * wy], 1);
             out[p] = D;
+            if (idx_out) idx_out[p] = i;
         }
     }
 }
@@ -548,6 +549,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
     constexpr int H = W / 2;
     const int s0 = cstart[blockIdx.x], s1 = cstart[blockIdx.x + 1];
     const int nslot = Ty * W;
+    // deterministic mode: warp wid owns z in [zlo, zhi) and adds every record
+    // of the block in order (plain adds: one writer per cell, ordered sums)
+    const int zlo = P.det ? (int)(((long long)wid * n2) / nw) : 0;
+    const int zhi = P.det ? (int)(((long long)(wid + 1) * n2) / nw) : n2;
     for (int c0r = s0; c0r < s1; c0r += kSpzChunk) {
         const int nch = min(kSpzChunk, s1 - c0r);
         __syncthreads();
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
             cp_async_wait_all();
         }
         __syncthreads();
-        for (int kk = wid; kk < nch; kk += nw) {
+        for (int kk = P.det ? 0 : wid; kk < nch; kk += P.det ? 1 : nw) {
             const SpRec<T, W>& R = srec[kk];
             const int base = R.base;
             const int ib2 = (base >> 16) & 1023;
@@ -577,6 +582,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
                 int z = ib2 - H + 1 + t;
                 z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
                 const T wyz = R.wy[ly] * R.wz[t];
+                if (P.det) {
+                    if (z < zlo || z >= zhi) continue;
+                    for (int lx = a0; lx <= e0; ++lx) {
+                        const T wv = R.wx[lx] * wyz;
+                        const int rl = lx * Ty + ly;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const int rlc = rl + c * txy;
+                            const T qc = c == 0 ? q0 : (c == 1 ? q1 : q2);
+                            accf[((rlc >> 1) * CS + z) * 2 + (rlc & 1)] += wv * qc;
+                        }
+                    }
+                    continue;
+                }
                 for (int lx = a0; lx <= e0; ++lx) {
                     const T wv = R.wx[lx] * wyz;
                     const int rl = lx * Ty + ly;  // real line of component 0
@@ -588,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
                     }
                 }
             }
+            if (P.det) __syncwarp();  // this record's adds precede the next record's
         }
     }
     __syncthreads();
@@ -840,7 +860,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_fft_x_kspa
     if (P.energy) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
-        if ((threadIdx.x & 31) == 0 && esum != 0.0) atomicAdd(P.energy, esum);
+        if (P.epart) {
+            // deterministic: warp sums in warp order, one partial per CTA
+            double* wsum = reinterpret_cast<double*>(a + (size_t)(want_psi ? 6 : 3) * MC * LS);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = esum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
+                P.epart[blockIdx.x] = t;
+            }
+        } else if ((threadIdx.x & 31) == 0 && esum != 0.0) {
+            atomicAdd(P.energy, esum);
+        }
     }
     __syncthreads();
     fft_inv_dit<T, RM>(a, (want_psi ? 6 : 3) * MC, want_psi ? P.d_lines_psi : P.d_lines, LS, P.plan0, tw0);
@@ -956,31 +989,37 @@ size_t col_rec_bytes(int w)
 }
 
 template <typename T, int W>
-static cudaError_t col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s)
+static cudaError_t col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s, bool det)
 {
-    k_col_scatter<T, W><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(P, (const LrRec<T>*)w.lr_rec, NQ,
-                                                                           w.col_cur, (SpRec<T, W>*)w.col_rec);
-    return cudaGetLastError();
+    // deterministic: copies go to the second buffer with their point indices,
+    // then every column block is ordered by point index
+    k_col_scatter<T, W><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+        P, (const LrRec<T>*)w.lr_rec, NQ, w.col_cur, (SpRec<T, W>*)(det ? w.col_rec2 : w.col_rec),
+        det ? w.col_idx : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !det) return e;
+    static_assert(sizeof(SpRec<T, W>) % 16 == 0, "records are moved as 16-byte words");
+    return launch_segsort_bytes(w.col_cnt, P.ncols, w.col_rec2, w.col_idx, w.col_rec, sizeof(SpRec<T, W>), s);
 }
 
 template <typename T>
-static cudaError_t launch_col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s)
+static cudaError_t launch_col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s, bool det)
 {
     switch (P.w) {
-    case 2: return col_scatter_w<T, 2>(P, w, NQ, s);
-    case 4: return col_scatter_w<T, 4>(P, w, NQ, s);
-    case 6: return col_scatter_w<T, 6>(P, w, NQ, s);
-    case 8: return col_scatter_w<T, 8>(P, w, NQ, s);
-    case 10: return col_scatter_w<T, 10>(P, w, NQ, s);
-    case 12: return col_scatter_w<T, 12>(P, w, NQ, s);
-    case 14: return col_scatter_w<T, 14>(P, w, NQ, s);
-    case 16: return col_scatter_w<T, 16>(P, w, NQ, s);
+    case 2: return col_scatter_w<T, 2>(P, w, NQ, s, det);
+    case 4: return col_scatter_w<T, 4>(P, w, NQ, s, det);
+    case 6: return col_scatter_w<T, 6>(P, w, NQ, s, det);
+    case 8: return col_scatter_w<T, 8>(P, w, NQ, s, det);
+    case 10: return col_scatter_w<T, 10>(P, w, NQ, s, det);
+    case 12: return col_scatter_w<T, 12>(P, w, NQ, s, det);
+    case 14: return col_scatter_w<T, 14>(P, w, NQ, s, det);
+    case 16: return col_scatter_w<T, 16>(P, w, NQ, s, det);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
-cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s)
+cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s, bool det)
 {
     cudaError_t e = cudaMemsetAsync(w.col_cnt, 0, sizeof(int) * (size_t)(P.ncols + 1), s);
     if (e != cudaSuccess) return e;
@@ -991,7 +1030,7 @@ cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s
     e = cudaMemcpyAsync(w.col_cur, w.col_cnt, sizeof(int) * (size_t)P.ncols, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     if (NQ > 0)
-        e = launch_col_scatter_w<T>(P, w, NQ, s);
+        e = launch_col_scatter_w<T>(P, w, NQ, s, det);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1106,6 +1145,7 @@ struct FftXLaunch {
         const int nl = (want_psi ? 6 : 3) * MC;
         size_t sm = (size_t)nl * P.ls * sizeof(C);
         if (P.spectrum) sm = std::max(sm, (size_t)3 * MC * P.ls * sizeof(C) + sizeof(double) * (size_t)P.nbins);
+        if (P.epart) sm += sizeof(double) * (kThreads / 32);
         cudaError_t e =
             cudaFuncSetAttribute(k_fft_x_kspace<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -1151,8 +1191,8 @@ cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s)
     return by_rm<T>(P.plan2, FftZLaunch<T>{ P, w, s });
 }
 
-template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaStream_t);
-template cudaError_t launch_col_sort<double>(const ColP&, const Work&, int, cudaStream_t);
+template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaStream_t, bool);
+template cudaError_t launch_col_sort<double>(const ColP&, const Work&, int, cudaStream_t, bool);
 template cudaError_t launch_spread_zfft<float>(const SpZP&, const Work&, cudaStream_t);
 template cudaError_t launch_spread_zfft<double>(const SpZP&, const Work&, cudaStream_t);
 template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, cudaStream_t);

@@ -510,7 +510,7 @@ template <typename T>
 __global__ void k_energy_line(const int64_t* __restrict__ off, const double* __restrict__ shift, int nfil, int nmax,
                               const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ Mm,
                               const T* __restrict__ Tper, const double* __restrict__ pls, const T* __restrict__ psr,
-                              double* __restrict__ acc)
+                              double* __restrict__ acc, double* __restrict__ per_fil)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double* sh_h = reinterpret_cast<double*>(sm_raw);
@@ -590,11 +590,16 @@ __global__ void k_energy_line(const int64_t* __restrict__ off, const double* __r
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) part += __shfl_xor_sync(0xffffffffu, part, k);
-    if (lane == 0) atomicAdd(acc, part);
+    if (lane == 0) {
+        if (per_fil)
+            per_fil[f] = part;  // deterministic: summed in filament order on the host
+        else
+            atomicAdd(acc, part);
+    }
 }
 
 template <typename T>
-cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s)
+cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s, bool det)
 {
     (void)nodes;
     if (nfil <= 0) return cudaSuccess;
@@ -605,12 +610,12 @@ cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int
     }
     k_energy_line<T><<<nfil, 32, sm, s>>>(w.off, w.shift, nfil, nmax, (const T*)w.hseg, (const T*)w.dp,
                                           (const T*)w.Mm, (const T*)w.Tper, w.pls, (const T*)w.psr,
-                                          w.energy_acc + 1);
+                                          w.energy_acc + 1, det ? w.lpart : nullptr);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_energy_line<float>(const double*, const Work&, int, int, cudaStream_t);
-template cudaError_t launch_energy_line<double>(const double*, const Work&, int, int, cudaStream_t);
+template cudaError_t launch_energy_line<float>(const double*, const Work&, int, int, cudaStream_t, bool);
+template cudaError_t launch_energy_line<double>(const double*, const Work&, int, int, cudaStream_t, bool);
 
 // Quadrature export for bs_get_quadrature (float64, wrapped positions).
 template <typename T>

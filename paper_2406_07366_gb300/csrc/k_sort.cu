@@ -111,19 +111,60 @@ cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The order inside a bin follows the atomics; idx_out (if non-null) records
+// each copy's source index so that the bins can be re-ordered by it.
 template <typename R>
 __global__ void k_scatter(const int* __restrict__ key, const R* __restrict__ in, int n, int* __restrict__ cur,
-                          R* __restrict__ out)
+                          R* __restrict__ out, int* __restrict__ idx_out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int p = atomicAdd(&cur[key[i]], 1);
         out[p] = in[i];
+        if (idx_out) idx_out[p] = i;
     }
+}
+
+// Warp per segment [start[s], start[s+1]): the copy with the r-th smallest key
+// goes to position start[s] + r (keys are distinct within a segment), records
+// moved as 16-byte words.
+__global__ void k_segsort(const int* __restrict__ start, int nseg, const int4* __restrict__ in,
+                          const int* __restrict__ key, int4* __restrict__ out, int words)
+{
+    const int lane = threadIdx.x & 31;
+    const int sg = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (sg >= nseg) return;
+    const int s0 = start[sg], n = start[sg + 1] - s0;
+    for (int a = lane; a < n; a += 32) {
+        const int ka = key[s0 + a];
+        int rank = 0;
+        for (int b = 0; b < n; ++b) rank += key[s0 + b] < ka;
+        const int4* src = in + (size_t)(s0 + a) * words;
+        int4* dst = out + (size_t)(s0 + rank) * words;
+        for (int k = 0; k < words; ++k) dst[k] = src[k];
+    }
+}
+
+cudaError_t launch_segsort_bytes(const int* start, int nseg, const void* in, const int* key, void* out,
+                                 size_t rec_bytes, cudaStream_t s)
+{
+    if (nseg <= 0) return cudaSuccess;
+    const int tb = 256;
+    const long long threads = 32LL * nseg;
+    k_segsort<<<(unsigned)((threads + tb - 1) / tb), tb, 0, s>>>(start, nseg, (const int4*)in, key, (int4*)out,
+                                                                 (int)(rec_bytes / 16));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_segsort(const int* start, int nseg, const R* in, const int* key, R* out, cudaStream_t s)
+{
+    static_assert(sizeof(R) % 16 == 0, "records are moved as 16-byte words");
+    return launch_segsort_bytes(start, nseg, in, key, out, sizeof(R), s);
 }
 
 template <typename R>
 static cudaError_t sort_records(const int* key, const R* in, R* out, int n, int* cnt, int* cur, int nbins, int* tmp,
-                                cudaStream_t s)
+                                cudaStream_t s, int* idx_out = nullptr)
 {
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nbins + 1), s);
     if (e != cudaSuccess) return e;
@@ -137,16 +178,24 @@ static cudaError_t sort_records(const int* key, const R* in, R* out, int n, int*
     if (e != cudaSuccess) return e;
     if (n > 0) {
         const int g = (n + kThreads - 1) / kThreads;
-        k_scatter<R><<<g, kThreads, 0, s>>>(key, in, n, cur, out);
+        k_scatter<R><<<g, kThreads, 0, s>>>(key, in, n, cur, out, idx_out);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_sort_sr(const Work& w, int NQ, int ncells, cudaStream_t s)
+cudaError_t launch_sort_sr(const Work& w, int NQ, int ncells, cudaStream_t s, bool det)
 {
-    return sort_records<SrRec<T>>(w.sr_key, (const SrRec<T>*)w.sr_rec, (SrRec<T>*)w.sr_sorted, NQ, w.cell_cnt,
-                                  w.cell_cur, ncells, w.scan_tmp, s);
+    if (!det)
+        return sort_records<SrRec<T>>(w.sr_key, (const SrRec<T>*)w.sr_rec, (SrRec<T>*)w.sr_sorted, NQ, w.cell_cnt,
+                                      w.cell_cur, ncells, w.scan_tmp, s);
+    // deterministic: bin into the second buffer with the source indices, then
+    // order every cell by source index
+    cudaError_t e = sort_records<SrRec<T>>(w.sr_key, (const SrRec<T>*)w.sr_rec, (SrRec<T>*)w.sr_sorted2, NQ,
+                                           w.cell_cnt, w.cell_cur, ncells, w.scan_tmp, s, w.sr_idx);
+    if (e != cudaSuccess) return e;
+    return launch_segsort<SrRec<T>>(w.cell_cnt, ncells, (const SrRec<T>*)w.sr_sorted2, w.sr_idx,
+                                    (SrRec<T>*)w.sr_sorted, s);
 }
 
 template <typename T>
@@ -156,8 +205,8 @@ cudaError_t launch_sort_lr(const Work& w, int NQ, int ntiles, cudaStream_t s)
                                   w.tile_cur, ntiles, w.scan_tmp2, s);
 }
 
-template cudaError_t launch_sort_sr<float>(const Work&, int, int, cudaStream_t);
-template cudaError_t launch_sort_sr<double>(const Work&, int, int, cudaStream_t);
+template cudaError_t launch_sort_sr<float>(const Work&, int, int, cudaStream_t, bool);
+template cudaError_t launch_sort_sr<double>(const Work&, int, int, cudaStream_t, bool);
 template cudaError_t launch_sort_lr<float>(const Work&, int, int, cudaStream_t);
 template cudaError_t launch_sort_lr<double>(const Work&, int, int, cudaStream_t);
 

@@ -172,3 +172,17 @@ def test_tangle_params_clamp_modes(B):
     for p in (small, mid, big):
         assert p.alpha * p.rc == pytest.approx(3.5, rel=1e-14)
         assert p.alpha == pytest.approx(((p.M[0] - 1) // 2) / (2 * 3.5), rel=1e-14)
+
+
+def test_library_has_no_unresolved_internal_symbols(B):
+    """Every template the translation units use across files is instantiated:
+    no symbol of the library's own namespace is left undefined (the dynamic
+    loader would refuse the library on the GPU host)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--undefined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    internal = [ln for ln in out.splitlines() if "_ZN3bsw" in ln]
+    assert not internal, internal
