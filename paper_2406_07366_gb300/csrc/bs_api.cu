@@ -220,7 +220,8 @@ int derive(const bs_params* p, Derived* d)
     if (p->rc > 0.5 * Lmin * (1 + 1e-12))
         return fail(BS_ERR_RC_GT_HALF_L, "rc = %g exceeds min(L)/2 = %g", p->rc, 0.5 * Lmin);
     if (p->quad_Q < 1 || p->quad_Q > kMaxQ) return fail(BS_ERR_ARG, "quad_Q must be in 1..%d", kMaxQ);
-    if (p->spline_order != 4) return fail(BS_ERR_ARG, "spline_order %d not supported (4 = cubic)", p->spline_order);
+    if (p->spline_order != 4 && p->spline_order != 6)
+        return fail(BS_ERR_ARG, "spline_order %d not supported (4 = cubic, 6 = quintic)", p->spline_order);
     if (p->nufft_w < 2 || p->nufft_w > kMaxW || (p->nufft_w & 1))
         return fail(BS_ERR_ARG, "nufft_w must be even in 2..16");
     if (!(p->nufft_sigma > 1.0) || p->nufft_sigma > 4.0) return fail(BS_ERR_ARG, "nufft_sigma must be in (1, 4]");
@@ -461,6 +462,13 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.dp, sizeof(T) * 3 * N));
     TRY(dalloc(c, L, &w.ds, sizeof(T) * 3 * N));
     TRY(dalloc(c, L, &w.Mm, sizeof(T) * 3 * N));
+    if (c->p.spline_order == 6) {
+        TRY(dalloc(c, L, &w.Dd, sizeof(T) * 3 * N));
+        TRY(dalloc(c, L, (void**)&w.qtmp, sizeof(double) * 18 * N));
+    } else {
+        w.Dd = nullptr;
+        w.qtmp = nullptr;
+    }
     TRY(dalloc(c, L, &w.cpr, sizeof(T) * N));
     TRY(dalloc(c, L, &w.zz, sizeof(T) * N));
     TRY(dalloc(c, L, &w.Tper, sizeof(T) * nf));
@@ -1086,6 +1094,7 @@ int bs_compute_energy(bs_ctx* c, const double* nodes, double* vel, double* psi, 
     if (c->N == 0) return BS_OK;
     if (!nodes) return fail(BS_ERR_ARG, "null nodes");
     if (!(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "the energy needs a context created with BS_WANT_PSI");
+    if (c->p.spline_order != 4) return fail(BS_ERR_ARG, "the energy line integral is implemented for cubic splines");
     if (5 * (size_t)c->w.nmax_fil * sizeof(double) > 200 * 1024)
         return fail(BS_ERR_ARG, "filament too long for the energy integral (%d nodes > 5120)", c->w.nmax_fil);
     double* v = vel ? vel : c->w.vel_out;

@@ -263,7 +263,9 @@ struct Work {
     void* hseg = nullptr;   // N
     void* dp = nullptr;     // N x 3 periodic increments
     void* ds = nullptr;     // N x 3 chord vectors
-    void* Mm = nullptr;     // N x 3 moments
+    void* Mm = nullptr;     // N x 3 moments (second derivatives at the nodes)
+    void* Dd = nullptr;     // N x 3 first derivatives at the nodes (quintic splines only)
+    double* qtmp = nullptr; // 18 N scratch of the quintic spline solve
     void* cpr = nullptr;    // N Thomas scratch
     void* zz = nullptr;     // N Sherman-Morrison vector
     void* Tper = nullptr;   // nfil

@@ -297,20 +297,29 @@ __device__ __forceinline__ double wrap_box(double x, double L, double iL, bool& 
 
 template <typename T>
 struct SegPoly {
-    T b[3], m[3], c3[3], drift[3], h;
+    T b[3], m[3], c3[3], c4[3], c5[3], drift[3], h;
+    // p(u) - p_j = b u + m u^2 / 2 + c3 u^3 + c4 u^4 + c5 u^5 (+ drift u)
     __device__ __forceinline__ void eval(T u, T* delta, T* sdot) const
     {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            delta[c] = ((c3[c] * u + (T)0.5 * m[c]) * u + b[c]) * u + drift[c] * u;
-            sdot[c] = ((T)3 * c3[c] * u + m[c]) * u + b[c] + drift[c];
+            delta[c] = (((((c5[c] * u + c4[c]) * u + c3[c]) * u + (T)0.5 * m[c]) * u + b[c]) + drift[c]) * u;
+            sdot[c] = (((((T)5 * c5[c] * u + (T)4 * c4[c]) * u + (T)3 * c3[c]) * u + m[c]) * u + b[c]) + drift[c];
         }
     }
 };
 
+// Segment j (to jn).  Cubic (Dd == nullptr): from the moments M, b_j =
+// dp_j / h - h (2 M_j + M_{j+1}) / 6, c3 = (M_{j+1} - M_j) / (6 h).  Quintic:
+// the Hermite quintic through p_j, p_{j+1} with first derivatives D_j,
+// D_{j+1} and second derivatives M_j, M_{j+1}:
+//   A = (dp - D_j h - M_j h^2 / 2) / h^3, B = (D_{j+1} - D_j - M_j h) / h^2,
+//   C = (M_{j+1} - M_j) / h,
+//   c3 = 10 A - 4 B + C / 2, c4 = (7 B - 15 A - C) / h, c5 = (6 A - 3 B + C / 2) / h^2.
 template <typename T>
 __device__ __forceinline__ void make_poly(SegPoly<T>& P, const T* __restrict__ hseg, const T* __restrict__ dp,
-                                          const T* __restrict__ Mm, int j, int jn, const T drift[3])
+                                          const T* __restrict__ Mm, int j, int jn, const T drift[3],
+                                          const T* __restrict__ Dd = nullptr)
 {
     const T h = hseg[j];
     P.h = h;
@@ -319,9 +328,22 @@ __device__ __forceinline__ void make_poly(SegPoly<T>& P, const T* __restrict__ h
     for (int c = 0; c < 3; ++c) {
         const T Mj = Mm[3 * j + c], Mn = Mm[3 * jn + c];
         P.m[c] = Mj;
-        P.b[c] = dp[3 * j + c] * ih - h * ((T)2 * Mj + Mn) / (T)6;
-        P.c3[c] = (Mn - Mj) * ih / (T)6;
         P.drift[c] = drift[c];
+        if (Dd) {
+            const T Dj = Dd[3 * j + c], Dn = Dd[3 * jn + c];
+            const T A = (dp[3 * j + c] - Dj * h - (T)0.5 * Mj * h * h) * ih * ih * ih;
+            const T B = (Dn - Dj - Mj * h) * ih * ih;
+            const T C = (Mn - Mj) * ih;
+            P.b[c] = Dj;
+            P.c3[c] = (T)10 * A - (T)4 * B + (T)0.5 * C;
+            P.c4[c] = ((T)7 * B - (T)15 * A - C) * ih;
+            P.c5[c] = ((T)6 * A - (T)3 * B + (T)0.5 * C) * ih * ih;
+        } else {
+            P.b[c] = dp[3 * j + c] * ih - h * ((T)2 * Mj + Mn) / (T)6;
+            P.c3[c] = (Mn - Mj) * ih / (T)6;
+            P.c4[c] = 0;
+            P.c5[c] = 0;
+        }
     }
 }
 
@@ -349,7 +371,8 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
                         int* __restrict__ sr_key, LrRec<T>* __restrict__ lr_rec, int* __restrict__ lr_key,
                         SrTgt<T>* __restrict__ tgt, double* __restrict__ vls, double* __restrict__ pls,
                         double* __restrict__ part_local, double* __restrict__ part_self,
-                        double* __restrict__ psi_local, double* __restrict__ psi_self, int* __restrict__ status)
+                        double* __restrict__ psi_local, double* __restrict__ psi_self, int* __restrict__ status,
+                        const T* __restrict__ Dd)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= P.N) return;
@@ -363,7 +386,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     int flags = 0;
 
     SegPoly<T> S;
-    make_poly(S, hseg, dp, Mm, j, jn, drift);
+    make_poly(S, hseg, dp, Mm, j, jn, drift, Dd);
     if ((double)S.h > P.seg_max || !(S.h > (T)0)) flags |= ST_GEOMETRY;
 
     T vs[3] = { 0, 0, 0 }, ps[3] = { 0, 0, 0 };
@@ -426,7 +449,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     // Incoming segment jp -> j: self term and l^-.
     {
         SegPoly<T> R;
-        make_poly(R, hseg, dp, Mm, jp, j, drift);
+        make_poly(R, hseg, dp, Mm, jp, j, drift, Dd);
         const T dsx = ds[3 * jp], dsy = ds[3 * jp + 1], dsz = ds[3 * jp + 2];
         for (int i = 0; i < P.Q; ++i) {
             const T u = (T)P.gh[i] * R.h;
@@ -622,7 +645,8 @@ template <typename T>
 __global__ void k_export_quad(GeomP P, const double* __restrict__ nodes, const int* __restrict__ fil_of,
                               const int64_t* __restrict__ off, const double* __restrict__ shift,
                               const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ Mm,
-                              const T* __restrict__ Tper, double* __restrict__ qX, double* __restrict__ qq)
+                              const T* __restrict__ Tper, double* __restrict__ qX, double* __restrict__ qq,
+                              const T* __restrict__ Dd)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= P.N) return;
@@ -631,7 +655,7 @@ __global__ void k_export_quad(GeomP P, const double* __restrict__ nodes, const i
     const T Tp = Tper[f];
     const T drift[3] = { (T)shift[3 * f] / Tp, (T)shift[3 * f + 1] / Tp, (T)shift[3 * f + 2] / Tp };
     SegPoly<T> S;
-    make_poly(S, hseg, dp, Mm, j, jn, drift);
+    make_poly(S, hseg, dp, Mm, j, jn, drift, Dd);
     for (int i = 0; i < P.Q; ++i) {
         const T u = (T)P.gh[i] * S.h;
         T del[3], sd[3];
@@ -647,10 +671,190 @@ __global__ void k_export_quad(GeomP P, const double* __restrict__ nodes, const i
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Quintic spline fit (order 6, Appendix B): one thread per filament, float64.
+// The periodic C4 quintic through the nodes at the chord-length knots is
+// written per segment as the Hermite quintic of its end values, first
+// derivatives D and second derivatives M (make_poly).  Continuity of the
+// third and fourth derivatives at node j gives, per component,
+//   L_j X_{j-1} + B_j X_j + U_j X_{j+1} = R_j,   X_j = (D_j, M_j),
+//   L_j = [[-24/a^2, -3/a], [-168/a^3, -24/a^2]]
+//   B_j = [[36/h^2 - 36/a^2, 9/a + 9/h], [-192/a^3 - 192/h^3, 36/a^2 - 36/h^2]]
+//   U_j = [[24/h^2, -3/h], [-168/h^3, 24/h^2]]
+//   R_j = (60 dp_j/h^3 - 60 dp_{j-1}/a^3, -360 dp_j/h^4 - 360 dp_{j-1}/a^4)
+// with a = h_{j-1}, h = h_j (cyclic in j).  Solved by block elimination on
+// X_0..X_{n-2} with X_{n-1} as a border: X_j = Y_j + Z_j X_{n-1}, then the
+// last equation gives X_{n-1} (a 2 x 2 system).  The three components share
+// the matrix: every right-hand side is a 2 x 5 block (3 components + 2
+// border columns).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void q_blocks(double a, double h, double L[4], double B[4], double U[4])
+{
+    const double a2 = a * a, a3 = a2 * a, h2 = h * h, h3 = h2 * h;
+    L[0] = -24.0 / a2; L[1] = -3.0 / a; L[2] = -168.0 / a3; L[3] = -24.0 / a2;
+    B[0] = 36.0 / h2 - 36.0 / a2; B[1] = 9.0 / a + 9.0 / h;
+    B[2] = -192.0 / a3 - 192.0 / h3; B[3] = 36.0 / a2 - 36.0 / h2;
+    U[0] = 24.0 / h2; U[1] = -3.0 / h; U[2] = -168.0 / h3; U[3] = 24.0 / h2;
+}
+
+// inverse of the 2 x 2 matrix m (row major)
+__device__ __forceinline__ void inv2(const double m[4], double r[4])
+{
+    const double id = 1.0 / (m[0] * m[3] - m[1] * m[2]);
+    r[0] = m[3] * id; r[1] = -m[1] * id; r[2] = -m[2] * id; r[3] = m[0] * id;
+}
+
+// c (2 x 5) = a (2 x 2) * b (2 x 5)
+__device__ __forceinline__ void mul25(const double a[4], const double b[10], double c[10])
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        c[k] = a[0] * b[k] + a[1] * b[5 + k];
+        c[5 + k] = a[2] * b[k] + a[3] * b[5 + k];
+    }
+}
+
+template <typename T>
+__global__ void k_spline_quintic(const double* __restrict__ nodes, const int64_t* __restrict__ off,
+                                 const double* __restrict__ shift, int nfil, T* __restrict__ hseg, T* __restrict__ dp,
+                                 T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ Dd, T* __restrict__ Tper,
+                                 double* __restrict__ tmp)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfil) return;
+    const int64_t o = off[f];
+    const int n = (int)(off[f + 1] - o);
+    const double sh[3] = { shift[3 * f], shift[3 * f + 1], shift[3 * f + 2] };
+    // per node in tmp: h, dp[3] (float64), then the eliminated block (4) and right sides (10)
+    double* t = tmp + 18 * (size_t)o;
+    double Tsum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double* a = nodes + 3 * (o + j);
+        const double* b = nodes + 3 * (j + 1 < n ? o + j + 1 : o);
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = b[c] + (j + 1 < n ? 0.0 : sh[c]) - a[c];
+        const double h = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        Tsum += h;
+        t[18 * j] = h;
+        for (int c = 0; c < 3; ++c) t[18 * j + 1 + c] = d[c];
+        hseg[o + j] = (T)h;
+        for (int c = 0; c < 3; ++c) ds[3 * (o + j) + c] = (T)d[c];
+    }
+    Tper[f] = (T)Tsum;
+    const double invT = 1.0 / Tsum;
+    for (int j = 0; j < n; ++j)
+        for (int c = 0; c < 3; ++c) {
+            t[18 * j + 1 + c] -= sh[c] * t[18 * j] * invT;  // periodic increments
+            dp[3 * (o + j) + c] = (T)t[18 * j + 1 + c];
+        }
+    const int m = n - 1;
+    double L[4], B[4], U[4], Wm[4], iv[4], Bp[10], tmp10[10];
+    // forward elimination over j = 0..m-1
+    for (int j = 0; j < m; ++j) {
+        const int jm = j == 0 ? n - 1 : j - 1;
+        const double a = t[18 * jm], h = t[18 * j];
+        q_blocks(a, h, L, B, U);
+        double rhs[10];
+        for (int c = 0; c < 3; ++c) {
+            const double dj = t[18 * j + 1 + c], dm = t[18 * jm + 1 + c];
+            rhs[c] = 60.0 * dj / (h * h * h) - 60.0 * dm / (a * a * a);
+            rhs[5 + c] = -360.0 * dj / (h * h * h * h) - 360.0 * dm / (a * a * a * a);
+        }
+        rhs[3] = rhs[4] = rhs[8] = rhs[9] = 0.0;
+        if (j == 0) {  // border column: -L_0 X_{n-1}
+            rhs[3] -= L[0]; rhs[4] -= L[1]; rhs[8] -= L[2]; rhs[9] -= L[3];
+        }
+        if (j == m - 1) {  // border column: -U_{m-1} X_{n-1}
+            rhs[3] -= U[0]; rhs[4] -= U[1]; rhs[8] -= U[2]; rhs[9] -= U[3];
+        }
+        double Bj[4] = { B[0], B[1], B[2], B[3] };
+        if (j > 0) {
+            // W = L_j Bp_{j-1}^{-1}; B'_j = B_j - W U_{j-1}; rhs'_j = rhs_j - W rhs'_{j-1}
+            const double* pb = t + 18 * (j - 1) + 4;
+            double Bprev[4] = { pb[0], pb[1], pb[2], pb[3] };
+            inv2(Bprev, iv);
+            Wm[0] = L[0] * iv[0] + L[1] * iv[2]; Wm[1] = L[0] * iv[1] + L[1] * iv[3];
+            Wm[2] = L[2] * iv[0] + L[3] * iv[2]; Wm[3] = L[2] * iv[1] + L[3] * iv[3];
+            double Lq[4], Bq[4], Uq[4];
+            const int jmm = j - 2 < 0 ? n - 1 : j - 2;  // U_{j-1} uses h_{j-2}, h_{j-1}
+            q_blocks(t[18 * jmm], t[18 * (j - 1)], Lq, Bq, Uq);
+            Bj[0] -= Wm[0] * Uq[0] + Wm[1] * Uq[2]; Bj[1] -= Wm[0] * Uq[1] + Wm[1] * Uq[3];
+            Bj[2] -= Wm[2] * Uq[0] + Wm[3] * Uq[2]; Bj[3] -= Wm[2] * Uq[1] + Wm[3] * Uq[3];
+            const double* pr = t + 18 * (j - 1) + 8;
+            for (int k = 0; k < 10; ++k) Bp[k] = pr[k];
+            mul25(Wm, Bp, tmp10);
+            for (int k = 0; k < 10; ++k) rhs[k] -= tmp10[k];
+        }
+        for (int k = 0; k < 4; ++k) t[18 * j + 4 + k] = Bj[k];
+        for (int k = 0; k < 10; ++k) t[18 * j + 8 + k] = rhs[k];
+    }
+    // back substitution: X_j = B'_j^{-1} (rhs'_j - U_j X_{j+1}), stored over rhs'_j
+    for (int j = m - 1; j >= 0; --j) {
+        double rhs[10];
+        for (int k = 0; k < 10; ++k) rhs[k] = t[18 * j + 8 + k];
+        if (j < m - 1) {
+            const int jm = j == 0 ? n - 1 : j - 1;
+            q_blocks(t[18 * jm], t[18 * j], L, B, U);
+            const double* xn = t + 18 * (j + 1) + 8;
+            for (int k = 0; k < 10; ++k) Bp[k] = xn[k];
+            mul25(U, Bp, tmp10);
+            for (int k = 0; k < 10; ++k) rhs[k] -= tmp10[k];
+        }
+        double Bj[4] = { t[18 * j + 4], t[18 * j + 5], t[18 * j + 6], t[18 * j + 7] };
+        inv2(Bj, iv);
+        mul25(iv, rhs, tmp10);
+        for (int k = 0; k < 10; ++k) t[18 * j + 8 + k] = tmp10[k];
+    }
+    // last equation: (L_{n-1} Z_{n-2} + B_{n-1} + U_{n-1} Z_0) X_{n-1} = R_{n-1} - L_{n-1} Y_{n-2} - U_{n-1} Y_0
+    {
+        const double a = t[18 * (m - 1)], h = t[18 * m];
+        q_blocks(a, h, L, B, U);
+        const double* x0 = t + 8;                 // X_0 (Y | Z)
+        const double* xl = t + 18 * (m - 1) + 8;  // X_{n-2}
+        double Sm[4];
+        // Z columns are entries 3, 4 (row 0) and 8, 9 (row 1)
+        Sm[0] = B[0] + L[0] * xl[3] + L[1] * xl[8] + U[0] * x0[3] + U[1] * x0[8];
+        Sm[1] = B[1] + L[0] * xl[4] + L[1] * xl[9] + U[0] * x0[4] + U[1] * x0[9];
+        Sm[2] = B[2] + L[2] * xl[3] + L[3] * xl[8] + U[2] * x0[3] + U[3] * x0[8];
+        Sm[3] = B[3] + L[2] * xl[4] + L[3] * xl[9] + U[2] * x0[4] + U[3] * x0[9];
+        inv2(Sm, iv);
+        double xlast[6];
+        for (int c = 0; c < 3; ++c) {
+            const double dj = t[18 * m + 1 + c], dm = t[18 * (m - 1) + 1 + c];
+            const double r0 = 60.0 * dj / (h * h * h) - 60.0 * dm / (a * a * a) - (L[0] * xl[c] + L[1] * xl[5 + c]) -
+                              (U[0] * x0[c] + U[1] * x0[5 + c]);
+            const double r1 = -360.0 * dj / (h * h * h * h) - 360.0 * dm / (a * a * a * a) -
+                              (L[2] * xl[c] + L[3] * xl[5 + c]) - (U[2] * x0[c] + U[3] * x0[5 + c]);
+            xlast[c] = iv[0] * r0 + iv[1] * r1;
+            xlast[3 + c] = iv[2] * r0 + iv[3] * r1;
+        }
+        for (int c = 0; c < 3; ++c) {
+            Dd[3 * (o + m) + c] = (T)xlast[c];
+            Mm[3 * (o + m) + c] = (T)xlast[3 + c];
+        }
+        for (int j = 0; j < m; ++j) {
+            const double* x = t + 18 * j + 8;
+            for (int c = 0; c < 3; ++c) {
+                const double Dj = x[c] + x[3] * xlast[c] + x[4] * xlast[3 + c];
+                const double Mj = x[5 + c] + x[8] * xlast[c] + x[9] * xlast[3 + c];
+                Dd[3 * (o + j) + c] = (T)Dj;
+                Mm[3 * (o + j) + c] = (T)Mj;
+            }
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_spline(const double* nodes, const Work& w, int nfil, cudaStream_t s)
 {
     if (nfil <= 0) return cudaSuccess;
+    if (w.Dd) {  // quintic
+        const int tb = 64;
+        k_spline_quintic<T><<<(nfil + tb - 1) / tb, tb, 0, s>>>(nodes, w.off, w.shift, nfil, (T*)w.hseg, (T*)w.dp,
+                                                                (T*)w.ds, (T*)w.Mm, (T*)w.Dd, (T*)w.Tper, w.qtmp);
+        return cudaGetLastError();
+    }
     const size_t sm = 9 * (size_t)w.nmax_fil * sizeof(T);
     if (sm <= kSplineSmemMax) {
         if (sm > 48 * 1024) {
@@ -677,7 +881,7 @@ cudaError_t launch_nodes(const GeomP& P, const double* nodes, const Work& w, dou
     k_nodes<T><<<(P.N + tb - 1) / tb, tb, 0, s>>>(
         P, nodes, w.fil_of, w.prev, w.off, w.shift, (const T*)w.hseg, (const T*)w.dp, (const T*)w.ds,
         (const T*)w.Mm, (const T*)w.Tper, (SrRec<T>*)w.sr_rec, w.sr_key, (LrRec<T>*)w.lr_rec, w.lr_key,
-        (SrTgt<T>*)w.tgt, w.vls, w.pls, part_local, part_self, psi_local, psi_self, w.status);
+        (SrTgt<T>*)w.tgt, w.vls, w.pls, part_local, part_self, psi_local, psi_self, w.status, (const T*)w.Dd);
     return cudaGetLastError();
 }
 
@@ -688,7 +892,8 @@ cudaError_t launch_export_quadrature(const GeomP& P, const double* nodes, const 
     if (P.N <= 0) return cudaSuccess;
     const int tb = 128;
     k_export_quad<T><<<(P.N + tb - 1) / tb, tb, 0, s>>>(P, nodes, w.fil_of, w.off, w.shift, (const T*)w.hseg,
-                                                         (const T*)w.dp, (const T*)w.Mm, (const T*)w.Tper, qX, qq);
+                                                         (const T*)w.dp, (const T*)w.Mm, (const T*)w.Tper, qX, qq,
+                                                         (const T*)w.Dd);
     return cudaGetLastError();
 }
 

@@ -133,7 +133,7 @@ def test_validation_errors(B):
     assert code(p) == B.BS_ERR_RC_GT_HALF_L
     p = B.make_params(L, M=32, w=7)
     assert code(p) == B.BS_ERR_ARG
-    p = B.make_params(L, M=32, order=6)
+    p = B.make_params(L, M=32, order=5)
     assert code(p) == B.BS_ERR_ARG
     assert "spline_order" in B.bs_last_error()
     p = B.make_params(L, M=32, sigma=1.0)

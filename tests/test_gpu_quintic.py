@@ -1,0 +1,92 @@
+"""Quintic splines with three quadrature points (``-m gpu``): the paper's
+production setting (Sec. 5.2, order 6, Q = 3), against the oracle's
+periodic quintic B-spline (Appendix B)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_07366_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KAPPA, A_CORE, DELTA = 1.0, 1e-6, 0.25
+
+
+def _B():
+    import paper_2406_07366_gb300 as B
+    return B
+
+
+def _rms(a, b):
+    return float(np.sqrt(np.mean(np.sum((a - b) ** 2, axis=1)) / np.mean(np.sum(b ** 2, axis=1))))
+
+
+def _params(B, f, **kw):
+    return B.make_params(f.L, kappa=KAPPA, a=A_CORE, delta=DELTA, order=6, Q=3, **kw)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["trefoil", "ellipses", "lines"])
+def test_quintic_quadrature_points_and_charges(case, prec):
+    """Quadrature points s(tau_j + h_i dtau_j) and charges w_i dtau_j s'(tau)
+    of the GPU's Hermite-form quintic equal the oracle's B-spline ones (the
+    periodic C4 quintic through the nodes is unique), closed and unclosed."""
+    B = _B()
+    f = {"trefoil": lambda: W.trefoil(N=48), "ellipses": lambda: W.ellipses(nfil=5, N_l=20, seed=13),
+         "lines": lambda: W.three_line_pairs(N_l=12)}[case]()
+    p = _params(B, f, M=32, precision=B.BS_FP64 if prec == "fp64" else B.BS_MIXED)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    qX, qq = bs.quadrature(torch.from_numpy(f.nodes).cuda())
+    qX, qq = qX.cpu().numpy(), qq.cpu().numpy()
+    bs.close()
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 6, 3)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    dX = qX - g.qX
+    dX -= f.L[None, :] * np.round(dX / f.L[None, :])
+    assert np.abs(dX).max() < tol * max(1.0, np.abs(f.nodes).max())
+    assert np.abs(qq - g.qq).max() < 10 * tol * np.abs(g.qq).max()
+
+
+def test_quintic_total_is_implementation_parity():
+    """beta = 8, w = 16, sigma = 2: the GPU total with the quintic curve
+    equals the converged oracle on the same quintic curve."""
+    B = _B()
+    f = W.ellipses(nfil=4, N_l=24, seed=5)
+    L = f.L[0]
+    beta = 8.0
+    alpha = 2 * beta / L
+    K = int(math.ceil(beta * alpha * L / math.pi))
+    p = _params(B, f, M=2 * K + 1, w=16, sigma=2.0, precision=B.BS_FP64, beta=beta, alpha=alpha,
+                flags=B.BS_WANT_PSI)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    v, psi = bs.velocity(torch.from_numpy(f.nodes).cuda(), want_psi=True)
+    v, psi = v.cpu().numpy(), psi.cpu().numpy()
+    bs.close()
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 6, 3)
+    vr, pr = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
+    assert _rms(v, vr) < 1e-10
+    assert _rms(psi, pr) < 1e-10
+
+
+def test_quintic_trefoil_mixed_and_energy_refusal():
+    """The mixed form with quintic curves stays in the float32 budget on the
+    trefoil; the energy (cubic line integral) refuses quintic curves."""
+    B = _B()
+    f = W.trefoil(N=96)
+    p = _params(B, f, M=48, w=8, precision=B.BS_MIXED)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    v = bs.velocity(torch.from_numpy(f.nodes).cuda()).cpu().numpy()
+    bs.close()
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 6, 3)
+    vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
+    assert _rms(v, vr) < 1e-5
+    # energy is implemented for cubic curves only
+    pe = _params(B, f, M=48, w=8, precision=B.BS_FP64, flags=B.BS_WANT_PSI)
+    be = B.BiotSavart(pe, f.offsets, f.closing)
+    with pytest.raises(B.BSError) as e:
+        be.energy(torch.from_numpy(f.nodes).cuda())
+    assert e.value.code == B.BS_ERR_ARG
+    be.close()
