@@ -224,6 +224,21 @@ int bs_get_quadrature(bs_ctx* ctx, const double* nodes, double* qX, double* qq);
 int bs_energy_spectrum(bs_ctx* ctx, const double* nodes, int smoothed, int nbins, double* Ek, double* dk_out);
 
 /*
+ * bs_coarse_velocity -- the long-range (Gaussian-filtered, coarse-grained)
+ * velocity v^(f) on the context's spread grid (Sec. 3.3 and Sec. 6): the
+ * same spread, transforms and k-space pass as bs_compute, with the spread's
+ * deconvolution only (no interpolation), so that
+ *   grid[c][x][y][z] = sum over the mode cube of v^(f)_k e^{i k . x_g},
+ *   x_g = (x L_0 / n_0, y L_1 / n_1, z L_2 / n_2), c = 0, 1, 2.
+ *   nodes (device) N x 3; grid (device) 3 n_0 n_1 n_2 float64, or NULL to
+ *   query the size; n_g (host, or NULL) receives n_0, n_1, n_2.
+ * Asynchronous on the context stream.  Needs the default transform path
+ * (BS_ERR_STATE with BS_FFT_CUFFT).  Errors: BS_ERR_ARG, BS_ERR_STATE,
+ * BS_ERR_CUDA.
+ */
+int bs_coarse_velocity(bs_ctx* ctx, const double* nodes, double* grid, int n_g[3]);
+
+/*
  * Capture one bs_compute(ctx, nodes, vel, psi) into a CUDA graph bound to
  * these device buffers (both branches of the evaluation become graph
  * branches), replacing any previous graph; bs_graph_launch replays it on

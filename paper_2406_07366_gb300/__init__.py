@@ -37,7 +37,7 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
            "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
-           "bs_autotune_alpha", "bs_energy_spectrum"]
+           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity"]
 
 
 class bs_params(ctypes.Structure):
@@ -96,6 +96,7 @@ def _load():
         "bs_rk4_step": ([vp, vp, ctypes.c_double], ctypes.c_int),
         "bs_rk4_capture": ([vp, vp, ctypes.c_double], ctypes.c_int),
         "bs_rk4_launch": ([vp, ctypes.c_int], ctypes.c_int),
+        "bs_coarse_velocity": ([vp, vp, vp, P(ctypes.c_int)], ctypes.c_int),
         "bs_energy_spectrum": ([vp, vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)],
                                ctypes.c_int),
         "bs_autotune_alpha": ([P(bs_params), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32), vp, ctypes.c_int,
@@ -233,6 +234,14 @@ def bs_rk4_capture(ctx, nodes, dt):
 
 def bs_rk4_launch(ctx, nsteps):
     _check(lib().bs_rk4_launch(ctx, int(nsteps)))
+
+
+def bs_coarse_velocity(ctx, nodes, grid=None):
+    """Grid shape (n0, n1, n2); with a device tensor ``grid`` (3 x n0 x n1 x n2
+    float64) also fills it with the coarse-grained long-range velocity."""
+    ng = (ctypes.c_int * 3)()
+    _check(lib().bs_coarse_velocity(ctx, _ptr(nodes), _ptr(grid), ng))
+    return tuple(ng)
 
 
 def bs_energy_spectrum(ctx, nodes, nbins, smoothed=False):
@@ -437,6 +446,13 @@ class BiotSavart:
     def energy(self, nodes, vel=None, psi=None):
         """Kinetic energy (and optionally velocity / streamfunction) of one evaluation."""
         return bs_compute_energy(self.ctx, nodes, vel, psi)
+
+    def coarse_velocity(self, nodes):
+        """The long-range velocity on the spread grid, 3 x n0 x n1 x n2 float64."""
+        shape = bs_coarse_velocity(self.ctx, None, None)
+        grid = self.torch.empty((3,) + shape, dtype=self.torch.float64, device="cuda")
+        bs_coarse_velocity(self.ctx, nodes, grid)
+        return grid
 
     def energy_spectrum(self, nodes, nbins, smoothed=False):
         """(k, E(k)) on the context's Fourier modes (Eq. def_energy_spectrum)."""

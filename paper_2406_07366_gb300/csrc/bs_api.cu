@@ -429,20 +429,24 @@ int alloc_grids(bs_ctx* c)
         TRY(dalloc(c, c->alloc_g, (void**)&c->w.epart, sizeof(double) * (size_t)c->w.nepart));
     }
     CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
-    // k-space tables e^{-k_d^2 / 4 alpha^2} / F_d(m)^2, m = 0..K_d
+    // k-space tables, m = 0..K_d: e^{-k_d^2 / 4 alpha^2} / F_d(m)^2 (deconvolved for
+    // the spread and for the interpolation), then e^{-k_d^2 / 4 alpha^2} / F_d(m)
+    // (the spread's deconvolution alone: the coarse-grained field on the grid)
     const int ntab = d.K[0] + d.K[1] + d.K[2] + 3;
-    std::vector<T> tab(ntab);
+    std::vector<T> tab(2 * (size_t)ntab);
     int o = 0;
     for (int ax = 0; ax < 3; ++ax) {
         std::vector<double> F(d.K[ax] + 1);
         kb_fourier(d.zeta, c->p.nufft_w, d.ng[ax], d.K[ax], F.data());
-        for (int m = 0; m <= d.K[ax]; ++m) {
+        for (int m = 0; m <= d.K[ax]; ++m, ++o) {
             const double k = 2.0 * kPi * m / c->p.L[ax];
-            tab[o++] = (T)(exp(-k * k / (4.0 * c->p.alpha * c->p.alpha)) / (F[m] * F[m]));
+            const double g = exp(-k * k / (4.0 * c->p.alpha * c->p.alpha));
+            tab[o] = (T)(g / (F[m] * F[m]));
+            tab[ntab + o] = (T)(g / F[m]);
         }
     }
-    TRY(dalloc(c, c->alloc_g, &c->w.ktab, sizeof(T) * ntab));
-    CUDA_TRY(cudaMemcpy(c->w.ktab, tab.data(), sizeof(T) * ntab, cudaMemcpyHostToDevice));
+    TRY(dalloc(c, c->alloc_g, &c->w.ktab, sizeof(T) * tab.size()));
+    CUDA_TRY(cudaMemcpy(c->w.ktab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
     if (c->p.flags & BS_FFT_CUFFT) return make_plans<T>(c);
     return BS_OK;
 }
@@ -579,7 +583,8 @@ int fft_inv(bs_ctx* c, void* spec, cudaStream_t s)
 // concurrent); stage i spans events [kStageBeg[i], kStageEnd[i]].
 template <typename T>
 int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts, double* psi_parts,
-        bool want_energy = false, double* spectrum = nullptr, int smoothed = 0, int nbins = 0)
+        bool want_energy = false, double* spectrum = nullptr, int smoothed = 0, int nbins = 0,
+        double* coarse = nullptr)
 {
     const bs_params& p = c->p;
     const Derived& d = c->d;
@@ -601,8 +606,8 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
                        psi_parts ? psi_parts : nullptr, psi_parts ? psi_parts + 3 * N3 : nullptr, s));
     rec(c, 1, s);
 
-    // short range on the side stream (not in spectrum mode)
-    if (!spectrum) {
+    // short range on the side stream (not for the spectrum or the grid field)
+    if (!spectrum && !coarse) {
     CE(cudaEventRecord(c->ev_fork, s));
     CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     cudaStream_t ss = c->side;
@@ -727,6 +732,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         XP.smoothed = smoothed;
         XP.dk = 2.0 * kPi / std::min(p.L[0], std::min(p.L[1], p.L[2]));
         XP.inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
+        XP.single_decon = coarse ? 1 : 0;
         if (spectrum) return (int)launch_fft_x_kspace<T>(XP, w, false, s) == (int)cudaSuccess
                                  ? BS_OK
                                  : fail(BS_ERR_CUDA, "spectrum kernel launch failed");
@@ -749,6 +755,11 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         ZP.d_ncl = make_fastdiv((unsigned)(d.yc / 2));
         CE(launch_fft_z_c2r<T>(ZP, w, s));
         rec(c, 8, s);
+        if (coarse) {  // the coarse-grained field on the grid: copy out, no interpolation
+            const size_t ng3 = (size_t)d.ng[0] * d.ng[1] * d.ng[2];
+            CE(launch_to_double<T>(w.grid, coarse, (int)(3 * ng3), s));
+            return BS_OK;
+        }
     }
     CE(cudaStreamWaitEvent(s, c->ev_join, 0));
     rec(c, 9, s);
@@ -1146,6 +1157,25 @@ int bs_energy_spectrum(bs_ctx* c, const double* nodes, int smoothed, int nbins, 
     const double sc = c->p.kappa / (c->p.L[0] * c->p.L[1] * c->p.L[2]);
     for (int m = 0; m < nb; ++m) Ek[m] *= sc * sc / (2.0 * dk);
     return BS_OK;
+}
+
+int bs_coarse_velocity(bs_ctx* c, const double* nodes, double* grid, int n_g[3])
+{
+    TRY(check_ctx(c));
+    if (c->p.flags & BS_FFT_CUFFT) return fail(BS_ERR_STATE, "the grid field needs the pruned transform path");
+    if (n_g)
+        for (int k = 0; k < 3; ++k) n_g[k] = c->d.ng[k];
+    if (!grid) return BS_OK;  // size query
+    const double ng3 = (double)c->d.ng[0] * c->d.ng[1] * c->d.ng[2];
+    if (3.0 * ng3 > 2147483647.0) return fail(BS_ERR_ARG, "grid too large for the copy-out");
+    if (c->N == 0) {
+        CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(double) * 3 * (size_t)ng3, c->stream));
+        return BS_OK;
+    }
+    if (!nodes) return fail(BS_ERR_ARG, "null nodes");
+    return c->p.precision == BS_FP64
+               ? run<double>(c, nodes, nullptr, nullptr, nullptr, nullptr, false, nullptr, 0, 0, grid)
+               : run<float>(c, nodes, nullptr, nullptr, nullptr, nullptr, false, nullptr, 0, 0, grid);
 }
 
 int bs_get_quadrature(bs_ctx* c, const double* nodes, double* qX, double* qq)

@@ -129,6 +129,7 @@ struct KspaceP {
     int smoothed;
     double dk;
     double inv4a2;      // 1 / (4 alpha^2)
+    int single_decon;   // k-space tables with the spread's deconvolution only (grid field)
 };
 
 // Exact unsigned division by a run-time constant d for 0 <= x < 2^31
@@ -229,6 +230,7 @@ struct FftXP {
     int smoothed;
     double dk;
     double inv4a2;      // 1 / (4 alpha^2)
+    int single_decon;   // k-space tables with the spread's deconvolution only (grid field)
 };
 
 struct FftZP {

@@ -1151,7 +1151,8 @@ struct FftXLaunch {
         if (e != cudaSuccess) return e;
         const int nk = P.K[2] + 1;
         const int nch = (nk + MC - 1) / MC;
-        const T* tab0 = (const T*)w.ktab;
+        const int ntab = P.K[0] + P.K[1] + P.K[2] + 3;
+        const T* tab0 = (const T*)w.ktab + (P.single_decon ? ntab : 0);
         const T* tab1 = tab0 + (P.K[0] + 1);
         const T* tab2 = tab1 + (P.K[1] + 1);
         k_fft_x_kspace<T, RM><<<(2 * P.K[1] + 1) * nch, kThreads, sm, s>>>(

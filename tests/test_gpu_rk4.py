@@ -114,3 +114,30 @@ def test_rk4_ring_translates_rigidly():
     r1 = np.linalg.norm(got[:, :2] - f.L[:2] / 2, axis=1)
     assert np.abs(r1 - r0).max() < 5e-5 * dist
     assert abs(e1 - e0) < 1e-5 * abs(e0)
+
+
+def test_rk4_quintic_leapfrog_matches_oracle():
+    """The paper's setting for the leapfrogging test (Sec. 5.2): quintic
+    curves, Q = 3.  The GPU trajectory follows the oracle's on the same
+    quintic curves, and the impulse is kept to the discretisation level."""
+    B = _B()
+    f = W.leapfrog_ellipses(N_l=48)
+    dt = B.kelvin_wave_period(_dmin(f), KAPPA, A_CORE, DELTA)
+    n = 10
+    ref = oracle.rk4_converged(f.nodes, f.offsets, f.closing, f.L, KAPPA, A_CORE, DELTA, dt, n, order=6, Q=3)
+    p = B.make_params(f.L, M=32, Q=3, order=6, w=8, precision=B.BS_FP64)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bs = B.BiotSavart(p, f.offsets, f.closing, stream=s)
+        x = torch.from_numpy(f.nodes).cuda()
+        bs.rk4_capture(x, dt)
+        bs.rk4_launch(n)
+        bs.status()
+        got = x.cpu().numpy()
+        bs.close()
+    travel = np.linalg.norm(ref - f.nodes, axis=1).max()
+    assert travel > 1e-3
+    assert np.linalg.norm(got - ref, axis=1).max() / travel < 2e-5
+    P0 = oracle.polygon_impulse(f.nodes, f.offsets, KAPPA)
+    P1 = oracle.polygon_impulse(got, f.offsets, KAPPA)
+    assert np.linalg.norm(P1 - P0) / np.linalg.norm(P0) < 1e-5

@@ -62,3 +62,30 @@ def test_spectrum_of_lines_and_argument_errors():
         bc.energy_spectrum(nodes, 10)
     assert e.value.code == B.BS_ERR_STATE
     bc.close()
+
+
+@pytest.mark.parametrize("prec,w,sigma,tol", [("fp64", 16, 2.0, 1e-10), ("mixed", 8, 1.5, 1e-5)])
+def test_coarse_velocity_on_the_grid_matches_fourier_sum(prec, w, sigma, tol):
+    """The coarse-grained (long-range) velocity written on the spread grid
+    equals the oracle's direct Fourier sum of v^(f) evaluated at those grid
+    points (sampled), relative to the field's largest value."""
+    import dataclasses
+    B = _B()
+    f = W.ellipses(nfil=6, N_l=24, seed=17)
+    P = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
+    p = B.make_params(f.L, M=32, Q=2, w=w, sigma=sigma, precision=P)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    grid = bs.coarse_velocity(torch.from_numpy(f.nodes).cuda()).cpu().numpy()
+    bs.close()
+    n0, n1, n2 = grid.shape[1:]
+    rng = np.random.default_rng(5)
+    pts = np.stack([rng.integers(0, n, 40) for n in (n0, n1, n2)], axis=1)
+    X = pts * (f.L / np.array([n0, n1, n2]))[None, :]
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 4, 2)
+    K = (p.M[0] - 1) // 2
+    om = oracle.fourier_coefs(g, f.L, KAPPA, np.array([K] * 3, np.int32))
+    ge = dataclasses.replace(g, nodes=np.ascontiguousarray(X))
+    vr, _ = oracle.fourier_eval(ge, f.L, p.alpha, np.array([K] * 3, np.int32), om, targets=np.arange(len(X)))
+    got = grid[:, pts[:, 0], pts[:, 1], pts[:, 2]].T
+    err = np.abs(got - vr).max() / np.abs(grid).max()
+    assert err < tol, err
