@@ -414,6 +414,41 @@ __device__ __forceinline__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, 
 }
 
 
+// Digit-reversed positions of 8 consecutive frequencies 8q + d (and of
+// n - 8q - d) when the plan's first radix is 8 (stride st0 = n / 8): the first
+// pass digit is d, so rev(8q + d) = rev(8q) + d st0, and, for d > 0,
+// rev(n - 8q - d) = rev(8 (n/8 - q - 1)) + (8 - d) st0.  Three table reads
+// instead of sixteen; other plans read the table per frequency.
+struct Rev8 {
+    int p0, pa, pb, st0;
+    bool ok;
+};
+
+__device__ __forceinline__ Rev8 rev8_bases(const int* __restrict__ rev, const FftPlan& pl, int q)
+{
+    Rev8 r;
+    r.ok = pl.r[0] == 8;
+    r.st0 = pl.st[0];
+    r.p0 = r.pa = r.pb = 0;
+    if (r.ok) {
+        const int n = pl.n;
+        r.p0 = rev[8 * q];
+        r.pa = rev[(n - 8 * q) % n];
+        r.pb = 8 * q + 8 <= n ? rev[n - 8 * q - 8] : 0;
+    }
+    return r;
+}
+
+__device__ __forceinline__ int rev8_pos(const Rev8& r, const int* __restrict__ rev, int k, int d)
+{
+    return r.ok ? r.p0 + d * r.st0 : rev[k];
+}
+
+__device__ __forceinline__ int rev8_neg(const Rev8& r, const int* __restrict__ rev, int n, int k, int d)
+{
+    return r.ok ? (d == 0 ? r.pa : r.pb + (8 - d) * r.st0) : rev[k == 0 ? 0 : n - k];
+}
+
 template <typename T>
 __device__ __forceinline__ T kb_val(T z, T zeta, T inorm)
 {
@@ -624,12 +659,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
         const int lx = fdiv(rem, P.d_ty), ly = rem - lx * Ty;
         const int x = bx * Tx + lx, y = by * Ty + ly;
         C* dst = F1 + (((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk;
+        const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int mz = 8 * q + d;
             if (mz >= nk) break;
-            const C zk = cb[l * CS + P.rev[mz]];
-            const C zn = cb[l * CS + P.rev[mz == 0 ? 0 : n2 - mz]];
+            const C zk = cb[l * CS + rev8_pos(rb, P.rev, mz, d)];
+            const C zn = cb[l * CS + rev8_neg(rb, P.rev, n2, mz, d)];
             C o;
             if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
                 o.x = (T)0.5 * (zk.x + zn.x);
@@ -808,12 +844,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_fft_x_kspa
     for (int i = threadIdx.x; i < nq * MC; i += blockDim.x) {
         const int lk = i / nq, q = i - lk * nq;
         const int mz = mz0 + lk;
+        const Rev8 rb = rev8_bases(P.rev, P.plan0, q);
 #pragma unroll 2
         for (int d = 0; d < 8; ++d) {
             const int xi = 8 * q + d;
             const int mx = xi <= n0 / 2 ? xi : xi - n0;
             const int amx = mx < 0 ? -mx : mx;
-            const int pos = P.rev[xi];
+            const int pos = rev8_pos(rb, P.rev, xi, d);
             C* r0 = a + ((0 * MC + lk) * LS + pos);
             C* r1 = a + ((1 * MC + lk) * LS + pos);
             C* r2 = a + ((2 * MC + lk) * LS + pos);
@@ -937,6 +974,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
                 Bv[d] = rowB[k];
             }
         }
+        const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int k = 8 * q + d;
@@ -949,10 +987,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
             } else {
                 z.x = A[d].x - Bv[d].y;
                 z.y = A[d].y + Bv[d].x;
-                a[l * CS + P.rev[k]] = z;
+                a[l * CS + rev8_pos(rb, P.rev, k, d)] = z;
                 z.x = A[d].x + Bv[d].y;
                 z.y = -A[d].y + Bv[d].x;
-                a[l * CS + P.rev[n2 - k]] = z;
+                a[l * CS + rev8_neg(rb, P.rev, n2, k, d)] = z;
             }
         }
     }
@@ -961,11 +999,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
     const size_t gsz = (size_t)P.ng[0] * n1 * n2;
     const int c = fdiv(cx, P.d_n0), x = cx - c * P.ng[0];
     T* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
-    // the CTA's YC rows of n2 reals are contiguous in the grid
-    for (int i = threadIdx.x; i < YC * n2; i += blockDim.x) {
-        const int yl = fdiv(i, P.d_n2), z = i - yl * n2;
-        const C v = a[(yl >> 1) * CS + z];
-        gout[i] = (yl & 1) ? v.y : v.x;
+    // the CTA's YC rows of n2 reals are contiguous in the grid; a thread reads
+    // two adjacent complex values of line l and writes the pair to each of the
+    // real rows 2l and 2l + 1 (n2 is even)
+    using T2 = typename Cx<T>::t;
+    const int h2 = n2 >> 1;
+    for (int i = threadIdx.x; i < ncl * h2; i += blockDim.x) {
+        const int l = i / h2, zz = i - l * h2;
+        const C v0 = a[l * CS + 2 * zz], v1 = a[l * CS + 2 * zz + 1];
+        T2 ra, rbv;
+        ra.x = v0.x;
+        ra.y = v1.x;
+        rbv.x = v0.y;
+        rbv.y = v1.y;
+        *reinterpret_cast<T2*>(gout + (size_t)(2 * l) * n2 + 2 * zz) = ra;
+        *reinterpret_cast<T2*>(gout + (size_t)(2 * l + 1) * n2 + 2 * zz) = rbv;
     }
 }
 
