@@ -82,13 +82,21 @@ enum {
  *                 |m_d| <= floor((M_d - 1)/2), k_max,d = (2 pi / L_d) floor((M_d-1)/2)
  *                 (Sec. 3.3, the Nyquist mode of even M is not used)
  *   quad_Q        Gauss-Legendre points per segment, 1..8 (Eq. line_integral_quadrature)
- *   spline_order  4 (cubic); the paper's 6 (quintic) is not built yet
+ *   spline_order  4 (cubic) or 6 (quintic, the paper's production setting)
  *   nufft_sigma   oversampling factor sigma > 1 (Appendix A)
  *   nufft_w       spreading width in grid points, even, 2..16 (Appendix A)
  *   precision     BS_FP64 or BS_MIXED
  *   flags         BS_WANT_PSI | BS_TIMING | BS_FFT_CUFFT | BS_DETERMINISTIC
  *   cell_div      cells per cut-off length m (cells of edge >= rc/m); the
  *                 paper uses 3 (Sec. 5.3); 0 selects the library default
+ *   local_frac    0: the local terms (Eqs. BS_local, streamfunction_local)
+ *                 cover the two whole local segments.  In (0, 1): the local
+ *                 segments are subdivided (Sec. 5.2): the Taylor expansions
+ *                 cover the fraction local_frac of each next to the node and
+ *                 the rest is integrated with the plain Biot-Savart kernel,
+ *                 quad_Q-point Gauss-Legendre on the pieces [f, 2f], [2f, 4f],
+ *                 ..., [2^m f, 1] of the segment (f = local_frac, measured from
+ *                 the node).  The paper uses about 0.1.
  */
 typedef struct {
     double L[3];
@@ -105,6 +113,7 @@ typedef struct {
     int precision;
     int flags;
     int cell_div;
+    double local_frac;
 } bs_params;
 
 typedef struct bs_ctx bs_ctx;

@@ -68,6 +68,9 @@ def _load():
         lib.or_local.argtypes = [ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, _dp, _dp]
         lib.or_local.restype = None
+        lib.or_local_sub.argtypes = [ctypes.c_long, _i64p, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        lib.or_local_sub.restype = ctypes.c_int
         lib.or_short_range.argtypes = [ctypes.c_long, _i64p, _dp, _i64p, _i64p, _dp, ctypes.c_long, ctypes.c_int,
                                        _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, _dp, _dp]
@@ -205,6 +208,19 @@ def local(g: Geometry, kappa, a, delta, targets=None):
     return v[t], psi[t]
 
 
+def local_subdivided(g: Geometry, kappa, a, delta, frac, order=4):
+    """Local terms with the local segments subdivided (Sec. 5.2): Taylor
+    expansions on the fraction frac of each local segment next to the node,
+    plain Biot-Savart Gauss-Legendre (g.Q points) on the rest.  (N x 3) v, psi."""
+    v = np.zeros((g.nodes.shape[0], 3))
+    psi = np.zeros((g.nodes.shape[0], 3))
+    rc = _load().or_local_sub(g.offsets.size - 1, _p(g.offsets, _i64p), _p(g.nodes), _p(g.shift), int(order),
+                              int(g.Q), float(frac), kappa, a, delta, _p(v), _p(psi))
+    if rc != 0:
+        raise RuntimeError(f"or_local_sub failed ({rc})")
+    return v, psi
+
+
 def short_range(g: Geometry, L, kappa, alpha, rc, all_images=False, targets=None):
     """v^(n), psi^(n) (Eqs. velocity_shortrange, streamfunction_shortrange)."""
     t = _targets(g, targets)
@@ -320,14 +336,20 @@ def converged_params(L, beta_o=6.0, alpha_scale=1.0):
 
 
 def velocity_converged(g: Geometry, L, kappa, a, delta, targets=None, beta_o=6.0, alpha_scale=1.0,
-                       return_parts=False):
+                       return_parts=False, local_frac=0.0, order=4):
     """Quadrature-discretised periodic Biot-Savart velocity and streamfunction.
 
     Evaluated with the oracle's own converged Ewald split (short range over
     all 27 images with no cut-off, long range over the mode cube K_o, self
     and local terms), combined with an exactly rounded sum."""
     alpha, K = converged_params(L, beta_o, alpha_scale)
-    vl, pl = local(g, kappa, a, delta, targets)
+    if local_frac > 0:
+        vl, pl = local_subdivided(g, kappa, a, delta, local_frac, order)
+        if targets is not None:
+            t = _targets(g, targets)
+            vl, pl = vl[t], pl[t]
+    else:
+        vl, pl = local(g, kappa, a, delta, targets)
     vs, ps = short_range(g, L, kappa, alpha, 0.0, all_images=True, targets=targets)
     vf, pf = long_range(g, L, kappa, alpha, K, targets=targets)
     vx, px = self_term(g, kappa, alpha, targets=targets)

@@ -413,6 +413,123 @@ void or_local(long N, const double* sp, const double* sxs, const double* lm, con
     }
 }
 
+/*
+ * Local terms with the local segments subdivided (Sec. 5.2): the Taylor
+ * expansions of Eqs. BS_local and streamfunction_local are applied only on
+ * the central portions of the two local segments, the fraction frac of each
+ * next to node j (l^- and l^+ their arc lengths, Q-point Gauss-Legendre),
+ * and the remaining portions of the two segments are integrated with the
+ * plain Biot-Savart kernel.  The paper does not say how; here each remaining
+ * portion is cut, from the node outwards, into pieces of the segment
+ * fraction [f, 2f], [2f, 4f], ..., [2^m f, 1] (a 1/r^2 integrand varies by at
+ * most 4x on a piece), with Q-point Gauss-Legendre on each:
+ *   v   += kappa/4pi sum w (s(x) - s_j) x s'(x) / |s(x) - s_j|^3,
+ *   psi += kappa/4pi sum w s'(x) / |s(x) - s_j|.
+ * frac = 1 gives or_local.  Per node: v, psi (N x 3).
+ */
+int or_local_sub(long nfil, const int64_t* off, const double* nodes, const double* shift, int k, int Q, double frac,
+                 double kappa, double a, double delta, double* v, double* psi)
+{
+    double h[64], w[64];
+    if (or_gauss_legendre(Q, h, w) != 0) return -1;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long f = 0; f < nfil; f++) {
+        long n = off[f + 1] - off[f];
+        const double* s = nodes + 3 * off[f];
+        const double* sh = shift + 3 * f;
+        double* tau = (double*)malloc((size_t)n * sizeof(double));
+        double* d = (double*)malloc((size_t)(n * 3) * sizeof(double));
+        double T;
+        if (n < k || fit_filament(n, s, sh, k, tau, &T, d) != 0) {
+#pragma omp atomic write
+            err = -4;
+            free(tau);
+            free(d);
+            continue;
+        }
+        kseq K = { tau, n, T };
+        const double drift[3] = { sh[0] / T, sh[1] / T, sh[2] / T };
+        for (long j = 0; j < n; j++) {
+            long g = off[f] + j;
+            long jm = (j + n - 1) % n;
+            const double t0 = tau[j];
+            const double hp = (j < n - 1 ? tau[j + 1] : T) - t0;      /* segment j */
+            const double tm = tau[jm];
+            const double hm = (jm < n - 1 ? tau[jm + 1] : T) - tm;    /* segment j-1 */
+            /* position (unwrapped) and tangent at parameter x of segment seg */
+            double sj[3];
+            for (int c = 0; c < 3; c++) sj[c] = s[3 * j + c];
+            csum lp = { 0, 0 }, lm = { 0, 0 };
+            csum av[3] = { { 0, 0 }, { 0, 0 }, { 0, 0 } }, ap[3] = { { 0, 0 }, { 0, 0 }, { 0, 0 } };
+            /* pieces: central of j and of j-1, then the geometric pieces of the
+             * remaining portions (fractions measured from the node) */
+            double pa[2 * 64 + 2], pb[2 * 64 + 2];
+            int pseg[2 * 64 + 2], pkind[2 * 64 + 2], np = 0;
+            pa[np] = 0.0; pb[np] = frac; pseg[np] = 0; pkind[np++] = 0;
+            pa[np] = 0.0; pb[np] = frac; pseg[np] = 1; pkind[np++] = 1;
+            for (int sd = 0; sd < 2; sd++) {
+                double x0 = frac;
+                while (x0 < 1.0 && np < 2 * 64) {
+                    double x1 = 2.0 * x0 < 1.0 ? 2.0 * x0 : 1.0;
+                    pa[np] = x0; pb[np] = x1; pseg[np] = sd; pkind[np++] = 2;
+                    x0 = x1;
+                }
+            }
+            for (int part = 0; part < np; part++) {
+                /* segment j runs away from the node, segment j-1 towards it */
+                long seg = pseg[part] == 0 ? j : jm;
+                double lo, len;
+                if (pseg[part] == 0) { lo = t0 + pa[part] * hp; len = (pb[part] - pa[part]) * hp; }
+                else { lo = tm + (1.0 - pb[part]) * hm; len = (pb[part] - pa[part]) * hm; }
+                for (int i = 0; i < Q; i++) {
+                    double x = lo + h[i] * len;
+                    double p0[3], p1[3];
+                    spline_eval(&K, k, d, seg, x, 0, p0);
+                    spline_eval(&K, k, d, seg, x, 1, p1);
+                    for (int c = 0; c < 3; c++) {
+                        p0[c] += drift[c] * x;
+                        p1[c] += drift[c];
+                    }
+                    /* the segment before node 0 ends at s_0 + shift */
+                    if (seg == jm && j == 0)
+                        for (int c = 0; c < 3; c++) p0[c] -= sh[c];
+                    double wt = w[i] * len;
+                    if (pkind[part] == 0) cs_add(&lp, wt * norm3(p1));
+                    else if (pkind[part] == 1) cs_add(&lm, wt * norm3(p1));
+                    else {
+                        double r[3] = { p0[0] - sj[0], p0[1] - sj[1], p0[2] - sj[2] };
+                        double rr = norm3(r);
+                        double q[3] = { wt * p1[0], wt * p1[1], wt * p1[2] };
+                        double cr[3];
+                        cross3(r, q, cr);
+                        for (int c = 0; c < 3; c++) {
+                            cs_add(&av[c], cr[c] / (rr * rr * rr));
+                            cs_add(&ap[c], q[c] / rr);
+                        }
+                    }
+                }
+            }
+            double d1[3], d2[3], bxs[3];
+            spline_eval(&K, k, d, j, tau[j], 1, d1);
+            spline_eval(&K, k, d, j, tau[j], 2, d2);
+            for (int c = 0; c < 3; c++) d1[c] += drift[c];
+            double sn = norm3(d1);
+            cross3(d1, d2, bxs);
+            double lg = log(2.0 * sqrt(cs_get(&lm) * cs_get(&lp)) / a);
+            for (int c = 0; c < 3; c++) {
+                v[3 * g + c] = kappa / (4.0 * OR_PI) * (bxs[c] / (sn * sn * sn) * (lg - delta) + cs_get(&av[c]));
+                if (psi)
+                    psi[3 * g + c] = kappa * d1[c] / sn / (2.0 * OR_PI) * (lg - (delta - 1.0)) +
+                                     kappa / (4.0 * OR_PI) * cs_get(&ap[c]);
+            }
+        }
+        free(tau);
+        free(d);
+    }
+    return err;
+}
+
 /* ------------------------------------------------------------------ */
 /* Weight functions, Eq. ewald_derivative_weight_functions             */
 /* ------------------------------------------------------------------ */

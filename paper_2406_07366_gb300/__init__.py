@@ -45,13 +45,13 @@ class bs_params(ctypes.Structure):
                 ("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("rc", ctypes.c_double),
                 ("M", ctypes.c_int * 3), ("quad_Q", ctypes.c_int), ("spline_order", ctypes.c_int),
                 ("nufft_sigma", ctypes.c_double), ("nufft_w", ctypes.c_int), ("precision", ctypes.c_int),
-                ("flags", ctypes.c_int), ("cell_div", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("cell_div", ctypes.c_int), ("local_frac", ctypes.c_double)]
 
     def as_dict(self):
         return dict(L=list(self.L), kappa=self.kappa, a=self.a, delta=self.delta, alpha=self.alpha, rc=self.rc,
                     M=list(self.M), quad_Q=self.quad_Q, spline_order=self.spline_order,
                     nufft_sigma=self.nufft_sigma, nufft_w=self.nufft_w, precision=self.precision,
-                    flags=self.flags, cell_div=self.cell_div)
+                    flags=self.flags, cell_div=self.cell_div, local_frac=self.local_frac)
 
 
 class BSError(RuntimeError):
@@ -347,7 +347,7 @@ def bs_short_range_static(L, kappa, alpha, rc, src_pos, src_q, src_seg, tgt_pos,
 
 # ------------------------------------------------------------- convenience
 def make_params(L, kappa=1.0, a=1e-6, delta=0.25, beta=3.5, M=32, Q=2, order=4, sigma=1.5, w=8,
-                precision=BS_FP64, flags=0, cell_div=0, alpha=None, rc=None) -> bs_params:
+                precision=BS_FP64, flags=0, cell_div=0, alpha=None, rc=None, local_frac=0.0) -> bs_params:
     """Parameters from beta and M (Sec. 4): k_max = (2 pi/L) floor((M-1)/2),
     alpha = k_max / (2 beta), r_c = beta / alpha, unless alpha / rc are given."""
     p = bs_params_from_beta(beta, L, M=M)
@@ -355,6 +355,7 @@ def make_params(L, kappa=1.0, a=1e-6, delta=0.25, beta=3.5, M=32, Q=2, order=4, 
     p.quad_Q, p.spline_order = Q, order
     p.nufft_sigma, p.nufft_w = sigma, w
     p.precision, p.flags, p.cell_div = precision, flags, cell_div
+    p.local_frac = local_frac
     if alpha is not None:
         p.alpha = alpha
         p.rc = beta / alpha if rc is None else rc

@@ -227,6 +227,7 @@ int derive(const bs_params* p, Derived* d)
     if (!(p->nufft_sigma > 1.0) || p->nufft_sigma > 4.0) return fail(BS_ERR_ARG, "nufft_sigma must be in (1, 4]");
     if (p->precision != BS_FP64 && p->precision != BS_MIXED) return fail(BS_ERR_ARG, "unknown precision");
     if (p->cell_div < 0 || p->cell_div > 8) return fail(BS_ERR_ARG, "cell_div must be in 0..8");
+    if (!(p->local_frac >= 0.0 && p->local_frac < 1.0)) return fail(BS_ERR_ARG, "local_frac must be in [0, 1)");
     for (int c = 0; c < 3; ++c) {
         if (p->M[c] < 3) return fail(BS_ERR_ARG, "M[%d] must be >= 3", c);
         d->K[c] = (p->M[c] - 1) / 2;
@@ -536,6 +537,7 @@ void fill_geom(const bs_ctx* c, GeomP& G)
     G.alpha = p.alpha;
     G.w = p.nufft_w;
     G.seg_max = 0.25 * std::min(p.L[0], std::min(p.L[1], p.L[2]));
+    G.local_frac = p.local_frac;
     for (int k = 0; k < 3; ++k) {
         G.iL[k] = 1.0 / p.L[k];
         G.ihc[k] = 1.0 / d.hc[k];
@@ -927,6 +929,7 @@ int bs_params_from_beta(double beta, const double L[3], int M, long long N, bs_p
     out->precision = BS_FP64;
     out->flags = 0;
     out->cell_div = 0;
+    out->local_frac = 0.0;
     return BS_OK;
 }
 

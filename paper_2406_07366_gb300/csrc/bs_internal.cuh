@@ -89,6 +89,7 @@ struct GeomP {
     double seg_max;     // longest allowed segment chord (min L / 4)
     double iL[3], ihc[3], ihg[3];  // reciprocals of L, hc, hg (binning multiplies: float64 division is slow here)
     int want_psi;
+    double local_frac;  // subdivided local segments (0: off)
 };
 
 struct ShortP {

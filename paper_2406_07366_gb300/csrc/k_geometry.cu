@@ -463,6 +463,55 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         }
     }
 
+    // Subdivided local segments (Sec. 5.2): l^+- cover the fraction f of each
+    // local segment next to the node; the rest of both segments, cut into the
+    // pieces [f, 2f], [2f, 4f], ..., [2^m f, 1] (fractions from the node), is
+    // summed with the plain Biot-Savart kernel, Q-point Gauss-Legendre each.
+    T vd[3] = { 0, 0, 0 }, pd[3] = { 0, 0, 0 };
+    if (P.local_frac > 0.0) {
+        const T fr = (T)P.local_frac;
+        SegPoly<T> R;
+        make_poly(R, hseg, dp, Mm, jp, j, drift, Dd);
+        const T dsp[3] = { ds[3 * jp], ds[3 * jp + 1], ds[3 * jp + 2] };
+        lp = 0;
+        lm = 0;
+        for (int i = 0; i < P.Q; ++i) {
+            const T gh = (T)P.gh[i], gw = (T)P.gw[i];
+            T del[3], sd[3];
+            S.eval(gh * fr * S.h, del, sd);
+            lp += gw * fr * S.h * tsqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+            R.eval(((T)1 - fr + gh * fr) * R.h, del, sd);
+            lm += gw * fr * R.h * tsqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+        }
+        for (int side = 0; side < 2; ++side) {
+            const SegPoly<T>& Gs = side == 0 ? S : R;
+            T x0 = fr;
+            for (int piece = 0; piece < 64 && x0 < (T)1; ++piece) {
+                const T x1 = (T)2 * x0 < (T)1 ? (T)2 * x0 : (T)1;
+                for (int i = 0; i < P.Q; ++i) {
+                    const T x = x0 + (x1 - x0) * (T)P.gh[i];  // fraction from the node
+                    const T u = side == 0 ? x * Gs.h : ((T)1 - x) * Gs.h;
+                    const T wt = (x1 - x0) * Gs.h * (T)P.gw[i];
+                    T del[3], sd[3];
+                    Gs.eval(u, del, sd);
+                    T r[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r[c] = side == 0 ? del[c] : del[c] - dsp[c];
+                    const T q[3] = { wt * sd[0], wt * sd[1], wt * sd[2] };
+                    const T rr = tsqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                    const T ir3 = (T)1 / (rr * rr * rr);
+                    vd[0] += (r[1] * q[2] - r[2] * q[1]) * ir3;
+                    vd[1] += (r[2] * q[0] - r[0] * q[2]) * ir3;
+                    vd[2] += (r[0] * q[1] - r[1] * q[0]) * ir3;
+                    pd[0] += q[0] / rr;
+                    pd[1] += q[1] / rr;
+                    pd[2] += q[2] / rr;
+                }
+                x0 = x1;
+            }
+        }
+    }
+
     // Node geometry: sdot = b + drift, sddot = M_j; s' x s'' = (sdot x sddot)/|sdot|^3.
     const T d0 = S.b[0] + drift[0], d1 = S.b[1] + drift[1], d2 = S.b[2] + drift[2];
     const T sn = tsqrt(d0 * d0 + d1 * d1 + d2 * d2);
@@ -472,8 +521,9 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     const T bz = (d0 * S.m[1] - d1 * S.m[0]) * is3;
     const double lg = log(2.0 * sqrt((double)lm * (double)lp) / P.a);
     const double pv = P.kappa / (4.0 * kPi);
-    const double vl[3] = { pv * (double)bx * (lg - P.delta), pv * (double)by * (lg - P.delta),
-                           pv * (double)bz * (lg - P.delta) };
+    const double vl[3] = { pv * ((double)bx * (lg - P.delta) + (double)vd[0]),
+                           pv * ((double)by * (lg - P.delta) + (double)vd[1]),
+                           pv * ((double)bz * (lg - P.delta) + (double)vd[2]) };
     const double vx[3] = { pv * (double)vs[0], pv * (double)vs[1], pv * (double)vs[2] };
 #pragma unroll
     for (int c = 0; c < 3; ++c) vls[3 * j + c] = vl[c] - vx[c];
@@ -487,8 +537,9 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     if (P.want_psi) {
         const double pp = P.kappa / (2.0 * kPi);
         const double ip = 1.0 / (double)sn;
-        const double pl[3] = { pp * (double)d0 * ip * (lg - (P.delta - 1.0)), pp * (double)d1 * ip * (lg - (P.delta - 1.0)),
-                               pp * (double)d2 * ip * (lg - (P.delta - 1.0)) };
+        const double pl[3] = { pp * (double)d0 * ip * (lg - (P.delta - 1.0)) + pv * (double)pd[0],
+                               pp * (double)d1 * ip * (lg - (P.delta - 1.0)) + pv * (double)pd[1],
+                               pp * (double)d2 * ip * (lg - (P.delta - 1.0)) + pv * (double)pd[2] };
         const double px[3] = { pv * (double)ps[0], pv * (double)ps[1], pv * (double)ps[2] };
 #pragma unroll
         for (int c = 0; c < 3; ++c) pls[3 * j + c] = pl[c] - px[c];

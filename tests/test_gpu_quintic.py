@@ -90,3 +90,35 @@ def test_quintic_trefoil_mixed_and_energy_refusal():
         be.energy(torch.from_numpy(f.nodes).cuda())
     assert e.value.code == B.BS_ERR_ARG
     be.close()
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_subdivided_local_segments_match_oracle(order):
+    """Sec. 5.2's subdivided local segments (f = 0.1, Q = 3): float64 at
+    beta = 8, w = 16, sigma = 2 equals the converged oracle with the same
+    subdivision (velocity and streamfunction); the mixed form stays in its
+    budget."""
+    B = _B()
+    f = W.leapfrog_ellipses(N_l=32)
+    L = f.L[0]
+    beta = 8.0
+    alpha = 2 * beta / L
+    K = int(math.ceil(beta * alpha * L / math.pi))
+    p = B.make_params(f.L, kappa=KAPPA, a=A_CORE, delta=DELTA, order=order, Q=3, M=2 * K + 1, w=16, sigma=2.0,
+                      precision=B.BS_FP64, beta=beta, alpha=alpha, flags=B.BS_WANT_PSI, local_frac=0.1)
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    nodes = torch.from_numpy(f.nodes).cuda()
+    v, psi = bs.velocity(nodes, want_psi=True)
+    v, psi = v.cpu().numpy(), psi.cpu().numpy()
+    bs.close()
+    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, order, 3)
+    vr, pr = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA, local_frac=0.1, order=order)
+    assert _rms(v, vr) < 1e-10
+    assert _rms(psi, pr) < 1e-10
+    pm = B.make_params(f.L, kappa=KAPPA, a=A_CORE, delta=DELTA, order=order, Q=3, M=32, w=8,
+                       precision=B.BS_MIXED, local_frac=0.1)
+    bm = B.BiotSavart(pm, f.offsets, f.closing)
+    vm = bm.velocity(nodes).cpu().numpy()
+    bm.close()
+    vr2, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA, local_frac=0.1, order=order)
+    assert _rms(vm, vr2) < 1e-5
