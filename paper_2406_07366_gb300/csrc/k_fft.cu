@@ -603,6 +603,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
             cp_async_wait_all();
         }
         __syncthreads();
+        if (!P.det && nslot <= 32) {
+            // Fast path: every lane owns the same (y column, z offset) slot in
+            // every record, so its slot indices and the parity of its real line
+            // are fixed; the shared address of (lx, component c) is
+            // abase + lx Ty CS + c txy CS (Ty and txy are even).
+            const int ly = lane / W, t = lane - ly * W;
+            const bool slot = lane < nslot;
+            const int sx = Ty * CS, sc = txy * CS;
+            for (int kk = wid; kk < nch; kk += nw) {
+                const SpRec<T, W>& R = srec[kk];
+                const int base = R.base;
+                const int r1 = ((base >> 8) & 255) - 128;
+                if (!slot || ly < r1 || ly > r1 + W - 1) continue;
+                const int ib2 = (base >> 16) & 1023;
+                const int r0 = (base & 255) - 128;
+                int z = ib2 - H + 1 + t;
+                z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
+                const int abase = ((ly >> 1) * CS + z) * 2 + (ly & 1);
+                const T wyz = R.wy[ly] * R.wz[t];
+                const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
+#pragma unroll
+                for (int lx = 0; lx < 4; ++lx) {
+                    if (lx >= Tx || lx < r0 || lx > r0 + W - 1) continue;
+                    const T wv = R.wx[lx] * wyz;
+                    const int ad = abase + lx * sx;
+                    atomicAdd(&accf[ad], wv * q0);
+                    atomicAdd(&accf[ad + sc], wv * q1);
+                    atomicAdd(&accf[ad + 2 * sc], wv * q2);
+                }
+            }
+            continue;
+        }
         for (int kk = P.det ? 0 : wid; kk < nch; kk += P.det ? 1 : nw) {
             const SpRec<T, W>& R = srec[kk];
             const int base = R.base;
@@ -660,21 +692,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
         const int x = bx * Tx + lx, y = by * Ty + ly;
         C* dst = F1 + (((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk;
         const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
+        C o[8];
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int mz = 8 * q + d;
             if (mz >= nk) break;
             const C zk = cb[l * CS + rev8_pos(rb, P.rev, mz, d)];
             const C zn = cb[l * CS + rev8_neg(rb, P.rev, n2, mz, d)];
-            C o;
             if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
-                o.x = (T)0.5 * (zk.x + zn.x);
-                o.y = (T)0.5 * (zk.y - zn.y);
+                o[d].x = (T)0.5 * (zk.x + zn.x);
+                o[d].y = (T)0.5 * (zk.y - zn.y);
             } else {              // B_k = (Z_k - conj Z_{n-k}) / (2i)
-                o.x = (T)0.5 * (zk.y + zn.y);
-                o.y = (T)0.5 * (zn.x - zk.x);
+                o[d].x = (T)0.5 * (zk.y + zn.y);
+                o[d].y = (T)0.5 * (zn.x - zk.x);
             }
-            dst[mz] = o;
+        }
+        if (sizeof(C) == 8 && (nk & 1) == 0 && 8 * q + 8 <= nk) {
+            // two modes per 16-byte store (rows of an even mode count are 16-byte aligned)
+            float4* d4 = reinterpret_cast<float4*>(dst + 8 * q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 v;
+                v.x = (float)o[2 * k].x;
+                v.y = (float)o[2 * k].y;
+                v.z = (float)o[2 * k + 1].x;
+                v.w = (float)o[2 * k + 1].y;
+                d4[k] = v;
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 8; ++d)
+                if (8 * q + d < nk) dst[8 * q + d] = o[d];
         }
     }
 }
