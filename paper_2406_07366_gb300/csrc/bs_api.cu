@@ -203,6 +203,7 @@ struct Derived {
     int nshell;                            // spectrum shells reaching the mode cube's corner
     int lmcy, lmcx, yc;                   // log2 chunk sizes of the y and x passes; inverse-z chunk
     int lsz;                              // padded stride of the real z-lines of the spread
+    int fuse_interp;                      // inverse z fused with the interpolation (no real grid)
 };
 
 int derive(const bs_params* p, Derived* d)
@@ -293,6 +294,11 @@ int derive(const bs_params* p, Derived* d)
     // lines at an odd stride keep every transform pass free of bank conflicts
     d->yc = (rb == 4 && d->ng[1] % 32 == 0) ? 32 : ((d->ng[1] % 16 == 0) ? 16 : 8);
     d->lsz = d->ng[2] + 1;
+    // the fused inverse z + interpolation gives every node copy one warp with
+    // a lane per (y column, z offset); its float sums are added atomically,
+    // so the deterministic mode keeps the grid and the gather kernel
+    d->fuse_interp = !(p->flags & (BS_FFT_CUFFT | BS_DETERMINISTIC)) &&
+                     zfft_interp_fits(d->tx, d->ty, p->nufft_w, d->ng[0], d->ng[1], d->nbx, d->nby);
     return BS_OK;
 }
 
@@ -420,7 +426,9 @@ int alloc_grids(bs_ctx* c)
     }
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cnt, sizeof(int) * (size_t)(d.ncells + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cur, sizeof(int) * (size_t)(d.ncells + 1)));
-    TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp, sizeof(int) * (size_t)scan_blocks((int)d.ncells)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp,
+               sizeof(int) * (size_t)std::max(scan_blocks((int)d.ncells), scan_blocks(d.ncols))));
+    if (d.fuse_interp) TRY(dalloc(c, c->alloc_g, (void**)&c->w.ncol_cnt, sizeof(int) * (size_t)(d.ncols + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.status, sizeof(int)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.energy_acc, 2 * sizeof(double)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.shell, sizeof(double) * (size_t)d.nshell));
@@ -489,6 +497,13 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.lr_sorted, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, (void**)&w.lr_key, sizeof(int) * NQ));
     TRY(dalloc(c, L, &w.col_rec, col_rec_bytes<T>(c->p.nufft_w) * NQ * (size_t)c->d.colcap));
+    if (c->d.fuse_interp) {
+        TRY(dalloc(c, L, &w.nd_rec, nd_rec_bytes<T>(c->p.nufft_w) * N));
+        TRY(dalloc(c, L, &w.nd_sorted, nd_rec_bytes<T>(c->p.nufft_w) * N));
+        TRY(dalloc(c, L, (void**)&w.nd_key, sizeof(int) * N));
+        TRY(dalloc(c, L, (void**)&w.nd_rank, sizeof(int) * N));
+        TRY(dalloc(c, L, &w.vacc, sizeof(T) * 3 * N));
+    }
     if (c->p.flags & BS_DETERMINISTIC) {
         TRY(dalloc(c, L, (void**)&w.sr_idx, sizeof(int) * NQ));
         TRY(dalloc(c, L, &w.sr_sorted2, sizeof(SrRec<T>) * NQ));
@@ -602,6 +617,28 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     fill_geom(c, G);
     G.want_psi = want_psi ? 1 : 0;
 
+    InterpP I;
+    I.N = (int)c->N;
+    for (int k = 0; k < 3; ++k) {
+        I.ng[k] = d.ng[k];
+        I.hg[k] = d.hg[k];
+        I.L[k] = p.L[k];
+        I.iL[k] = 1.0 / p.L[k];
+        I.ihg[k] = 1.0 / d.hg[k];
+    }
+    I.w = p.nufft_w;
+    I.zeta = d.zeta;
+    I.want_psi = want_psi ? 1 : 0;
+    ColP CP;
+    CP.tx = d.tx;
+    CP.ty = d.ty;
+    CP.nbx = d.nbx;
+    CP.nby = d.nby;
+    CP.ncols = d.ncols;
+    CP.w = p.nufft_w;
+    CP.zeta = d.zeta;
+    const bool fused = d.fuse_interp && !spectrum && !coarse;
+
     rec(c, 0, s);
     CE(launch_spline<T>(nodes, w, c->nfil, s));
     CE(launch_nodes<T>(G, nodes, w, parts ? parts : nullptr, parts ? parts + 3 * N3 : nullptr,
@@ -630,6 +667,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     S.want_psi = want_psi ? 1 : 0;
     CE(launch_short<T>(S, w, ss));
     rec(c, 3, ss);
+    if (fused) CE(launch_node_bin<T>(CP, I, nodes, w, ss));
     CE(cudaEventRecord(c->ev_join, ss));
     }
 
@@ -664,14 +702,6 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         TRY(fft_inv<T>(c, w.spec, s));
         rec(c, 8, s);
     } else {
-        ColP CP;
-        CP.tx = d.tx;
-        CP.ty = d.ty;
-        CP.nbx = d.nbx;
-        CP.nby = d.nby;
-        CP.ncols = d.ncols;
-        CP.w = p.nufft_w;
-        CP.zeta = d.zeta;
         CE(launch_col_sort<T>(CP, w, (int)c->NQ, s, det));
         rec(c, 4, s);
         SpZP SZ;
@@ -741,6 +771,12 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
         rec(c, 7, s);
         CE(launch_fft_y<T>(YP, w, w.f2, +1, s));
+        if (fused) {
+            rec(c, 8, s);
+            CE(cudaStreamWaitEvent(s, c->ev_join, 0));
+            rec(c, 9, s);
+            CE(launch_zfft_interp<T>(SZ, w, s));
+        } else {
         FftZP ZP;
         for (int k = 0; k < 3; ++k) {
             ZP.ng[k] = d.ng[k];
@@ -762,24 +798,18 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             CE(launch_to_double<T>(w.grid, coarse, (int)(3 * ng3), s));
             return BS_OK;
         }
+        }
     }
-    CE(cudaStreamWaitEvent(s, c->ev_join, 0));
-    rec(c, 9, s);
+    if (!fused) {
+        CE(cudaStreamWaitEvent(s, c->ev_join, 0));
+        rec(c, 9, s);
+    }
     if (want_energy) CE(launch_energy_line<T>(nodes, w, c->nfil, w.nmax_fil, s, det));
 
-    InterpP I;
-    I.N = (int)c->N;
-    for (int k = 0; k < 3; ++k) {
-        I.ng[k] = d.ng[k];
-        I.hg[k] = d.hg[k];
-        I.L[k] = p.L[k];
-        I.iL[k] = 1.0 / p.L[k];
-        I.ihg[k] = 1.0 / d.hg[k];
-    }
-    I.w = p.nufft_w;
-    I.zeta = d.zeta;
-    I.want_psi = want_psi ? 1 : 0;
-    if (parts) {
+    if (fused) {
+        CE(launch_interp_sum<T>((int)c->N, w, parts ? 2 : 0, vel, parts ? parts + 2 * N3 : nullptr, s));
+        if (parts) CE(launch_to_double<T>(w.vsr, parts + N3, (int)N3, s));
+    } else if (parts) {
         CE(launch_interp<T>(I, nodes, w, w.grid, 2, nullptr, parts + 2 * N3, s));
         CE(launch_to_double<T>(w.vsr, parts + N3, (int)N3, s));
     } else {
@@ -974,7 +1004,12 @@ int bs_create(bs_ctx** out, const bs_params* p, void* stream)
     }
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = set_fft_constants();
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    // the short-range branch runs at the highest stream priority: its few
+    // CTAs are dispatched ahead of the long-range kernels' waiting ones, so
+    // the branch ends while the spread is still running
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     for (int i = 0; i < bs_ctx::kStages && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev_t[i]);
@@ -1224,7 +1259,7 @@ int bs_graph_capture(bs_ctx* c, const double* nodes, double* vel, double* psi)
     }
     if (e != cudaSuccess) return fail(BS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
     c->graph = g;
-    CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, cudaGraphInstantiateFlagUseNodePriority));
     return BS_OK;
 }
 
@@ -1266,7 +1301,7 @@ int bs_rk4_capture(bs_ctx* c, double* nodes, double dt)
     }
     if (e != cudaSuccess) return fail(BS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
     c->rk_graph = g;
-    CUDA_TRY(cudaGraphInstantiate(&c->rk_exec, c->rk_graph, 0));
+    CUDA_TRY(cudaGraphInstantiate(&c->rk_exec, c->rk_graph, cudaGraphInstantiateFlagUseNodePriority));
     return BS_OK;
 }
 
@@ -1504,7 +1539,7 @@ int bs_batch_compute(bs_batch* b, const double* nodes, double* vel)
         }
         if (e != cudaSuccess) return fail(BS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
         b->graph = g;
-        CUDA_TRY(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+        CUDA_TRY(cudaGraphInstantiate(&b->gexec, b->graph, cudaGraphInstantiateFlagUseNodePriority));
         b->g_nodes = nodes;
         b->g_vel = vel;
     }

@@ -56,6 +56,17 @@ template <typename T, int W> struct __align__(16) SpRec {
     T wz[W];
 };
 
+// Interpolation target with its kernel weights along the three axes
+// (support point t of axis d at grid index ib_d - W/2 + 1 + t), binned once
+// by the z-column block that holds its grid cell.
+template <typename T, int W> struct __align__(16) NdW {
+    int base;  // ib0 | ib1 << 10 | ib2 << 20
+    int j;     // node index
+    T wx[W];
+    T wy[W];
+    T wz[W];
+};
+
 template <typename T> struct LrRec;
 template <> struct __align__(16) LrRec<float> {
     float f[3];
@@ -317,6 +328,14 @@ struct Work {
     void* col_rec = nullptr;  // duplicated spread records, by z-column block
     int* col_cnt = nullptr;   // ncols + 1
     int* col_cur = nullptr;
+    // fused inverse-z interpolation: the nodes with their weights, counting-
+    // sorted by the z-column block of their grid cell
+    void* nd_rec = nullptr;     // N NdW records, node order
+    void* nd_sorted = nullptr;  // N NdW records, block order
+    int* nd_key = nullptr;      // block of every node
+    int* nd_rank = nullptr;     // rank of the node within its block
+    int* ncol_cnt = nullptr;    // ncols + 1 block starts
+    void* vacc = nullptr;       // N x 3 accumulated long-range velocity
     // host staging for bs_compute_host
     double* nodes_in = nullptr;
     double* vel_out = nullptr;
@@ -361,6 +380,23 @@ template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s);
+// Shapes the fused inverse-z interpolation handles: Ty even (a complex line
+// is a pair of adjacent y rows), and the home blocks a CTA gathers distinct
+// and at most 64 (the grid wider than the support plus a block along x, y).
+inline bool zfft_interp_fits(int tx, int ty, int w, int n0, int n1, int nbx, int nby)
+{
+    if (ty % 2 != 0) return false;
+    const int nhx = (tx + w - 2) / tx + 2, nhy = (ty + w - 2) / ty + 2;
+    return nhx * nhy <= 64 && nhx <= nbx && nhy <= nby && n0 >= w + tx && n1 >= w + ty;
+}
+template <typename T>
+cudaError_t launch_zfft_interp(const SpZP& P, const Work& w, cudaStream_t s);
+template <typename T>
+cudaError_t launch_node_bin(const ColP& P, const InterpP& I, const double* nodes, const Work& w, cudaStream_t s);
+template <typename T>
+size_t nd_rec_bytes(int w);
+template <typename T>
+cudaError_t launch_interp_sum(int N, const Work& w, int what, double* out, double* part_long, cudaStream_t s);
 template <typename T>
 size_t spread_zfft_smem(const SpZP& P);
 

@@ -1066,6 +1066,264 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
 }
 
 // ---------------------------------------------------------------------------
+// E': inverse z real FFT fused with the interpolation of the velocity at the
+// nodes (the type-2 step of Eq. long_range_velocity_interp).  One CTA per
+// Tx x Ty block of z-columns with all three components, as in the spread:
+// the modes 0..K2 of the 3 Tx Ty real lines are read two lines per complex
+// line (real line 2l in .x, 2l+1 in .y; with Ty even the pair is two
+// adjacent y rows of one (c, x)), transformed in place, and the nodes whose
+// support reaches the block then take their weighted sums straight from
+// shared memory, so the real grid is never written.  The nodes are sorted
+// once by the block of their grid cell; a CTA gathers the few neighbouring
+// blocks' lists (in flight while its lines are transformed).  A node's W^3
+// sum is split over the blocks its support reaches; a thread sums the part
+// inside its block and adds it into the node's accumulator.
+// ---------------------------------------------------------------------------
+constexpr int kZiMaxRanges = 64;
+
+__device__ __forceinline__ int floor_div(int a, int b)
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+template <typename T, int W, int RM>
+__global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* __restrict__ cstart,
+                                                          const NdW<T, W>* __restrict__ nds,
+                                                          const typename Cx<T>::t* __restrict__ F1,
+                                                          const typename Cx<T>::t* __restrict__ tw2,
+                                                          T* __restrict__ vacc)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int r_beg[kZiMaxRanges], r_pre[kZiMaxRanges + 1];  // home-block ranges and their prefix
+    const int Tx = P.tx, Ty = P.ty, n0 = P.ng[0], n1 = P.ng[1], n2 = P.ng[2], nk = P.K[2] + 1;
+    const int txy = Tx * Ty;
+    const int ncl = 3 * txy / 2;
+    const int CS = P.cls;
+    C* cb = reinterpret_cast<C*>(smem_raw);
+    const T* accf = reinterpret_cast<const T*>(cb);
+    NdW<T, W>* srec = reinterpret_cast<NdW<T, W>*>(cb + (size_t)ncl * CS);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int by = fdiv(blockIdx.x, P.d_nbx);
+    const int bx = blockIdx.x - by * P.nbx;
+    constexpr int H = W / 2;
+    // home blocks whose cells' supports can reach this block: cell index
+    // ib with [ib - H + 1, ib + H] meeting [b T, b T + T - 1]
+    const int hx0 = floor_div(bx * Tx - H, Tx), hx1 = floor_div(bx * Tx + Tx + H - 2, Tx);
+    const int hy0 = floor_div(by * Ty - H, Ty), hy1 = floor_div(by * Ty + Ty + H - 2, Ty);
+    const int nhx = hx1 - hx0 + 1, nr = nhx * (hy1 - hy0 + 1);
+    // the range starts and lengths are fetched while the buffer is cleared
+    int rb0 = 0, rlen = 0;
+    if (tid < nr) {
+        const int hy = hy0 + tid / nhx, hx = hx0 + tid % nhx;
+        const int wx = hx < 0 ? hx + P.nbx : (hx >= P.nbx ? hx - P.nbx : hx);
+        const int wy = hy < 0 ? hy + P.nby : (hy >= P.nby ? hy - P.nby : hy);
+        const int b = wx + P.nbx * wy;
+        rb0 = cstart[b];
+        rlen = cstart[b + 1] - rb0;
+    }
+    constexpr int kWords = (int)(sizeof(NdW<T, W>) / 16);
+    auto stage = [&](int c0, int nch) {
+        int4* dst = reinterpret_cast<int4*>(srec);
+        for (int i = tid; i < nch * kWords; i += blockDim.x) {
+            const int k = c0 + i / kWords, wd = i % kWords;
+            int r = 0;
+            while (r + 1 < nr && r_pre[r + 1] <= k) ++r;
+            const int4* src = reinterpret_cast<const int4*>(nds + r_beg[r] + (k - r_pre[r])) + wd;
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+        }
+    };
+    C zero;
+    zero.x = 0;
+    zero.y = 0;
+    for (int i = tid; i < ncl * CS; i += blockDim.x) cb[i] = zero;
+    if (tid < kZiMaxRanges) {
+        r_beg[tid] = rb0;
+        r_pre[tid + 1] = rlen;
+    }
+    __syncthreads();
+    if (wid == 0) {  // inclusive prefix of the lengths, two ranges per lane
+        int v0 = r_pre[lane + 1], v1 = r_pre[lane + 33];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u0 = __shfl_up_sync(0xffffffffu, v0, o), u1 = __shfl_up_sync(0xffffffffu, v1, o);
+            if (lane >= o) {
+                v0 += u0;
+                v1 += u1;
+            }
+        }
+        v1 += __shfl_sync(0xffffffffu, v0, 31);
+        r_pre[lane + 1] = v0;
+        r_pre[lane + 33] = v1;
+        if (lane == 0) r_pre[0] = 0;
+    }
+    // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k) at the digit-reversed
+    // positions, 8 consecutive k of one line pair per thread
+    const int nq = (nk + 7) >> 3;
+    for (int i = tid; i < ncl * nq; i += blockDim.x) {
+        const int l = i / nq, q = i - l * nq;
+        const int rl = 2 * l;
+        const int c = fdiv(rl, P.d_txy), rem = rl - c * txy;
+        const int lx = fdiv(rem, P.d_ty), ly = rem - lx * Ty;
+        const C* rowA = F1 + (((size_t)c * n0 + bx * Tx + lx) * n1 + by * Ty + ly) * nk;
+        const C* rowB = rowA + nk;
+        C A[8], Bv[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int k = 8 * q + d;
+            if (k < nk) {
+                A[d] = rowA[k];
+                Bv[d] = rowB[k];
+            }
+        }
+        const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int k = 8 * q + d;
+            if (k >= nk) break;
+            C z;
+            if (k == 0) {
+                z.x = A[d].x;
+                z.y = Bv[d].x;
+                cb[l * CS] = z;
+            } else {
+                z.x = A[d].x - Bv[d].y;
+                z.y = A[d].y + Bv[d].x;
+                cb[l * CS + rev8_pos(rb, P.rev, k, d)] = z;
+                z.x = A[d].x + Bv[d].y;
+                z.y = -A[d].y + Bv[d].x;
+                cb[l * CS + rev8_neg(rb, P.rev, n2, k, d)] = z;
+            }
+        }
+    }
+    __syncthreads();
+    const int ncand = r_pre[nr];
+    stage(0, min(kSpzChunk, ncand));  // in flight during the transform
+    fft_inv_dit<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
+    // real line rl = c txy + lx Ty + ly at position z is the float
+    // ((rl >> 1) CS + z) 2 + (rl & 1) = rbase(lx, ly) + 2 z + c txy CS
+    const int sc = txy * CS;
+    for (int c0 = 0; c0 < ncand; c0 += kSpzChunk) {
+        const int nch = min(kSpzChunk, ncand - c0);
+        if (c0 != 0) {
+            __syncthreads();
+            stage(c0, nch);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // a thread per node: its W^3 support clipped to the block
+        for (int kk = tid; kk < nch; kk += blockDim.x) {
+            const NdW<T, W>& R = srec[kk];
+            const int base = R.base;
+            // support start relative to the block, taking the periodic image
+            // that meets it (the grid is wider than W + T)
+            int r0 = (base & 1023) - H + 1 - bx * Tx;
+            r0 = r0 > Tx - 1 ? r0 - n0 : (r0 + W - 1 < 0 ? r0 + n0 : r0);
+            int r1 = ((base >> 10) & 1023) - H + 1 - by * Ty;
+            r1 = r1 > Ty - 1 ? r1 - n1 : (r1 + W - 1 < 0 ? r1 + n1 : r1);
+            if (r0 > Tx - 1 || r0 + W - 1 < 0 || r1 > Ty - 1 || r1 + W - 1 < 0) continue;
+            const int z0 = ((base >> 20) & 1023) - H + 1;
+            int zo[W];
+            T wz[W];
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                const int z = z0 + t;
+                zo[t] = 2 * (z < 0 ? z + n2 : (z >= n2 ? z - n2 : z));
+                wz[t] = R.wz[t];
+            }
+            const int lx0 = max(r0, 0), lx1 = min(r0 + W - 1, Tx - 1);
+            const int ly0 = max(r1, 0), ly1 = min(r1 + W - 1, Ty - 1);
+            T a0 = 0, a1 = 0, a2 = 0;
+            for (int ly = ly0; ly <= ly1; ++ly) {
+                const T wy = R.wy[ly - r1];
+                for (int lx = lx0; lx <= lx1; ++lx) {
+                    const T* row = accf + (ly >> 1) * 2 * CS + (ly & 1) + lx * Ty * CS;
+                    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+                    for (int t = 0; t < W; ++t) {
+                        s0 += wz[t] * row[zo[t]];
+                        s1 += wz[t] * row[zo[t] + sc];
+                        s2 += wz[t] * row[zo[t] + 2 * sc];
+                    }
+                    const T wxy = R.wx[lx - r0] * wy;
+                    a0 += wxy * s0;
+                    a1 += wxy * s1;
+                    a2 += wxy * s2;
+                }
+            }
+            const size_t j = (size_t)R.j;
+            atomicAdd(&vacc[3 * j + 0], a0);
+            atomicAdd(&vacc[3 * j + 1], a1);
+            atomicAdd(&vacc[3 * j + 2], a2);
+        }
+    }
+}
+
+// One thread per node: grid cell and fraction (the interpolation's binning),
+// the 3 W kernel weights, and the node's rank within the block of its cell
+// (one atomic per run of equal blocks in a warp).
+template <typename T, int W>
+__global__ void k_node_w(InterpP P, int tx, int ty, int nbx, const double* __restrict__ nodes,
+                         NdW<T, W>* __restrict__ out, int* __restrict__ key, int* __restrict__ rank,
+                         int* __restrict__ cnt)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = j < P.N;
+    constexpr int H = W / 2;
+    int b = -1;
+    if (live) {
+        NdW<T, W> R;
+        int ib[3];
+        T fr[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x = nodes[3 * j + d];
+            if (!isfinite(x)) x = 0.0;
+            double xw = x - P.L[d] * floor(x * P.iL[d]);
+            if (xw >= P.L[d]) xw -= P.L[d];
+            if (xw < 0.0) xw = 0.0;
+            const double g = xw * P.ihg[d];
+            int k = (int)floor(g);
+            k = k < 0 ? 0 : (k >= P.ng[d] ? P.ng[d] - 1 : k);
+            double f = g - (double)k;
+            f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+            ib[d] = k;
+            fr[d] = (T)f;
+        }
+        const T zeta = (T)P.zeta;
+        const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            R.wx[t] = kb_val((fr[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+            R.wy[t] = kb_val((fr[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+            R.wz[t] = kb_val((fr[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        }
+        R.base = ib[0] | (ib[1] << 10) | (ib[2] << 20);
+        R.j = j;
+        out[j] = R;
+        b = ib[0] / tx + nbx * (ib[1] / ty);
+        key[j] = b;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int r = 0;
+    if (live && lane == leader) r = atomicAdd(&cnt[b], __popc(peers));
+    r = __shfl_sync(0xffffffffu, r, leader);
+    if (live) rank[j] = r + __popc(peers & ((1u << lane) - 1u));
+}
+
+template <typename T, int W>
+__global__ void k_node_scatter(int N, const NdW<T, W>* __restrict__ in, const int* __restrict__ key,
+                               const int* __restrict__ rank, const int* __restrict__ start,
+                               NdW<T, W>* __restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) out[start[key[j]] + rank[j]] = in[j];
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -1128,6 +1386,58 @@ cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s
     if (NQ > 0)
         e = launch_col_scatter_w<T>(P, w, NQ, s, det);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename T, int W>
+static cudaError_t node_bin_w(const ColP& P, const InterpP& I, const double* nodes, const Work& w, cudaStream_t s)
+{
+    const int N = I.N;
+    const int g = (N + kThreads - 1) / kThreads;
+    k_node_w<T, W><<<g, kThreads, 0, s>>>(I, P.tx, P.ty, P.nbx, nodes, (NdW<T, W>*)w.nd_rec, w.nd_key, w.nd_rank,
+                                           w.ncol_cnt);
+    cudaError_t e = scan_exclusive(w.ncol_cnt, P.ncols, w.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_node_scatter<T, W><<<g, kThreads, 0, s>>>(N, (const NdW<T, W>*)w.nd_rec, w.nd_key, w.nd_rank, w.ncol_cnt,
+                                                 (NdW<T, W>*)w.nd_sorted);
+    return cudaGetLastError();
+}
+
+// Sorts the nodes with their weights by the z-column block of their grid
+// cell for the fused inverse-z interpolation, and clears the accumulator it
+// adds into.
+template <typename T>
+cudaError_t launch_node_bin(const ColP& P, const InterpP& I, const double* nodes, const Work& w, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(w.vacc, 0, sizeof(T) * 3 * (size_t)I.N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ncol_cnt, 0, sizeof(int) * (size_t)(P.ncols + 1), s);
+    if (e != cudaSuccess || I.N == 0) return e;
+    switch (P.w) {
+    case 2: return node_bin_w<T, 2>(P, I, nodes, w, s);
+    case 4: return node_bin_w<T, 4>(P, I, nodes, w, s);
+    case 6: return node_bin_w<T, 6>(P, I, nodes, w, s);
+    case 8: return node_bin_w<T, 8>(P, I, nodes, w, s);
+    case 10: return node_bin_w<T, 10>(P, I, nodes, w, s);
+    case 12: return node_bin_w<T, 12>(P, I, nodes, w, s);
+    case 14: return node_bin_w<T, 14>(P, I, nodes, w, s);
+    case 16: return node_bin_w<T, 16>(P, I, nodes, w, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+size_t nd_rec_bytes(int w)
+{
+    switch (w) {
+    case 2: return sizeof(NdW<T, 2>);
+    case 4: return sizeof(NdW<T, 4>);
+    case 6: return sizeof(NdW<T, 6>);
+    case 8: return sizeof(NdW<T, 8>);
+    case 10: return sizeof(NdW<T, 10>);
+    case 12: return sizeof(NdW<T, 12>);
+    case 14: return sizeof(NdW<T, 14>);
+    case 16: return sizeof(NdW<T, 16>);
+    default: return 0;
+    }
 }
 
 template <typename T>
@@ -1194,6 +1504,49 @@ cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s)
     case 12: return spz_w<T, 12>(P, w, s);
     case 14: return spz_w<T, 14>(P, w, s);
     case 16: return spz_w<T, 16>(P, w, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int W>
+struct ZiLaunch {
+    const SpZP& P;
+    const Work& w;
+    cudaStream_t s;
+    template <int RM>
+    cudaError_t run()
+    {
+        using C = typename Cx<T>::t;
+        const size_t sm = (size_t)(3 * P.tx * P.ty / 2) * P.cls * sizeof(C) + kSpzChunk * sizeof(NdW<T, W>);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_zfft_interp<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_zfft_interp<T, W, RM><<<P.nbx * P.nby, kThreads, sm, s>>>(
+            P, w.ncol_cnt, (const NdW<T, W>*)w.nd_sorted, (const C*)w.spec, (const C*)w.tw + P.ng[0] + P.ng[1],
+            (T*)w.vacc);
+        return cudaGetLastError();
+    }
+};
+
+template <typename T, int W>
+static cudaError_t zi_w(const SpZP& P, const Work& w, cudaStream_t s)
+{
+    if (!zfft_interp_fits(P.tx, P.ty, W, P.ng[0], P.ng[1], P.nbx, P.nby)) return cudaErrorInvalidValue;
+    return by_rm<T>(P.plan2, ZiLaunch<T, W>{ P, w, s });
+}
+
+template <typename T>
+cudaError_t launch_zfft_interp(const SpZP& P, const Work& w, cudaStream_t s)
+{
+    switch (P.w) {
+    case 2: return zi_w<T, 2>(P, w, s);
+    case 4: return zi_w<T, 4>(P, w, s);
+    case 6: return zi_w<T, 6>(P, w, s);
+    case 8: return zi_w<T, 8>(P, w, s);
+    case 10: return zi_w<T, 10>(P, w, s);
+    case 12: return zi_w<T, 12>(P, w, s);
+    case 14: return zi_w<T, 14>(P, w, s);
+    case 16: return zi_w<T, 16>(P, w, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1292,6 +1645,12 @@ template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaS
 template cudaError_t launch_col_sort<double>(const ColP&, const Work&, int, cudaStream_t, bool);
 template cudaError_t launch_spread_zfft<float>(const SpZP&, const Work&, cudaStream_t);
 template cudaError_t launch_spread_zfft<double>(const SpZP&, const Work&, cudaStream_t);
+template cudaError_t launch_zfft_interp<float>(const SpZP&, const Work&, cudaStream_t);
+template cudaError_t launch_zfft_interp<double>(const SpZP&, const Work&, cudaStream_t);
+template cudaError_t launch_node_bin<float>(const ColP&, const InterpP&, const double*, const Work&, cudaStream_t);
+template cudaError_t launch_node_bin<double>(const ColP&, const InterpP&, const double*, const Work&, cudaStream_t);
+template size_t nd_rec_bytes<float>(int);
+template size_t nd_rec_bytes<double>(int);
 template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, cudaStream_t);
 template cudaError_t launch_fft_y<double>(const FftYP&, const Work&, void*, int, cudaStream_t);
 template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool, cudaStream_t);

@@ -390,6 +390,32 @@ cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, 
     }
 }
 
+// The velocity (or the long-range part alone) from the accumulated
+// long-range sums of the fused inverse-z interpolation, with the same sum
+// order as the interpolation kernel's epilogue.
+template <typename T>
+__global__ void k_interp_sum(int n3, const T* __restrict__ acc, const double* __restrict__ add_d,
+                             const T* __restrict__ add_t, double* __restrict__ out, double* __restrict__ part)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+        const double a = (double)acc[i];
+        if (part) part[i] = a;
+        if (out) out[i] = (a + (double)add_t[i]) + add_d[i];
+    }
+}
+
+template <typename T>
+cudaError_t launch_interp_sum(int N, const Work& w, int what, double* out, double* part_long, cudaStream_t s)
+{
+    if (N <= 0) return cudaSuccess;
+    const int n3 = 3 * N;
+    int g = (n3 + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_interp_sum<T><<<g, 256, 0, s>>>(n3, (const T*)w.vacc, w.vls, (const T*)w.vsr, what == 2 ? nullptr : out,
+                                      part_long);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s)
 {
@@ -408,6 +434,8 @@ template cudaError_t launch_interp<float>(const InterpP&, const double*, const W
                                           double*, cudaStream_t);
 template cudaError_t launch_interp<double>(const InterpP&, const double*, const Work&, const void*, int, double*,
                                            double*, cudaStream_t);
+template cudaError_t launch_interp_sum<float>(int, const Work&, int, double*, double*, cudaStream_t);
+template cudaError_t launch_interp_sum<double>(int, const Work&, int, double*, double*, cudaStream_t);
 template cudaError_t launch_to_double<float>(const void*, double*, int, cudaStream_t);
 template cudaError_t launch_to_double<double>(const void*, double*, int, cudaStream_t);
 
