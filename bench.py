@@ -35,7 +35,9 @@ import numpy as np  # noqa: E402
 METRIC = "filament nodes/s per Biot–Savart eval at 1e-6 rel. err; FP32/batched vs FP64"
 UNIT = "nodes/s"
 L2_FLUSH_BYTES = 512 << 20
-KERNELS_PER_STEP = 19  # spline, nodes, 2 x (count, 3 scan, scatter), short, spread+z FFT, y FFT, x FFT+k-space, inverse y, inverse z, interp
+# spline, nodes, 3 x (count, 3 scan, scatter: short-range cells, spread blocks, node blocks), short range,
+# spread + z FFT, y FFT, x FFT + k-space, inverse y, inverse z + interpolation, final sum
+KERNELS_PER_STEP = 24
 
 
 def parse():

@@ -380,14 +380,21 @@ template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s);
-// Shapes the fused inverse-z interpolation handles: Ty even (a complex line
-// is a pair of adjacent y rows), and the home blocks a CTA gathers distinct
-// and at most 64 (the grid wider than the support plus a block along x, y).
-inline bool zfft_interp_fits(int tx, int ty, int w, int n0, int n1, int nbx, int nby)
+// Blocks whose points are gathered from home-block lists (the points sorted
+// once by the block of their grid cell): the home blocks a CTA gathers are
+// distinct and at most 64, and one periodic image of a support meets a block
+// (the grid wider than the support plus a block).
+inline bool home_fits(int tx, int ty, int w, int n0, int n1, int nbx, int nby)
 {
-    if (ty % 2 != 0) return false;
     const int nhx = (tx + w - 2) / tx + 2, nhy = (ty + w - 2) / ty + 2;
     return nhx * nhy <= 64 && nhx <= nbx && nhy <= nby && n0 >= w + tx && n1 >= w + ty;
+}
+
+// The fused inverse-z interpolation also pairs adjacent y rows into one
+// complex line (Ty even).
+inline bool zfft_interp_fits(int tx, int ty, int w, int n0, int n1, int nbx, int nby)
+{
+    return ty % 2 == 0 && home_fits(tx, ty, w, n0, n1, nbx, nby);
 }
 template <typename T>
 cudaError_t launch_zfft_interp(const SpZP& P, const Work& w, cudaStream_t s);

@@ -490,6 +490,19 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
     }
 }
 
+// Rank of a point within its block b (b < 0: no point), one atomic per run of
+// equal blocks in the warp; every lane of the warp calls it.
+__device__ __forceinline__ int warp_rank(int b, int* __restrict__ cnt)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int r = 0;
+    if (b >= 0 && lane == leader) r = atomicAdd(&cnt[b], __popc(peers));
+    r = __shfl_sync(0xffffffffu, r, leader);
+    return r + __popc(peers & ((1u << lane) - 1u));
+}
+
 // One thread per point: the 3 W kernel weights are evaluated once, then the
 // point is written into every block its support reaches, with the x and y
 // weights of that block's local columns picked out (zero outside the support).
@@ -543,6 +556,144 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
             const int p = atomicAdd(&cur[wx + P.nbx * wy], 1);
             out[p] = D;
             if (idx_out) idx_out[p] = i;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Points sorted once by the z-column block of their grid cell ("home"
+// block).  A CTA gathers the lists of the home blocks whose cells' supports
+// reach its block: cell index ib with [ib - W/2 + 1, ib + W/2] meeting
+// [b T, b T + T - 1], at most kHomeMax blocks, each once.
+// ---------------------------------------------------------------------------
+constexpr int kHomeMax = 64;
+
+__device__ __forceinline__ int floor_div(int a, int b)
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// Number of home ranges of block (bx, by); thread tid < nr fetches the start
+// and length of range tid.
+__device__ __forceinline__ int home_fetch(const SpZP& P, const int* __restrict__ cstart, int bx, int by, int H,
+                                          int& rb0, int& rlen)
+{
+    const int Tx = P.tx, Ty = P.ty, tid = threadIdx.x;
+    const int hx0 = floor_div(bx * Tx - H, Tx), hx1 = floor_div(bx * Tx + Tx + H - 2, Tx);
+    const int hy0 = floor_div(by * Ty - H, Ty), hy1 = floor_div(by * Ty + Ty + H - 2, Ty);
+    const int nhx = hx1 - hx0 + 1, nr = nhx * (hy1 - hy0 + 1);
+    rb0 = 0;
+    rlen = 0;
+    if (tid < nr) {
+        const int hy = hy0 + tid / nhx, hx = hx0 + tid % nhx;
+        const int wx = hx < 0 ? hx + P.nbx : (hx >= P.nbx ? hx - P.nbx : hx);
+        const int wy = hy < 0 ? hy + P.nby : (hy >= P.nby ? hy - P.nby : hy);
+        const int b = wx + P.nbx * wy;
+        rb0 = cstart[b];
+        rlen = cstart[b + 1] - rb0;
+    }
+    return nr;
+}
+
+// After the fetched starts and lengths were stored (r_beg[r], r_pre[r + 1])
+// and a barrier: warp 0 turns the lengths into the prefix r_pre[0..64].
+__device__ __forceinline__ void home_prefix(int* r_pre)
+{
+    const int lane = threadIdx.x & 31;
+    if ((threadIdx.x >> 5) != 0) return;
+    int v0 = r_pre[lane + 1], v1 = r_pre[lane + 33];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u0 = __shfl_up_sync(0xffffffffu, v0, o), u1 = __shfl_up_sync(0xffffffffu, v1, o);
+        if (lane >= o) {
+            v0 += u0;
+            v1 += u1;
+        }
+    }
+    v1 += __shfl_sync(0xffffffffu, v0, 31);
+    r_pre[lane + 1] = v0;
+    r_pre[lane + 33] = v1;
+    if (lane == 0) r_pre[0] = 0;
+}
+
+// Starts the asynchronous copy of candidates [c0, c0 + nch) of the gathered
+// ranges into shared memory (records are whole 16-byte words).
+template <typename R>
+__device__ __forceinline__ void home_stage(R* srec, const R* __restrict__ recs, const int* r_beg, const int* r_pre,
+                                           int nr, int c0, int nch)
+{
+    constexpr int kWords = (int)(sizeof(R) / 16);
+    int4* dst = reinterpret_cast<int4*>(srec);
+    for (int i = threadIdx.x; i < nch * kWords; i += blockDim.x) {
+        const int k = c0 + i / kWords, wd = i % kWords;
+        int r = 0;
+        while (r + 1 < nr && r_pre[r + 1] <= k) ++r;
+        const int4* src = reinterpret_cast<const int4*>(recs + r_beg[r] + (k - r_pre[r])) + wd;
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+    }
+}
+
+// Support start of a point relative to a block (cell index ib, block start
+// b0, block width T, grid n), for the periodic image that meets the block.
+__device__ __forceinline__ int home_rel(int ib, int H, int b0, int T, int n, int W)
+{
+    int r = ib - H + 1 - b0;
+    return r > T - 1 ? r - n : (r + W - 1 < 0 ? r + n : r);
+}
+
+// Separates the two real transforms of every complex z-line of a spread
+// block and writes modes 0..K2.  A thread takes 8 consecutive modes of one
+// line: with the lanes on consecutive groups, the digit-reversed positions
+// of one instruction fall in distinct banks.
+template <typename T>
+__device__ __forceinline__ void spz_unpack(const SpZP& P, const typename Cx<T>::t* cb, typename Cx<T>::t* F1,
+                                           int bx, int by)
+{
+    using C = typename Cx<T>::t;
+    const int Tx = P.tx, Ty = P.ty, n2 = P.ng[2], CS = P.cls;
+    const int txy = Tx * Ty, nreal = 3 * txy, tid = threadIdx.x;
+    const int nk = P.K[2] + 1;
+    const int nq = (nk + 7) >> 3;
+    for (int i = tid; i < nreal * nq; i += blockDim.x) {
+        const int rl = i / nq, q = i - rl * nq;
+        const int l = rl >> 1;
+        const int c = fdiv(rl, P.d_txy), rem = rl - c * txy;
+        const int lx = fdiv(rem, P.d_ty), ly = rem - lx * Ty;
+        const int x = bx * Tx + lx, y = by * Ty + ly;
+        C* dst = F1 + (((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk;
+        const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
+        C o[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int mz = 8 * q + d;
+            if (mz >= nk) break;
+            const C zk = cb[l * CS + rev8_pos(rb, P.rev, mz, d)];
+            const C zn = cb[l * CS + rev8_neg(rb, P.rev, n2, mz, d)];
+            if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
+                o[d].x = (T)0.5 * (zk.x + zn.x);
+                o[d].y = (T)0.5 * (zk.y - zn.y);
+            } else {              // B_k = (Z_k - conj Z_{n-k}) / (2i)
+                o[d].x = (T)0.5 * (zk.y + zn.y);
+                o[d].y = (T)0.5 * (zn.x - zk.x);
+            }
+        }
+        if (sizeof(C) == 8 && (nk & 1) == 0 && 8 * q + 8 <= nk) {
+            // two modes per 16-byte store (rows of an even mode count are 16-byte aligned)
+            float4* d4 = reinterpret_cast<float4*>(dst + 8 * q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 v;
+                v.x = (float)o[2 * k].x;
+                v.y = (float)o[2 * k].y;
+                v.z = (float)o[2 * k + 1].x;
+                v.w = (float)o[2 * k + 1].y;
+                d4[k] = v;
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 8; ++d)
+                if (8 * q + d < nk) dst[8 * q + d] = o[d];
         }
     }
 }
@@ -679,52 +830,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
     }
     __syncthreads();
     fft_fwd_dif<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
-    // separate the two real transforms and write modes 0..K2.  A thread takes
-    // 8 consecutive modes of one line: with the lanes on consecutive groups,
-    // the digit-reversed positions of one instruction fall in distinct banks.
-    const int nk = P.K[2] + 1;
-    const int nq = (nk + 7) >> 3;
-    for (int i = tid; i < nreal * nq; i += blockDim.x) {
-        const int rl = i / nq, q = i - rl * nq;
-        const int l = rl >> 1;
-        const int c = fdiv(rl, P.d_txy), rem = rl - c * txy;
-        const int lx = fdiv(rem, P.d_ty), ly = rem - lx * Ty;
-        const int x = bx * Tx + lx, y = by * Ty + ly;
-        C* dst = F1 + (((size_t)c * P.ng[0] + x) * P.ng[1] + y) * nk;
-        const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
-        C o[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const int mz = 8 * q + d;
-            if (mz >= nk) break;
-            const C zk = cb[l * CS + rev8_pos(rb, P.rev, mz, d)];
-            const C zn = cb[l * CS + rev8_neg(rb, P.rev, n2, mz, d)];
-            if ((rl & 1) == 0) {  // A_k = (Z_k + conj Z_{n-k}) / 2
-                o[d].x = (T)0.5 * (zk.x + zn.x);
-                o[d].y = (T)0.5 * (zk.y - zn.y);
-            } else {              // B_k = (Z_k - conj Z_{n-k}) / (2i)
-                o[d].x = (T)0.5 * (zk.y + zn.y);
-                o[d].y = (T)0.5 * (zn.x - zk.x);
-            }
-        }
-        if (sizeof(C) == 8 && (nk & 1) == 0 && 8 * q + 8 <= nk) {
-            // two modes per 16-byte store (rows of an even mode count are 16-byte aligned)
-            float4* d4 = reinterpret_cast<float4*>(dst + 8 * q);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float4 v;
-                v.x = (float)o[2 * k].x;
-                v.y = (float)o[2 * k].y;
-                v.z = (float)o[2 * k + 1].x;
-                v.w = (float)o[2 * k + 1].y;
-                d4[k] = v;
-            }
-        } else {
-#pragma unroll
-            for (int d = 0; d < 8; ++d)
-                if (8 * q + d < nk) dst[8 * q + d] = o[d];
-        }
-    }
+    spz_unpack<T>(P, cb, F1, bx, by);
 }
 
 // ---------------------------------------------------------------------------
@@ -1079,13 +1185,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
 // sum is split over the blocks its support reaches; a thread sums the part
 // inside its block and adds it into the node's accumulator.
 // ---------------------------------------------------------------------------
-constexpr int kZiMaxRanges = 64;
-
-__device__ __forceinline__ int floor_div(int a, int b)
-{
-    return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
 template <typename T, int W, int RM>
 __global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* __restrict__ cstart,
                                                           const NdW<T, W>* __restrict__ nds,
@@ -1095,7 +1194,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* 
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int r_beg[kZiMaxRanges], r_pre[kZiMaxRanges + 1];  // home-block ranges and their prefix
+    __shared__ int r_beg[kHomeMax], r_pre[kHomeMax + 1];  // home ranges and their prefix
     const int Tx = P.tx, Ty = P.ty, n0 = P.ng[0], n1 = P.ng[1], n2 = P.ng[2], nk = P.K[2] + 1;
     const int txy = Tx * Ty;
     const int ncl = 3 * txy / 2;
@@ -1103,61 +1202,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* 
     C* cb = reinterpret_cast<C*>(smem_raw);
     const T* accf = reinterpret_cast<const T*>(cb);
     NdW<T, W>* srec = reinterpret_cast<NdW<T, W>*>(cb + (size_t)ncl * CS);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x;
     const int by = fdiv(blockIdx.x, P.d_nbx);
     const int bx = blockIdx.x - by * P.nbx;
     constexpr int H = W / 2;
-    // home blocks whose cells' supports can reach this block: cell index
-    // ib with [ib - H + 1, ib + H] meeting [b T, b T + T - 1]
-    const int hx0 = floor_div(bx * Tx - H, Tx), hx1 = floor_div(bx * Tx + Tx + H - 2, Tx);
-    const int hy0 = floor_div(by * Ty - H, Ty), hy1 = floor_div(by * Ty + Ty + H - 2, Ty);
-    const int nhx = hx1 - hx0 + 1, nr = nhx * (hy1 - hy0 + 1);
-    // the range starts and lengths are fetched while the buffer is cleared
-    int rb0 = 0, rlen = 0;
-    if (tid < nr) {
-        const int hy = hy0 + tid / nhx, hx = hx0 + tid % nhx;
-        const int wx = hx < 0 ? hx + P.nbx : (hx >= P.nbx ? hx - P.nbx : hx);
-        const int wy = hy < 0 ? hy + P.nby : (hy >= P.nby ? hy - P.nby : hy);
-        const int b = wx + P.nbx * wy;
-        rb0 = cstart[b];
-        rlen = cstart[b + 1] - rb0;
-    }
-    constexpr int kWords = (int)(sizeof(NdW<T, W>) / 16);
-    auto stage = [&](int c0, int nch) {
-        int4* dst = reinterpret_cast<int4*>(srec);
-        for (int i = tid; i < nch * kWords; i += blockDim.x) {
-            const int k = c0 + i / kWords, wd = i % kWords;
-            int r = 0;
-            while (r + 1 < nr && r_pre[r + 1] <= k) ++r;
-            const int4* src = reinterpret_cast<const int4*>(nds + r_beg[r] + (k - r_pre[r])) + wd;
-            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
-        }
-    };
+    // the home ranges are fetched while the buffer is cleared
+    int rb0, rlen;
+    const int nr = home_fetch(P, cstart, bx, by, H, rb0, rlen);
     C zero;
     zero.x = 0;
     zero.y = 0;
     for (int i = tid; i < ncl * CS; i += blockDim.x) cb[i] = zero;
-    if (tid < kZiMaxRanges) {
+    if (tid < kHomeMax) {
         r_beg[tid] = rb0;
         r_pre[tid + 1] = rlen;
     }
     __syncthreads();
-    if (wid == 0) {  // inclusive prefix of the lengths, two ranges per lane
-        int v0 = r_pre[lane + 1], v1 = r_pre[lane + 33];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u0 = __shfl_up_sync(0xffffffffu, v0, o), u1 = __shfl_up_sync(0xffffffffu, v1, o);
-            if (lane >= o) {
-                v0 += u0;
-                v1 += u1;
-            }
-        }
-        v1 += __shfl_sync(0xffffffffu, v0, 31);
-        r_pre[lane + 1] = v0;
-        r_pre[lane + 33] = v1;
-        if (lane == 0) r_pre[0] = 0;
-    }
+    home_prefix(r_pre);
     // Z_k = A_k + i B_k, Z_{n-k} = conj(A_k) + i conj(B_k) at the digit-reversed
     // positions, 8 consecutive k of one line pair per thread
     const int nq = (nk + 7) >> 3;
@@ -1199,7 +1260,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* 
     }
     __syncthreads();
     const int ncand = r_pre[nr];
-    stage(0, min(kSpzChunk, ncand));  // in flight during the transform
+    home_stage(srec, nds, r_beg, r_pre, nr, 0, min(kSpzChunk, ncand));  // in flight during the transform
     fft_inv_dit<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
     // real line rl = c txy + lx Ty + ly at position z is the float
     // ((rl >> 1) CS + z) 2 + (rl & 1) = rbase(lx, ly) + 2 z + c txy CS
@@ -1208,7 +1269,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* 
         const int nch = min(kSpzChunk, ncand - c0);
         if (c0 != 0) {
             __syncthreads();
-            stage(c0, nch);
+            home_stage(srec, nds, r_beg, r_pre, nr, c0, nch);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -1218,10 +1279,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* 
             const int base = R.base;
             // support start relative to the block, taking the periodic image
             // that meets it (the grid is wider than W + T)
-            int r0 = (base & 1023) - H + 1 - bx * Tx;
-            r0 = r0 > Tx - 1 ? r0 - n0 : (r0 + W - 1 < 0 ? r0 + n0 : r0);
-            int r1 = ((base >> 10) & 1023) - H + 1 - by * Ty;
-            r1 = r1 > Ty - 1 ? r1 - n1 : (r1 + W - 1 < 0 ? r1 + n1 : r1);
+            const int r0 = home_rel(base & 1023, H, bx * Tx, Tx, n0, W);
+            const int r1 = home_rel((base >> 10) & 1023, H, by * Ty, Ty, n1, W);
             if (r0 > Tx - 1 || r0 + W - 1 < 0 || r1 > Ty - 1 || r1 + W - 1 < 0) continue;
             const int z0 = ((base >> 20) & 1023) - H + 1;
             int zo[W];
@@ -1305,13 +1364,8 @@ __global__ void k_node_w(InterpP P, int tx, int ty, int nbx, const double* __res
         b = ib[0] / tx + nbx * (ib[1] / ty);
         key[j] = b;
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int r = 0;
-    if (live && lane == leader) r = atomicAdd(&cnt[b], __popc(peers));
-    r = __shfl_sync(0xffffffffu, r, leader);
-    if (live) rank[j] = r + __popc(peers & ((1u << lane) - 1u));
+    const int r = warp_rank(b, cnt);
+    if (live) rank[j] = r;
 }
 
 template <typename T, int W>
