@@ -548,6 +548,7 @@ void fill_geom(const bs_ctx* c, GeomP& G)
     }
     G.kappa = p.kappa;
     G.a = p.a;
+    G.log2a = std::log(2.0 / p.a);
     G.delta = p.delta;
     G.alpha = p.alpha;
     G.w = p.nufft_w;
@@ -628,6 +629,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     }
     I.w = p.nufft_w;
     I.zeta = d.zeta;
+    I.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
     I.want_psi = want_psi ? 1 : 0;
     ColP CP;
     CP.tx = d.tx;
@@ -637,6 +639,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     CP.ncols = d.ncols;
     CP.w = p.nufft_w;
     CP.zeta = d.zeta;
+    CP.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
     const bool fused = d.fuse_interp && !spectrum && !coarse;
 
     rec(c, 0, s);
@@ -683,6 +686,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         }
         SP.w = p.nufft_w;
         SP.zeta = d.zeta;
+        SP.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
         CE(launch_spread<T>(SP, w, d.ntiles, s));
         rec(c, 5, s);
         TRY(fft_fwd<T>(c, s));

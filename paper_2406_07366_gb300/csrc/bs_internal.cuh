@@ -101,6 +101,7 @@ struct GeomP {
     double iL[3], ihc[3], ihg[3];  // reciprocals of L, hc, hg (binning multiplies: float64 division is slow here)
     int want_psi;
     double local_frac;  // subdivided local segments (0: off)
+    double log2a;       // log(2 / a): the local term's logarithm is log(l- l+) / 2 + log(2 / a)
 };
 
 struct ShortP {
@@ -120,7 +121,7 @@ struct SpreadP {
     int tile[3];
     int ntile[3];
     int w;
-    double zeta;
+    double zeta, inorm;
 };
 
 struct KspaceP {
@@ -194,7 +195,8 @@ struct FftPlan {
 // Column binning of the spread records (blocks of tx x ty full z-columns).
 struct ColP {
     int tx, ty, nbx, nby, ncols, w;
-    double zeta;  // kernel shape parameter
+    double zeta;   // kernel shape parameter
+    double inorm;  // 1 / (1 - e^{-2 zeta}), the kernel's normalisation
 };
 
 struct SpZP {
@@ -262,7 +264,7 @@ struct InterpP {
     double L[3];
     double iL[3], ihg[3];  // reciprocals of L and hg
     int w;
-    double zeta;
+    double zeta, inorm;
     int want_psi;
 };
 

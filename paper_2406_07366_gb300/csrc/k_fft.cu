@@ -471,25 +471,6 @@ __device__ __forceinline__ void col_range(int ib, int H, int Tb, int& b0, int& b
     b1 = hi / Tb;
 }
 
-template <typename T>
-__global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cnt)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int base = rec[i].base;
-    const int ib0 = base & 1023, ib1 = (base >> 10) & 1023;
-    int x0, x1, y0, y1;
-    col_range(ib0, P.w / 2, P.tx, x0, x1);
-    col_range(ib1, P.w / 2, P.ty, y0, y1);
-    for (int by = y0; by <= y1; ++by) {
-        const int wy = ((by % P.nby) + P.nby) % P.nby;
-        for (int bx = x0; bx <= x1; ++bx) {
-            const int wx = ((bx % P.nbx) + P.nbx) % P.nbx;
-            atomicAdd(&cnt[wx + P.nbx * wy], 1);
-        }
-    }
-}
-
 // Rank of a point within its block b (b < 0: no point), one atomic per run of
 // equal blocks in the warp; every lane of the warp calls it.
 __device__ __forceinline__ int warp_rank(int b, int* __restrict__ cnt)
@@ -503,6 +484,42 @@ __device__ __forceinline__ int warp_rank(int b, int* __restrict__ cnt)
     return r + __popc(peers & ((1u << lane) - 1u));
 }
 
+// Blocks reached by a point: x blocks [x0, x0 + nx), y blocks [y0, y0 + ny)
+// (unwrapped), nx ny copies.
+__device__ __forceinline__ void col_span(const ColP& P, int base, int& x0, int& nx, int& y0, int& ny)
+{
+    int x1, y1;
+    col_range(base & 1023, P.w / 2, P.tx, x0, x1);
+    col_range((base >> 10) & 1023, P.w / 2, P.ty, y0, y1);
+    nx = x1 - x0 + 1;
+    ny = y1 - y0 + 1;
+}
+
+__device__ __forceinline__ int col_wrap(int b, int nb)
+{
+    return b < 0 ? b + nb : (b >= nb ? b - nb : b);
+}
+
+// Copies per block.  The lanes of a warp take their k-th copies together,
+// one atomic per run of equal blocks (neighbouring points along a filament
+// mostly reach the same blocks).
+template <typename T>
+__global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int x0 = 0, nx = 0, y0 = 0, ny = 0;
+    if (i < n) col_span(P, rec[i].base, x0, nx, y0, ny);
+    const int nk = __reduce_max_sync(0xffffffffu, nx * ny);
+    for (int k = 0; k < nk; ++k) {
+        int b = -1;
+        if (k < nx * ny) {
+            const int ky = k / nx;
+            b = col_wrap(x0 + (k - ky * nx), P.nbx) + P.nbx * col_wrap(y0 + ky, P.nby);
+        }
+        warp_rank(b, cnt);
+    }
+}
+
 // One thread per point: the 3 W kernel weights are evaluated once, then the
 // point is written into every block its support reaches, with the x and y
 // weights of that block's local columns picked out (zero outside the support).
@@ -511,30 +528,42 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
                               SpRec<T, W>* __restrict__ out, int* __restrict__ idx_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const LrRec<T> R = rec[i];
-    const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
     constexpr int H = W / 2;
+    LrRec<T> R;
+    R.base = 0;
+    int x0 = 0, nx = 0, y0 = 0, ny = 0;
+    if (i < n) {
+        R = rec[i];
+        col_span(P, R.base, x0, nx, y0, ny);
+    }
+    const int nk = __reduce_max_sync(0xffffffffu, nx * ny);
+    if (nk == 0) return;
+    const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
     const T zeta = (T)P.zeta;
-    const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+    const T inorm = (T)P.inorm;
     // weight of support point t along axis d: psi((f_d + H - 1 - t) / (W / 2))
     T kx[W], ky[W];
     SpRec<T, W> D;
+    if (i < n) {
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-        kx[t] = kb_val((R.f[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-        ky[t] = kb_val((R.f[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-        D.wz[t] = kb_val((R.f[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        for (int t = 0; t < W; ++t) {
+            kx[t] = kb_val((R.f[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+            ky[t] = kb_val((R.f[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+            D.wz[t] = kb_val((R.f[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        }
+        D.q[0] = R.q[0];
+        D.q[1] = R.q[1];
+        D.q[2] = R.q[2];
     }
-    D.q[0] = R.q[0];
-    D.q[1] = R.q[1];
-    D.q[2] = R.q[2];
-    int x0, x1, y0, y1;
-    col_range(ib0, H, P.tx, x0, x1);
-    col_range(ib1, H, P.ty, y0, y1);
-    for (int by = y0; by <= y1; ++by) {
-        const int wy = ((by % P.nby) + P.nby) % P.nby;
+    for (int k = 0; k < nk; ++k) {
+        const bool live = k < nx * ny;
+        const int kyi = live ? k / nx : 0;
+        const int bx = x0 + (k - kyi * nx), by = y0 + kyi;
+        const int b = live ? col_wrap(bx, P.nbx) + P.nbx * col_wrap(by, P.nby) : -1;
+        const int p = warp_rank(b, cur);
+        if (!live) continue;
         const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block
+        const int r0 = ib0 - H + 1 - bx * P.tx;
 #pragma unroll
         for (int ly = 0; ly < 4; ++ly) {
             T v = (T)0;
@@ -542,21 +571,16 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
             for (int t = 0; t < W; ++t) v = (t + r1 == ly) ? ky[t] : v;
             D.wy[ly] = v;
         }
-        for (int bx = x0; bx <= x1; ++bx) {
-            const int wx = ((bx % P.nbx) + P.nbx) % P.nbx;
-            const int r0 = ib0 - H + 1 - bx * P.tx;
 #pragma unroll
-            for (int lx = 0; lx < 4; ++lx) {
-                T v = (T)0;
+        for (int lx = 0; lx < 4; ++lx) {
+            T v = (T)0;
 #pragma unroll
-                for (int t = 0; t < W; ++t) v = (t + r0 == lx) ? kx[t] : v;
-                D.wx[lx] = v;
-            }
-            D.base = (r0 + 128) | ((r1 + 128) << 8) | (ib2 << 16);
-            const int p = atomicAdd(&cur[wx + P.nbx * wy], 1);
-            out[p] = D;
-            if (idx_out) idx_out[p] = i;
+            for (int t = 0; t < W; ++t) v = (t + r0 == lx) ? kx[t] : v;
+            D.wx[lx] = v;
         }
+        D.base = (r0 + 128) | ((r1 + 128) << 8) | (ib2 << 16);
+        out[p] = D;
+        if (idx_out) idx_out[p] = i;
     }
 }
 
@@ -1351,7 +1375,7 @@ __global__ void k_node_w(InterpP P, int tx, int ty, int nbx, const double* __res
             fr[d] = (T)f;
         }
         const T zeta = (T)P.zeta;
-        const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+        const T inorm = (T)P.inorm;
 #pragma unroll
         for (int t = 0; t < W; ++t) {
             R.wx[t] = kb_val((fr[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);

@@ -382,8 +382,11 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     const T Tp = Tper[f];
     const T drift[3] = { (T)shift[3 * f] / Tp, (T)shift[3 * f + 1] / Tp, (T)shift[3 * f + 2] / Tp };
     const double sj[3] = { nodes[3 * j], nodes[3 * j + 1], nodes[3 * j + 2] };
-    bool bad = false;
+    bool bad = false, bad_node = false;
     int flags = 0;
+    double sw[3];  // the node wrapped into the box
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sw[c] = wrap_box(sj[c], P.L[c], P.iL[c], bad_node);
 
     SegPoly<T> S;
     make_poly(S, hseg, dp, Mm, j, jn, drift, Dd);
@@ -403,11 +406,16 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         lp += wq * tsqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
         self_add(del, q, alpha, vs, ps);
 
+        // the point is near the wrapped node: it is mostly in the box already
         bool b2 = false;
         double xw[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xw[c] = wrap_box(sj[c] + (double)del[c], P.L[c], P.iL[c], b2);
-        if (b2) {
+        for (int c = 0; c < 3; ++c) {
+            double x = sw[c] + (double)del[c];
+            if (!(x >= 0.0 && x < P.L[c])) x = wrap_box(x, P.L[c], P.iL[c], b2);
+            xw[c] = x;
+        }
+        if (b2 || bad_node) {
             bad = true;
             q[0] = q[1] = q[2] = 0;
         }
@@ -436,9 +444,9 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
             int k = (int)floor(g);
             k = k < 0 ? 0 : (k >= P.ng[c] ? P.ng[c] - 1 : k);
             ib[c] = k;
-            double fr = g - (double)k;
-            fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
-            G.f[c] = (T)fr;
+            T fr = (T)(g - (double)k);
+            fr = fr < (T)0 ? (T)0 : (fr > (T)1 ? (T)1 : fr);
+            G.f[c] = fr;
             G.q[c] = q[c];
         }
         G.base = ib[0] | (ib[1] << 10) | (ib[2] << 20);
@@ -519,7 +527,8 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     const T bx = (d1 * S.m[2] - d2 * S.m[1]) * is3;
     const T by = (d2 * S.m[0] - d0 * S.m[2]) * is3;
     const T bz = (d0 * S.m[1] - d1 * S.m[0]) * is3;
-    const double lg = log(2.0 * sqrt((double)lm * (double)lp) / P.a);
+    // log(2 sqrt(l- l+) / a): the l-dependent half in the kernel precision
+    const double lg = (double)((T)0.5 * log(lm * lp)) + P.log2a;
     const double pv = P.kappa / (4.0 * kPi);
     const double vl[3] = { pv * ((double)bx * (lg - P.delta) + (double)vd[0]),
                            pv * ((double)by * (lg - P.delta) + (double)vd[1]),
@@ -554,12 +563,11 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
 
     // Target record of the node for the short range.
     {
-        bool b2 = false;
         SrTgt<T> tg;
         int ci[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double xw = wrap_box(sj[c], P.L[c], P.iL[c], b2);
+            const double xw = sw[c];
             int k = (int)(xw * P.ihc[c]);
             k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
             ci[c] = k;
@@ -567,7 +575,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
         }
         tg.cell = ci[0] + P.nc[0] * (ci[1] + P.nc[1] * ci[2]);
         tgt[j] = tg;
-        if (b2) bad = true;
+        if (bad_node) bad = true;
     }
     if (bad) flags |= ST_NONFINITE;
     if (flags) atomicOr(status, flags);

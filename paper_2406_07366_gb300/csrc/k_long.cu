@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_spread(SpreadP P, const int* __res
     __syncthreads();
 
     const T zeta = (T)P.zeta;
-    const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+    const T inorm = (T)P.inorm;
     T* kw = ktab + wid * 3 * W;
     constexpr int H = W / 2;
     const int total = bpre[27];
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(128) k_interp(InterpP P, const double* __restr
     if (j >= P.N) return;
     constexpr int H = W / 2;
     const T zeta = (T)P.zeta;
-    const T inorm = (T)(1.0 / (1.0 - exp(-2.0 * P.zeta)));
+    const T inorm = (T)P.inorm;
     int ib[3];
     T fr[3];
 #pragma unroll
