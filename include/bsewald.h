@@ -344,8 +344,11 @@ int bs_status(bs_ctx* ctx);
  * one, each stage timed by CUDA events on its own stream).  ms[0..n-1]
  * receive, in order: geometry, short-range binning, short range, spread
  * binning, spread, forward FFT, k-space, inverse FFT, interpolation + sum
- * (from the join of both branches), whole evaluation.  Synchronises the
- * streams.  Returns the number of entries through *n_out.
+ * (from the join of both branches), whole evaluation.  Where the inverse z
+ * transform is fused with the interpolation (the default pruned path), the
+ * inverse-FFT entry covers the inverse y transform and the interpolation
+ * entry the inverse z transform, the interpolation and the sum.
+ * Synchronises the streams.  Returns the number of entries through *n_out.
  */
 int bs_stage_times(bs_ctx* ctx, float* ms, int n, int* n_out);
 
