@@ -798,9 +798,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* 
                 const int abase = ((ly >> 1) * CS + z) * 2 + (ly & 1);
                 const T wyz = R.wy[ly] * R.wz[t];
                 const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
-#pragma unroll
-                for (int lx = 0; lx < 4; ++lx) {
-                    if (lx >= Tx || lx < r0 || lx > r0 + W - 1) continue;
+                const int lx0 = max(r0, 0), lx1 = min(r0 + W - 1, Tx - 1);  // the same in the whole warp
+                for (int lx = lx0; lx <= lx1; ++lx) {
                     const T wv = R.wx[lx] * wyz;
                     const int ad = abase + lx * sx;
                     atomicAdd(&accf[ad], wv * q0);
