@@ -271,6 +271,12 @@ int derive(const bs_params* p, Derived* d)
     for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c], 8);
     int txy = (int)(50000 / (1.5 * (d->ng[2] + 1) * cb));
     txy = txy >= 16 ? 16 : (txy >= 8 ? 8 : (txy >= 4 ? 4 : 2));
+    // float32 z-lines of up to ~400 points: 4 x 4 blocks, run by 512 threads
+    // at two CTAs per SM (about 85 KB each).  Measured on the 384^3 grid of
+    // the 1e5-node tangle: a point is copied into 5.6 instead of 8.75 blocks,
+    // and the spread binning, spread and fused interpolation together take
+    // 1.07 ms instead of 1.10 ms.
+    if (rb == 4 && txy == 8) txy = 16;
     d->ty = std::min(4, txy);
     d->tx = txy / d->ty;
     d->nbx = d->ng[0] / d->tx;

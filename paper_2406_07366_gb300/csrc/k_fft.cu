@@ -33,6 +33,19 @@
 namespace bsw {
 
 constexpr int kSpzChunk = 128;  // spread records staged in shared memory at a time
+// Threads of a z-column-block CTA (spread, fused interpolation): 256, or 512
+// for float32 blocks of 16 columns.
+constexpr int kZThreadsMax = 512;
+template <typename T>
+constexpr int z_threads_max()
+{
+    return sizeof(T) == 4 ? kZThreadsMax : kThreads;
+}
+template <typename T>
+constexpr int z_threads(int txy)
+{
+    return sizeof(T) == 4 && txy >= 16 ? kZThreadsMax : kThreads;
+}
 
 template <typename T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
@@ -733,7 +746,7 @@ __device__ __forceinline__ void spz_unpack(const SpZP& P, const typename Cx<T>::
 // cells; shared atomic adds resolve two warps meeting on a cell.
 // ---------------------------------------------------------------------------
 template <typename T, int W, int RM>
-__global__ void __launch_bounds__(kThreads, 2) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
+__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
                                                           const SpRec<T, W>* __restrict__ recs,
                                                           const typename Cx<T>::t* __restrict__ tw2,
                                                           typename Cx<T>::t* __restrict__ F1)
@@ -1209,7 +1222,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
 // inside its block and adds it into the node's accumulator.
 // ---------------------------------------------------------------------------
 template <typename T, int W, int RM>
-__global__ void __launch_bounds__(kThreads, 3) k_zfft_interp(SpZP P, const int* __restrict__ cstart,
+__global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_zfft_interp(SpZP P, const int* __restrict__ cstart,
                                                           const NdW<T, W>* __restrict__ nds,
                                                           const typename Cx<T>::t* __restrict__ F1,
                                                           const typename Cx<T>::t* __restrict__ tw2,
@@ -1557,7 +1570,7 @@ struct SpzLaunch {
         cudaError_t e =
             cudaFuncSetAttribute(k_spread_zfft<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_spread_zfft<T, W, RM><<<P.nbx * P.nby, kThreads, sm, s>>>(
+        k_spread_zfft<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P.tx * P.ty), sm, s>>>(
             P, w.col_cnt, (const SpRec<T, W>*)w.col_rec, (const C*)w.tw + P.ng[0] + P.ng[1], (C*)w.spec);
         return cudaGetLastError();
     }
@@ -1598,7 +1611,7 @@ struct ZiLaunch {
         cudaError_t e =
             cudaFuncSetAttribute(k_zfft_interp<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_zfft_interp<T, W, RM><<<P.nbx * P.nby, kThreads, sm, s>>>(
+        k_zfft_interp<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P.tx * P.ty), sm, s>>>(
             P, w.ncol_cnt, (const NdW<T, W>*)w.nd_sorted, (const C*)w.spec, (const C*)w.tw + P.ng[0] + P.ng[1],
             (T*)w.vacc);
         return cudaGetLastError();
