@@ -269,14 +269,16 @@ int derive(const bs_params* p, Derived* d)
     const size_t rb = p->precision == BS_FP64 ? 8 : 4;
     const size_t cb = 2 * rb;
     for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c], 8);
-    int txy = (int)(50000 / (1.5 * (d->ng[2] + 1) * cb));
+    // Float32 blocks of 8 or more columns are run by 512 threads at two CTAs
+    // per SM (about 85 KB each), float64 blocks by 256 threads (about 50 KB).
+    // Larger blocks mean fewer copies of each spread point: measured, on the
+    // 384^3 grid of the 1e5-node tangle 4 x 4 blocks (5.6 copies) against
+    // 2 x 4 (8.75 copies) take the spread binning, spread and fused
+    // interpolation from 1.10 to 1.07 ms, and on the 768^3 grid of the
+    // 4e6-node tangle 2 x 4 blocks against 1 x 4 take a whole evaluation
+    // from 58.1 to 53.5 ms.
+    int txy = (int)((rb == 4 ? 100000 : 50000) / (1.5 * (d->ng[2] + 1) * cb));
     txy = txy >= 16 ? 16 : (txy >= 8 ? 8 : (txy >= 4 ? 4 : 2));
-    // float32 z-lines of up to ~400 points: 4 x 4 blocks, run by 512 threads
-    // at two CTAs per SM (about 85 KB each).  Measured on the 384^3 grid of
-    // the 1e5-node tangle: a point is copied into 5.6 instead of 8.75 blocks,
-    // and the spread binning, spread and fused interpolation together take
-    // 1.07 ms instead of 1.10 ms.
-    if (rb == 4 && txy == 8) txy = 16;
     d->ty = std::min(4, txy);
     d->tx = txy / d->ty;
     d->nbx = d->ng[0] / d->tx;

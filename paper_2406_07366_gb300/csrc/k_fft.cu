@@ -34,7 +34,7 @@ namespace bsw {
 
 constexpr int kSpzChunk = 128;  // spread records staged in shared memory at a time
 // Threads of a z-column-block CTA (spread, fused interpolation): 256, or 512
-// for float32 blocks of 16 columns.
+// for float32 blocks of 8 or more columns.
 constexpr int kZThreadsMax = 512;
 template <typename T>
 constexpr int z_threads_max()
@@ -44,7 +44,7 @@ constexpr int z_threads_max()
 template <typename T>
 constexpr int z_threads(int txy)
 {
-    return sizeof(T) == 4 && txy >= 16 ? kZThreadsMax : kThreads;
+    return sizeof(T) == 4 && txy >= 8 ? kZThreadsMax : kThreads;
 }
 
 template <typename T> struct Cx;
