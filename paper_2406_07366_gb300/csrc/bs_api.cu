@@ -202,6 +202,7 @@ struct Derived {
     int tx, ty, nbx, nby, ncols, colcap;  // z-column blocks; records per source at most
     int nshell;                            // spectrum shells reaching the mode cube's corner
     int lmcy, lmcx, yc;                   // log2 chunk sizes of the y and x passes; inverse-z chunk
+    int zthreads;                         // threads of a z-column-block CTA (256 or 512)
     int lsz;                              // padded stride of the real z-lines of the spread
     int fuse_interp;                      // inverse z fused with the interpolation (no real grid)
 };
@@ -269,16 +270,24 @@ int derive(const bs_params* p, Derived* d)
     const size_t rb = p->precision == BS_FP64 ? 8 : 4;
     const size_t cb = 2 * rb;
     for (int c = 0; c < 3; ++c) d->plan[c] = make_plan(d->ng[c], 8);
-    // Float32 blocks of 8 or more columns are run by 512 threads at two CTAs
-    // per SM (about 85 KB each), float64 blocks by 256 threads (about 50 KB).
-    // Larger blocks mean fewer copies of each spread point: measured, on the
+    // Blocks of z-columns sized for about 50 KB of shared memory per CTA of
+    // 256 threads; float32 blocks on grids of more than ~260 points per axis
+    // are doubled and run by 512 threads at two CTAs per SM (about 85 KB
+    // each).  Larger blocks mean fewer copies of each spread point (small
+    // grids keep 256 threads: there the CTA count is what fills the GPU,
+    // measured on the batch of 64 tangles).  Measured, on the
     // 384^3 grid of the 1e5-node tangle 4 x 4 blocks (5.6 copies) against
     // 2 x 4 (8.75 copies) take the spread binning, spread and fused
     // interpolation from 1.10 to 1.07 ms, and on the 768^3 grid of the
     // 4e6-node tangle 2 x 4 blocks against 1 x 4 take a whole evaluation
     // from 58.1 to 53.5 ms.
-    int txy = (int)((rb == 4 ? 100000 : 50000) / (1.5 * (d->ng[2] + 1) * cb));
+    int txy = (int)(50000 / (1.5 * (d->ng[2] + 1) * cb));
     txy = txy >= 16 ? 16 : (txy >= 8 ? 8 : (txy >= 4 ? 4 : 2));
+    d->zthreads = 256;
+    if (rb == 4 && txy < 16) {  // grids of more than ~260 points per axis
+        txy *= 2;
+        d->zthreads = 512;
+    }
     d->ty = std::min(4, txy);
     d->tx = txy / d->ty;
     d->nbx = d->ng[0] / d->tx;
@@ -718,6 +727,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         rec(c, 4, s);
         SpZP SZ;
         SZ.det = det ? 1 : 0;
+        SZ.nthreads = d.zthreads;
         for (int k = 0; k < 3; ++k) {
             SZ.ng[k] = d.ng[k];
             SZ.K[k] = d.K[k];

@@ -201,6 +201,7 @@ struct ColP {
 
 struct SpZP {
     int det;  // deterministic accumulation: each warp owns a z-range and adds in record order
+    int nthreads;  // threads per CTA (256, or 512 for float32 on large grids)
     int ng[3];
     int K[3];
     int tx, ty, nbx, nby;

@@ -33,8 +33,8 @@
 namespace bsw {
 
 constexpr int kSpzChunk = 128;  // spread records staged in shared memory at a time
-// Threads of a z-column-block CTA (spread, fused interpolation): 256, or 512
-// for float32 blocks of 8 or more columns.
+// Threads of a z-column-block CTA (spread, fused interpolation): 256, or up
+// to 512 for float32.
 constexpr int kZThreadsMax = 512;
 template <typename T>
 constexpr int z_threads_max()
@@ -42,9 +42,9 @@ constexpr int z_threads_max()
     return sizeof(T) == 4 ? kZThreadsMax : kThreads;
 }
 template <typename T>
-constexpr int z_threads(int txy)
+int z_threads(const SpZP& P)
 {
-    return sizeof(T) == 4 && txy >= 8 ? kZThreadsMax : kThreads;
+    return P.nthreads > 0 && P.nthreads <= z_threads_max<T>() ? P.nthreads : kThreads;
 }
 
 template <typename T> struct Cx;
@@ -1570,7 +1570,7 @@ struct SpzLaunch {
         cudaError_t e =
             cudaFuncSetAttribute(k_spread_zfft<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_spread_zfft<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P.tx * P.ty), sm, s>>>(
+        k_spread_zfft<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P), sm, s>>>(
             P, w.col_cnt, (const SpRec<T, W>*)w.col_rec, (const C*)w.tw + P.ng[0] + P.ng[1], (C*)w.spec);
         return cudaGetLastError();
     }
@@ -1611,7 +1611,7 @@ struct ZiLaunch {
         cudaError_t e =
             cudaFuncSetAttribute(k_zfft_interp<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_zfft_interp<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P.tx * P.ty), sm, s>>>(
+        k_zfft_interp<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P), sm, s>>>(
             P, w.ncol_cnt, (const NdW<T, W>*)w.nd_sorted, (const C*)w.spec, (const C*)w.tw + P.ng[0] + P.ng[1],
             (T*)w.vacc);
         return cudaGetLastError();
