@@ -58,9 +58,9 @@ __device__ __forceinline__ double erfc_e<double>(double x, double) { return erfc
 
 // One warp per target node.  The lanes first list the source ranges of the
 // (2m+1)^2 neighbour rows (32 rows at a time; a row wrapping around the box
-// gives two ranges), prefix-sum their lengths, then stride through the
-// flattened candidate list, so every lane has work however short the rows
-// are.  Each lane finds the row of its candidate by a binary search over the
+// gives two ranges; rows and row ends beyond r_c are cut), prefix-sum their
+// lengths, then stride through the flattened candidate list, so every lane
+// has work however short the rows are.  Each lane finds the row of its candidate by a binary search over the
 // lanes' inclusive sums.  The per-lane partial sums are reduced at the end.
 template <typename T>
 __global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restrict__ tgt, const int* __restrict__ prev,
@@ -86,21 +86,12 @@ __global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restr
     const bool fullx = (2 * m + 1 >= nc0), fully = (2 * m + 1 >= nc1), fullz = (2 * m + 1 >= nc2);
     const int ny = fully ? nc1 : 2 * m + 1, nz = fullz ? nc2 : 2 * m + 1;
     const int nrows = ny * nz;
-    // x-ranges of every row: one or two contiguous runs [xa0, xb0], [xa1, xb1]
-    int xa0, xb0, xa1 = 0, xb1 = -1;
-    if (fullx) {
-        xa0 = 0;
-        xb0 = nc0 - 1;
-    } else {
-        const int lo = cx - m, hi = cx + m;
-        if (lo < 0) {
-            xa0 = lo + nc0; xb0 = nc0 - 1; xa1 = 0; xb1 = hi;
-        } else if (hi >= nc0) {
-            xa0 = lo; xb0 = nc0 - 1; xa1 = 0; xb1 = hi - nc0;
-        } else {
-            xa0 = lo; xb0 = hi;
-        }
-    }
+    // Rows whose y-z slab lies wholly beyond r_c of the node are skipped, and
+    // a row's x cells are cut to those meeting the chord of the r_c sphere
+    // at the slab's distance.  The pair test below stays exact; the margin
+    // keeps the cut conservative under rounding.
+    const T rcm2 = rc2 * (T)1.0001;
+    const T ih0 = (T)1 / h0;
 
     T v0 = 0, v1 = 0, v2 = 0, p0 = 0, p1 = 0, p2 = 0;
     for (int rb = 0; rb < nrows; rb += 32) {
@@ -113,12 +104,39 @@ __global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restr
             const int yc = fully ? iy : imod(cy - m + iy, nc1);
             dzi = cdiff(zc, cz, nc2);
             dyi = cdiff(yc, cy, nc1);
-            const int row = (zc * nc1 + yc) * nc0;
-            s0 = start[row + xa0];
-            n0 = start[row + xb0 + 1] - s0;
-            if (xb1 >= xa1) {
-                s1 = start[row + xa1];
-                n1r = start[row + xb1 + 1] - s1;
+            // gaps between the node and the row's y and z slabs
+            T gy = (T)0, gz = (T)0;
+            if (!fully) gy = dyi > 0 ? dyi * h1 - t.o[1] : (dyi < 0 ? t.o[1] - (dyi + 1) * h1 : (T)0);
+            if (!fullz) gz = dzi > 0 ? dzi * h2 - t.o[2] : (dzi < 0 ? t.o[2] - (dzi + 1) * h2 : (T)0);
+            gy = gy > (T)0 ? gy : (T)0;
+            gz = gz > (T)0 ? gz : (T)0;
+            const T d2 = gy * gy + gz * gz;
+            if (d2 < rcm2) {
+                // x-ranges of the row: one or two contiguous runs [xa0, xb0], [xa1, xb1]
+                int xa0, xb0, xa1 = 0, xb1 = -1;
+                if (fullx) {
+                    xa0 = 0;
+                    xb0 = nc0 - 1;
+                } else {
+                    const T ext = sqrt(rcm2 - d2);
+                    int lo = (int)floor((t.o[0] - ext) * ih0), hi = (int)floor((t.o[0] + ext) * ih0);
+                    lo = cx + (lo < -m ? -m : lo);
+                    hi = cx + (hi > m ? m : hi);
+                    if (lo < 0) {
+                        xa0 = lo + nc0; xb0 = nc0 - 1; xa1 = 0; xb1 = hi;
+                    } else if (hi >= nc0) {
+                        xa0 = lo; xb0 = nc0 - 1; xa1 = 0; xb1 = hi - nc0;
+                    } else {
+                        xa0 = lo; xb0 = hi;
+                    }
+                }
+                const int row = (zc * nc1 + yc) * nc0;
+                s0 = start[row + xa0];
+                n0 = start[row + xb0 + 1] - s0;
+                if (xb1 >= xa1) {
+                    s1 = start[row + xa1];
+                    n1r = start[row + xb1 + 1] - s1;
+                }
             }
         }
         // inclusive prefix sum of the lanes' candidate counts
