@@ -228,6 +228,7 @@ struct FftXP {
     int ng[3];
     int K[3];
     int lmc;            // log2 of the chunk of z-modes per CTA
+    int nthreads;       // threads per CTA (256, or 512 for float32 on large grids)
     int ls;             // line stride in shared memory
     double kk[3];
     double scale;

@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
 // curl couples them).  tabs: e^{-k_d^2/4alpha^2} / F_d(m)^2 per axis.
 // ---------------------------------------------------------------------------
 template <typename T, int RM>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
+__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
                                                            typename Cx<T>::t* __restrict__ F2psi,
                                                            const typename Cx<T>::t* __restrict__ tw0,
                                                            const T* __restrict__ tab0, const T* __restrict__ tab1,
@@ -1684,7 +1684,7 @@ struct FftXLaunch {
         const int nl = (want_psi ? 6 : 3) * MC;
         size_t sm = (size_t)nl * P.ls * sizeof(C);
         if (P.spectrum) sm = std::max(sm, (size_t)3 * MC * P.ls * sizeof(C) + sizeof(double) * (size_t)P.nbins);
-        if (P.epart) sm += sizeof(double) * (kThreads / 32);
+        if (P.epart) sm += sizeof(double) * (kZThreadsMax / 32);
         cudaError_t e =
             cudaFuncSetAttribute(k_fft_x_kspace<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -1694,7 +1694,8 @@ struct FftXLaunch {
         const T* tab0 = (const T*)w.ktab + (P.single_decon ? ntab : 0);
         const T* tab1 = tab0 + (P.K[0] + 1);
         const T* tab2 = tab1 + (P.K[1] + 1);
-        k_fft_x_kspace<T, RM><<<(2 * P.K[1] + 1) * nch, kThreads, sm, s>>>(
+        const int nt = P.nthreads > 0 && P.nthreads <= z_threads_max<T>() ? P.nthreads : kThreads;
+        k_fft_x_kspace<T, RM><<<(2 * P.K[1] + 1) * nch, nt, sm, s>>>(
             P, (C*)w.f2, want_psi ? (C*)w.f2psi : nullptr, (const C*)w.tw, tab0, tab1, tab2);
         return cudaGetLastError();
     }
