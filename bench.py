@@ -272,6 +272,40 @@ def spread_zfft_bytes(p, ng, K, NQ, real_bytes):
     return rec * NQ + 3 * ng[0] * ng[1] * (K[2] + 1) * 2 * real_bytes
 
 
+def stage_rooflines(ng, K, NQ, N, w, real_bytes, stage_ms, peak_gbs):
+    """Algorithmic bytes of each long-range stage of the pruned pipeline and
+    the fraction of the HBM peak its live stage time reaches (stages of the
+    concurrent evaluation, so shared with the short-range branch).  3 real
+    components, complex modes of 2 * real_bytes; retained z-modes K_z + 1,
+    y-modes 2 K_y + 1."""
+    cb = 2 * real_bytes
+    nk, ny2 = K[2] + 1, 2 * K[1] + 1
+    full = 3 * ng[0] * ng[1] * nk * cb      # F1: every (x, y) column, retained z-modes
+    half = 3 * ng[0] * ny2 * nk * cb        # F2: every x, retained y- and z-modes
+    nd = -(-(8 + 3 * w * real_bytes) // 16) * 16  # sorted node record with its weights
+    rec = 32 if real_bytes == 4 else 64
+    stage_bytes = {
+        "spread": rec * NQ + full,
+        "fft_fwd": full + half,
+        "kspace": 2 * half,
+        "fft_inv": half + full,
+        # inverse z + interpolation: modes in, node records in, sums added, final float64 sum
+        "interp": full + N * (nd + 3 * real_bytes + 3 * real_bytes + 24 + 24 + 24),
+    }
+    out = {}
+    for k, b in stage_bytes.items():
+        gbs = b / (stage_ms[k] * 1e-3) / 1e9
+        out[k] = {"bytes": int(b), "ms": stage_ms[k], "gbs": gbs, "frac": gbs / peak_gbs}
+    return out
+
+
+def short_range_pairs(rc, L, N, NQ):
+    """Useful short-range pairs per evaluation at uniform density: each of
+    the N targets sees (4 pi / 3) r_c^3 NQ / V sources inside r_c."""
+    V = float(L[0]) * float(L[1]) * float(L[2])
+    return N * (4.0 * math.pi / 3.0) * rc ** 3 * NQ / V
+
+
 def ncu_traffic(kernel, workload, source):
     """Per-launch DRAM traffic from the committed ncu summary of this kernel and
     workload, if the summary was taken from the current source (else None)."""
@@ -405,6 +439,13 @@ def run_ours(args, rank, world, dist):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = sb / (stage_mean["spread"] * 1e-3) / 1e9
+    stage_roof = stage_rooflines(ng, Kd, NQ, f.N, p.nufft_w, real_bytes, stage_mean, peak)
+    pairs = short_range_pairs(p.rc, f.L, f.N, NQ)
+    short = {"pairs_est": pairs, "pairs_per_s": pairs / (stage_mean["short_range"] * 1e-3),
+             "note": "uniform-density estimate of the pairs inside r_c; live stage time (concurrent branch)"}
+    torch.cuda.synchronize()
+    fma_peak = {"fp32_tflops": B.bs_fma_peak(B.BS_MIXED) / 1e12, "fp64_tflops": B.bs_fma_peak(B.BS_FP64) / 1e12,
+                "how": "bs_fma_peak: 8 independent FMA chains per thread, 8 x 256-thread CTAs per SM"}
 
     # end to end through the host-buffer entry point (pinned memory)
     hn = torch.from_numpy(f.nodes).pin_memory()
@@ -506,6 +547,9 @@ def run_ours(args, rank, world, dist):
             "ms_per_step_graph_replay": statistics.median(graph_ms),
             "clocks": clk,
             "stages_ms": stage_mean,
+            "stage_roofline": stage_roof,
+            "short_range": short,
+            "fma_peak": fma_peak,
             "fp64_form": fp64,
             "batched_form": batched,
             "large_form": large,

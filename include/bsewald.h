@@ -387,6 +387,18 @@ int bs_short_range_static(const double L[3], double kappa, double alpha, double 
                           const double* src_q, const int* src_seg, int ntgt, const double* tgt_pos,
                           const int* tgt_omit, double* vel, void* stream);
 
+/*
+ * bs_fma_peak -- measured fused multiply-add throughput of the current
+ * device in flop/s (2 per FMA), precision BS_FP64 or BS_MIXED (float32):
+ * the denominator of the roofline of the ALU-bound kernels (the short
+ * range; the method has no dense contraction, Sec. 3.2).  Eight
+ * independent FMA chains per thread, 8 CTAs of 256 threads per SM, best of
+ * three timed launches after a warm-up (about 0.1 s each).  Synchronous on
+ * the legacy default stream.  Errors: BS_ERR_ARG (null output),
+ * BS_ERR_OOM, BS_ERR_CUDA.
+ */
+int bs_fma_peak(int precision, double* flops_per_s);
+
 /* Device bytes held by the context's workspace. */
 int bs_workspace_bytes(bs_ctx* ctx, long long* bytes);
 

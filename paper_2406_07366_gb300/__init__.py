@@ -37,7 +37,7 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
            "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
-           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity"]
+           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity", "bs_fma_peak"]
 
 
 class bs_params(ctypes.Structure):
@@ -81,6 +81,7 @@ def _load():
         "bs_status": ([vp], ctypes.c_int),
         "bs_stage_times": ([vp, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
         "bs_workspace_bytes": ([vp, P(ctypes.c_longlong)], ctypes.c_int),
+        "bs_fma_peak": ([ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
         "bs_destroy": ([vp], None),
         "bs_last_error": ([], ctypes.c_char_p),
         "bs_graph_capture": ([vp, vp, vp, vp], ctypes.c_int),
@@ -321,6 +322,13 @@ def bs_stage_times(ctx):
     n = ctypes.c_int()
     _check(lib().bs_stage_times(ctx, ms, 16, ctypes.byref(n)))
     return {STAGES[i]: float(ms[i]) for i in range(n.value)}
+
+
+def bs_fma_peak(precision):
+    """Measured FMA throughput of the current device in flop/s (BS_FP64 or BS_MIXED = float32)."""
+    f = ctypes.c_double()
+    _check(lib().bs_fma_peak(int(precision), ctypes.byref(f)))
+    return f.value
 
 
 def bs_workspace_bytes(ctx):

@@ -21,7 +21,8 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libbsewald.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["bs_api.cu", "k_geometry.cu", "k_sort.cu", "k_short.cu", "k_long.cu", "k_fft.cu", "k_static_short.cu", "k_rk4.cu"]
+SOURCES = ["bs_api.cu", "k_geometry.cu", "k_sort.cu", "k_short.cu", "k_long.cu", "k_fft.cu", "k_static_short.cu", "k_rk4.cu",
+           "k_peak.cu"]
 
 
 def _nvcc() -> str:

@@ -186,3 +186,7 @@ def test_library_has_no_unresolved_internal_symbols(B):
     out = subprocess.run([nm, "-D", "--undefined-only", B.LIB_PATH], capture_output=True, text=True).stdout
     internal = [ln for ln in out.splitlines() if "_ZN3bsw" in ln]
     assert not internal, internal
+
+
+def test_fma_peak_rejects_a_null_output(B):
+    assert B.lib().bs_fma_peak(B.BS_MIXED, None) == B.BS_ERR_ARG
