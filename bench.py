@@ -10,7 +10,7 @@ of the workload: spline fit, quadrature sources, short range, long range
 
 Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
 replica of the workload (a single configuration does not shard without an
-exchange step; see DESIGN.md) and `value` counts the nodes of all ranks
+exchange step) and `value` counts the nodes of all ranks
 over the slowest rank's time.  `--impl reference` times the FP64 CPU oracle
 on the host cores instead (rank 0 only).
 """
@@ -306,17 +306,28 @@ def short_range_pairs(rc, L, N, NQ):
     return N * (4.0 * math.pi / 3.0) * rc ** 3 * NQ / V
 
 
+def source_digest(path):
+    """SHA-1 (12 hex digits) of a CUDA source with its comments removed and
+    its whitespace collapsed: the code that ran, whatever its comments say."""
+    import hashlib
+    import re
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", " ", txt)
+    txt = " ".join(txt.split())
+    return hashlib.sha1(txt.encode()).hexdigest()[:12]
+
+
 def ncu_traffic(kernel, workload, source):
     """Per-launch DRAM traffic from the committed ncu summary of this kernel and
-    workload, if the summary was taken from the current source (else None)."""
-    import hashlib
+    workload, if the summary was taken from the current code (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    sha = hashlib.sha1(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:12]
+    sha = source_digest(os.path.join(ROOT, source))
     tb = [ln.split(":")[1].strip() for ln in txt.splitlines() if ln.startswith("traffic_bytes_per_launch:")]
-    src = [ln.split()[-1] for ln in txt.splitlines() if ln.startswith("source:")]
+    src = [ln.split()[1] for ln in txt.splitlines() if ln.startswith("source:")]
     if tb and src and src[0] == sha:
         return int(tb[0])
     return None

@@ -12,8 +12,12 @@
 //   C  x FFT of F2, the k-space pass (deconvolution, Gaussian filter, curl,
 //      1/k^2, truncation, k = 0), inverse x FFT, back into F2 (and F2psi).
 //   D  inverse y FFT (zero-padded) into F1.
-//   E  inverse z real FFT (zero-padded) into the real grid for the
-//      interpolation.
+//   E  inverse z real FFT (zero-padded) fused with the interpolation: the
+//      CTA of a column block transforms its 3 Tx Ty z-lines in shared memory
+//      and every node whose support reaches the block adds its part of the
+//      type-2 sum (k_zfft_interp); the real grid is not written.  For psi,
+//      the deterministic mode and the coarse-grained field the inverse z
+//      transform writes the real grid instead (k_fft_z_c2r).
 //
 // The 1-D transforms run in place on lines held in shared memory (lengths
 // 2^a 3^b; radix 8, 4, 3, 2), unnormalised, forward sign e^{-2 pi i jk/n}:
