@@ -683,6 +683,46 @@ __device__ __forceinline__ int home_rel(int ib, int H, int b0, int T, int n, int
     return r > T - 1 ? r - n : (r + W - 1 < 0 ? r + n : r);
 }
 
+// Eight consecutive complex values v[8q .. 8q+7] of a row of nk (entries at
+// or past nk are left unset): 16-byte loads for float32 rows of an even
+// length (16-byte aligned), else one load per value.
+template <typename C>
+__device__ __forceinline__ void load8(const C* __restrict__ row, int nk, int q, C* v)
+{
+    if (sizeof(C) == 8 && (nk & 1) == 0 && 8 * q + 8 <= nk) {
+        const float4* r4 = reinterpret_cast<const float4*>(row + 8 * q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 u = r4[k];
+            v[2 * k].x = u.x;
+            v[2 * k].y = u.y;
+            v[2 * k + 1].x = u.z;
+            v[2 * k + 1].y = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+            if (8 * q + d < nk) v[d] = row[8 * q + d];
+    }
+}
+
+// Zeroes n complex values of shared memory (16-byte stores for float32
+// when n is even; the buffer is 16-byte aligned).
+template <typename C>
+__device__ __forceinline__ void zero_cx(C* buf, int n)
+{
+    if (sizeof(C) == 8 && (n & 1) == 0) {
+        float4* b4 = reinterpret_cast<float4*>(buf);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) b4[i] = z;
+    } else {
+        C zero;
+        zero.x = 0;
+        zero.y = 0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = zero;
+    }
+}
+
 // Separates the two real transforms of every complex z-line of a spread
 // block and writes modes 0..K2.  A thread takes 8 consecutive modes of one
 // line: with the lanes on consecutive groups, the digit-reversed positions
@@ -768,10 +808,7 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, c
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int by = fdiv(blockIdx.x, P.d_nbx);
     const int bx = blockIdx.x - by * P.nbx;
-    C zero;
-    zero.x = 0;
-    zero.y = 0;
-    for (int i = tid; i < ncl * CS; i += blockDim.x) cb[i] = zero;
+    zero_cx(cb, ncl * CS);
 
     constexpr int H = W / 2;
     const int s0 = cstart[blockIdx.x], s1 = cstart[blockIdx.x + 1];
@@ -1249,10 +1286,7 @@ __global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_
     // the home ranges are fetched while the buffer is cleared
     int rb0, rlen;
     const int nr = home_fetch(P, cstart, bx, by, H, rb0, rlen);
-    C zero;
-    zero.x = 0;
-    zero.y = 0;
-    for (int i = tid; i < ncl * CS; i += blockDim.x) cb[i] = zero;
+    zero_cx(cb, ncl * CS);
     if (tid < kHomeMax) {
         r_beg[tid] = rb0;
         r_pre[tid + 1] = rlen;
@@ -1270,14 +1304,8 @@ __global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_
         const C* rowA = F1 + (((size_t)c * n0 + bx * Tx + lx) * n1 + by * Ty + ly) * nk;
         const C* rowB = rowA + nk;
         C A[8], Bv[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const int k = 8 * q + d;
-            if (k < nk) {
-                A[d] = rowA[k];
-                Bv[d] = rowB[k];
-            }
-        }
+        load8(rowA, nk, q, A);
+        load8(rowB, nk, q, Bv);
         const Rev8 rb = rev8_bases(P.rev, P.plan2, q);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
