@@ -8,6 +8,12 @@ of the workload: spline fit, quadrature sources, short range, long range
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--impl ours|reference]
 
+The headline workload is the largest single-GPU one, tangle4e6 (20000
+filaments x 200 nodes, M = 512 modes, 768^3 spread grid, float32 kernels).
+The same line carries the float64 form on that workload, the 1e5-node
+tangle, the 64-tangle batch and RK4 stepping, each with its accuracy against
+stored converged-oracle samples (tests/golden/oracle_<workload>.json).
+
 Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
 replica of the workload (a single configuration does not shard without an
 exchange step) and `value` counts the nodes of all ranks
@@ -43,17 +49,19 @@ KERNELS_PER_STEP = 24
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="tangle1e5")
+    ap.add_argument("--workload", default="tangle4e6")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--cpu-sample", type=int, default=16, help="oracle targets timed for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="oracle targets timed for cpu_baseline (0: four per host thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-batched-form", action="store_true")
     ap.add_argument("--no-large-form", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 1e5-node tangle forms")
     ap.add_argument("--rk4-steps", type=int, default=100, help="RK4 steps of the large tangle")
     return ap.parse_args()
 
@@ -121,9 +129,7 @@ def workload(name):
 
 
 def make_params(B, spec, f, precision, flags=0):
-    w = spec["w"] if precision == B.BS_MIXED else max(spec["w"], 8)
-    return B.make_params(f.L, kappa=spec["kappa"], a=spec["a"], delta=spec["delta"], beta=spec["beta"],
-                         M=spec["M"], Q=spec["Q"], w=w, sigma=spec["sigma"], precision=precision, flags=flags)
+    return B.workload_params(spec, f.L, precision, flags)
 
 
 def max_over_ranks(x, dist, device=None):
@@ -142,6 +148,79 @@ def whole_job_rate(n_per_rank, world, seconds):
     return n_per_rank * world / seconds
 
 
+def golden(name):
+    """Stored converged-oracle velocities at sampled nodes of a workload
+    (tests/golden/make_oracle_samples.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def rel_errors(v, vr):
+    """rms relative error (Sec. 5.1, Eq. def_relative_errors) and the largest
+    per-node relative error."""
+    d = v - vr
+    rms = float(np.sqrt(np.mean(np.sum(d ** 2, 1)) / np.mean(np.sum(vr ** 2, 1))))
+    mx = float(np.max(np.linalg.norm(d, axis=1) / np.linalg.norm(vr, axis=1)))
+    return rms, mx
+
+
+def polygon_length(f):
+    nxt = np.arange(f.N) + 1
+    nxt[f.offsets[1:] - 1] = f.offsets[:-1]
+    return float(np.linalg.norm(f.nodes[nxt] - f.nodes, axis=1).sum())
+
+
+def accuracy_of(B, name, f, p, vel):
+    """Accuracy of one evaluation (vel: host array, N x 3) against the stored
+    oracle samples of the workload, next to the Sec. 4 estimate."""
+    doc = golden(name)
+    if doc is None:
+        return None
+    tg = np.asarray(doc["targets"], dtype=np.int64)
+    vr = np.asarray(doc["velocity"])
+    rms, mx = rel_errors(vel[tg], vr)
+    eps_v, _ = B.bs_error_estimate(p, polygon_length(f))
+    vrms = float(np.sqrt(np.mean(np.sum(vr ** 2, 1))))
+    return {"rms_rel_err": rms, "max_rel_err": mx, "targets": int(tg.size), "eps_v_over_vrms": eps_v / vrms,
+            "against": "converged FP64 CPU oracle at sampled nodes (tests/golden/oracle_%s.json)" % name}
+
+
+def time_form(B, stream, flush, spec, f, nodes, prec, steps, graph=False):
+    """Mean CUDA-event milliseconds of `steps` evaluations of a workload in one
+    precision (after two untimed ones), and the last velocity (host)."""
+    import torch
+    p = make_params(B, spec, f, prec)
+    bs = B.BiotSavart(p, f.offsets, f.closing, stream=stream)
+    vel = torch.empty_like(nodes)
+    if graph:
+        bs.capture(nodes, vel)
+        run = bs.launch
+    else:
+        def run():
+            bs.velocity(nodes, vel)
+    for _ in range(2):
+        run()
+    bs.status()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    bs.status()
+    out = vel.cpu().numpy()
+    bs.close()
+    del vel
+    return statistics.mean(ms), out, p
+
+
 def run_batched_form(B, dev, stream, flush, steps):
     """The batched form: 64 independent Fourier tangles with node counts
     log-uniform in [10^3, 10^5] (100 nodes per filament), grids matched to
@@ -150,8 +229,7 @@ def run_batched_form(B, dev, stream, flush, steps):
     import torch
     from paper_2406_07366_gb300 import workloads as W
     fs = W.tangle_batch(nconf=64, seed=5)
-    params = [B.tangle_params(f.N, f.L, beta=3.5, M_min=32, M_max=128, Q=2, w=6, sigma=1.5,
-                              precision=B.BS_MIXED) for f in fs]
+    params = B.tangle_batch_params(fs, B.BS_MIXED)
     bt = B.BiotSavartBatch(params, fs, stream=stream)
     nodes = torch.from_numpy(np.concatenate([f.nodes for f in fs])).to(dev)
     vel = torch.empty_like(nodes)
@@ -168,30 +246,41 @@ def run_batched_form(B, dev, stream, flush, steps):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     bt.status()
+    v = vel.cpu().numpy()
+    off = bt.offsets
     bt.close()
     t = statistics.mean(ms)
     Ms = sorted(p.M[0] for p in params)
-    return {"value": bt.N / (t * 1e-3), "ms_per_step": t, "steps": steps, "nconf": len(fs), "N_total": bt.N,
-            "N_range": [min(f.N for f in fs), max(f.N for f in fs)], "M_range": [Ms[0], Ms[-1]],
-            "issue": "one CUDA graph per evaluation, members on 8 concurrent streams"}
+    out = {"value": bt.N / (t * 1e-3), "ms_per_step": t, "steps": steps, "nconf": len(fs), "N_total": bt.N,
+           "N_range": [min(f.N for f in fs), max(f.N for f in fs)], "M_range": [Ms[0], Ms[-1]],
+           "issue": "one CUDA graph per evaluation, members on 8 concurrent streams"}
+    doc = golden("tangle_batch")
+    if doc is not None:
+        errs, mxs = [], []
+        for i, m in enumerate(doc["members"]):
+            tg = np.asarray(m["targets"], dtype=np.int64)
+            r, x = rel_errors(v[off[i]:off[i + 1]][tg], np.asarray(m["velocity"]))
+            errs.append(r)
+            mxs.append(x)
+        out["accuracy"] = {"worst_member_rms_rel_err": max(errs), "median_member_rms_rel_err": statistics.median(errs),
+                           "max_rel_err": max(mxs), "targets_per_member": len(doc["members"][0]["targets"]),
+                           "against": "converged FP64 CPU oracle at sampled nodes (tests/golden/oracle_tangle_batch.json)"}
+    return out
 
 
-def run_autotuned(B, dev, spec, f, prec):
+def run_autotuned(B, dev, spec, f, prec, cands=(1.0, 1.25, 1.5, 1.71, 2.0)):
     """Sec. 5.3's alpha = C_beta N^(1/3) / L re-chosen by timing on this GPU at
     the same beta (accuracy): C_beta candidates around the paper's 1.71."""
     import torch
     base = make_params(B, spec, f, prec)
     nodes = torch.from_numpy(f.nodes).to(dev)
-    cands = [1.0, 1.25, 1.5, 1.71, 2.0, 2.5, 3.0]
-    best, ms = B.bs_autotune_alpha(base, f.offsets, f.closing, nodes, cands, reps=5)
+    cands = list(cands)
+    best, ms = B.bs_autotune_alpha(base, f.offsets, f.closing, nodes, cands, reps=3)
     i = min(range(len(ms)), key=lambda k: ms[k])
-    nxt = np.arange(f.N) + 1
-    nxt[f.offsets[1:] - 1] = f.offsets[:-1]  # closed polygons
-    length = float(np.linalg.norm(f.nodes[nxt] - f.nodes, axis=1).sum())
-    eps_v, _ = B.bs_error_estimate(best, length)
+    eps_v, _ = B.bs_error_estimate(best, polygon_length(f))
     return {"candidates_C_beta": cands, "ms": ms, "best_C_beta": cands[i], "M": list(best.M), "alpha": best.alpha,
             "rc": best.rc, "value": f.N / (ms[i] * 1e-3), "unit": UNIT, "eps_v": eps_v,
-            "note": "beta = 3.5 kept; the headline keeps the workload's M = 256"}
+            "note": "beta = 3.5 kept; the headline keeps the workload's M"}
 
 
 def polygon_impulse(nodes, offsets, kappa=1.0):
@@ -202,65 +291,43 @@ def polygon_impulse(nodes, offsets, kappa=1.0):
     return 0.5 * kappa * np.cross(x, x[nxt]).sum(axis=0)
 
 
-def run_large_form(B, dev, stream, flush, steps, rk_steps):
-    """Large tangle: 20000 filaments x 200 nodes (4e6 nodes), M = 512, mixed
-    precision; one evaluation replayed from its CUDA graph, then rk_steps RK4
-    steps (Sec. 5.2, dt = Kelvin-wave period at the smallest node spacing)
-    replayed from the captured step, with the energy and impulse drift."""
+def run_rk4(B, dev, stream, spec, f, rk_steps):
+    """rk_steps RK4 steps of the workload (Sec. 5.2, dt = Kelvin-wave period at
+    the smallest node spacing) replayed from the captured step, mixed
+    precision, with the energy (float64 evaluation) and impulse drift."""
     import torch
-    spec, f = workload("tangle4e6")
-    p = make_params(B, spec, f, B.BS_MIXED, flags=B.BS_WANT_PSI)
+    p = make_params(B, spec, f, B.BS_MIXED)
     bs = B.BiotSavart(p, f.offsets, f.closing, stream=stream)
     nodes = torch.from_numpy(f.nodes).to(dev)
-    vel = torch.empty_like(nodes)
-    bs.capture(nodes, vel)
-    for _ in range(2):
-        bs.launch()
-    bs.status()
+    seg = []
+    for l in range(f.nfil):
+        s = f.nodes[f.offsets[l]:f.offsets[l + 1]]
+        seg.append(np.linalg.norm(np.roll(s, -1, axis=0) - s, axis=1).min())
+    dt = B.kelvin_wave_period(min(seg), spec["kappa"], spec["a"], spec["delta"])
+    # the energies come from a float64 evaluation, so that the drift is the
+    # motion's and not the float32 evaluation noise
+    b64 = B.BiotSavart(make_params(B, spec, f, B.BS_FP64, flags=B.BS_WANT_PSI), f.offsets, f.closing, stream=stream)
+    E0 = b64.energy(nodes)
+    P0 = polygon_impulse(f.nodes, f.offsets, spec["kappa"])
+    bs.rk4_capture(nodes, dt)
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms = []
-    for _ in range(steps):
-        flush.zero_()
-        e0.record(stream)
-        bs.launch()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    t = statistics.mean(ms)
-    out = {"workload": "tangle4e6: 20000 closed filaments x 200 nodes, N=4e6, M=512^3 modes, beta=3.5",
-           "value": f.N / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "steps": steps, "n_g": B.bs_nufft_setup(
-               p, want_table=False)[0], "mode": "CUDA graph replay"}
-    if rk_steps > 0:
-        seg = []
-        x = f.nodes
-        for l in range(f.nfil):
-            s = x[f.offsets[l]:f.offsets[l + 1]]
-            seg.append(np.linalg.norm(np.roll(s, -1, axis=0) - s, axis=1).min())
-        dt = B.kelvin_wave_period(min(seg), spec["kappa"], spec["a"], spec["delta"])
-        # the energies come from a float64 evaluation, so that the drift is
-        # the motion's and not the float32 evaluation noise
-        b64 = B.BiotSavart(make_params(B, spec, f, B.BS_FP64, flags=B.BS_WANT_PSI), f.offsets, f.closing,
-                           stream=stream)
-        E0 = b64.energy(nodes)
-        P0 = polygon_impulse(nodes.cpu().numpy(), f.offsets, spec["kappa"])
-        bs.rk4_capture(nodes, dt)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        bs.rk4_launch(rk_steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rk_ms = e0.elapsed_time(e1)
-        bs.status()
-        E1 = b64.energy(nodes)
-        b64.close()
-        P1 = polygon_impulse(nodes.cpu().numpy(), f.offsets, spec["kappa"])
-        out["rk4"] = {"steps": rk_steps, "dt": dt, "ms": rk_ms, "ms_per_step": rk_ms / rk_steps,
-                      "evaluations_per_s": 4 * rk_steps / (rk_ms * 1e-3),
-                      "energy_rel_drift": (E1 - E0) / E0, "energy_eval": "float64 form",
-                      "impulse_rel_drift": float(np.linalg.norm(P1 - P0) / np.linalg.norm(P0)),
-                      "max_node_displacement": float(np.abs(nodes.cpu().numpy() - f.nodes).max())}
+    e0.record(stream)
+    bs.rk4_launch(rk_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rk_ms = e0.elapsed_time(e1)
+    bs.status()
+    E1 = b64.energy(nodes)
+    b64.close()
+    x1 = nodes.cpu().numpy()
+    P1 = polygon_impulse(x1, f.offsets, spec["kappa"])
     bs.close()
-    return out
+    return {"steps": rk_steps, "dt": dt, "ms": rk_ms, "ms_per_step": rk_ms / rk_steps,
+            "evaluations_per_s": 4 * rk_steps / (rk_ms * 1e-3),
+            "energy_rel_drift": (E1 - E0) / E0, "energy_eval": "float64 form",
+            "impulse_rel_drift": float(np.linalg.norm(P1 - P0) / np.linalg.norm(P0)),
+            "max_node_displacement": float(np.abs(x1 - f.nodes).max())}
 
 
 def spread_zfft_bytes(p, ng, K, NQ, real_bytes):
@@ -333,40 +400,66 @@ def ncu_traffic(kernel, workload, source):
     return None
 
 
-def oracle_fixed(f, spec):
-    """The oracle's per-evaluation fixed work: spline fit and quadrature of
-    all filaments, and the Fourier coefficients of all sources."""
+def oracle_subset(f, nfil_sub):
+    """The first nfil_sub filaments of a workload (the same curves and sizes),
+    the source sample on which the oracle is timed."""
+    from paper_2406_07366_gb300 import workloads as W
+    k = min(int(nfil_sub), f.nfil)
+    off = f.offsets[:k + 1].copy()
+    return W.Filaments(f.nodes[:off[-1]].copy(), off, f.closing[:k].copy(), f.L.copy(), f.name + f"[:{k}]")
+
+
+def oracle_fixed(f, spec, nfil_sub):
+    """Time the oracle's per-evaluation fixed work on a sample of filaments:
+    the spline fit and quadrature (per filament) and the Fourier coefficients
+    (per source, over the oracle's mode cube); both scale linearly, so the
+    full evaluation's share is the sample's times nfil / nfil_sub."""
     import oracle
+    fs = oracle_subset(f, nfil_sub)
     t0 = time.perf_counter()
-    g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 4, spec["Q"])
+    g = oracle.geometry(fs.nodes, fs.offsets, fs.closing, fs.L, 4, spec["Q"])
+    t_geom = time.perf_counter() - t0
     alpha, K = oracle.converged_params(f.L)
+    t0 = time.perf_counter()
     om = oracle.fourier_coefs(g, f.L, spec["kappa"], K)
-    return dict(g=g, alpha=alpha, K=K, om=om, fixed_s=time.perf_counter() - t0, threads=oracle.get_threads())
+    t_coef = time.perf_counter() - t0
+    scale = f.nfil / fs.nfil
+    return dict(g=g, fs=fs, alpha=alpha, K=K, om=om, scale=scale, sample_s=t_geom + t_coef,
+                fixed_s=(t_geom + t_coef) * scale, threads=oracle.get_threads())
 
 
 def oracle_targets(f, spec, fx, tg):
-    """The oracle's per-target work on targets tg: short range over all
-    sources and 27 images, Fourier synthesis, self and local terms."""
+    """Time the oracle's per-target work for targets tg of the sample: the
+    short range over all sample sources and 27 images (scaled by NQ / NQ_sample
+    to all sources: its cost per source is uniform), the Fourier synthesis
+    over the oracle's modes, the self and local terms."""
     import oracle
-    g, alpha, K = fx["g"], fx["alpha"], fx["K"]
+    g = fx["g"]
     t0 = time.perf_counter()
-    vs, _ = oracle.short_range(g, f.L, spec["kappa"], alpha, 0.0, all_images=True, targets=tg)
-    vf, _ = oracle.fourier_eval(g, f.L, alpha, K, fx["om"], targets=tg)
-    vx, _ = oracle.self_term(g, spec["kappa"], alpha, targets=tg)
-    vl, _ = oracle.local(g, spec["kappa"], spec["a"], spec["delta"], targets=tg)
-    return vl + vs + vf - vx, time.perf_counter() - t0
+    oracle.short_range(g, f.L, spec["kappa"], fx["alpha"], 0.0, all_images=True, targets=tg)
+    t_short = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.fourier_eval(g, f.L, fx["alpha"], fx["K"], fx["om"], targets=tg)
+    oracle.self_term(g, spec["kappa"], fx["alpha"], targets=tg)
+    oracle.local(g, spec["kappa"], spec["a"], spec["delta"], targets=tg)
+    t_rest = time.perf_counter() - t0
+    return (t_short * fx["scale"] + t_rest) / tg.size, t_short + t_rest
 
 
-def oracle_sample(f, spec, n_sample, seed=0):
-    """Time the oracle on n_sample random targets and extrapolate a full
-    evaluation as fixed work + N x per-target work."""
+def oracle_rate(f, spec, nfil_sub, n_targets, seed=0):
+    """Nodes/s of a full oracle evaluation extrapolated from a bounded sample:
+    fixed work on nfil_sub filaments, per-target work on n_targets targets."""
+    fx = oracle_fixed(f, spec, nfil_sub)
     rng = np.random.default_rng(seed)
-    tg = np.sort(rng.choice(f.N, min(n_sample, f.N), replace=False))
-    fx = oracle_fixed(f, spec)
-    v, tt = oracle_targets(f, spec, fx, tg)
-    per_target = tt / tg.size
-    return dict(v=v, targets=tg, geom=fx["g"], fixed_s=fx["fixed_s"], per_target_s=per_target,
-                full_s=fx["fixed_s"] + per_target * f.N, sample_s=fx["fixed_s"] + tt, threads=fx["threads"])
+    tg = np.sort(rng.choice(fx["fs"].N, min(n_targets, fx["fs"].N), replace=False))
+    per_target, tt = oracle_targets(f, spec, fx, tg)
+    full = fx["fixed_s"] + per_target * f.N
+    return dict(full_s=full, value=f.N / full, threads=fx["threads"], fixed_s=fx["fixed_s"], per_target_s=per_target,
+                sample_s=fx["sample_s"] + tt, n_targets=int(tg.size), nfil_sub=fx["fs"].nfil)
+
+
+# filaments of the oracle's timing sample per workload (about 1e5 nodes)
+ORACLE_SUB = {"tangle4e6": 500, "tangle1e5": 1000}
 
 
 # ------------------------------------------------------------------ our arm
@@ -390,39 +483,15 @@ def run_ours(args, rank, world, dist):
         bs.velocity(nodes, vel)
     bs.status()
     torch.cuda.synchronize()
-    # direct calls (no graph), for reference
-    ed0, ed1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    direct = []
-    for _ in range(5):
-        flush.zero_()
-        ed0.record(stream)
-        bs.velocity(nodes, vel)
-        ed1.record(stream)
-        torch.cuda.synchronize()
-        direct.append(ed0.elapsed_time(ed1))
     # the same evaluation replayed from a CUDA graph (context without stage events)
-    bsg = B.BiotSavart(make_params(B, spec, f, prec), f.offsets, f.closing, stream=stream)
-    velg = torch.empty_like(nodes)
-    bsg.capture(nodes, velg)
-    for _ in range(3):
-        bsg.launch()
-    torch.cuda.synchronize()
-    graph_ms = []
-    for _ in range(10):
-        flush.zero_()
-        ed0.record(stream)
-        bsg.launch()
-        ed1.record(stream)
-        torch.cuda.synchronize()
-        graph_ms.append(ed0.elapsed_time(ed1))
-    bsg.close()
+    graph_ms, _, _ = time_form(B, stream, flush, spec, f, nodes, prec, 10, graph=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
 
     clocks = Clocks(dev.index if dev.index is not None else 0)
     clocks.start()
-    step_ms, stages = [], []
+    stages = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
         flush.zero_()  # L2 flush between steps, outside the timed events
@@ -439,6 +508,7 @@ def run_ours(args, rank, world, dist):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     ms = max_over_ranks(ms, dist, dev)
+    vhead = vel.cpu().numpy()
 
     stage_mean = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
     ng, _ = B.bs_nufft_setup(p, want_table=False)
@@ -472,63 +542,52 @@ def run_ours(args, rank, world, dist):
     e2e_s = (time.perf_counter() - t0) / ke
     ctx2.close()
     e2e_s = max_over_ranks(e2e_s, dist, dev)
+    bs.close()
+    del hn, hv
 
-    autotuned = None
-    if not args.no_autotune and world == 1:
-        autotuned = run_autotuned(B, dev, spec, f, prec)
-
-    large = None
-    if not args.no_large_form and world == 1:
-        large = run_large_form(B, dev, stream, flush, 5, args.rk4_steps)
-
-    batched = None
-    if not args.no_batched_form and world == 1:
-        batched = run_batched_form(B, dev, stream, flush, min(args.steps, 20))
-
-    # the float64 form on the same workload, for the FP32-vs-FP64 comparison
-    fp64 = None
-    if not args.no_fp64_form and prec == B.BS_MIXED:
-        p64 = make_params(B, spec, f, B.BS_FP64)
-        b64 = B.BiotSavart(p64, f.offsets, f.closing, stream=stream)
-        v64 = torch.empty_like(nodes)
-        for _ in range(2):
-            b64.velocity(nodes, v64)
-        torch.cuda.synchronize()
-        k64 = min(args.steps, 5)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tot = 0.0
-        for _ in range(k64):
-            flush.zero_()
-            e0.record(stream)
-            b64.velocity(nodes, v64)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        b64.close()
-        ms64 = tot / k64
-        fp64 = {"value": whole_job_rate(f.N, world, ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
-                "nufft_w": p64.nufft_w}
+    extras = {}
+    if world == 1:
+        # the float64 form on the same workload (the metric's "vs FP64")
+        if not args.no_fp64_form and prec == B.BS_MIXED:
+            ms64, v64, p64 = time_form(B, stream, flush, spec, f, nodes, B.BS_FP64, 3)
+            extras["fp64_form"] = {"value": f.N / (ms64 * 1e-3), "ms_per_step": ms64, "steps": 3,
+                                   "nufft_w": p64.nufft_w, "accuracy": accuracy_of(B, args.workload, f, p64, v64)}
+            torch.cuda.empty_cache()
+        if not args.no_large_form and args.rk4_steps > 0:
+            extras["rk4"] = run_rk4(B, dev, stream, spec, f, args.rk4_steps)
+            torch.cuda.empty_cache()
+        if not args.no_secondary and args.workload != "tangle1e5":
+            s2, f2 = workload("tangle1e5")
+            n2 = torch.from_numpy(f2.nodes).to(dev)
+            msm, vm, pm = time_form(B, stream, flush, s2, f2, n2, B.BS_MIXED, 20)
+            msd, vd, pd = time_form(B, stream, flush, s2, f2, n2, B.BS_FP64, 5)
+            extras["tangle1e5"] = {
+                "workload": "tangle1e5: 1000 closed filaments x 100 nodes, N=1e5, M=256^3 modes (384^3 grid)",
+                "mixed": {"value": f2.N / (msm * 1e-3), "ms_per_step": msm, "nufft_w": pm.nufft_w,
+                          "accuracy": accuracy_of(B, "tangle1e5", f2, pm, vm)},
+                "fp64": {"value": f2.N / (msd * 1e-3), "ms_per_step": msd, "nufft_w": pd.nufft_w,
+                         "accuracy": accuracy_of(B, "tangle1e5", f2, pd, vd)}}
+            del n2
+        if not args.no_batched_form:
+            extras["batched_form"] = run_batched_form(B, dev, stream, flush, min(args.steps, 20))
+        if not args.no_autotune:
+            extras["autotuned"] = run_autotuned(B, dev, spec, f, prec)
 
     result = None
     if rank == 0:
         cpu = None
-        accuracy = None
         if world == 1 and not args.no_cpu_baseline:
-            vgpu = vel.cpu().numpy()
-            o = oracle_sample(f, spec, args.cpu_sample)
-            tg = o["targets"]
-            d = vgpu[tg] - o["v"]
-            rms = float(np.sqrt(np.mean(np.sum(d ** 2, 1)) / np.mean(np.sum(o["v"] ** 2, 1))))
-            mx = float(np.max(np.linalg.norm(d, axis=1) / np.linalg.norm(o["v"], axis=1)))
-            eps_v, _ = B.bs_error_estimate(p, float(o["geom"].lp.sum()))
-            vrms = float(np.sqrt(np.mean(np.sum(o["v"] ** 2, 1))))
-            accuracy = {"rms_rel_err": rms, "max_rel_err": mx, "targets": int(tg.size),
-                        "eps_v_over_vrms": eps_v / vrms, "against": "FP64 CPU oracle (converged Ewald sum)"}
-            cpu = {"value": f.N / o["full_s"], "unit": UNIT, "cores": o["threads"], "kind": "oracle",
-                   "sample": (f"{tg.size} random target nodes of the {f.N}-node workload timed in full "
-                              f"({o['sample_s']:.1f} s: spline fit, Fourier coefficients of all sources, "
-                              f"27-image short range); full evaluation extrapolated as fixed "
-                              f"{o['fixed_s']:.2f} s + N x {o['per_target_s'] * 1e3:.2f} ms")}
+            import oracle
+            n_t = args.cpu_sample or 4 * oracle.get_threads()
+            o = oracle_rate(f, spec, ORACLE_SUB.get(args.workload, f.nfil), n_t)
+            cpu = {"value": o["value"], "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+                   "sample": (f"timed on the first {o['nfil_sub']} of {f.nfil} filaments ({o['sample_s']:.1f} s): "
+                              f"spline fit and Fourier coefficients of their sources, and {o['n_targets']} random "
+                              f"targets in full over their sources (27 images, Fourier synthesis, self and local "
+                              f"terms); fixed work scaled by the filament count, short range by the source "
+                              f"count; full evaluation extrapolated as {o['fixed_s']:.1f} s + N x "
+                              f"{o['per_target_s']:.3f} s"),
+                   "ms_per_step_kind": "extrapolated full evaluation"}
         launches = KERNELS_PER_STEP * args.steps
         result = {
             "metric": METRIC, "value": whole_job_rate(f.N, world, ms * 1e-3), "unit": UNIT, "n_gpus": world,
@@ -542,7 +601,8 @@ def run_ours(args, rank, world, dist):
                        if prec == B.BS_MIXED else "f64",
                        "N": f.N, "nfil": f.nfil, "M": spec["M"], "n_g": ng, "Q": spec["Q"], "w": p.nufft_w,
                        "sigma": spec["sigma"], "beta": spec["beta"], "alpha": p.alpha, "rc": p.rc,
-                       "l2": "512 MiB L2 flush between timed steps (outside the events)",
+                       "l2": "512 MiB L2 flush between timed steps (outside the events); the workspace is far "
+                             "larger than L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": "k_spread_zfft", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
@@ -555,52 +615,54 @@ def run_ours(args, rank, world, dist):
                     "d2h_bytes_per_step": int(f.N * 24), "ms_per_step": e2e_s * 1e3,
                     "api": "bs_compute_host (pinned host buffers)"},
             "gpu_launches": launches,
-            "ms_per_step_graph_replay": statistics.median(graph_ms),
+            "ms_per_step_graph_replay": graph_ms,
             "clocks": clk,
             "stages_ms": stage_mean,
             "stage_roofline": stage_roof,
             "short_range": short,
             "fma_peak": fma_peak,
-            "fp64_form": fp64,
-            "batched_form": batched,
-            "large_form": large,
-            "autotuned": autotuned,
-            "accuracy": accuracy,
+            "accuracy": accuracy_of(B, args.workload, f, p, vhead),
         }
-    bs.close()
+        result.update(extras)
     return result
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
 def run_reference(args):
-    """The oracle as the reference arm: its fixed work (spline fit, Fourier
-    coefficients of all sources) is timed once; each step then evaluates a
-    fresh random sample of targets in full (all sources, 27 images), and the
-    full-evaluation rate is N / (fixed + N x mean per-target time)."""
+    """The oracle as the reference arm, timed like cpu_baseline: its fixed work
+    (spline fit, Fourier coefficients) on a sample of filaments, scaled to the
+    workload; each step then evaluates a fresh random sample of targets in full
+    over the sample's sources, and the full-evaluation rate is
+    N / (fixed + N x mean per-target time)."""
+    import oracle
     spec, f = workload(args.workload)
-    n = max(1, min(args.cpu_sample // 2, 8))
-    fx = oracle_fixed(f, spec)
+    n = args.cpu_sample or oracle.get_threads()
+    fx = oracle_fixed(f, spec, ORACLE_SUB.get(args.workload, f.nfil))
     rng = np.random.default_rng(1234)
     for _ in range(args.warmup):
-        oracle_targets(f, spec, fx, np.sort(rng.choice(f.N, n, replace=False)))
+        oracle_targets(f, spec, fx, np.sort(rng.choice(fx["fs"].N, n, replace=False)))
     per = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, tt = oracle_targets(f, spec, fx, np.sort(rng.choice(f.N, n, replace=False)))
-        per.append(tt / n)
+        pt, _ = oracle_targets(f, spec, fx, np.sort(rng.choice(fx["fs"].N, n, replace=False)))
+        per.append(pt)
     wall = time.perf_counter() - t0
     full = fx["fixed_s"] + statistics.mean(per) * f.N
     v = f.N / full
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-phase Fourier tangles)",
+            "warmup": args.warmup, "ms_per_step": full * 1e3, "ms_per_step_kind": "extrapolated full evaluation",
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-phase Fourier tangles, no dataset)",
             "impl": "reference",
-            "config": {"workload": args.workload, "N": f.N, "M": spec["M"]},
+            "config": {"workload": f"{args.workload}: {f.nfil} closed filaments x {f.N // max(f.nfil, 1)} nodes, "
+                                   f"N={f.N}, L=2pi, M={spec['M']}^3 modes, beta={spec['beta']}",
+                       "N": f.N, "M": spec["M"]},
             "cpu_baseline": {"kind": "oracle", "cores": fx["threads"], "value": v, "unit": UNIT,
-                             "sample": (f"fixed work once ({fx['fixed_s']:.1f} s: spline fit + Fourier coefficients "
-                                        f"of all {f.N * spec['Q']} sources); each of {args.steps} steps: {n} random "
-                                        f"targets in full ({wall:.1f} s total); ms_per_step = extrapolated full "
-                                        f"evaluation")},
+                             "sample": (f"fixed work timed once on the first {fx['fs'].nfil} of {f.nfil} filaments "
+                                        f"({fx['sample_s']:.1f} s, scaled by the filament count); each of "
+                                        f"{args.steps} steps: {n} random targets in full over those filaments' "
+                                        f"sources ({wall:.1f} s total, short range scaled by the source count); "
+                                        f"ms_per_step = extrapolated full evaluation")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -365,9 +365,9 @@ int bs_stage_times(bs_ctx* ctx, float* ms, int n, int* n_out);
  * 9 MiB compiled into the library, present on every device that loads the
  * library until the process exits.  Limits: nsrc <= 131072 sources and at
  * most 65536 cells (cells of edge >= rc/m, m lowered from 3 to 1 to fit;
- * BS_ERR_ARG with a message beyond that).  The first call on a device looks
- * up the scratch address there (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  Every call
+ * BS_ERR_ARG with a message beyond that).  Every call looks up the
+ * scratch address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing), so a device reset between calls is harmless.  Every call
  * shares the one array and leaves its contents behind; the call clears
  * what must start at zero.  Calls whose work overlaps on the GPU (two
  * streams, two threads) race on the array: serialise them.
@@ -398,6 +398,19 @@ int bs_short_range_static(const double L[3], double kappa, double alpha, double 
  * BS_ERR_OOM, BS_ERR_CUDA.
  */
 int bs_fma_peak(int precision, double* flops_per_s);
+
+/*
+ * bs_erfc_f32 -- the float32 complementary error function that the
+ * short-range kernels use for g^(n) and f^(n) (Sec. 3.1, Eq.
+ * ewald_green_functions): erfc(x) = exp(-x^2) erfcx(x), erfcx a fitted
+ * polynomial in 1 / (1 + x/2) on [0, 8].  A diagnostic, so that its error
+ * can be measured against CUDA's erfcf / erfc.
+ *   x   (device) n float32 arguments in [0, 8]
+ *   out (device) n float32 results
+ * Asynchronous on stream (NULL = legacy default stream).  Errors:
+ * BS_ERR_ARG, BS_ERR_CUDA.
+ */
+int bs_erfc_f32(int n, const float* x, float* out, void* stream);
 
 /* Device bytes held by the context's workspace. */
 int bs_workspace_bytes(bs_ctx* ctx, long long* bytes);

@@ -578,7 +578,7 @@ void or_short_range(long ntgt, const int64_t* tgt, const double* nodes, const in
                     double kappa, double alpha, double rc, int all_images, double* v, double* psi)
 {
     const double pref = kappa / (4.0 * OR_PI);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 1)
     for (long t = 0; t < ntgt; t++) {
         long j = tgt[t];
         long jp = prev_node(off, fil_of, j);
@@ -712,7 +712,7 @@ void or_fourier_eval(long ntgt, const int64_t* tgt, const double* nodes, const d
         G[mi] = (k2s == 0.0) ? 0.0 : exp(-k2s / (4.0 * alpha * alpha)) / k2s;
     }
 
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 1)
     for (long t = 0; t < ntgt; t++) {
         const double* x = nodes + 3 * tgt[t];
         double* tb = (double*)malloc((size_t)(nax * 2) * sizeof(double));
@@ -895,7 +895,7 @@ void or_open_space(long ntgt, const int64_t* tgt, const double* nodes, const int
                    long NQ, int Q, const double* qX, const double* qq, double kappa, double* v, double* psi)
 {
     const double pref = kappa / (4.0 * OR_PI);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 1)
     for (long t = 0; t < ntgt; t++) {
         long j = tgt[t];
         long jp = prev_node(off, fil_of, j);

@@ -37,7 +37,7 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
            "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
-           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity", "bs_fma_peak"]
+           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity", "bs_fma_peak", "bs_erfc_f32"]
 
 
 class bs_params(ctypes.Structure):
@@ -82,6 +82,7 @@ def _load():
         "bs_stage_times": ([vp, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
         "bs_workspace_bytes": ([vp, P(ctypes.c_longlong)], ctypes.c_int),
         "bs_fma_peak": ([ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
+        "bs_erfc_f32": ([ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "bs_destroy": ([vp], None),
         "bs_last_error": ([], ctypes.c_char_p),
         "bs_graph_capture": ([vp, vp, vp, vp], ctypes.c_int),
@@ -331,6 +332,20 @@ def bs_fma_peak(precision):
     return f.value
 
 
+def bs_erfc_f32(x, out, stream=None):
+    """The short-range kernels' float32 erfc at the device float32 tensor x,
+    written to the device float32 tensor out (same length)."""
+    import torch
+    for t in (x, out):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise BSError(BS_ERR_ARG, "bs_erfc_f32: contiguous CUDA float32 tensors expected")
+    if x.numel() != out.numel():
+        raise BSError(BS_ERR_ARG, "bs_erfc_f32: x and out differ in length")
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib().bs_erfc_f32(int(x.numel()), _ptr(x), _ptr(out), ctypes.c_void_p(stream)))
+
+
 def bs_workspace_bytes(ctx):
     b = ctypes.c_longlong()
     _check(lib().bs_workspace_bytes(ctx, ctypes.byref(b)))
@@ -344,13 +359,33 @@ def bs_destroy(ctx):
 
 def bs_short_range_static(L, kappa, alpha, rc, src_pos, src_q, src_seg, tgt_pos, tgt_omit, vel, stream=None):
     """Short-range velocity sum with the library's fixed scratch (no device
-    allocation; for callers that cannot allocate).  Arrays are device tensors:
-    src_pos, src_q (nsrc x 3 float64), src_seg (nsrc int32), tgt_pos (ntgt x 3
-    float64), tgt_omit (ntgt x 2 int32), vel (ntgt x 3 float64, written)."""
+    allocation; for callers that cannot allocate).  Arrays are contiguous device
+    tensors on one device: src_pos, src_q (nsrc x 3 float64), src_seg (nsrc
+    int32), tgt_pos (ntgt x 3 float64), tgt_omit (ntgt x 2 int32), vel (ntgt x 3
+    float64, written); anything else raises BSError(BS_ERR_ARG) before the
+    call.  stream: a torch stream or a cudaStream_t handle, default torch's
+    current stream on that device."""
+    import torch
+    ns, nt = int(src_pos.shape[0]), int(tgt_pos.shape[0])
+    want = ((src_pos, torch.float64, (ns, 3), "src_pos"), (src_q, torch.float64, (ns, 3), "src_q"),
+            (src_seg, torch.int32, (ns,), "src_seg"), (tgt_pos, torch.float64, (nt, 3), "tgt_pos"),
+            (tgt_omit, torch.int32, (nt, 2), "tgt_omit"), (vel, torch.float64, (nt, 3), "vel"))
+    for t, dt, shape, name in want:
+        # the kernels index these arrays by the counts taken from src_pos and
+        # tgt_pos: a wrong dtype, shape or placement would read or write out
+        # of bounds, so it is refused here
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or tuple(t.shape) != shape or not t.is_cuda \
+                or not t.is_contiguous() or t.device != src_pos.device:
+            raise BSError(BS_ERR_ARG, f"bs_short_range_static: {name} must be a contiguous CUDA {dt} tensor of "
+                                      f"shape {shape} on {src_pos.device}")
+    if stream is None:
+        stream = torch.cuda.current_stream(src_pos.device).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
     Lc = (ctypes.c_double * 3)(*np.broadcast_to(np.asarray(L, dtype=float), (3,)))
-    _check(lib().bs_short_range_static(Lc, float(kappa), float(alpha), float(rc), int(src_pos.shape[0]),
-                                       _ptr(src_pos), _ptr(src_q), _ptr(src_seg), int(tgt_pos.shape[0]),
-                                       _ptr(tgt_pos), _ptr(tgt_omit), _ptr(vel), stream))
+    _check(lib().bs_short_range_static(Lc, float(kappa), float(alpha), float(rc), ns, _ptr(src_pos), _ptr(src_q),
+                                       _ptr(src_seg), nt, _ptr(tgt_pos), _ptr(tgt_omit), _ptr(vel),
+                                       ctypes.c_void_p(stream)))
 
 
 # ------------------------------------------------------------- convenience
@@ -380,6 +415,25 @@ def tangle_params(N, L, beta=3.5, M_min=32, M_max=128, **kw) -> bs_params:
     M = bs_params_from_beta(beta, L, M=0, N=int(N)).M[0]
     M = int(min(max(M, M_min), M_max))
     return make_params(L, beta=beta, M=M, **kw)
+
+
+def workload_params(spec, L, precision=BS_MIXED, flags=0) -> bs_params:
+    """Parameters of a named workload (a ``workloads.WORKLOADS`` entry): its
+    beta, M, Q and sigma; the width w of the entry for the mixed form and at
+    least 8 for the float64 form (Table tab:performance: w = 8 for 1e-6)."""
+    w = spec["w"] if precision == BS_MIXED else max(spec["w"], 8)
+    return make_params(L, kappa=spec["kappa"], a=spec["a"], delta=spec["delta"], beta=spec["beta"], M=spec["M"],
+                       Q=spec["Q"], order=spec.get("order", 4), w=w, sigma=spec["sigma"], precision=precision,
+                       flags=flags)
+
+
+def tangle_batch_params(filaments, precision=BS_MIXED, flags=0):
+    """Parameters of the members of a batch of tangles: beta = 3.5, grids of
+    32..128 modes matched to k_max (``tangle_params``), Q = 2, w = 6 for the
+    mixed form (8 for float64), sigma = 1.5."""
+    w = 6 if precision == BS_MIXED else 8
+    return [tangle_params(f.N, f.L, beta=3.5, M_min=32, M_max=128, Q=2, w=w, sigma=1.5, precision=precision,
+                          flags=flags) for f in filaments]
 
 
 class BiotSavartBatch:

@@ -234,4 +234,31 @@ cudaError_t launch_short(const ShortP& P, const Work& w, cudaStream_t s)
 template cudaError_t launch_short<float>(const ShortP&, const Work&, cudaStream_t);
 template cudaError_t launch_short<double>(const ShortP&, const Work&, cudaStream_t);
 
+// The float32 complementary error function as the short-range kernels take
+// it (erfc_e with e = expf(-x^2)), one thread per argument.
+__global__ void k_erfc_f32(int n, const float* __restrict__ x, float* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float xi = x[i];
+        out[i] = erfc_e<float>(xi, expf(-xi * xi));
+    }
+}
+
 }  // namespace bsw
+
+extern "C" int bs_erfc_f32(int n, const float* x, float* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) {
+        bsw::set_last_error("bs_erfc_f32: bad arguments");
+        return BS_ERR_ARG;
+    }
+    if (n == 0) return BS_OK;
+    bsw::k_erfc_f32<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, x, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        bsw::set_last_error(cudaGetErrorString(e));
+        return BS_ERR_CUDA;
+    }
+    return BS_OK;
+}

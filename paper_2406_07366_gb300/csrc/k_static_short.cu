@@ -15,7 +15,6 @@
 #include <math.h>
 #include <stddef.h>
 
-#include <mutex>
 
 #include "bs_internal.cuh"
 
@@ -227,9 +226,6 @@ __global__ void k_st_pairs(StP P, const double* __restrict__ tpos, const int* __
 
 // Device address of g_scratch, looked up once per device (with that device
 // current) on the first call made on it.
-std::mutex g_mu;
-void* g_addr[128] = {};
-
 int st_fail(int code, const char* msg)
 {
     bsw::set_last_error(msg);
@@ -259,16 +255,20 @@ extern "C" int bs_short_range_static(const double L[3], double kappa, double alp
     StP P;
     P.m = 3;
     for (;;) {
-        long long tot = 1;
+        // the cell counts are formed in double and clamped before the int
+        // conversion, so that a strongly anisotropic box (one axis many
+        // times r_c) cannot overflow them
+        double tot = 1.0;
         for (int d = 0; d < 3; ++d) {
-            int n = (int)floor(L[d] * P.m / rc);
-            n = n < 1 ? 1 : n;
+            double nd = floor(L[d] * P.m / rc);
+            nd = nd < 1.0 ? 1.0 : (nd > (double)kStaticMaxCells + 1.0 ? (double)kStaticMaxCells + 1.0 : nd);
+            const int n = (int)nd;
             P.nc[d] = n;
             P.hc[d] = L[d] / n;
             P.L[d] = L[d];
-            tot *= n;
+            tot *= nd;
         }
-        if (tot <= kStaticMaxCells) break;
+        if (tot <= (double)kStaticMaxCells) break;
         if (P.m == 1)
             return st_fail(BS_ERR_ARG, "bs_short_range_static: rc too small for the 65536-cell static scratch");
         P.m -= 1;
@@ -280,18 +280,15 @@ extern "C" int bs_short_range_static(const double L[3], double kappa, double alp
     P.nsrc = nsrc;
     P.ntgt = ntgt;
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return st_fail(BS_ERR_CUDA, "no CUDA device");
+    // The scratch address is looked up on every call, with the caller's
+    // device current: in host code g_scratch names a host-side stand-in,
+    // and the device copy can move when the context is torn down and made
+    // again (cudaDeviceReset, a released primary context).  The lookup
+    // allocates nothing.
     void* base = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-            if (e != cudaSuccess || !p) return st_fail(BS_ERR_CUDA, cudaGetErrorString(e));
-            g_addr[dev] = p;
-        }
-        base = g_addr[dev];
+        cudaError_t e = cudaGetSymbolAddress(&base, g_scratch);
+        if (e != cudaSuccess || !base) return st_fail(BS_ERR_CUDA, cudaGetErrorString(e));
     }
     StScratch* S = (StScratch*)base;
     int* start = (int*)((char*)base + offsetof(StScratch, start));

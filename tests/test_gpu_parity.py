@@ -265,51 +265,9 @@ def test_ellipses40_fp64_and_alpha_sweep():
 
 
 # ------------------------------------------------------------------ full-size workloads
-def test_tangle1e5_mixed_sampled():
-    """Random tangle, 1000 filaments x 100 nodes, M = 256, mixed precision,
-    in the configuration the benchmark times: 64 sampled nodes against the
-    converged oracle (which sums over all 2e5 sources)."""
-    B = _B()
-    spec = W.WORKLOADS["tangle1e5"]
-    f = spec["gen"]()
-    p = params(f, M=spec["M"], Q=spec["Q"], w=spec["w"], sigma=spec["sigma"], precision=B.BS_MIXED)
-    v = gpu_velocity(f, p)
-    assert np.all(np.isfinite(v))
-    rng = np.random.default_rng(0)
-    tg = np.sort(rng.choice(f.N, 64, replace=False))
-    g = geom(f, 4, spec["Q"])
-    vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA, targets=tg)
-    assert rms_rel(v[tg], vr) < 1e-5
-
-
-def test_tangle1e5_fp64_sampled():
-    B = _B()
-    spec = W.WORKLOADS["tangle1e5"]
-    f = spec["gen"]()
-    p = params(f, M=spec["M"], Q=spec["Q"], w=8, sigma=1.5, precision=B.BS_FP64)
-    v = gpu_velocity(f, p)
-    rng = np.random.default_rng(1)
-    tg = np.sort(rng.choice(f.N, 32, replace=False))
-    g = geom(f, 4, spec["Q"])
-    vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA, targets=tg)
-    assert rms_rel(v[tg], vr) < 2e-6
-
-
-def test_tangle4e6_mixed_sampled():
-    """Large tangle, 20000 filaments x 200 nodes (4e6 nodes, 8e6 sources),
-    M = 512 (768^3 spread grid), mixed precision: 8 sampled nodes against the
-    converged oracle summing over all sources, plus every velocity finite."""
-    B = _B()
-    spec = W.WORKLOADS["tangle4e6"]
-    f = spec["gen"]()
-    p = params(f, M=spec["M"], Q=spec["Q"], w=spec["w"], sigma=spec["sigma"], precision=B.BS_MIXED)
-    v = gpu_velocity(f, p)
-    assert np.all(np.isfinite(v))
-    rng = np.random.default_rng(4)
-    tg = np.sort(rng.choice(f.N, 8, replace=False))
-    g = geom(f, 4, spec["Q"])
-    vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA, targets=tg)
-    assert rms_rel(v[tg], vr) < 1e-5
+# The benchmarked workloads (tangle1e5, tangle4e6, the 64-tangle batch) are
+# checked against stored converged-oracle samples in
+# tests/test_gpu_workload_accuracy.py.
 
 
 # ------------------------------------------------------------------ edge cases

@@ -1,0 +1,128 @@
+"""Accuracy of the benchmarked workloads against the converged oracle (``-m gpu``).
+
+The full-size workloads are evaluated exactly as ``bench.py`` times them and
+compared, at sampled nodes, with the converged-oracle velocities stored in
+tests/golden/oracle_<workload>.json (written by
+tests/golden/make_oracle_samples.py, which calls only the oracle).  The
+gates are the rms relative errors of Sec. 5.1 (Eq. def_relative_errors):
+  * float64 form: <= 1e-6, and within twice the Sec. 4 truncation estimate
+    eps_v / v_rms (Eq. error_trunc_velocity) at beta = 3.5;
+  * mixed form (float32 kernels): <= 1e-5.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2406_07366_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"oracle_{name}.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def _checksum(nodes):
+    x = np.asarray(nodes, dtype=np.float64)
+    w = (np.arange(x.shape[0]) % 97).astype(np.float64)
+    return np.array([np.abs(x).sum(), (w[:, None] * x).sum()])
+
+
+def _same_nodes(f, doc):
+    """The seeded generator draws the curves the stored samples were made from
+    (up to the last-bit differences of sin/cos between machines)."""
+    a, b = _checksum(f.nodes), np.asarray(doc["nodes_checksum"])
+    assert np.all(np.abs(a - b) <= 1e-12 * np.abs(b)), (a, b)
+
+
+def rms_rel(a, b):
+    return float(np.sqrt(np.mean(np.sum((a - b) ** 2, axis=1)) / np.mean(np.sum(b ** 2, axis=1))))
+
+
+def max_rel(a, b):
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+
+def _velocity(B, f, p):
+    bs = B.BiotSavart(p, f.offsets, f.closing)
+    nodes = torch.from_numpy(f.nodes).cuda()
+    v = bs.velocity(nodes)
+    bs.status()
+    torch.cuda.synchronize()
+    out = v.cpu().numpy()
+    bs.close()
+    del nodes, v
+    torch.cuda.empty_cache()
+    return out
+
+
+def _workload_params(B, name, prec):
+    spec = W.WORKLOADS[name]
+    f = spec["gen"]()
+    return f, B.workload_params(spec, f.L, prec)
+
+
+@pytest.mark.parametrize("name", ["tangle1e5", "tangle4e6"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_benchmarked_tangle_against_oracle_samples(name, prec):
+    """The random tangles of the benchmark (1000 x 100 nodes, M = 256; 20000 x
+    200 nodes, M = 512), 256 sampled nodes each against the converged sum over
+    every source."""
+    import paper_2406_07366_gb300 as B
+    doc = _golden(name)
+    f, p = _workload_params(B, name, B.BS_FP64 if prec == "fp64" else B.BS_MIXED)
+    _same_nodes(f, doc)
+    v = _velocity(B, f, p)
+    assert np.all(np.isfinite(v))
+    tg = np.asarray(doc["targets"], dtype=np.int64)
+    vr = np.asarray(doc["velocity"])
+    assert tg.size >= 256
+    err = rms_rel(v[tg], vr)
+    if prec == "fp64":
+        # the Sec. 4 estimate with the curve length of the polygon through the nodes
+        nxt = np.arange(f.N) + 1
+        nxt[f.offsets[1:] - 1] = f.offsets[:-1]
+        length = float(np.linalg.norm(f.nodes[nxt] - f.nodes, axis=1).sum())
+        eps_v, _ = B.bs_error_estimate(p, length)
+        vrms = float(np.sqrt(np.mean(np.sum(vr ** 2, axis=1))))
+        assert err < 1e-6, err
+        assert err < 2 * eps_v / vrms, (err, eps_v / vrms)
+    else:
+        assert err < 1e-5, err
+        # the worst node stays within a few times the budget (the w = 6 NUFFT
+        # error of the long-range part dominates it, Appendix A)
+        assert max_rel(v[tg], vr) < 1e-4
+
+
+def test_benchmarked_batch_against_oracle_samples():
+    """The 64-member batch of the benchmark (node counts log-uniform in
+    [1e3, 1e5], grids 41^3..128^3 modes, float32 kernels), 32 sampled nodes of
+    every member against the converged sum over that member's sources."""
+    import paper_2406_07366_gb300 as B
+    doc = _golden("tangle_batch")
+    fs = W.tangle_batch(nconf=64, seed=5)
+    assert len(fs) == len(doc["members"]) == 64
+    params = B.tangle_batch_params(fs, B.BS_MIXED)
+    bt = B.BiotSavartBatch(params, fs)
+    nodes = torch.from_numpy(np.concatenate([f.nodes for f in fs])).cuda()
+    vel = bt.velocity(nodes)
+    bt.status()
+    torch.cuda.synchronize()
+    v = vel.cpu().numpy()
+    off = bt.offsets
+    bt.close()
+    errs = []
+    for i, (f, m) in enumerate(zip(fs, doc["members"])):
+        _same_nodes(f, m)
+        tg = np.asarray(m["targets"], dtype=np.int64)
+        assert tg.size >= 32 or tg.size == f.N
+        e = rms_rel(v[off[i]:off[i + 1]][tg], np.asarray(m["velocity"]))
+        errs.append(e)
+    assert max(errs) < 1e-5, (int(np.argmax(errs)), max(errs))

@@ -306,14 +306,18 @@ def test_rk4_energy_and_impulse_drift_shrink_with_resolution():
     the curves are refined (leapfrogging ellipses, N_l = 32 -> 64, same
     physical time).  A wrong sign or a dropped term in any velocity part
     breaks the conservation at every resolution."""
-    import paper_2406_07366_gb300 as B
+    def kelvin_wave_period(lam):
+        # Sec. 5.2: T = (2 lam^2 / kappa) / [ln(lam / (pi a)) + 1/2 - (Delta + gamma_E)]
+        gamma_e = 0.57721566490153286061
+        return 2.0 * lam * lam / KAPPA / (math.log(lam / (math.pi * A_CORE)) + 0.5 - (DELTA + gamma_e))
+
     drifts = []
     T = None
     for N_l in (32, 64):
         f = W.leapfrog_ellipses(N_l=N_l)
         dmin = min(np.linalg.norm(np.diff(f.nodes[f.offsets[l]:f.offsets[l + 1]], axis=0, append=f.nodes[
             f.offsets[l]:f.offsets[l] + 1]), axis=1).min() for l in range(f.nfil))
-        dt = B.kelvin_wave_period(dmin, KAPPA, A_CORE, DELTA)
+        dt = kelvin_wave_period(dmin)
         if T is None:
             T = 10 * dt
         n = int(round(T / dt))
