@@ -276,7 +276,7 @@ def run_autotuned(B, dev, spec, f, prec, cands=(1.0, 1.25, 1.5, 1.71, 2.0)):
     nodes = torch.from_numpy(f.nodes).to(dev)
     cands = list(cands)
     best, ms = B.bs_autotune_alpha(base, f.offsets, f.closing, nodes, cands, reps=3)
-    i = min(range(len(ms)), key=lambda k: ms[k])
+    i = min((k for k in range(len(ms)) if ms[k] > 0), key=lambda k: ms[k])
     eps_v, _ = B.bs_error_estimate(best, polygon_length(f))
     return {"candidates_C_beta": cands, "ms": ms, "best_C_beta": cands[i], "M": list(best.M), "alpha": best.alpha,
             "rc": best.rc, "value": f.N / (ms[i] * 1e-3), "unit": UNIT, "eps_v": eps_v,

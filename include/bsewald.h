@@ -65,9 +65,15 @@ enum {
     BS_TIMING = 2,     /* record per-stage CUDA-event times (bs_stage_times) */
     BS_FFT_CUFFT = 4,  /* long range through full cuFFT R2C/C2R transforms instead of
                           the library's pruned per-axis transforms (a cross-check path) */
-    BS_DETERMINISTIC = 8  /* bitwise-reproducible results on a given GPU and build: the binned
-                             sources keep a fixed order and no floating-point sum depends on thread
-                             timing (slower spread); not with BS_FFT_CUFFT (BS_ERR_ARG) */
+    BS_DETERMINISTIC = 8,  /* bitwise-reproducible results on a given GPU and build: the binned
+                              sources keep a fixed order and no floating-point sum depends on thread
+                              timing (slower spread); not with BS_FFT_CUFFT (BS_ERR_ARG) */
+    /* Short-range kernel choice (Sec. 3.2); by default the library picks by the
+       mean count of nodes per r_c cube (8 or more: tiled).  The two give the
+       same sum up to rounding order. */
+    BS_SHORT_TILED = 16,    /* a CTA per r_c cube of nodes stages its neighbour sources in
+                               shared memory (cells per cut-off up to 4) */
+    BS_SHORT_PER_NODE = 32  /* a warp per node walks its neighbour rows in global memory */
 };
 
 /*
@@ -86,7 +92,8 @@ enum {
  *   nufft_sigma   oversampling factor sigma > 1 (Appendix A)
  *   nufft_w       spreading width in grid points, even, 2..16 (Appendix A)
  *   precision     BS_FP64 or BS_MIXED
- *   flags         BS_WANT_PSI | BS_TIMING | BS_FFT_CUFFT | BS_DETERMINISTIC
+ *   flags         BS_WANT_PSI | BS_TIMING | BS_FFT_CUFFT | BS_DETERMINISTIC |
+ *                 BS_SHORT_TILED | BS_SHORT_PER_NODE
  *   cell_div      cells per cut-off length m (cells of edge >= rc/m); the
  *                 paper uses 3 (Sec. 5.3); 0 selects the library default
  *   local_frac    0: the local terms (Eqs. BS_local, streamfunction_local)
@@ -325,11 +332,12 @@ void bs_batch_destroy(bs_batch* b);
  * reps times on an internal stream, timed with CUDA events.
  *   best   (host) the fastest candidate's parameters
  *   ms_out (host, ncand, or NULL) mean milliseconds per evaluation, -1 for
- *          candidates not reached after an error
+ *          candidates the library cannot take (spread grid above 1024 points,
+ *          r_c above L/2: skipped) or not reached after an error
  * Allocates and frees one context at a time (and an N x 3 scratch); run it
  * before other work on the device, not inside a stream capture.  Errors:
- * BS_ERR_ARG, the codes of bs_create / bs_set_filaments / bs_compute,
- * BS_ERR_CUDA.
+ * BS_ERR_ARG (also when no candidate is admissible), the codes of
+ * bs_set_filaments / bs_compute, BS_ERR_CUDA.
  */
 int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t* offsets, const int32_t* closing,
                       const double* nodes, int ncand, const double* cbeta, int reps, bs_params* best, float* ms_out);

@@ -26,6 +26,7 @@ BS_ERR_NONFINITE, BS_ERR_OOM, BS_ERR_CUDA, BS_ERR_CUFFT, BS_ERR_TIMEOUT = 5, 6, 
 BS_ERR_STATE, BS_ERR_GEOMETRY = 10, 11
 BS_FP64, BS_MIXED = 0, 1
 BS_WANT_PSI, BS_TIMING, BS_FFT_CUFFT, BS_DETERMINISTIC = 1, 2, 4, 8
+BS_SHORT_TILED, BS_SHORT_PER_NODE = 16, 32
 
 STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", "kspace", "fft_inv", "interp",
           "total"]

@@ -216,6 +216,8 @@ int derive(const bs_params* p, Derived* d)
     if (!(p->a > 0) || !isfinite(p->a)) return fail(BS_ERR_ARG, "core radius a must be positive");
     if (!isfinite(p->delta)) return fail(BS_ERR_ARG, "delta must be finite");
     if (!(p->alpha > 0) || !isfinite(p->alpha)) return fail(BS_ERR_ARG, "alpha must be positive");
+    if ((p->flags & BS_SHORT_TILED) && (p->flags & BS_SHORT_PER_NODE))
+        return fail(BS_ERR_ARG, "BS_SHORT_TILED and BS_SHORT_PER_NODE exclude each other");
     if ((p->flags & BS_DETERMINISTIC) && (p->flags & BS_FFT_CUFFT))
         return fail(BS_ERR_ARG, "BS_DETERMINISTIC needs the default transform path, not BS_FFT_CUFFT");
     if (!(p->rc > 0) || !isfinite(p->rc)) return fail(BS_ERR_ARG, "rc must be positive");
@@ -412,7 +414,10 @@ int alloc_grids(bs_ctx* c)
     const Derived& d = c->d;
     const size_t rsz = (size_t)d.ng[0] * d.ng[1] * d.ng[2];
     const size_t csz = (size_t)d.ng[0] * d.ng[1] * d.nh;
-    TRY(dalloc(c, c->alloc_g, &c->w.grid, 3 * rsz * sizeof(T)));
+    // the real grid: written only for psi, the deterministic mode, the cuFFT
+    // form and the unfused interpolation (1.4 GB at 384^3 float32, 5.4 GB at 768^3)
+    const bool need_grid = (c->p.flags & (BS_WANT_PSI | BS_DETERMINISTIC | BS_FFT_CUFFT)) || !d.fuse_interp;
+    if (need_grid) TRY(dalloc(c, c->alloc_g, &c->w.grid, 3 * rsz * sizeof(T)));
     TRY(dalloc(c, c->alloc_g, &c->w.spec, 3 * csz * 2 * sizeof(T)));
     if ((c->p.flags & BS_WANT_PSI) && (c->p.flags & BS_FFT_CUFFT))
         TRY(dalloc(c, c->alloc_g, &c->w.spec_psi, 3 * csz * 2 * sizeof(T)));
@@ -443,6 +448,13 @@ int alloc_grids(bs_ctx* c)
             for (int k = 0; k < d.ng[ax]; ++k) rev[o++] = rev_pos_host(k, d.plan[ax]);
         TRY(dalloc(c, c->alloc_g, (void**)&c->w.rev, sizeof(int) * rev.size()));
         CUDA_TRY(cudaMemcpy(c->w.rev, rev.data(), sizeof(int) * rev.size(), cudaMemcpyHostToDevice));
+    }
+    {
+        // nodes binned by target block (m x m x m cells) for the tiled short range
+        long long nblk = 1;
+        for (int k = 0; k < 3; ++k) nblk *= (d.nc[k] + d.m - 1) / d.m;
+        TRY(dalloc(c, c->alloc_g, (void**)&c->w.tb_cnt, sizeof(int) * (size_t)(nblk + 1)));
+        TRY(dalloc(c, c->alloc_g, (void**)&c->w.tb_cur, sizeof(int) * (size_t)(nblk + 1)));
     }
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cnt, sizeof(int) * (size_t)(d.ncells + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.cell_cur, sizeof(int) * (size_t)(d.ncells + 1)));
@@ -507,8 +519,10 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.Tper, sizeof(T) * nf));
     TRY(dalloc(c, L, (void**)&w.vls, sizeof(double) * 3 * N));
     TRY(dalloc(c, L, (void**)&w.pls, sizeof(double) * 3 * N));
-    TRY(dalloc(c, L, &w.vsr, sizeof(T) * 3 * N));
-    TRY(dalloc(c, L, &w.psr, sizeof(T) * 3 * N));
+    TRY(dalloc(c, L, (void**)&w.vsr, sizeof(double) * 3 * N));
+    TRY(dalloc(c, L, (void**)&w.psr, sizeof(double) * 3 * N));
+    TRY(dalloc(c, L, (void**)&w.tb_key, sizeof(int) * N));
+    TRY(dalloc(c, L, (void**)&w.tb_idx, sizeof(int) * N));
     TRY(dalloc(c, L, &w.tgt, sizeof(SrTgt<T>) * N));
     TRY(dalloc(c, L, &w.sr_rec, sizeof(SrRec<T>) * NQ));
     TRY(dalloc(c, L, &w.sr_sorted, sizeof(SrRec<T>) * NQ));
@@ -684,6 +698,8 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         S.L[k] = p.L[k];
     }
     S.m = d.m;
+    for (int k = 0; k < 3; ++k) S.nb[k] = (d.nc[k] + d.m - 1) / d.m;
+    S.kernel = (p.flags & BS_SHORT_TILED) ? 1 : ((p.flags & BS_SHORT_PER_NODE) ? 2 : 0);
     S.rc2 = p.rc * p.rc;
     S.alpha = p.alpha;
     S.pref = p.kappa / (4.0 * kPi);
@@ -817,13 +833,12 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         ZP.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
         ZP.d_n2 = make_fastdiv((unsigned)d.ng[2]);
         ZP.d_ncl = make_fastdiv((unsigned)(d.yc / 2));
-        CE(launch_fft_z_c2r<T>(ZP, w, s));
-        rec(c, 8, s);
-        if (coarse) {  // the coarse-grained field on the grid: copy out, no interpolation
-            const size_t ng3 = (size_t)d.ng[0] * d.ng[1] * d.ng[2];
-            CE(launch_to_double<T>(w.grid, coarse, (int)(3 * ng3), s));
+        if (coarse) {  // the coarse-grained field on the grid, written straight in float64; no interpolation
+            CE(launch_fft_z_c2r<T>(ZP, w, s, coarse));
             return BS_OK;
         }
+        CE(launch_fft_z_c2r<T>(ZP, w, s));
+        rec(c, 8, s);
         }
     }
     if (!fused) {
@@ -834,10 +849,10 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
 
     if (fused) {
         CE(launch_interp_sum<T>((int)c->N, w, parts ? 2 : 0, vel, parts ? parts + 2 * N3 : nullptr, s));
-        if (parts) CE(launch_to_double<T>(w.vsr, parts + N3, (int)N3, s));
+        if (parts) CE(cudaMemcpyAsync(parts + N3, w.vsr, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s));
     } else if (parts) {
         CE(launch_interp<T>(I, nodes, w, w.grid, 2, nullptr, parts + 2 * N3, s));
-        CE(launch_to_double<T>(w.vsr, parts + N3, (int)N3, s));
+        CE(cudaMemcpyAsync(parts + N3, w.vsr, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s));
     } else {
         CE(launch_interp<T>(I, nodes, w, w.grid, 0, vel, nullptr, s));
     }
@@ -875,7 +890,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         }
         if (psi_parts) {
             CE(launch_interp<T>(I, nodes, w, w.grid, 2, nullptr, psi_parts + 2 * N3, s));
-            CE(launch_to_double<T>(w.psr, psi_parts + N3, (int)N3, s));
+            CE(cudaMemcpyAsync(psi_parts + N3, w.psr, sizeof(double) * N3, cudaMemcpyDeviceToDevice, s));
         } else {
             CE(launch_interp<T>(I, nodes, w, w.grid, 1, psi, nullptr, s));
         }
@@ -1640,7 +1655,15 @@ extern "C" int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t*
         for (int c = 0; c < 3; ++c) q.M[c] = p.M[c];
         q.flags &= ~BS_TIMING;
         bs_ctx* c = nullptr;
-        if ((rc = bs_create(&c, &q, s)) != BS_OK) break;
+        if ((rc = bs_create(&c, &q, s)) != BS_OK) {
+            // a candidate the library cannot take (its spread grid too large,
+            // r_c beyond L/2) is skipped, with -1 in ms_out
+            if (rc == BS_ERR_ARG || rc == BS_ERR_RC_GT_HALF_L) {
+                rc = BS_OK;
+                continue;
+            }
+            break;
+        }
         rc = bs_set_filaments(c, nfil, offsets, closing);
         float t = 0.0f;
         for (int r = 0; r < reps + 1 && rc == BS_OK; ++r) {  // the first call warms up
@@ -1668,5 +1691,6 @@ extern "C" int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t*
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
+    if (rc == BS_OK && nbest < 0) return fail(BS_ERR_ARG, "no autotune candidate is admissible");
     return rc;
 }

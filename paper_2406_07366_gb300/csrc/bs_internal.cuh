@@ -114,7 +114,13 @@ struct ShortP {
     double alpha;
     double pref;        // kappa / 4 pi
     int want_psi;
+    int nb[3];          // target blocks of m x m x m cells per axis, ceil(nc / m)
+    int kernel;         // 0: by size, 1: tiled, 2: warp per node (BS_SHORT_TILED / BS_SHORT_PER_NODE)
 };
+
+// The tiled short range takes cells per cut-off up to this (larger m: the
+// warp-per-node kernel).
+constexpr int kShortTileMaxM = 4;
 
 struct SpreadP {
     int ng[3];
@@ -291,8 +297,12 @@ struct Work {
     // node outputs
     double* vls = nullptr;  // N x 3  v_local - v_self
     double* pls = nullptr;  // N x 3  psi_local - psi_self
-    void* vsr = nullptr;    // N x 3  short range
-    void* psr = nullptr;
+    double* vsr = nullptr;  // N x 3  short range (float64 sums of the pair terms)
+    double* psr = nullptr;
+    int* tb_key = nullptr;  // N  target block of every node (short range)
+    int* tb_idx = nullptr;  // N  nodes sorted by target block
+    int* tb_cnt = nullptr;  // nblocks + 1 block starts
+    int* tb_cur = nullptr;  // nblocks scatter cursors
     void* tgt = nullptr;    // N SrTgt
     // sources
     void* sr_rec = nullptr;   // NQ
@@ -309,7 +319,7 @@ struct Work {
     int* scan_tmp = nullptr;   // short-range sort (side stream)
     int* scan_tmp2 = nullptr;  // long-range sort (main stream)
     // grids
-    void* grid = nullptr;     // 3 x ng^3 real
+    void* grid = nullptr;     // 3 x ng^3 real (allocated only where a path writes it)
     void* spec = nullptr;     // 3 x ng0 ng1 nh complex
     void* spec_psi = nullptr; // 3 x ... (psi)
     void* ktab = nullptr;     // per-axis k-space tables
@@ -382,8 +392,10 @@ template <typename T>
 cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s);
+// Inverse z transform into the real grid (w.grid), or, with out64, into a
+// float64 grid of the same layout (the coarse-grained field).
 template <typename T>
-cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s);
+cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s, double* out64 = nullptr);
 // Blocks whose points are gathered from home-block lists (the points sorted
 // once by the block of their grid cell): the home blocks a CTA gathers are
 // distinct and at most 64, and one periodic image of a support meets a block

@@ -355,7 +355,7 @@ __device__ __forceinline__ bool plan_is(const FftPlan& pl)
 }
 
 // Plans with a compiled form (float): 384 = 8 x 8 x 6 at 12, 16 or 24 lines
-// (the 1e5-node tangle), 768 = 8 x 6 x 4 x 4 at 6, 8 or 16 lines (the 4e6-node
+// (the 1e5-node tangle), 768 = 8 x 6 x 4 x 4 at 6, 8, 12 or 16 lines (the 4e6-node
 // tangle), 192 = 8 x 6 x 4 at 16 or 24 lines (the largest batch members).
 template <typename T, bool DIF>
 __device__ __forceinline__ bool fft_const(typename Cx<T>::t* buf, int nlines, int ls, const FftPlan& pl,
@@ -373,6 +373,7 @@ __device__ __forceinline__ bool fft_const(typename Cx<T>::t* buf, int nlines, in
             switch (nlines) {
             case 6: fft_c<T, DIF, 6, 8, 6, 4, 4>(buf, ls, tw); return true;
             case 8: fft_c<T, DIF, 8, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 12: fft_c<T, DIF, 12, 8, 6, 4, 4>(buf, ls, tw); return true;
             case 16: fft_c<T, DIF, 16, 8, 6, 4, 4>(buf, ls, tw); return true;
             default: break;
             }
@@ -1168,10 +1169,10 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P,
 // E: inverse z real FFT.  One CTA per (c, x, chunk of YC y-lines); two real
 // lines per complex transform.
 // ---------------------------------------------------------------------------
-template <typename T, int RM>
+template <typename T, int RM, typename TO>
 __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typename Cx<T>::t* __restrict__ F1,
                                                         const typename Cx<T>::t* __restrict__ tw2,
-                                                        T* __restrict__ grid)
+                                                        TO* __restrict__ grid)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1229,11 +1230,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
     fft_inv_dit<T, RM>(a, ncl, P.d_ncl, CS, P.plan2, tw2);
     const size_t gsz = (size_t)P.ng[0] * n1 * n2;
     const int c = fdiv(cx, P.d_n0), x = cx - c * P.ng[0];
-    T* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
+    TO* gout = grid + c * gsz + ((size_t)x * n1 + y0) * n2;
     // the CTA's YC rows of n2 reals are contiguous in the grid; a thread reads
     // two adjacent complex values of line l and writes the pair to each of the
     // real rows 2l and 2l + 1 (n2 is even)
-    using T2 = typename Cx<T>::t;
+    using T2 = typename Cx<TO>::t;
     const int h2 = n2 >> 1;
     for (int i = threadIdx.x; i < ncl * h2; i += blockDim.x) {
         const int l = i / h2, zz = i - l * h2;
@@ -1739,10 +1740,11 @@ cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cu
     return by_rm<T>(P.plan0, FftXLaunch<T>{ P, w, want_psi, s });
 }
 
-template <typename T>
+template <typename T, typename TO>
 struct FftZLaunch {
     const FftZP& P;
     const Work& w;
+    TO* out;
     cudaStream_t s;
     template <int RM>
     cudaError_t run()
@@ -1750,18 +1752,20 @@ struct FftZLaunch {
         using C = typename Cx<T>::t;
         const size_t sm = (size_t)(P.yc / 2) * P.cls * sizeof(C);
         cudaError_t e =
-            cudaFuncSetAttribute(k_fft_z_c2r<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k_fft_z_c2r<T, RM, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_fft_z_c2r<T, RM><<<3 * P.ng[0] * (P.ng[1] / P.yc), kThreads, sm, s>>>(
-            P, (const C*)w.spec, (const C*)w.tw + P.ng[0] + P.ng[1], (T*)w.grid);
+        k_fft_z_c2r<T, RM, TO><<<3 * P.ng[0] * (P.ng[1] / P.yc), kThreads, sm, s>>>(
+            P, (const C*)w.spec, (const C*)w.tw + P.ng[0] + P.ng[1], out);
         return cudaGetLastError();
     }
 };
 
 template <typename T>
-cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s)
+cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s, double* out64)
 {
-    return by_rm<T>(P.plan2, FftZLaunch<T>{ P, w, s });
+    if (out64) return by_rm<T>(P.plan2, FftZLaunch<T, double>{ P, w, out64, s });
+    if (!w.grid) return cudaErrorInvalidValue;
+    return by_rm<T>(P.plan2, FftZLaunch<T, T>{ P, w, (T*)w.grid, s });
 }
 
 template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaStream_t, bool);
@@ -1778,8 +1782,8 @@ template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, 
 template cudaError_t launch_fft_y<double>(const FftYP&, const Work&, void*, int, cudaStream_t);
 template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool, cudaStream_t);
 template cudaError_t launch_fft_x_kspace<double>(const FftXP&, const Work&, bool, cudaStream_t);
-template cudaError_t launch_fft_z_c2r<float>(const FftZP&, const Work&, cudaStream_t);
-template cudaError_t launch_fft_z_c2r<double>(const FftZP&, const Work&, cudaStream_t);
+template cudaError_t launch_fft_z_c2r<float>(const FftZP&, const Work&, cudaStream_t, double*);
+template cudaError_t launch_fft_z_c2r<double>(const FftZP&, const Work&, cudaStream_t, double*);
 // Writes the composite-radix twiddles into the current device's constant
 // bank (once per device).
 cudaError_t set_fft_constants()

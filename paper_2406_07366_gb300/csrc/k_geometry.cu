@@ -591,7 +591,7 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
 template <typename T>
 __global__ void k_energy_line(const int64_t* __restrict__ off, const double* __restrict__ shift, int nfil, int nmax,
                               const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ Mm,
-                              const T* __restrict__ Tper, const double* __restrict__ pls, const T* __restrict__ psr,
+                              const T* __restrict__ Tper, const double* __restrict__ pls, const double* __restrict__ psr,
                               double* __restrict__ acc, double* __restrict__ per_fil)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -617,7 +617,7 @@ __global__ void k_energy_line(const int64_t* __restrict__ off, const double* __r
             const double Mj = (double)Mm[3 * (o + j) + c], Mn = (double)Mm[3 * (o + jn) + c];
             const double drc = c == 0 ? dr0 : (c == 1 ? dr1 : dr2);
             const double sdot = (double)dp[3 * (o + j) + c] / h - h * (2.0 * Mj + Mn) / 6.0 + drc;
-            const double psi = pls[3 * (o + j) + c] + (double)psr[3 * (o + j) + c];
+            const double psi = pls[3 * (o + j) + c] + psr[3 * (o + j) + c];
             fj += psi * sdot;
         }
         sh_f[j] = fj;
@@ -691,7 +691,7 @@ cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int
         if (e != cudaSuccess) return e;
     }
     k_energy_line<T><<<nfil, 32, sm, s>>>(w.off, w.shift, nfil, nmax, (const T*)w.hseg, (const T*)w.dp,
-                                          (const T*)w.Mm, (const T*)w.Tper, w.pls, (const T*)w.psr,
+                                          (const T*)w.Mm, (const T*)w.Tper, w.pls, w.psr,
                                           w.energy_acc + 1, det ? w.lpart : nullptr);
     return cudaGetLastError();
 }

@@ -213,13 +213,13 @@ __global__ void k_kspace(KspaceP P, typename Cplx<T>::t* __restrict__ spec, type
 }
 
 // Type-2 interpolation at the nodes, plus the epilogue sum
-//   out = add_d (float64: local - self) + add_t (short range, T) + interp.
+//   out = add_d (float64: local - self) + add_t (short range, float64) + interp.
 // part (optional) receives the interpolated long-range part alone.  The
 // weights of the last two axes live in registers (static indices); those of
 // the first axis are computed in the outer loop.
 template <typename T, int W>
 __global__ void __launch_bounds__(128) k_interp(InterpP P, const double* __restrict__ nodes, const T* __restrict__ grid,
-                                                const double* __restrict__ add_d, const T* __restrict__ add_t,
+                                                const double* __restrict__ add_d, const double* __restrict__ add_t,
                                                 double* __restrict__ out, double* __restrict__ part)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,7 +357,7 @@ cudaError_t launch_kspace(const KspaceP& P, const Work& w, cudaStream_t s)
 }
 
 template <typename T, int W>
-static cudaError_t interp_w(const InterpP& P, const double* nodes, const void* grid, const double* add_d, const T* add_t,
+static cudaError_t interp_w(const InterpP& P, const double* nodes, const void* grid, const double* add_d, const double* add_t,
                             double* out, double* part, cudaStream_t s)
 {
     const int tb = 128;
@@ -373,9 +373,9 @@ cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, 
 {
     if (P.N <= 0) return cudaSuccess;
     const double* add_d = nullptr;
-    const T* add_t = nullptr;
-    if (what == 0) { add_d = w.vls; add_t = (const T*)w.vsr; }
-    if (what == 1) { add_d = w.pls; add_t = (const T*)w.psr; }
+    const double* add_t = nullptr;
+    if (what == 0) { add_d = w.vls; add_t = w.vsr; }
+    if (what == 1) { add_d = w.pls; add_t = w.psr; }
     if (what == 2) out = nullptr;
     switch (P.w) {
     case 2: return interp_w<T, 2>(P, nodes, grid, add_d, add_t, out, part_long, s);
@@ -395,7 +395,7 @@ cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, 
 // order as the interpolation kernel's epilogue.
 template <typename T>
 __global__ void k_interp_sum(int n3, const T* __restrict__ acc, const double* __restrict__ add_d,
-                             const T* __restrict__ add_t, double* __restrict__ out, double* __restrict__ part)
+                             const double* __restrict__ add_t, double* __restrict__ out, double* __restrict__ part)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
         const double a = (double)acc[i];
@@ -411,7 +411,7 @@ cudaError_t launch_interp_sum(int N, const Work& w, int what, double* out, doubl
     const int n3 = 3 * N;
     int g = (n3 + 255) / 256;
     if (g > 4096) g = 4096;
-    k_interp_sum<T><<<g, 256, 0, s>>>(n3, (const T*)w.vacc, w.vls, (const T*)w.vsr, what == 2 ? nullptr : out,
+    k_interp_sum<T><<<g, 256, 0, s>>>(n3, (const T*)w.vacc, w.vls, w.vsr, what == 2 ? nullptr : out,
                                       part_long);
     return cudaGetLastError();
 }
