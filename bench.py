@@ -330,6 +330,60 @@ def run_rk4(B, dev, stream, spec, f, rk_steps):
             "max_node_displacement": float(np.abs(x1 - f.nodes).max())}
 
 
+def run_leapfrog(B, dev, nsteps=1000):
+    """Sec. 5.2's conservation run in the paper's production setting: two
+    leapfrogging elliptical rings (32 and 64 nodes each), quintic curves,
+    Q = 3, subdivided local segments (f = 0.1), beta = 3.5, alpha = 7/L,
+    float64, RK4 with the Kelvin-wave step; the largest relative change of
+    the energy (every nsteps/10 steps) and the change of the impulse
+    (kappa/2) oint s x ds on the spline."""
+    import torch
+    from paper_2406_07366_gb300 import workloads as W
+    out = {}
+    for N_l in (32, 64):
+        f = W.leapfrog_ellipses(N_l=N_l)
+        L = float(f.L[0])
+        alpha = 7.0 / L
+        K = int(math.ceil(3.5 * alpha * L / math.pi))
+        p = B.make_params(f.L, kappa=1.0, a=1e-6, delta=0.25, order=6, Q=3, M=2 * K + 1, w=8,
+                          precision=B.BS_FP64, alpha=alpha, flags=B.BS_WANT_PSI, local_frac=0.1)
+        nodes = torch.from_numpy(f.nodes.copy()).to(dev)
+        dmin = min(np.linalg.norm(np.roll(f.nodes[f.offsets[l]:f.offsets[l + 1]], -1, axis=0)
+                                  - f.nodes[f.offsets[l]:f.offsets[l + 1]], axis=1).min() for l in range(f.nfil))
+        dt = B.kelvin_wave_period(dmin, 1.0, 1e-6, 0.25)
+        s = torch.cuda.Stream(device=dev)
+        bs = B.BiotSavart(p, f.offsets, f.closing, stream=s)
+        def impulse():
+            # (kappa/2) oint s x ds on the spline: sum over the quadrature points
+            # of s_q x q_q, each point at the image nearest its node
+            qX, qq = bs.quadrature(nodes)
+            x = nodes.cpu().numpy()
+            qX, qq = qX.cpu().numpy(), qq.cpu().numpy()
+            xn = np.repeat(x, 3, axis=0)
+            qX = qX - f.L[None, :] * np.round((qX - xn) / f.L[None, :])
+            return 0.5 * np.cross(qX, qq).sum(axis=0)
+        with torch.cuda.stream(s):
+            E0 = bs.energy(nodes)
+            P0 = impulse()
+            Es = [E0]
+            bs.rk4_capture(nodes, dt)
+            for _ in range(10):
+                bs.rk4_launch(nsteps // 10)
+                bs.status()
+                Es.append(bs.energy(nodes))
+            x1 = nodes.cpu().numpy()
+            P1 = impulse()
+        bs.close()
+        out[f"N_l={N_l}"] = {"steps": nsteps, "dt": dt, "time": nsteps * dt,
+                             "energy_max_rel_change": float(max(abs(e - E0) for e in Es) / abs(E0)),
+                             "impulse_rel_change": float(np.linalg.norm(P1 - P0) / np.linalg.norm(P0)),
+                             "max_node_displacement": float(np.abs(x1 - f.nodes).max())}
+    out["setting"] = ("two leapfrogging elliptical rings, quintic curves, Q = 3, local segments subdivided "
+                      "(f = 0.1), beta = 3.5, alpha = 7/L, float64, RK4 at the Kelvin-wave step")
+    out["paper"] = "energy and impulse variations within 1e-6 (Sec. 5.2)"
+    return out
+
+
 def spread_zfft_bytes(p, ng, K, NQ, real_bytes):
     """Algorithmic bytes of one fused spread + z-transform launch: read every
     spread record once (32 B float / 64 B double) and write the retained
@@ -556,6 +610,7 @@ def run_ours(args, rank, world, dist):
         if not args.no_large_form and args.rk4_steps > 0:
             extras["rk4"] = run_rk4(B, dev, stream, spec, f, args.rk4_steps)
             torch.cuda.empty_cache()
+            extras["leapfrog"] = run_leapfrog(B, dev)
         if not args.no_secondary and args.workload != "tangle1e5":
             s2, f2 = workload("tangle1e5")
             n2 = torch.from_numpy(f2.nodes).to(dev)

@@ -198,13 +198,15 @@ int bs_compute_host(bs_ctx* ctx, const double* nodes, double* vel, double* psi);
  * the same evaluation.  The long-range part is the float64 Fourier
  * reduction (1/2) sum_{k != 0} e^{-k^2/4 alpha^2} |omega_k|^2 / k^2 over the
  * resolved modes; the rest (psi_local + psi^(n) - psi^(f)_self at the nodes,
- * dotted with the tau-derivative of the curve) is interpolated by the same
- * periodic cubic spline and integrated exactly along each filament.
+ * dotted with the tau-derivative of the curve) is interpolated by a periodic
+ * spline of the curve's order (cubic or quintic) on the same knots and
+ * integrated exactly along each filament.
  *   nodes  (device) N x 3
  *   vel    (device) N x 3 output, or NULL
  *   psi    (device) N x 3 output, or NULL
  *   energy (host)   scalar output
- * Needs BS_WANT_PSI; synchronises the stream.  Filaments up to 5120 nodes.
+ * Needs BS_WANT_PSI; synchronises the stream.  Cubic curves: filaments up
+ * to 5120 nodes.
  */
 int bs_compute_energy(bs_ctx* ctx, const double* nodes, double* vel, double* psi, double* energy);
 

@@ -509,7 +509,8 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.Mm, sizeof(T) * 3 * N));
     if (c->p.spline_order == 6) {
         TRY(dalloc(c, L, &w.Dd, sizeof(T) * 3 * N));
-        TRY(dalloc(c, L, (void**)&w.qtmp, sizeof(double) * 18 * N));
+        // the quintic solver's scratch (18 per node), and f_j of the energy line integral
+        TRY(dalloc(c, L, (void**)&w.qtmp, sizeof(double) * 19 * N));
     } else {
         w.Dd = nullptr;
         w.qtmp = nullptr;
@@ -1184,8 +1185,7 @@ int bs_compute_energy(bs_ctx* c, const double* nodes, double* vel, double* psi, 
     if (c->N == 0) return BS_OK;
     if (!nodes) return fail(BS_ERR_ARG, "null nodes");
     if (!(c->p.flags & BS_WANT_PSI)) return fail(BS_ERR_ARG, "the energy needs a context created with BS_WANT_PSI");
-    if (c->p.spline_order != 4) return fail(BS_ERR_ARG, "the energy line integral is implemented for cubic splines");
-    if (5 * (size_t)c->w.nmax_fil * sizeof(double) > 200 * 1024)
+    if (c->p.spline_order == 4 && 5 * (size_t)c->w.nmax_fil * sizeof(double) > 200 * 1024)
         return fail(BS_ERR_ARG, "filament too long for the energy integral (%d nodes > 5120)", c->w.nmax_fil);
     double* v = vel ? vel : c->w.vel_out;
     double* ps = psi ? psi : c->w.psi_out;

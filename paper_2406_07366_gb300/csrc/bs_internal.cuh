@@ -289,7 +289,7 @@ struct Work {
     void* ds = nullptr;     // N x 3 chord vectors
     void* Mm = nullptr;     // N x 3 moments (second derivatives at the nodes)
     void* Dd = nullptr;     // N x 3 first derivatives at the nodes (quintic splines only)
-    double* qtmp = nullptr; // 18 N scratch of the quintic spline solve
+    double* qtmp = nullptr; // 19 N scratch of the quintic spline solve (and of the quintic energy integral)
     void* cpr = nullptr;    // N Thomas scratch
     void* zz = nullptr;     // N Sherman-Morrison vector
     void* Tper = nullptr;   // nfil

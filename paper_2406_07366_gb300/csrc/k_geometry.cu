@@ -680,11 +680,85 @@ __global__ void k_energy_line(const int64_t* __restrict__ off, const double* __r
     }
 }
 
+// The periodic quintic spline solve of the curve fit below (k_spline_quintic).
+__device__ void q_solve(int n, double* __restrict__ t, double xlast[6]);
+__device__ __forceinline__ void q_node(const double* __restrict__ t, int m, const double xlast[6], int j, int c,
+                                       double& D, double& M);
+
+// The same line integral on a quintic curve (order 6): f_j = psi_j .
+// sdot(tau_j), with sdot = D_j + n_l L / T the first derivative of the
+// quintic at the node, is interpolated by the periodic quintic spline with
+// the same knots (q_solve on the increments f_{j+1} - f_j, no drift) and
+// integrated exactly, segment by segment (the Hermite quintic's integral):
+//   int f dtau = h (f_j + f_{j+1}) / 2 + h^2 (F'_j - F'_{j+1}) / 10 + h^3 (F''_j + F''_{j+1}) / 120.
+// One thread per filament; ftmp holds 19 float64 per node (the solver's 18
+// and f_j).
+template <typename T>
+__global__ void k_energy_line_quintic(const int64_t* __restrict__ off, const double* __restrict__ shift, int nfil,
+                                      const T* __restrict__ hseg, const T* __restrict__ Dd,
+                                      const T* __restrict__ Tper, const double* __restrict__ pls,
+                                      const double* __restrict__ psr, double* __restrict__ ftmp,
+                                      double* __restrict__ acc, double* __restrict__ per_fil)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfil) return;
+    const int64_t o = off[f];
+    const int n = (int)(off[f + 1] - o);
+    double* t = ftmp + 19 * (size_t)o;
+    double* fv = t + 18 * (size_t)n;  // f_j after the solver's scratch
+    const double Tp = (double)Tper[f];
+    const double dr[3] = { shift[3 * f] / Tp, shift[3 * f + 1] / Tp, shift[3 * f + 2] / Tp };
+    for (int j = 0; j < n; ++j) {
+        double fj = 0.0;
+        for (int c = 0; c < 3; ++c)
+            fj += (pls[3 * (o + j) + c] + psr[3 * (o + j) + c]) * ((double)Dd[3 * (o + j) + c] + dr[c]);
+        fv[j] = fj;
+    }
+    for (int j = 0; j < n; ++j) {
+        t[18 * j] = (double)hseg[o + j];
+        t[18 * j + 1] = fv[j + 1 < n ? j + 1 : 0] - fv[j];
+        t[18 * j + 2] = 0.0;
+        t[18 * j + 3] = 0.0;
+    }
+    double xlast[6];
+    q_solve(n, t, xlast);
+    const int m = n - 1;
+    double part = 0.0;
+    double Dj, Mj;
+    q_node(t, m, xlast, 0, 0, Dj, Mj);
+    const double D0 = Dj, M0 = Mj;
+    for (int j = 0; j < n; ++j) {
+        const int jn = j + 1 < n ? j + 1 : 0;
+        double Dn, Mn;
+        if (jn == 0) {
+            Dn = D0;
+            Mn = M0;
+        } else {
+            q_node(t, m, xlast, jn, 0, Dn, Mn);
+        }
+        const double h = t[18 * j];
+        part += 0.5 * h * (fv[j] + fv[jn]) + h * h * (Dj - Dn) / 10.0 + h * h * h * (Mj + Mn) / 120.0;
+        Dj = Dn;
+        Mj = Mn;
+    }
+    if (per_fil)
+        per_fil[f] = part;  // deterministic: summed in filament order on the host
+    else
+        atomicAdd(acc, part);
+}
+
 template <typename T>
 cudaError_t launch_energy_line(const double* nodes, const Work& w, int nfil, int nmax, cudaStream_t s, bool det)
 {
     (void)nodes;
     if (nfil <= 0) return cudaSuccess;
+    if (w.Dd) {  // quintic curves
+        const int tb = 64;
+        k_energy_line_quintic<T><<<(nfil + tb - 1) / tb, tb, 0, s>>>(w.off, w.shift, nfil, (const T*)w.hseg,
+                                                                     (const T*)w.Dd, (const T*)w.Tper, w.pls, w.psr,
+                                                                     w.qtmp, w.energy_acc + 1, det ? w.lpart : nullptr);
+        return cudaGetLastError();
+    }
     const size_t sm = 5 * (size_t)nmax * sizeof(double);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_energy_line<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -774,39 +848,12 @@ __device__ __forceinline__ void mul25(const double a[4], const double b[10], dou
     }
 }
 
-template <typename T>
-__global__ void k_spline_quintic(const double* __restrict__ nodes, const int64_t* __restrict__ off,
-                                 const double* __restrict__ shift, int nfil, T* __restrict__ hseg, T* __restrict__ dp,
-                                 T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ Dd, T* __restrict__ Tper,
-                                 double* __restrict__ tmp)
+// Solves the cyclic block system above for the node lengths t[18 j] and
+// the three increments t[18 j + 1 + c] of every node j of one filament (18
+// float64 per node of scratch; n >= 3).  On return (D_j, M_j) of component c
+// are q_node(t, m, xlast, j, c, D, M), m = n - 1.
+__device__ void q_solve(int n, double* __restrict__ t, double xlast[6])
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfil) return;
-    const int64_t o = off[f];
-    const int n = (int)(off[f + 1] - o);
-    const double sh[3] = { shift[3 * f], shift[3 * f + 1], shift[3 * f + 2] };
-    // per node in tmp: h, dp[3] (float64), then the eliminated block (4) and right sides (10)
-    double* t = tmp + 18 * (size_t)o;
-    double Tsum = 0.0;
-    for (int j = 0; j < n; ++j) {
-        const double* a = nodes + 3 * (o + j);
-        const double* b = nodes + 3 * (j + 1 < n ? o + j + 1 : o);
-        double d[3];
-        for (int c = 0; c < 3; ++c) d[c] = b[c] + (j + 1 < n ? 0.0 : sh[c]) - a[c];
-        const double h = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        Tsum += h;
-        t[18 * j] = h;
-        for (int c = 0; c < 3; ++c) t[18 * j + 1 + c] = d[c];
-        hseg[o + j] = (T)h;
-        for (int c = 0; c < 3; ++c) ds[3 * (o + j) + c] = (T)d[c];
-    }
-    Tper[f] = (T)Tsum;
-    const double invT = 1.0 / Tsum;
-    for (int j = 0; j < n; ++j)
-        for (int c = 0; c < 3; ++c) {
-            t[18 * j + 1 + c] -= sh[c] * t[18 * j] * invT;  // periodic increments
-            dp[3 * (o + j) + c] = (T)t[18 * j + 1 + c];
-        }
     const int m = n - 1;
     double L[4], B[4], U[4], Wm[4], iv[4], Bp[10], tmp10[10];
     // forward elimination over j = 0..m-1
@@ -866,42 +913,85 @@ __global__ void k_spline_quintic(const double* __restrict__ nodes, const int64_t
         for (int k = 0; k < 10; ++k) t[18 * j + 8 + k] = tmp10[k];
     }
     // last equation: (L_{n-1} Z_{n-2} + B_{n-1} + U_{n-1} Z_0) X_{n-1} = R_{n-1} - L_{n-1} Y_{n-2} - U_{n-1} Y_0
-    {
-        const double a = t[18 * (m - 1)], h = t[18 * m];
-        q_blocks(a, h, L, B, U);
-        const double* x0 = t + 8;                 // X_0 (Y | Z)
-        const double* xl = t + 18 * (m - 1) + 8;  // X_{n-2}
-        double Sm[4];
-        // Z columns are entries 3, 4 (row 0) and 8, 9 (row 1)
-        Sm[0] = B[0] + L[0] * xl[3] + L[1] * xl[8] + U[0] * x0[3] + U[1] * x0[8];
-        Sm[1] = B[1] + L[0] * xl[4] + L[1] * xl[9] + U[0] * x0[4] + U[1] * x0[9];
-        Sm[2] = B[2] + L[2] * xl[3] + L[3] * xl[8] + U[2] * x0[3] + U[3] * x0[8];
-        Sm[3] = B[3] + L[2] * xl[4] + L[3] * xl[9] + U[2] * x0[4] + U[3] * x0[9];
-        inv2(Sm, iv);
-        double xlast[6];
-        for (int c = 0; c < 3; ++c) {
-            const double dj = t[18 * m + 1 + c], dm = t[18 * (m - 1) + 1 + c];
-            const double r0 = 60.0 * dj / (h * h * h) - 60.0 * dm / (a * a * a) - (L[0] * xl[c] + L[1] * xl[5 + c]) -
-                              (U[0] * x0[c] + U[1] * x0[5 + c]);
-            const double r1 = -360.0 * dj / (h * h * h * h) - 360.0 * dm / (a * a * a * a) -
-                              (L[2] * xl[c] + L[3] * xl[5 + c]) - (U[2] * x0[c] + U[3] * x0[5 + c]);
-            xlast[c] = iv[0] * r0 + iv[1] * r1;
-            xlast[3 + c] = iv[2] * r0 + iv[3] * r1;
-        }
-        for (int c = 0; c < 3; ++c) {
-            Dd[3 * (o + m) + c] = (T)xlast[c];
-            Mm[3 * (o + m) + c] = (T)xlast[3 + c];
-        }
-        for (int j = 0; j < m; ++j) {
-            const double* x = t + 18 * j + 8;
-            for (int c = 0; c < 3; ++c) {
-                const double Dj = x[c] + x[3] * xlast[c] + x[4] * xlast[3 + c];
-                const double Mj = x[5 + c] + x[8] * xlast[c] + x[9] * xlast[3 + c];
-                Dd[3 * (o + j) + c] = (T)Dj;
-                Mm[3 * (o + j) + c] = (T)Mj;
-            }
-        }
+    const double a = t[18 * (m - 1)], h = t[18 * m];
+    q_blocks(a, h, L, B, U);
+    const double* x0 = t + 8;                 // X_0 (Y | Z)
+    const double* xl = t + 18 * (m - 1) + 8;  // X_{n-2}
+    double Sm[4];
+    // Z columns are entries 3, 4 (row 0) and 8, 9 (row 1)
+    Sm[0] = B[0] + L[0] * xl[3] + L[1] * xl[8] + U[0] * x0[3] + U[1] * x0[8];
+    Sm[1] = B[1] + L[0] * xl[4] + L[1] * xl[9] + U[0] * x0[4] + U[1] * x0[9];
+    Sm[2] = B[2] + L[2] * xl[3] + L[3] * xl[8] + U[2] * x0[3] + U[3] * x0[8];
+    Sm[3] = B[3] + L[2] * xl[4] + L[3] * xl[9] + U[2] * x0[4] + U[3] * x0[9];
+    inv2(Sm, iv);
+    for (int c = 0; c < 3; ++c) {
+        const double dj = t[18 * m + 1 + c], dm = t[18 * (m - 1) + 1 + c];
+        const double r0 = 60.0 * dj / (h * h * h) - 60.0 * dm / (a * a * a) - (L[0] * xl[c] + L[1] * xl[5 + c]) -
+                          (U[0] * x0[c] + U[1] * x0[5 + c]);
+        const double r1 = -360.0 * dj / (h * h * h * h) - 360.0 * dm / (a * a * a * a) -
+                          (L[2] * xl[c] + L[3] * xl[5 + c]) - (U[2] * x0[c] + U[3] * x0[5 + c]);
+        xlast[c] = iv[0] * r0 + iv[1] * r1;
+        xlast[3 + c] = iv[2] * r0 + iv[3] * r1;
     }
+}
+
+// First and second derivative of component c at node j after q_solve.
+__device__ __forceinline__ void q_node(const double* __restrict__ t, int m, const double xlast[6], int j, int c,
+                                       double& D, double& M)
+{
+    if (j == m) {
+        D = xlast[c];
+        M = xlast[3 + c];
+        return;
+    }
+    const double* x = t + 18 * j + 8;
+    D = x[c] + x[3] * xlast[c] + x[4] * xlast[3 + c];
+    M = x[5 + c] + x[8] * xlast[c] + x[9] * xlast[3 + c];
+}
+
+template <typename T>
+__global__ void k_spline_quintic(const double* __restrict__ nodes, const int64_t* __restrict__ off,
+                                 const double* __restrict__ shift, int nfil, T* __restrict__ hseg, T* __restrict__ dp,
+                                 T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ Dd, T* __restrict__ Tper,
+                                 double* __restrict__ tmp)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfil) return;
+    const int64_t o = off[f];
+    const int n = (int)(off[f + 1] - o);
+    const double sh[3] = { shift[3 * f], shift[3 * f + 1], shift[3 * f + 2] };
+    // per node in tmp: h, dp[3] (float64), then the eliminated block (4) and right sides (10)
+    double* t = tmp + 18 * (size_t)o;
+    double Tsum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double* a = nodes + 3 * (o + j);
+        const double* b = nodes + 3 * (j + 1 < n ? o + j + 1 : o);
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = b[c] + (j + 1 < n ? 0.0 : sh[c]) - a[c];
+        const double h = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        Tsum += h;
+        t[18 * j] = h;
+        for (int c = 0; c < 3; ++c) t[18 * j + 1 + c] = d[c];
+        hseg[o + j] = (T)h;
+        for (int c = 0; c < 3; ++c) ds[3 * (o + j) + c] = (T)d[c];
+    }
+    Tper[f] = (T)Tsum;
+    const double invT = 1.0 / Tsum;
+    for (int j = 0; j < n; ++j)
+        for (int c = 0; c < 3; ++c) {
+            t[18 * j + 1 + c] -= sh[c] * t[18 * j] * invT;  // periodic increments
+            dp[3 * (o + j) + c] = (T)t[18 * j + 1 + c];
+        }
+    double xlast[6];
+    q_solve(n, t, xlast);
+    const int m = n - 1;
+    for (int j = 0; j < n; ++j)
+        for (int c = 0; c < 3; ++c) {
+            double D, M;
+            q_node(t, m, xlast, j, c, D, M);
+            Dd[3 * (o + j) + c] = (T)D;
+            Mm[3 * (o + j) + c] = (T)M;
+        }
 }
 
 template <typename T>

@@ -71,25 +71,79 @@ def test_quintic_total_is_implementation_parity():
     assert _rms(psi, pr) < 1e-10
 
 
-def test_quintic_trefoil_mixed_and_energy_refusal():
+def test_quintic_trefoil_mixed_and_energy():
     """The mixed form with quintic curves stays in the float32 budget on the
-    trefoil; the energy (cubic line integral) refuses quintic curves."""
+    trefoil.  The energy of a quintic curve (Eq. kinetic_energy_streamfunction;
+    the line integral interpolates psi . sdot by the periodic quintic on the
+    curve's knots) equals the oracle's at the same split: to 1e-10 at w = 16,
+    sigma = 2, to 1e-6 at w = 8 and to 1e-5 in the mixed form."""
     B = _B()
     f = W.trefoil(N=96)
     p = _params(B, f, M=48, w=8, precision=B.BS_MIXED)
     bs = B.BiotSavart(p, f.offsets, f.closing)
-    v = bs.velocity(torch.from_numpy(f.nodes).cuda()).cpu().numpy()
+    nodes = torch.from_numpy(f.nodes).cuda()
+    v = bs.velocity(nodes).cpu().numpy()
     bs.close()
     g = oracle.geometry(f.nodes, f.offsets, f.closing, f.L, 6, 3)
     vr, _ = oracle.velocity_converged(g, f.L, KAPPA, A_CORE, DELTA)
     assert _rms(v, vr) < 1e-5
-    # energy is implemented for cubic curves only
-    pe = _params(B, f, M=48, w=8, precision=B.BS_FP64, flags=B.BS_WANT_PSI)
-    be = B.BiotSavart(pe, f.offsets, f.closing)
-    with pytest.raises(B.BSError) as e:
-        be.energy(torch.from_numpy(f.nodes).cuda())
-    assert e.value.code == B.BS_ERR_ARG
-    be.close()
+    for prec, w, sigma, tol in ((B.BS_FP64, 16, 2.0, 1e-10), (B.BS_FP64, 8, 1.5, 1e-6), (B.BS_MIXED, 8, 1.5, 1e-5)):
+        pe = _params(B, f, M=48, w=w, sigma=sigma, precision=prec, flags=B.BS_WANT_PSI)
+        be = B.BiotSavart(pe, f.offsets, f.closing)
+        E = be.energy(nodes)
+        be.close()
+        Em = oracle.energy(g, f.L, KAPPA, A_CORE, DELTA, pe.alpha, pe.rc, (pe.M[0] - 1) // 2, order=6)
+        assert abs(E - Em) < tol * abs(Em), (prec, w, E, Em)
+
+
+def _spline_impulse(bs, nodes, L, Q):
+    """p = (kappa/2) oint s x ds (Sec. 5.2) on the spline curve: the sum over
+    the quadrature points of s_q x q_q (q = w_i dtau s'), every point taken
+    at the image nearest its node (the points come back wrapped into the box)."""
+    qX, qq = bs.quadrature(nodes)
+    x = nodes.cpu().numpy()
+    qX, qq = qX.cpu().numpy(), qq.cpu().numpy()
+    xn = np.repeat(x, Q, axis=0)
+    qX = qX - L[None, :] * np.round((qX - xn) / L[None, :])
+    return 0.5 * KAPPA * np.cross(qX, qq).sum(axis=0)
+
+
+def test_leapfrogging_rings_conserve_energy_and_impulse():
+    """Sec. 5.2's conservation run in the paper's production setting: two
+    leapfrogging elliptical rings of 32 nodes, quintic curves, Q = 3,
+    subdivided local segments (f = 0.1), beta = 3.5 with alpha = 7/L, float64,
+    RK4 with the Kelvin-wave step.  The energy and impulse are invariants of
+    the motion; over 400 steps they move by a few 1e-6 of their size (the paper
+    reports variations within 1e-6 over its run), while the rings travel."""
+    B = _B()
+    f = W.leapfrog_ellipses(N_l=32)
+    L = f.L[0]
+    alpha = 7.0 / L
+    K = int(math.ceil(3.5 * alpha * L / math.pi))
+    p = _params(B, f, M=2 * K + 1, w=8, precision=B.BS_FP64, alpha=alpha, flags=B.BS_WANT_PSI, local_frac=0.1)
+    nodes = torch.from_numpy(f.nodes.copy()).cuda()
+    dmin = min(np.linalg.norm(np.roll(f.nodes[f.offsets[l]:f.offsets[l + 1]], -1, axis=0)
+                              - f.nodes[f.offsets[l]:f.offsets[l + 1]], axis=1).min() for l in range(f.nfil))
+    dt = B.kelvin_wave_period(dmin, KAPPA, A_CORE, DELTA)
+    stream = torch.cuda.Stream()
+    bs = B.BiotSavart(p, f.offsets, f.closing, stream=stream)
+    with torch.cuda.stream(stream):
+        E0 = bs.energy(nodes)
+        P0 = _spline_impulse(bs, nodes, f.L, 3)
+        Es = [E0]
+        for _ in range(4):
+            bs.rk4_capture(nodes, dt)
+            bs.rk4_launch(100)
+            bs.status()
+            Es.append(bs.energy(nodes))
+        x1 = nodes.cpu().numpy()
+        P1 = _spline_impulse(bs, nodes, f.L, 3)
+    bs.close()
+    dE = max(abs(e - E0) for e in Es) / abs(E0)
+    dP = float(np.linalg.norm(P1 - P0) / np.linalg.norm(P0))
+    assert np.abs(x1 - f.nodes).max() > 0.05 * L / 32, "the rings must move"
+    assert dE < 1e-5, dE
+    assert dP < 1e-5, dP
 
 
 @pytest.mark.parametrize("order", [4, 6])
