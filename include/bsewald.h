@@ -104,6 +104,14 @@ enum {
  *                 quad_Q-point Gauss-Legendre on the pieces [f, 2f], [2f, 4f],
  *                 ..., [2^m f, 1] of the segment (f = local_frac, measured from
  *                 the node).  The paper uses about 0.1.
+ *   block_x, block_y   z-column block of the spread, the fused inverse-z
+ *                 interpolation and the x pass: block_x x block_y grid
+ *                 columns per CTA, each in {1, 2, 4}, block_y even unless
+ *                 the interpolation may run unfused; 0, 0 selects the
+ *                 library default (blocks sized for about 50-85 KB of shared
+ *                 memory).  bs_autotune_tiles picks them by timing.
+ *   block_threads threads per CTA of those kernels: 256, or 512 (float32
+ *                 only); 0 selects the default
  */
 typedef struct {
     double L[3];
@@ -121,6 +129,9 @@ typedef struct {
     int flags;
     int cell_div;
     double local_frac;
+    int block_x;
+    int block_y;
+    int block_threads;
 } bs_params;
 
 typedef struct bs_ctx bs_ctx;
@@ -343,6 +354,30 @@ void bs_batch_destroy(bs_batch* b);
  */
 int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t* offsets, const int32_t* closing,
                       const double* nodes, int ncand, const double* cbeta, int reps, bs_params* best, float* ms_out);
+
+/*
+ * bs_autotune_tiles -- pick the tile shapes and bin sizes of a context by
+ * timing on this GPU (an implementation choice: the paper's CPU code has no
+ * counterpart): for each candidate i, the z-column block
+ * cand[4 i] x cand[4 i + 1] with cand[4 i + 2] threads per CTA (see
+ * bs_params.block_x / block_y / block_threads; 0, 0, 0 is the library
+ * default) and cand[4 i + 3] cells per cut-off of the short-range cell lists
+ * (bs_params.cell_div; 0 the default).  Every other field comes from *base;
+ * the method and its accuracy are unchanged (the results differ only by
+ * rounding order).  Each candidate context evaluates the filaments (as
+ * bs_autotune_alpha: offsets, closing, nodes on the device) once to warm up,
+ * then reps times, timed with CUDA events; candidates the library cannot take
+ * (too large for shared memory, odd block_y with the fused interpolation)
+ * are skipped.
+ *   best   (host) the fastest candidate's parameters
+ *   ms_out (host, ncand, or NULL) mean milliseconds per evaluation, -1 for
+ *          skipped candidates
+ * Allocates and frees one context at a time (and an N x 3 scratch); not
+ * inside a stream capture.  Errors: BS_ERR_ARG (also when no candidate is
+ * admissible), the codes of bs_set_filaments / bs_compute, BS_ERR_CUDA.
+ */
+int bs_autotune_tiles(const bs_params* base, int nfil, const int64_t* offsets, const int32_t* closing,
+                      const double* nodes, int ncand, const int* cand, int reps, bs_params* best, float* ms_out);
 
 /* Synchronise the stream and return the device status word as a status
  * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY); clears it. */

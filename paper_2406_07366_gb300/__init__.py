@@ -38,7 +38,8 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
            "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
            "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
-           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity", "bs_fma_peak", "bs_erfc_f32"]
+           "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity", "bs_fma_peak", "bs_erfc_f32",
+           "bs_autotune_tiles"]
 
 
 class bs_params(ctypes.Structure):
@@ -46,13 +47,15 @@ class bs_params(ctypes.Structure):
                 ("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("rc", ctypes.c_double),
                 ("M", ctypes.c_int * 3), ("quad_Q", ctypes.c_int), ("spline_order", ctypes.c_int),
                 ("nufft_sigma", ctypes.c_double), ("nufft_w", ctypes.c_int), ("precision", ctypes.c_int),
-                ("flags", ctypes.c_int), ("cell_div", ctypes.c_int), ("local_frac", ctypes.c_double)]
+                ("flags", ctypes.c_int), ("cell_div", ctypes.c_int), ("local_frac", ctypes.c_double),
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("block_threads", ctypes.c_int)]
 
     def as_dict(self):
         return dict(L=list(self.L), kappa=self.kappa, a=self.a, delta=self.delta, alpha=self.alpha, rc=self.rc,
                     M=list(self.M), quad_Q=self.quad_Q, spline_order=self.spline_order,
                     nufft_sigma=self.nufft_sigma, nufft_w=self.nufft_w, precision=self.precision,
-                    flags=self.flags, cell_div=self.cell_div, local_frac=self.local_frac)
+                    flags=self.flags, cell_div=self.cell_div, local_frac=self.local_frac, block_x=self.block_x,
+                    block_y=self.block_y, block_threads=self.block_threads)
 
 
 class BSError(RuntimeError):
@@ -104,6 +107,8 @@ def _load():
                                ctypes.c_int),
         "bs_autotune_alpha": ([P(bs_params), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32), vp, ctypes.c_int,
                                P(ctypes.c_double), ctypes.c_int, P(bs_params), P(ctypes.c_float)], ctypes.c_int),
+        "bs_autotune_tiles": ([P(bs_params), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32), vp, ctypes.c_int,
+                               P(ctypes.c_int), ctypes.c_int, P(bs_params), P(ctypes.c_float)], ctypes.c_int),
         "bs_short_range_static": ([P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
@@ -267,6 +272,22 @@ def bs_autotune_alpha(base, offsets, closing, nodes, cbeta, reps=3):
     _check(lib().bs_autotune_alpha(ctypes.byref(base), nfil, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   _ptr(nodes), cb.size, cb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  int(reps), ctypes.byref(best), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return best, [float(x) for x in ms]
+
+
+def bs_autotune_tiles(base, offsets, closing, nodes, cand, reps=3):
+    """Time each candidate (block_x, block_y, block_threads, cell_div) on these
+    filaments; returns (best params, ms list, -1 for skipped candidates)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nfil = off.size - 1
+    cl = None if closing is None else np.ascontiguousarray(closing, dtype=np.int32).reshape(nfil, 3)
+    cd = np.ascontiguousarray(np.asarray(cand, dtype=np.int32).reshape(-1, 4))
+    ms = np.zeros(cd.shape[0], dtype=np.float32)
+    best = bs_params()
+    _check(lib().bs_autotune_tiles(ctypes.byref(base), nfil, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  _ptr(nodes), cd.shape[0], cd.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                   int(reps), ctypes.byref(best), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     return best, [float(x) for x in ms]
 

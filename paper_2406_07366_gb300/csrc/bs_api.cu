@@ -292,6 +292,22 @@ int derive(const bs_params* p, Derived* d)
     }
     d->ty = std::min(4, txy);
     d->tx = txy / d->ty;
+    if (p->block_x > 0 || p->block_y > 0 || p->block_threads > 0) {
+        // a chosen block (bs_autotune_tiles): shapes in {1, 2, 4}^2, 256 or
+        // 512 threads (512 in float32 only), within the shared memory of a CTA
+        const int bx = p->block_x > 0 ? p->block_x : d->tx, by = p->block_y > 0 ? p->block_y : d->ty;
+        const int bt = p->block_threads > 0 ? p->block_threads : d->zthreads;
+        auto ok = [](int v) { return v == 1 || v == 2 || v == 4; };
+        if (!ok(bx) || !ok(by) || bx * by < 2) return fail(BS_ERR_ARG, "block_x, block_y must be in {1, 2, 4}");
+        if (bt != 256 && !(bt == 512 && rb == 4)) return fail(BS_ERR_ARG, "block_threads must be 256 (or 512 in float32)");
+        const size_t lines = (size_t)(3 * bx * by / 2) * (size_t)(d->ng[2] + 33) * cb;
+        if (lines + 128 * (size_t)(16 + 24 * rb + 16 * (size_t)rb * p->nufft_w / 4) > 220 * 1024)
+            return fail(BS_ERR_ARG, "block %d x %d does not fit in shared memory at %d points per line", bx, by,
+                        d->ng[2]);
+        d->tx = bx;
+        d->ty = by;
+        d->zthreads = bt;
+    }
     d->nbx = d->ng[0] / d->tx;
     d->nby = d->ng[1] / d->ty;
     d->ncols = d->nbx * d->nby;
@@ -1002,6 +1018,7 @@ int bs_params_from_beta(double beta, const double L[3], int M, long long N, bs_p
     out->flags = 0;
     out->cell_div = 0;
     out->local_frac = 0.0;
+    out->block_x = out->block_y = out->block_threads = 0;
     return BS_OK;
 }
 
@@ -1692,5 +1709,74 @@ extern "C" int bs_autotune_alpha(const bs_params* base, int nfil, const int64_t*
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (rc == BS_OK && nbest < 0) return fail(BS_ERR_ARG, "no autotune candidate is admissible");
+    return rc;
+}
+
+extern "C" int bs_autotune_tiles(const bs_params* base, int nfil, const int64_t* offsets, const int32_t* closing,
+                                 const double* nodes, int ncand, const int* cand, int reps, bs_params* best,
+                                 float* ms_out)
+{
+    if (!base || !cand || !best || !nodes || ncand <= 0 || reps <= 0 || nfil <= 0 || !offsets)
+        return fail(BS_ERR_ARG, "bad autotune arguments");
+    const long long N = offsets[nfil];
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    double* vel = nullptr;
+    if (ce == cudaSuccess) ce = cudaMalloc(&vel, sizeof(double) * 3 * (size_t)std::max<long long>(N, 1));
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamDestroy(s);
+        return fail(BS_ERR_CUDA, "autotune set-up failed: %s", cudaGetErrorString(ce));
+    }
+    int rc = BS_OK, nbest = -1;
+    float tbest = 0.0f;
+    for (int i = 0; i < ncand && rc == BS_OK; ++i) {
+        if (ms_out) ms_out[i] = -1.0f;
+        bs_params q = *base;
+        q.block_x = cand[4 * i];
+        q.block_y = cand[4 * i + 1];
+        q.block_threads = cand[4 * i + 2];
+        q.cell_div = cand[4 * i + 3];
+        q.flags &= ~BS_TIMING;
+        bs_ctx* c = nullptr;
+        if ((rc = bs_create(&c, &q, s)) != BS_OK) {
+            if (rc == BS_ERR_ARG) {  // a block the library cannot take: skipped
+                rc = BS_OK;
+                continue;
+            }
+            break;
+        }
+        rc = bs_set_filaments(c, nfil, offsets, closing);
+        float t = 0.0f;
+        for (int r = 0; r < reps + 1 && rc == BS_OK; ++r) {  // the first call warms up
+            if (r == 1) cudaEventRecord(e0, s);
+            rc = bs_compute(c, nodes, vel, nullptr);
+        }
+        if (rc == BS_OK) {
+            cudaEventRecord(e1, s);
+            ce = cudaEventSynchronize(e1);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            if (ce != cudaSuccess) rc = fail(BS_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
+        }
+        if (rc == BS_OK) rc = bs_status(c);
+        bs_destroy(c);
+        if (rc != BS_OK) break;
+        t /= (float)reps;
+        if (ms_out) ms_out[i] = t;
+        if (nbest < 0 || t < tbest) {
+            nbest = i;
+            tbest = t;
+            *best = q;
+        }
+    }
+    cudaFree(vel);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (rc == BS_OK && nbest < 0) return fail(BS_ERR_ARG, "no tile candidate is admissible");
     return rc;
 }

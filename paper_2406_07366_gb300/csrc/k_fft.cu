@@ -780,6 +780,15 @@ __device__ __forceinline__ void spz_unpack(const SpZP& P, const typename Cx<T>::
     }
 }
 
+// Bytes of a block's complex z-lines in shared memory, rounded up to 16 so
+// that the record buffer after them takes 16-byte copies (an odd count of
+// float32 lines at an odd stride would leave it 8-byte aligned).
+template <typename T>
+__host__ __device__ __forceinline__ size_t zlines_bytes(int ncl, int cls)
+{
+    return ((size_t)ncl * cls * 2 * sizeof(T) + 15) & ~(size_t)15;
+}
+
 // ---------------------------------------------------------------------------
 // A: spread + z real FFT.
 // The 3 Tx Ty real z-lines are accumulated directly as complex lines (real
@@ -805,7 +814,7 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, c
     const int CS = P.cls;
     C* cb = reinterpret_cast<C*>(smem_raw);
     T* accf = reinterpret_cast<T*>(cb);  // real line rl, position z at float ((rl>>1) CS + z) 2 + (rl&1)
-    SpRec<T, W>* srec = reinterpret_cast<SpRec<T, W>*>(cb + (size_t)ncl * CS);
+    SpRec<T, W>* srec = reinterpret_cast<SpRec<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int by = fdiv(blockIdx.x, P.d_nbx);
     const int bx = blockIdx.x - by * P.nbx;
@@ -1279,7 +1288,7 @@ __global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_
     const int CS = P.cls;
     C* cb = reinterpret_cast<C*>(smem_raw);
     const T* accf = reinterpret_cast<const T*>(cb);
-    NdW<T, W>* srec = reinterpret_cast<NdW<T, W>*>(cb + (size_t)ncl * CS);
+    NdW<T, W>* srec = reinterpret_cast<NdW<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));
     const int tid = threadIdx.x;
     const int by = fdiv(blockIdx.x, P.d_nbx);
     const int bx = blockIdx.x - by * P.nbx;
@@ -1568,7 +1577,7 @@ size_t spread_zfft_smem(const SpZP& P)
 {
     using C = typename Cx<T>::t;
     const int ncl = 3 * P.tx * P.ty / 2;
-    return (size_t)ncl * P.cls * sizeof(C) + kSpzChunk * col_rec_bytes<T>(P.w);
+    return zlines_bytes<T>(ncl, P.cls) + kSpzChunk * col_rec_bytes<T>(P.w);
 }
 
 // Register-budget class of a plan: the largest radix it uses, rounded up to
@@ -1640,7 +1649,7 @@ struct ZiLaunch {
     cudaError_t run()
     {
         using C = typename Cx<T>::t;
-        const size_t sm = (size_t)(3 * P.tx * P.ty / 2) * P.cls * sizeof(C) + kSpzChunk * sizeof(NdW<T, W>);
+        const size_t sm = zlines_bytes<T>(3 * P.tx * P.ty / 2, P.cls) + kSpzChunk * sizeof(NdW<T, W>);
         cudaError_t e =
             cudaFuncSetAttribute(k_zfft_interp<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;

@@ -50,3 +50,37 @@ def test_autotune_rejects_bad_arguments():
     with pytest.raises(B.BSError) as e:
         B.bs_autotune_alpha(base, f.offsets, f.closing, nodes, [], reps=1)
     assert e.value.code == B.BS_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tile_autotune_changes_speed_not_results(prec):
+    """bs_autotune_tiles: z-column blocks, threads and cells per cut-off are
+    implementation choices; every admissible candidate gives the same
+    velocity up to rounding order, inadmissible ones are skipped (-1), and
+    the returned parameters are the fastest candidate's."""
+    import paper_2406_07366_gb300 as B
+    f = W.fourier_tangle(nfil=200, N_l=50, seed=72, amp=2 * math.pi / 64)
+    P = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
+    base = B.make_params(f.L, beta=3.5, M=96, Q=2, w=6 if prec == "mixed" else 8, precision=P)
+    nodes = torch.from_numpy(f.nodes).cuda()
+    cands = [(0, 0, 0, 0), (2, 4, 256, 2), (4, 4, 256, 3), (1, 2, 256, 1), (4, 4, 512, 2), (3, 4, 256, 2)]
+    best, ms = B.bs_autotune_tiles(base, f.offsets, f.closing, nodes, cands, reps=2)
+    assert ms[5] == -1.0  # block_x = 3 is not a tile shape
+    if prec == "fp64":
+        assert ms[4] == -1.0  # 512 threads are for float32 only
+    ok = [i for i, t in enumerate(ms) if t > 0]
+    i = min(ok, key=lambda k: ms[k])
+    assert (best.block_x, best.block_y, best.block_threads, best.cell_div) == cands[i]
+    outs = []
+    for k in ok:
+        q = B.make_params(f.L, beta=3.5, M=96, Q=2, w=base.nufft_w, precision=P)
+        q.block_x, q.block_y, q.block_threads = cands[k][:3]
+        q.cell_div = cands[k][3]
+        bs = B.BiotSavart(q, f.offsets, f.closing)
+        outs.append(bs.velocity(nodes).cpu().numpy())
+        bs.status()
+        bs.close()
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    scale = np.abs(outs[0]).max()
+    for o in outs[1:]:
+        assert np.abs(o - outs[0]).max() < tol * scale
