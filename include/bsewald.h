@@ -73,7 +73,11 @@ enum {
        same sum up to rounding order. */
     BS_SHORT_TILED = 16,    /* a CTA per r_c cube of nodes stages its neighbour sources in
                                shared memory (cells per cut-off up to 4) */
-    BS_SHORT_PER_NODE = 32  /* a warp per node walks its neighbour rows in global memory */
+    BS_SHORT_PER_NODE = 32, /* a warp per node walks its neighbour rows in global memory */
+    BS_BATCH_PER_MEMBER = 64, /* bs_batch_create only: issue this member's evaluation by
+                                 itself on the stream pool, whatever its size */
+    BS_BATCH_STAGED = 128     /* bs_batch_create only: this member joins the one-launch-per-
+                                 stage group whatever its size (when it can take that path) */
 };
 
 /*
@@ -305,15 +309,29 @@ int bs_rk4_launch(bs_ctx* ctx, int nsteps);
  * each with its own parameters and grid, in one call).
  *
  * bs_batch_create: nconf members, params[i] for member i (host array,
- * copied; BS_TIMING is ignored).  stream: cudaStream_t the batch runs on;
- * with a non-default stream bs_batch_compute captures the whole batch into
- * one CUDA graph on its first call (again whenever the node or velocity
- * pointer changes, or after bs_batch_set) and replays it, members running
- * concurrently on an internal pool of up to 8 streams; with the legacy
- * default stream (NULL) the members are issued directly.
+ * copied; BS_TIMING is ignored).  stream: cudaStream_t the batch runs on.
+ * The staged group: members that take the plain velocity path (no
+ * BS_WANT_PSI, BS_DETERMINISTIC, BS_FFT_CUFFT or BS_SHORT_TILED, cubic
+ * curves, no subdivided local segments) and have at most 8192 nodes (or carry
+ * BS_BATCH_STAGED; never with BS_BATCH_PER_MEMBER), with the precision,
+ * kernel width and z-column CTA size of the first of them.  Each stage of
+ * the group's evaluation is ONE launch for all its members: member m runs
+ * its own blocks of the launch with its own parameters, taken from a device
+ * table (about 30 launches whatever the member count).  Every other member's
+ * evaluation is issued by itself on an internal pool of up to 8 streams,
+ * concurrently with the group.  Passing both batch flags on one member is
+ * BS_ERR_ARG.  With a non-default
+ * stream bs_batch_compute captures the whole batch into one CUDA graph on
+ * its first call (again whenever the node or velocity pointer changes, or
+ * after bs_batch_set) and replays it; with the legacy default stream (NULL)
+ * the work is issued directly.  The stage tables are built (cudaMalloc and a
+ * synchronous copy) when the node or velocity pointer changes.
  * bs_batch_set: filaments of member i, as bs_set_filaments.
  * bs_batch_node_offsets: offsets[0..nconf] (host) of each member's nodes in
  * the concatenated node array.
+ * bs_batch_staged_members: staged[0..nconf-1] (host) = 1 for the members of
+ * the staged group, 0 for those issued by themselves (as of the last
+ * bs_batch_set).
  * bs_batch_compute: nodes (device, N_total x 3 float64, members back to
  * back in index order) -> vel (device, same layout).  Asynchronous.
  * bs_batch_status: synchronise and return the first member status that is
@@ -327,6 +345,7 @@ typedef struct bs_batch bs_batch;
 int bs_batch_create(bs_batch** out, int nconf, const bs_params* params, void* stream);
 int bs_batch_set(bs_batch* b, int i, int nfil, const int64_t* offsets, const int32_t* closing);
 int bs_batch_node_offsets(bs_batch* b, int64_t* offsets);
+int bs_batch_staged_members(bs_batch* b, int32_t* staged);
 int bs_batch_compute(bs_batch* b, const double* nodes, double* vel);
 int bs_batch_status(bs_batch* b);
 int bs_batch_member(bs_batch* b, int i, bs_ctx** member);

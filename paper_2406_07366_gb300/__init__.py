@@ -26,7 +26,7 @@ BS_ERR_NONFINITE, BS_ERR_OOM, BS_ERR_CUDA, BS_ERR_CUFFT, BS_ERR_TIMEOUT = 5, 6, 
 BS_ERR_STATE, BS_ERR_GEOMETRY = 10, 11
 BS_FP64, BS_MIXED = 0, 1
 BS_WANT_PSI, BS_TIMING, BS_FFT_CUFFT, BS_DETERMINISTIC = 1, 2, 4, 8
-BS_SHORT_TILED, BS_SHORT_PER_NODE = 16, 32
+BS_SHORT_TILED, BS_SHORT_PER_NODE, BS_BATCH_PER_MEMBER, BS_BATCH_STAGED = 16, 32, 64, 128
 
 STAGES = ["geometry", "sr_sort", "short_range", "lr_sort", "spread", "fft_fwd", "kspace", "fft_inv", "interp",
           "total"]
@@ -36,7 +36,7 @@ EXPORTS = ["bs_params_from_beta", "bs_error_estimate", "bs_nufft_setup", "bs_cre
            "bs_set_filaments", "bs_compute", "bs_compute_host", "bs_compute_parts", "bs_get_quadrature",
            "bs_status", "bs_stage_times", "bs_workspace_bytes", "bs_destroy", "bs_last_error",
            "bs_short_range_static", "bs_graph_capture", "bs_graph_launch", "bs_compute_energy",
-           "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_compute", "bs_batch_status",
+           "bs_batch_create", "bs_batch_set", "bs_batch_node_offsets", "bs_batch_staged_members", "bs_batch_compute", "bs_batch_status",
            "bs_batch_member", "bs_batch_destroy", "bs_rk4_step", "bs_rk4_capture", "bs_rk4_launch",
            "bs_autotune_alpha", "bs_energy_spectrum", "bs_coarse_velocity", "bs_fma_peak", "bs_erfc_f32",
            "bs_autotune_tiles"]
@@ -95,6 +95,7 @@ def _load():
         "bs_batch_create": ([P(vp), ctypes.c_int, P(bs_params), vp], ctypes.c_int),
         "bs_batch_set": ([vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32)], ctypes.c_int),
         "bs_batch_node_offsets": ([vp, P(ctypes.c_int64)], ctypes.c_int),
+        "bs_batch_staged_members": ([vp, P(ctypes.c_int32)], ctypes.c_int),
         "bs_batch_compute": ([vp, vp, vp], ctypes.c_int),
         "bs_batch_status": ([vp], ctypes.c_int),
         "bs_batch_member": ([vp, ctypes.c_int, P(vp)], ctypes.c_int),
@@ -322,6 +323,12 @@ def bs_batch_node_offsets(b, nconf):
     return off
 
 
+def bs_batch_staged_members(b, nconf):
+    st = np.zeros(nconf, dtype=np.int32)
+    _check(lib().bs_batch_staged_members(b, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return st.astype(bool)
+
+
 def bs_batch_compute(b, nodes, vel):
     _check(lib().bs_batch_compute(b, _ptr(nodes), _ptr(vel)))
 
@@ -473,6 +480,7 @@ class BiotSavartBatch:
         for i, f in enumerate(filaments):
             bs_batch_set(self.b, i, f.offsets, f.closing)
         self.offsets = bs_batch_node_offsets(self.b, len(self.params))
+        self.staged = bs_batch_staged_members(self.b, len(self.params))
         self.N = int(self.offsets[-1])
 
     def velocity(self, nodes, vel=None):

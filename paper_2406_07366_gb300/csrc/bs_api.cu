@@ -646,6 +646,131 @@ int fft_inv(bs_ctx* c, void* spec, cudaStream_t s)
     return BS_OK;
 }
 
+// Stage parameters of a context (shared by run() and the batched form).
+void fill_interp(const bs_ctx* c, bool want_psi, InterpP& I)
+{
+    const bs_params& p = c->p;
+    const Derived& d = c->d;
+    I.N = (int)c->N;
+    for (int k = 0; k < 3; ++k) {
+        I.ng[k] = d.ng[k];
+        I.hg[k] = d.hg[k];
+        I.L[k] = p.L[k];
+        I.iL[k] = 1.0 / p.L[k];
+        I.ihg[k] = 1.0 / d.hg[k];
+    }
+    I.w = p.nufft_w;
+    I.zeta = d.zeta;
+    I.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
+    I.want_psi = want_psi ? 1 : 0;
+}
+
+void fill_colp(const bs_ctx* c, ColP& CP)
+{
+    const Derived& d = c->d;
+    CP.tx = d.tx;
+    CP.ty = d.ty;
+    CP.nbx = d.nbx;
+    CP.nby = d.nby;
+    CP.ncols = d.ncols;
+    CP.w = c->p.nufft_w;
+    CP.zeta = d.zeta;
+    CP.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
+}
+
+void fill_short(const bs_ctx* c, bool want_psi, ShortP& S)
+{
+    const bs_params& p = c->p;
+    const Derived& d = c->d;
+    memset(&S, 0, sizeof S);
+    S.N = (int)c->N;
+    for (int k = 0; k < 3; ++k) {
+        S.nc[k] = d.nc[k];
+        S.hc[k] = d.hc[k];
+        S.L[k] = p.L[k];
+    }
+    S.m = d.m;
+    for (int k = 0; k < 3; ++k) S.nb[k] = (d.nc[k] + d.m - 1) / d.m;
+    S.kernel = (p.flags & BS_SHORT_TILED) ? 1 : ((p.flags & BS_SHORT_PER_NODE) ? 2 : 0);
+    S.rc2 = p.rc * p.rc;
+    S.alpha = p.alpha;
+    S.pref = p.kappa / (4.0 * kPi);
+    S.want_psi = want_psi ? 1 : 0;
+}
+
+template <typename T>
+void fill_spzp(const bs_ctx* c, bool det, SpZP& SZ)
+{
+    const bs_params& p = c->p;
+    const Derived& d = c->d;
+    const Work& w = c->w;
+    SZ.det = det ? 1 : 0;
+    SZ.nthreads = d.zthreads;
+    for (int k = 0; k < 3; ++k) {
+        SZ.ng[k] = d.ng[k];
+        SZ.K[k] = d.K[k];
+    }
+    SZ.tx = d.tx;
+    SZ.ty = d.ty;
+    SZ.nbx = d.nbx;
+    SZ.nby = d.nby;
+    SZ.w = p.nufft_w;
+    SZ.cls = line_stride(d.ng[2], 3 * d.tx * d.ty / 2, 128 / (2 * (int)sizeof(T)));
+    SZ.ls = d.lsz;
+    while (SZ.ls < SZ.cls) SZ.ls += 32;  // the real region also holds the complex lines
+    SZ.zeta = d.zeta;
+    SZ.plan2 = d.plan[2];
+    SZ.rev = w.rev + d.ng[0] + d.ng[1];
+    SZ.d_nbx = make_fastdiv((unsigned)d.nbx);
+    SZ.d_n2 = make_fastdiv((unsigned)d.ng[2]);
+    SZ.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
+    SZ.d_txy = make_fastdiv((unsigned)(d.tx * d.ty));
+    SZ.d_ty = make_fastdiv((unsigned)d.ty);
+    SZ.d_ncl = make_fastdiv((unsigned)(3 * d.tx * d.ty / 2));
+}
+
+template <typename T>
+void fill_fftyp(const bs_ctx* c, FftYP& YP)
+{
+    const Derived& d = c->d;
+    for (int k = 0; k < 3; ++k) {
+        YP.ng[k] = d.ng[k];
+        YP.K[k] = d.K[k];
+    }
+    YP.lmc = d.lmcy;
+    YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
+    YP.plan1 = d.plan[1];
+    YP.rev = c->w.rev + d.ng[0];
+    YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
+    YP.d_lines = make_fastdiv(1u << d.lmcy);
+}
+
+// The x pass with the velocity's k-space pass (no energy, spectrum or psi).
+template <typename T>
+void fill_fftxp(const bs_ctx* c, FftXP& XP)
+{
+    const bs_params& p = c->p;
+    const Derived& d = c->d;
+    memset(&XP, 0, sizeof XP);
+    for (int k = 0; k < 3; ++k) {
+        XP.ng[k] = d.ng[k];
+        XP.K[k] = d.K[k];
+        XP.kk[k] = 2.0 * kPi / p.L[k];
+    }
+    XP.lmc = d.lmcx;
+    XP.nthreads = d.zthreads;
+    XP.ls = line_stride(d.ng[0], 3 << d.lmcx, 128 / (2 * (int)sizeof(T)));
+    XP.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
+    XP.plan0 = d.plan[0];
+    XP.rev = c->w.rev;
+    XP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcx) - 1) >> d.lmcx));
+    XP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
+    XP.d_lines = make_fastdiv(3u << d.lmcx);
+    XP.d_lines_psi = make_fastdiv(6u << d.lmcx);
+    XP.dk = 2.0 * kPi / std::min(p.L[0], std::min(p.L[1], p.L[2]));
+    XP.inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
+}
+
 // The pipeline.  parts (4 x N x 3) / psi_parts switch the output to the
 // separate parts of Eq. ewald_velocity_splitting.  With BS_TIMING, events
 // are recorded on the stream each stage runs on (the two branches stay
@@ -670,27 +795,9 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     G.want_psi = want_psi ? 1 : 0;
 
     InterpP I;
-    I.N = (int)c->N;
-    for (int k = 0; k < 3; ++k) {
-        I.ng[k] = d.ng[k];
-        I.hg[k] = d.hg[k];
-        I.L[k] = p.L[k];
-        I.iL[k] = 1.0 / p.L[k];
-        I.ihg[k] = 1.0 / d.hg[k];
-    }
-    I.w = p.nufft_w;
-    I.zeta = d.zeta;
-    I.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
-    I.want_psi = want_psi ? 1 : 0;
+    fill_interp(c, want_psi, I);
     ColP CP;
-    CP.tx = d.tx;
-    CP.ty = d.ty;
-    CP.nbx = d.nbx;
-    CP.nby = d.nby;
-    CP.ncols = d.ncols;
-    CP.w = p.nufft_w;
-    CP.zeta = d.zeta;
-    CP.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
+    fill_colp(c, CP);
     const bool fused = d.fuse_interp && !spectrum && !coarse;
 
     rec(c, 0, s);
@@ -707,20 +814,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
     CE(launch_sort_sr<T>(w, (int)c->NQ, (int)d.ncells, ss, det));
     rec(c, 2, ss);
     ShortP S;
-    memset(&S, 0, sizeof S);
-    S.N = (int)c->N;
-    for (int k = 0; k < 3; ++k) {
-        S.nc[k] = d.nc[k];
-        S.hc[k] = d.hc[k];
-        S.L[k] = p.L[k];
-    }
-    S.m = d.m;
-    for (int k = 0; k < 3; ++k) S.nb[k] = (d.nc[k] + d.m - 1) / d.m;
-    S.kernel = (p.flags & BS_SHORT_TILED) ? 1 : ((p.flags & BS_SHORT_PER_NODE) ? 2 : 0);
-    S.rc2 = p.rc * p.rc;
-    S.alpha = p.alpha;
-    S.pref = p.kappa / (4.0 * kPi);
-    S.want_psi = want_psi ? 1 : 0;
+    fill_short(c, want_psi, S);
     CE(launch_short<T>(S, w, ss));
     rec(c, 3, ss);
     if (fused) CE(launch_node_bin<T>(CP, I, nodes, w, ss));
@@ -762,67 +856,20 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         CE(launch_col_sort<T>(CP, w, (int)c->NQ, s, det));
         rec(c, 4, s);
         SpZP SZ;
-        SZ.det = det ? 1 : 0;
-        SZ.nthreads = d.zthreads;
-        for (int k = 0; k < 3; ++k) {
-            SZ.ng[k] = d.ng[k];
-            SZ.K[k] = d.K[k];
-        }
-        SZ.tx = d.tx;
-        SZ.ty = d.ty;
-        SZ.nbx = d.nbx;
-        SZ.nby = d.nby;
-        SZ.w = p.nufft_w;
-        SZ.cls = line_stride(d.ng[2], 3 * d.tx * d.ty / 2, 128 / (2 * (int)sizeof(T)));
-        SZ.ls = d.lsz;
-        while (SZ.ls < SZ.cls) SZ.ls += 32;  // the real region also holds the complex lines
-        SZ.zeta = d.zeta;
-        SZ.plan2 = d.plan[2];
-        SZ.rev = w.rev + d.ng[0] + d.ng[1];
-        SZ.d_nbx = make_fastdiv((unsigned)d.nbx);
-        SZ.d_n2 = make_fastdiv((unsigned)d.ng[2]);
-        SZ.d_nk = make_fastdiv((unsigned)(d.K[2] + 1));
-        SZ.d_txy = make_fastdiv((unsigned)(d.tx * d.ty));
-        SZ.d_ty = make_fastdiv((unsigned)d.ty);
-        SZ.d_ncl = make_fastdiv((unsigned)(3 * d.tx * d.ty / 2));
+        fill_spzp<T>(c, det, SZ);
         CE(launch_spread_zfft<T>(SZ, w, s));
         rec(c, 5, s);
         FftYP YP;
-        for (int k = 0; k < 3; ++k) {
-            YP.ng[k] = d.ng[k];
-            YP.K[k] = d.K[k];
-        }
-        YP.lmc = d.lmcy;
-        YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
-        YP.plan1 = d.plan[1];
-            YP.rev = w.rev + d.ng[0];
-        YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
-        YP.d_lines = make_fastdiv(1u << d.lmcy);
+        fill_fftyp<T>(c, YP);
         CE(launch_fft_y<T>(YP, w, w.f2, -1, s));
         rec(c, 6, s);
         FftXP XP;
+        fill_fftxp<T>(c, XP);
         XP.epart = (want_energy && det) ? w.epart : nullptr;
-        for (int k = 0; k < 3; ++k) {
-            XP.ng[k] = d.ng[k];
-            XP.K[k] = d.K[k];
-            XP.kk[k] = 2.0 * kPi / p.L[k];
-        }
-        XP.lmc = d.lmcx;
-        XP.nthreads = d.zthreads;
-        XP.ls = line_stride(d.ng[0], 3 << d.lmcx, 128 / (2 * (int)sizeof(T)));
-        XP.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
-        XP.plan0 = d.plan[0];
-        XP.rev = w.rev;
-        XP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcx) - 1) >> d.lmcx));
-        XP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
-        XP.d_lines = make_fastdiv(3u << d.lmcx);
-        XP.d_lines_psi = make_fastdiv(6u << d.lmcx);
         XP.energy = want_energy ? w.energy_acc : nullptr;
         XP.spectrum = spectrum;
         XP.nbins = nbins;
         XP.smoothed = smoothed;
-        XP.dk = 2.0 * kPi / std::min(p.L[0], std::min(p.L[1], p.L[2]));
-        XP.inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
         XP.single_decon = coarse ? 1 : 0;
         if (spectrum) return (int)launch_fft_x_kspace<T>(XP, w, false, s) == (int)cudaSuccess
                                  ? BS_OK
@@ -878,16 +925,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
             TRY(fft_inv<T>(c, w.spec_psi, s));
         } else {
             FftYP YP;
-            for (int k = 0; k < 3; ++k) {
-                YP.ng[k] = d.ng[k];
-                YP.K[k] = d.K[k];
-            }
-            YP.lmc = d.lmcy;
-            YP.ls = line_stride(d.ng[1], 1 << d.lmcy, 128 / (2 * (int)sizeof(T)));
-            YP.plan1 = d.plan[1];
-            YP.rev = w.rev + d.ng[0];
-            YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
-            YP.d_lines = make_fastdiv(1u << d.lmcy);
+            fill_fftyp<T>(c, YP);
             CE(launch_fft_y<T>(YP, w, w.f2psi, +1, s));
             FftZP ZP;
             for (int k = 0; k < 3; ++k) {
@@ -1443,13 +1481,33 @@ void bs_destroy(bs_ctx* c)
 
 // ---------------------------------------------------------------------------
 // Batches of independent configurations.  Member i is a full context with
-// its own grid sizes; the members' evaluations are issued on a pool of
-// streams (largest members first, round-robin) and captured together into
-// one CUDA graph, so small members run concurrently and the whole batch
-// costs one graph launch.
+// its own grid sizes.  Small members share one launch per stage (the staged
+// group: each stage's CTAs look up their member in a table); the others are
+// issued one by one on a pool of streams (largest first, round-robin).  Both
+// run concurrently and are captured together into one CUDA graph, so the
+// whole batch costs one graph launch.
 // ---------------------------------------------------------------------------
+
+// Members up to this many nodes join the staged group by default.  Measured
+// on GB300 (mixed form, float32 kernels): 1024 members of ~400 nodes take
+// 12.2 ms staged against 20.0 ms issued one by one, 256 of ~1e3 nodes 6.8
+// against 7.7 ms; 64 members of 1e4..3e4 nodes take 19.2 against 16.1 ms and
+// 16 of ~1e5 nodes 12.2 against 11.4 ms (a stage ends only when its slowest
+// member does, where separate members overlap their stages).
+constexpr int64_t kStageMaxNodes = 8192;
+
 struct bs_batch {
     int nconf = 0;
+    // the staged group: the members' descriptors and block starts in one
+    // device arena, bound to the node and velocity buffers it was built for
+    std::vector<char> grouped;  // member i is in the staged group
+    int ngrouped = 0;
+    std::vector<int> mode;      // per member: 0 size rule, BS_BATCH_PER_MEMBER, BS_BATCH_STAGED
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    const double* a_nodes = nullptr;
+    double* a_vel = nullptr;
+    std::vector<BatchL> stages;
     std::vector<bs_ctx*> ctx;
     std::vector<int64_t> node_off;  // nconf + 1, member i owns nodes [node_off[i], node_off[i+1])
     std::vector<int> order;         // issue order, largest member first
@@ -1457,6 +1515,8 @@ struct bs_batch {
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> ev_done;
     cudaEvent_t ev_start = nullptr;
+    cudaStream_t side = nullptr;  // the staged group's short range
+    cudaEvent_t ev_side = nullptr;
     int device = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -1476,18 +1536,483 @@ void batch_drop_graph(bs_batch* b)
     b->g_vel = nullptr;
 }
 
-// Issue every member's evaluation on the pool, joined back to b->stream.
+// Drops the staged launches' descriptors (the members changed).
+void batch_drop_stages(bs_batch* b)
+{
+    if (b->arena) cudaFree(b->arena);
+    b->arena = nullptr;
+    b->arena_bytes = 0;
+    b->a_nodes = nullptr;
+    b->a_vel = nullptr;
+    b->stages.clear();
+}
+
+// Host image of the batched launches' device arena: descriptor arrays and
+// block starts, 256-byte aligned; BatchL pointers are offsets until upload.
+struct Arena {
+    std::vector<unsigned char> bytes;
+    size_t put(const void* p, size_t n)
+    {
+        const size_t o = (bytes.size() + 255) & ~(size_t)255;
+        bytes.resize(o + n);
+        memcpy(bytes.data() + o, p, n);
+        return o;
+    }
+};
+
+// One stage: a descriptor per member and its CTA count.
+template <typename D>
+BatchL stage(Arena& A, const std::vector<D>& desc, const std::vector<int>& blocks, int threads, size_t smem)
+{
+    std::vector<int> bs(desc.size() + 1, 0);
+    for (size_t m = 0; m < desc.size(); ++m) bs[m + 1] = bs[m] + blocks[m];
+    BatchL L;
+    L.desc = (const void*)A.put(desc.data(), sizeof(D) * desc.size());
+    L.bstart = (const int*)A.put(bs.data(), sizeof(int) * bs.size());
+    L.n = (int)desc.size();
+    L.total = bs.back();
+    L.threads = threads;
+    L.smem = smem;
+    return L;
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Address of complex element k of a T-complex array.
+template <typename T>
+const void* cx_at(const void* p, size_t k)
+{
+    return (const unsigned char*)p + k * 2 * sizeof(T);
+}
+
+// Whether a member can take the batched stage launches: the plain velocity
+// path (fused interpolation, cubic curves on the warp spline, no psi, cuFFT
+// or deterministic mode, the warp-per-node short range).
+bool batch_stageable(const bs_ctx* c)
+{
+    const bs_params& p = c->p;
+    if ((p.flags & (BS_WANT_PSI | BS_DETERMINISTIC | BS_FFT_CUFFT | BS_SHORT_TILED)) || !c->d.fuse_interp ||
+        p.spline_order != 4 || p.local_frac > 0.0)
+        return false;
+    const size_t rb = p.precision == BS_FP64 ? 8 : 4;
+    return 9 * (size_t)c->w.nmax_fil * rb <= kSplineSmemMax && c->d.m <= 8;
+}
+
+// Chooses the staged group: the non-empty members that can take the stage
+// launches and ask for it (BS_BATCH_STAGED) or, by default, have at most
+// kStageMaxNodes nodes; all of them with the precision, kernel width and
+// z-column CTA size of the first such member.
+void batch_group(bs_batch* b)
+{
+    b->grouped.assign(b->nconf, 0);
+    b->ngrouped = 0;
+    const bs_ctx* c0 = nullptr;
+    for (int i = 0; i < b->nconf; ++i) {
+        const bs_ctx* c = b->ctx[i];
+        if (c->N == 0 || b->mode[i] == BS_BATCH_PER_MEMBER || !batch_stageable(c)) continue;
+        if (b->mode[i] == 0 && c->N > kStageMaxNodes) continue;
+        if (c0 && (c->p.precision != c0->p.precision || c->p.nufft_w != c0->p.nufft_w ||
+                   c->d.zthreads != c0->d.zthreads))
+            continue;
+        if (!c0) c0 = c;
+        b->grouped[i] = 1;
+        ++b->ngrouped;
+    }
+}
+
+// Builds the descriptors of every batched stage for these node and velocity
+// buffers and uploads them (synchronously; not inside a stream capture).
+template <typename T>
+int batch_build(bs_batch* b, const double* nodes, double* vel)
+{
+    Arena A;
+    std::vector<BatchL> st;
+    std::vector<int> blk;
+    std::vector<bs_ctx*> mem;
+    std::vector<int64_t> noff;
+    for (int i = 0; i < b->nconf; ++i)
+        if (b->grouped[i]) {
+            mem.push_back(b->ctx[i]);
+            noff.push_back(b->node_off[i]);
+        }
+    const size_t nm = mem.size();
+    const int zt = mem[0]->d.zthreads;
+    auto add = [&](auto& desc, int threads, size_t smem) {
+        st.push_back(stage(A, desc, blk, threads, smem));
+        blk.clear();
+    };
+    {   // 0 spline
+        std::vector<SplineD<T>> D;
+        size_t sm = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const Work& w = c->w;
+            D.push_back({ nodes + 3 * noff[m], w.off, w.shift, c->nfil, w.nmax_fil, (T*)w.hseg, (T*)w.dp, (T*)w.ds,
+                          (T*)w.Mm, (T*)w.Tper });
+            blk.push_back(c->nfil);
+            sm = std::max(sm, spline_smem<T>(w.nmax_fil));
+        }
+        add(D, 32, sm);
+    }
+    {   // 1 nodes
+        std::vector<NodesD<T>> D;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const Work& w = c->w;
+            NodesD<T> e;
+            fill_geom(c, e.P);
+            e.P.want_psi = 0;
+            e.nodes = nodes + 3 * noff[m];
+            e.fil_of = w.fil_of;
+            e.prev = w.prev;
+            e.off = w.off;
+            e.shift = w.shift;
+            e.hseg = (const T*)w.hseg;
+            e.dp = (const T*)w.dp;
+            e.ds = (const T*)w.ds;
+            e.Mm = (const T*)w.Mm;
+            e.Tper = (const T*)w.Tper;
+            e.Dd = nullptr;
+            e.sr_rec = (SrRec<T>*)w.sr_rec;
+            e.sr_key = w.sr_key;
+            e.lr_rec = (LrRec<T>*)w.lr_rec;
+            e.lr_key = w.lr_key;
+            e.tgt = (SrTgt<T>*)w.tgt;
+            e.vls = w.vls;
+            e.pls = w.pls;
+            e.status = w.status;
+            D.push_back(e);
+            blk.push_back(cdiv(c->N, 128));
+        }
+        add(D, 128, 0);
+    }
+    // counting sorts: zero the counts, count, scan, copy to the cursors, scatter
+    auto zero_stage = [&](auto cnt_of, auto n_of) {
+        std::vector<ZeroD> Z;
+        for (size_t m = 0; m < nm; ++m) {
+            Z.push_back({ cnt_of(mem[m]), n_of(mem[m]) + 1 });
+            blk.push_back(std::min(cdiv(n_of(mem[m]) + 1, 256), 256));
+        }
+        add(Z, 256, 0);
+    };
+    auto scan_stage = [&](auto cnt_of, auto n_of, auto tmp_of) {
+        std::vector<ScanD> S;
+        std::vector<int> one;
+        for (size_t m = 0; m < nm; ++m) {
+            const int n = n_of(mem[m]);
+            S.push_back({ cnt_of(mem[m]), n, tmp_of(mem[m]), scan_blocks(n) });
+            blk.push_back(scan_blocks(n));
+            one.push_back(1);
+        }
+        add(S, 1024, 0);
+        blk = one;
+        add(S, 1024, 0);
+    };
+    auto copy_stage = [&](auto cnt_of, auto n_of, auto cur_of) {
+        std::vector<CopyD> Cd;
+        for (size_t m = 0; m < nm; ++m) {
+            Cd.push_back({ cnt_of(mem[m]), cur_of(mem[m]), n_of(mem[m]) });
+            blk.push_back(std::min(cdiv(n_of(mem[m]), 256), 256));
+        }
+        add(Cd, 256, 0);
+    };
+    auto cell_cnt = [](bs_ctx* c) { return c->w.cell_cnt; };
+    auto cell_n = [](bs_ctx* c) { return (int)c->d.ncells; };
+    auto cell_tmp = [](bs_ctx* c) { return c->w.scan_tmp; };
+    auto cell_cur = [](bs_ctx* c) { return c->w.cell_cur; };
+    zero_stage(cell_cnt, cell_n);                                                          // 2 zero
+    {   // 3 count
+        std::vector<CountD> D;
+        for (size_t m = 0; m < nm; ++m) {
+            D.push_back({ mem[m]->w.sr_key, (int)mem[m]->NQ, mem[m]->w.cell_cnt });
+            blk.push_back(cdiv(mem[m]->NQ, kThreads));
+        }
+        add(D, kThreads, 0);
+    }
+    scan_stage(cell_cnt, cell_n, cell_tmp);                                                // 4, 5 scan
+    copy_stage(cell_cnt, cell_n, cell_cur);                                                // 6 copy
+    {   // 7 scatter
+        std::vector<ScatterD<SrRec<T>>> D;
+        for (size_t m = 0; m < nm; ++m) {
+            const Work& w = mem[m]->w;
+            D.push_back({ w.sr_key, (const SrRec<T>*)w.sr_rec, (int)mem[m]->NQ, w.cell_cur, (SrRec<T>*)w.sr_sorted });
+            blk.push_back(cdiv(mem[m]->NQ, kThreads));
+        }
+        add(D, kThreads, 0);
+    }
+    {   // 8 short range (warp per node)
+        std::vector<ShortD<T>> D;
+        for (size_t m = 0; m < nm; ++m) {
+            const Work& w = mem[m]->w;
+            ShortD<T> e;
+            fill_short(mem[m], false, e.P);
+            e.tgt = (const SrTgt<T>*)w.tgt;
+            e.prev = w.prev;
+            e.start = w.cell_cnt;
+            e.src = (const SrRec<T>*)w.sr_sorted;
+            e.vsr = w.vsr;
+            e.psr = w.psr;
+            D.push_back(e);
+            blk.push_back(cdiv(32LL * mem[m]->N, 256));
+        }
+        add(D, 256, 0);
+    }
+    auto col_cnt = [](bs_ctx* c) { return c->w.col_cnt; };
+    auto col_n = [](bs_ctx* c) { return c->d.ncols; };
+    auto col_tmp = [](bs_ctx* c) { return c->w.scan_tmp2; };
+    auto col_cur = [](bs_ctx* c) { return c->w.col_cur; };
+    zero_stage(col_cnt, col_n);                                                            // 9 zero
+    {   // 10 column count, 13 column scatter share the descriptor shape
+        std::vector<ColD<T>> D;
+        for (size_t m = 0; m < nm; ++m) {
+            const Work& w = mem[m]->w;
+            ColD<T> e;
+            fill_colp(mem[m], e.P);
+            e.rec = (const LrRec<T>*)w.lr_rec;
+            e.n = (int)mem[m]->NQ;
+            e.cnt = w.col_cnt;
+            e.out = nullptr;
+            D.push_back(e);
+            blk.push_back(cdiv(mem[m]->NQ, kThreads));
+        }
+        add(D, kThreads, 0);
+    }
+    scan_stage(col_cnt, col_n, col_tmp);                                                   // 11, 12 scan
+    copy_stage(col_cnt, col_n, col_cur);                                                   // 13 copy
+    {   // 14 column scatter
+        std::vector<ColD<T>> D;
+        for (size_t m = 0; m < nm; ++m) {
+            const Work& w = mem[m]->w;
+            ColD<T> e;
+            fill_colp(mem[m], e.P);
+            e.rec = (const LrRec<T>*)w.lr_rec;
+            e.n = (int)mem[m]->NQ;
+            e.cnt = w.col_cur;
+            e.out = w.col_rec;
+            D.push_back(e);
+            blk.push_back(cdiv(mem[m]->NQ, kThreads));
+        }
+        add(D, kThreads, 0);
+    }
+    {   // 15 spread + z transform
+        std::vector<SpzD<T>> D;
+        size_t sm = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const Work& w = c->w;
+            SpzD<T> e;
+            fill_spzp<T>(c, false, e.P);
+            e.cstart = w.col_cnt;
+            e.recs = w.col_rec;
+            e.tw2 = cx_at<T>(w.tw, c->d.ng[0] + c->d.ng[1]);
+            e.F1 = w.spec;
+            e.vacc = nullptr;
+            D.push_back(e);
+            blk.push_back(c->d.nbx * c->d.nby);
+            sm = std::max(sm, spread_zfft_smem<T>(e.P));
+        }
+        add(D, zt, sm);
+    }
+    auto ffty = [&](int sign) {
+        std::vector<FftYD<T>> D;
+        size_t sm = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const Work& w = c->w;
+            FftYD<T> e;
+            fill_fftyp<T>(c, e.P);
+            e.F1 = w.spec;
+            e.F2 = w.f2;
+            e.tw1 = cx_at<T>(w.tw, c->d.ng[0]);
+            e.sign = sign;
+            D.push_back(e);
+            const int MC = 1 << e.P.lmc, nk = c->d.K[2] + 1;
+            blk.push_back(3 * c->d.ng[0] * ((nk + MC - 1) / MC));
+            sm = std::max(sm, fft_y_smem<T>(e.P));
+        }
+        add(D, kThreads, sm);
+    };
+    ffty(-1);  // 16
+    {   // 17 x transform + k-space pass + inverse x transform
+        std::vector<FftXD<T>> D;
+        size_t sm = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const Work& w = c->w;
+            FftXD<T> e;
+            fill_fftxp<T>(c, e.P);
+            e.F2 = w.f2;
+            e.tw0 = w.tw;
+            e.tab0 = (const T*)w.ktab;
+            e.tab1 = e.tab0 + (c->d.K[0] + 1);
+            e.tab2 = e.tab1 + (c->d.K[1] + 1);
+            D.push_back(e);
+            const int MC = 1 << e.P.lmc, nk = c->d.K[2] + 1;
+            blk.push_back((2 * c->d.K[1] + 1) * ((nk + MC - 1) / MC));
+            sm = std::max(sm, fft_x_smem<T>(e.P));
+        }
+        add(D, zt, sm);
+    }
+    ffty(+1);  // 18
+    {   // 19 zero: the interpolation sums and the node-block counts
+        std::vector<ZeroD> Z;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const int nv = (int)(3 * c->N * (long long)sizeof(T) / sizeof(int));
+            Z.push_back({ (int*)c->w.vacc, nv });
+            blk.push_back(std::min(cdiv(nv, 256), 256));
+            Z.push_back({ c->w.ncol_cnt, c->d.ncols + 1 });
+            blk.push_back(std::min(cdiv(c->d.ncols + 1, 256), 256));
+        }
+        add(Z, 256, 0);
+    }
+    std::vector<NodeWD<T>> NW;
+    for (size_t m = 0; m < nm; ++m) {
+        const bs_ctx* c = mem[m];
+        const Work& w = c->w;
+        NodeWD<T> e;
+        fill_interp(c, false, e.P);
+        e.tx = c->d.tx;
+        e.ty = c->d.ty;
+        e.nbx = c->d.nbx;
+        e.nodes = nodes + 3 * noff[m];
+        e.rec = w.nd_rec;
+        e.key = w.nd_key;
+        e.rank = w.nd_rank;
+        e.cnt = w.ncol_cnt;
+        e.sorted = w.nd_sorted;
+        NW.push_back(e);
+        blk.push_back(cdiv(c->N, kThreads));
+    }
+    add(NW, kThreads, 0);                                                                  // 20 node weights
+    auto nb_cnt = [](bs_ctx* c) { return c->w.ncol_cnt; };
+    auto nb_tmp = [](bs_ctx* c) { return c->w.scan_tmp; };
+    scan_stage(nb_cnt, col_n, nb_tmp);                                                     // 21, 22 scan
+    for (size_t m = 0; m < nm; ++m) blk.push_back(cdiv(mem[m]->N, kThreads));
+    add(NW, kThreads, 0);                                                                  // 23 node scatter
+    {   // 24 inverse z transform + interpolation
+        std::vector<SpzD<T>> D;
+        size_t sm = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            const Work& w = c->w;
+            SpzD<T> e;
+            fill_spzp<T>(c, false, e.P);
+            e.cstart = w.ncol_cnt;
+            e.recs = w.nd_sorted;
+            e.tw2 = cx_at<T>(w.tw, c->d.ng[0] + c->d.ng[1]);
+            e.F1 = w.spec;
+            e.vacc = (T*)w.vacc;
+            D.push_back(e);
+            blk.push_back(c->d.nbx * c->d.nby);
+            sm = std::max(sm, zfft_interp_smem<T>(e.P));
+        }
+        add(D, zt, sm);
+    }
+    {   // 25 final sum
+        std::vector<SumD<T>> D;
+        for (size_t m = 0; m < nm; ++m) {
+            const bs_ctx* c = mem[m];
+            D.push_back({ (int)(3 * c->N), (const T*)c->w.vacc, c->w.vls, c->w.vsr, vel + 3 * noff[m] });
+            blk.push_back(std::min(cdiv(3 * c->N, 256), 4096));
+        }
+        add(D, 256, 0);
+    }
+    // upload, then turn the offsets into device pointers
+    if (b->arena) cudaFree(b->arena);
+    b->arena = nullptr;
+    CUDA_TRY(cudaMalloc(&b->arena, A.bytes.size()));
+    b->arena_bytes = A.bytes.size();
+    CUDA_TRY(cudaMemcpy(b->arena, A.bytes.data(), A.bytes.size(), cudaMemcpyHostToDevice));
+    for (BatchL& L : st) {
+        L.desc = (const unsigned char*)b->arena + (size_t)L.desc;
+        L.bstart = (const int*)((const unsigned char*)b->arena + (size_t)L.bstart);
+    }
+    b->stages = st;
+    b->a_nodes = nodes;
+    b->a_vel = vel;
+    return BS_OK;
+}
+
+// Issues the staged group's launches (one per stage, every grouped member in
+// each) on s, the short range and the node binning on b->side.
+template <typename T>
+int batch_issue_staged(bs_batch* b, cudaStream_t s)
+{
+    const std::vector<BatchL>& L = b->stages;
+    int w = 0;
+    for (int i = 0; i < b->nconf; ++i)
+        if (b->grouped[i]) {
+            w = b->ctx[i]->p.nufft_w;
+            break;
+        }
+    CE(launch_spline_b<T>(L[0], s));
+    CE(launch_nodes_b<T>(L[1], s));
+    // the short range and the node binning on a side stream, as in run()
+    cudaStream_t ss = b->side;
+    CE(cudaEventRecord(b->ev_side, s));
+    CE(cudaStreamWaitEvent(ss, b->ev_side, 0));
+    CE(launch_zero_b(L[2], ss));
+    CE(launch_count_b(L[3], ss));
+    CE(launch_scan_b(L[4], L[5], ss));
+    CE(launch_copy_b(L[6], ss));
+    CE(launch_scatter_b<SrRec<T>>(L[7], ss));
+    CE(launch_short_b<T>(L[8], ss));
+    CE(launch_zero_b(L[19], ss));
+    CE(launch_node_w_b<T>(w, L[20], ss));
+    CE(launch_scan_b(L[21], L[22], ss));
+    CE(launch_node_scatter_b<T>(w, L[23], ss));
+    CE(cudaEventRecord(b->ev_side, ss));
+    CE(launch_zero_b(L[9], s));
+    CE(launch_col_count_b<T>(L[10], s));
+    CE(launch_scan_b(L[11], L[12], s));
+    CE(launch_copy_b(L[13], s));
+    CE(launch_col_scatter_b<T>(w, L[14], s));
+    CE(launch_spread_zfft_b<T>(w, L[15], s));
+    CE(launch_fft_y_b<T>(L[16], s));
+    CE(launch_fft_x_kspace_b<T>(L[17], s));
+    CE(launch_fft_y_b<T>(L[18], s));
+    CE(cudaStreamWaitEvent(s, b->ev_side, 0));
+    CE(launch_zfft_interp_b<T>(w, L[24], s));
+    CE(launch_interp_sum_b<T>(L[25], s));
+    return BS_OK;
+}
+
+// Precision of the staged group (false: empty or float32 kernels).
+bool group_f64(const bs_batch* b)
+{
+    for (int i = 0; i < b->nconf; ++i)
+        if (b->grouped[i]) return b->ctx[i]->p.precision == BS_FP64;
+    return false;
+}
+
+// (Re)builds the staged group's tables for these buffers if needed.
+int batch_ensure_stages(bs_batch* b, const double* nodes, double* vel)
+{
+    if (b->ngrouped == 0 || (b->a_nodes == nodes && b->a_vel == vel)) return BS_OK;
+    return group_f64(b) ? batch_build<double>(b, nodes, vel) : batch_build<float>(b, nodes, vel);
+}
+
+// Issues the staged group on b->stream and every other member's evaluation
+// on the pool, joined back to b->stream.
 int batch_issue(bs_batch* b, const double* nodes, double* vel)
 {
     CUDA_TRY(cudaEventRecord(b->ev_start, b->stream));
     for (cudaStream_t s : b->pool) CUDA_TRY(cudaStreamWaitEvent(s, b->ev_start, 0));
     for (int i : b->order) {
         bs_ctx* c = b->ctx[i];
-        if (c->N == 0) continue;
+        if (c->N == 0 || b->grouped[i]) continue;
         const size_t o = 3 * (size_t)b->node_off[i];
         const int rc = c->p.precision == BS_FP64 ? run<double>(c, nodes + o, vel + o, nullptr, nullptr, nullptr)
                                                  : run<float>(c, nodes + o, vel + o, nullptr, nullptr, nullptr);
         if (rc != BS_OK) return rc;
+    }
+    if (b->ngrouped > 0) {
+        const int rc = batch_ensure_stages(b, nodes, vel);
+        if (rc != BS_OK) return rc;
+        const int rs = group_f64(b) ? batch_issue_staged<double>(b, b->stream)
+                                    : batch_issue_staged<float>(b, b->stream);
+        if (rs != BS_OK) return rs;
     }
     for (size_t k = 0; k < b->pool.size(); ++k) {
         CUDA_TRY(cudaEventRecord(b->ev_done[k], b->pool[k]));
@@ -1505,11 +2030,16 @@ void bs_batch_destroy(bs_batch* b)
     if (!b) return;
     cudaSetDevice(b->device);
     for (cudaStream_t s : b->pool) cudaStreamSynchronize(s);
+    if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graph(b);
+    batch_drop_stages(b);
     for (bs_ctx* c : b->ctx) bs_destroy(c);
+    if (b->side) cudaStreamSynchronize(b->side);
     for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
     if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->ev_side) cudaEventDestroy(b->ev_side);
     for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
+    if (b->side) cudaStreamDestroy(b->side);
     delete b;
 }
 
@@ -1532,14 +2062,26 @@ int bs_batch_create(bs_batch** out, int nconf, const bs_params* params, void* st
         if (e == cudaSuccess) b->ev_done.push_back(ev);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_side, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         const int rc = fail(BS_ERR_CUDA, "CUDA set-up failed: %s", cudaGetErrorString(e));
         bs_batch_destroy(b);
         return rc;
     }
     for (int i = 0; i < nconf; ++i) {
+        const int f = params[i].flags & (BS_BATCH_PER_MEMBER | BS_BATCH_STAGED);
+        if (f == (BS_BATCH_PER_MEMBER | BS_BATCH_STAGED)) {
+            bs_batch_destroy(b);
+            return fail(BS_ERR_ARG, "batch member %d asks for both BS_BATCH_PER_MEMBER and BS_BATCH_STAGED", i);
+        }
+        b->mode.push_back(f);
+    }
+    b->grouped.assign(nconf, 0);
+    for (int i = 0; i < nconf; ++i) {
         bs_params p = params[i];
-        p.flags &= ~BS_TIMING;  // stage events cannot be read back from a graph
+        // stage events cannot be read back from a graph
+        p.flags &= ~(BS_TIMING | BS_BATCH_PER_MEMBER | BS_BATCH_STAGED);
         bs_ctx* c = nullptr;
         const int rc = bs_create(&c, &p, nullptr);
         if (rc != BS_OK) {
@@ -1558,14 +2100,25 @@ int bs_batch_set(bs_batch* b, int i, int nfil, const int64_t* offsets, const int
 {
     if (!b || i < 0 || i >= b->nconf) return fail(BS_ERR_ARG, "bad batch or member index");
     batch_drop_graph(b);
+    batch_drop_stages(b);
     const int rc = bs_set_filaments(b->ctx[i], nfil, offsets, closing);
     if (rc != BS_OK) return rc;
+    batch_group(b);
     for (int k = 0; k < b->nconf; ++k) b->node_off[k + 1] = b->node_off[k] + b->ctx[k]->N;
     b->order.resize(b->nconf);
     for (int k = 0; k < b->nconf; ++k) b->order[k] = k;
     std::stable_sort(b->order.begin(), b->order.end(),
                      [b](int x, int y) { return b->ctx[x]->N > b->ctx[y]->N; });
-    for (size_t r = 0; r < b->order.size(); ++r) b->ctx[b->order[r]]->stream = b->pool[r % b->pool.size()];
+    size_t r = 0;  // the members issued one by one, round-robin over the pool
+    for (int k : b->order)
+        if (!b->grouped[k]) b->ctx[k]->stream = b->pool[r++ % b->pool.size()];
+    return BS_OK;
+}
+
+int bs_batch_staged_members(bs_batch* b, int32_t* staged)
+{
+    if (!b || !staged) return fail(BS_ERR_ARG, "null argument");
+    for (int k = 0; k < b->nconf; ++k) staged[k] = b->grouped[k] ? 1 : 0;
     return BS_OK;
 }
 
@@ -1587,6 +2140,9 @@ int bs_batch_compute(bs_batch* b, const double* nodes, double* vel)
     if (!b->stream) return batch_issue(b, nodes, vel);  // the legacy stream cannot be captured
     if (!b->gexec || b->g_nodes != nodes || b->g_vel != vel) {
         batch_drop_graph(b);
+        // the staged launches' descriptors are uploaded before the capture
+        const int rb = batch_ensure_stages(b, nodes, vel);
+        if (rb != BS_OK) return rb;
         CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         const int rc = batch_issue(b, nodes, vel);
         cudaGraph_t g = nullptr;

@@ -442,6 +442,177 @@ cudaError_t launch_rk4_final(double* x, const double* k1, const double* k2, cons
 
 void set_last_error(const char* msg);
 
+// ---------------------------------------------------------------------------
+// Batched stage launches.  One launch serves every member of a batch: member
+// m owns the launch's CTAs [bstart[m], bstart[m + 1]) and runs them as its
+// blocks 0 .. bstart[m + 1] - bstart[m] - 1, with its own arguments (a
+// descriptor per member, in device memory).  No CTA waits on another.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_member(const int* __restrict__ bstart, int n, int& bid, int& nb)
+{
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = n;  // bstart[lo] <= b < bstart[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(bstart + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    const int b0 = __ldg(bstart + lo);
+    bid = b - b0;
+    nb = __ldg(bstart + lo + 1) - b0;
+    return lo;
+}
+
+// A member's parameter struct copied into shared memory by the CTA (the
+// transform loops read the plan at every pass: shared memory instead of the
+// descriptor in global memory).  Every thread calls it; it ends with a barrier.
+template <typename PT>
+__device__ __forceinline__ void batch_param_copy(PT& dst, const PT& src)
+{
+    static_assert(sizeof(PT) % 4 == 0, "parameter structs are copied as 4-byte words");
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(PT) / 4); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
+// A batched launch: descriptors and block starts in device memory.
+struct BatchL {
+    const void* desc;
+    const int* bstart;
+    int n;        // members
+    int total;    // CTAs of the launch
+    int threads;  // threads per CTA
+    size_t smem;  // dynamic shared memory per CTA (the largest member's)
+};
+
+// Descriptors of the batched stages (one per member).
+struct ZeroD { int* p; int n; };                  // p[0..n) = 0
+struct CopyD { const int* src; int* dst; int n; };
+struct CountD { const int* key; int n; int* cnt; };
+struct ScanD { int* cnt; int n; int* part; int nb; };
+template <typename R> struct ScatterD { const int* key; const R* in; int n; int* cur; R* out; };
+
+template <typename T> struct SplineD {
+    const double* nodes;
+    const int64_t* off;
+    const double* shift;
+    int nfil, nmax;
+    T *hseg, *dp, *ds, *Mm, *Tper;
+};
+template <typename T> struct NodesD {
+    GeomP P;
+    const double* nodes;
+    const int* fil_of;
+    const int* prev;
+    const int64_t* off;
+    const double* shift;
+    const T *hseg, *dp, *ds, *Mm, *Tper, *Dd;
+    SrRec<T>* sr_rec;
+    int* sr_key;
+    LrRec<T>* lr_rec;
+    int* lr_key;
+    SrTgt<T>* tgt;
+    double *vls, *pls;
+    int* status;
+};
+template <typename T> struct ShortD {
+    ShortP P;
+    const SrTgt<T>* tgt;
+    const int* prev;
+    const int* start;
+    const SrRec<T>* src;
+    double *vsr, *psr;
+};
+template <typename T> struct ColD {      // k_col_count (out unused) and k_col_scatter
+    ColP P;
+    const LrRec<T>* rec;
+    int n;
+    int* cnt;                             // counts (count) or cursors (scatter)
+    void* out;                            // SpRec<T, W> copies
+};
+template <typename T> struct SpzD {      // k_spread_zfft and k_zfft_interp
+    SpZP P;
+    const int* cstart;
+    const void* recs;                     // SpRec<T, W> (spread) or NdW<T, W> (interpolation)
+    const void* tw2;
+    void* F1;                             // written (spread) or read (interpolation)
+    T* vacc;                              // interpolation sums
+};
+template <typename T> struct FftYD {
+    FftYP P;
+    void* F1;
+    void* F2;
+    const void* tw1;
+    int sign;
+};
+template <typename T> struct FftXD {
+    FftXP P;
+    void* F2;
+    const void* tw0;
+    const T *tab0, *tab1, *tab2;
+};
+template <typename T> struct NodeWD {   // k_node_w and k_node_scatter
+    InterpP P;
+    int tx, ty, nbx;
+    const double* nodes;
+    void* rec;                            // NdW<T, W>, node order
+    int* key;
+    int* rank;
+    int* cnt;                             // block counts, then starts
+    void* sorted;                         // NdW<T, W>, block order
+};
+template <typename T> struct SumD {
+    int n3;
+    const T* acc;
+    const double* add_d;
+    const double* add_t;
+    double* out;
+};
+
+template <typename T>
+cudaError_t launch_spline_b(const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_nodes_b(const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_short_b(const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_col_count_b(const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_col_scatter_b(int w, const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread_zfft_b(int w, const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_y_b(const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_x_kspace_b(const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_node_w_b(int w, const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_node_scatter_b(int w, const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zfft_interp_b(int w, const BatchL& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_interp_sum_b(const BatchL& L, cudaStream_t s);
+// shared memory of one member's CTA in the launches above
+template <typename T>
+size_t spline_smem(int nmax);
+template <typename T>
+size_t fft_y_smem(const FftYP& P);
+template <typename T>
+size_t fft_x_smem(const FftXP& P);
+template <typename T>
+size_t zfft_interp_smem(const SpZP& P);
+
+cudaError_t launch_zero_b(const BatchL& L, cudaStream_t s);
+cudaError_t launch_copy_b(const BatchL& L, cudaStream_t s);
+cudaError_t launch_count_b(const BatchL& L, cudaStream_t s);
+// the three phases of the exclusive scan, per member: L1 over each member's
+// scan tiles (scan_blocks(n)), L2 one CTA per member
+cudaError_t launch_scan_b(const BatchL& L1, const BatchL& L2, cudaStream_t s);
+template <typename R>
+cudaError_t launch_scatter_b(const BatchL& L, cudaStream_t s);
+
 // Exclusive scan of n ints in place (cnt[n] receives the total); tmp holds
 // scan_blocks(n) ints.
 cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s);

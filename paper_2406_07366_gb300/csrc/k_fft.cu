@@ -522,9 +522,10 @@ __device__ __forceinline__ int col_wrap(int b, int nb)
 // one atomic per run of equal blocks (neighbouring points along a filament
 // mostly reach the same blocks).
 template <typename T>
-__global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cnt)
+__device__ __forceinline__ void k_col_count_body(const ColP& P, const LrRec<T>* __restrict__ rec, int n,
+                                                 int* __restrict__ cnt, int bid)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid * blockDim.x + threadIdx.x;
     int x0 = 0, nx = 0, y0 = 0, ny = 0;
     if (i < n) col_span(P, rec[i].base, x0, nx, y0, ny);
     const int nk = __reduce_max_sync(0xffffffffu, nx * ny);
@@ -538,14 +539,21 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
     }
 }
 
+template <typename T>
+__global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cnt)
+{
+    k_col_count_body<T>(P, rec, n, cnt, blockIdx.x);
+}
+
 // One thread per point: the 3 W kernel weights are evaluated once, then the
 // point is written into every block its support reaches, with the x and y
 // weights of that block's local columns picked out (zero outside the support).
 template <typename T, int W>
-__global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cur,
-                              SpRec<T, W>* __restrict__ out, int* __restrict__ idx_out)
+__device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>* __restrict__ rec, int n,
+                                                   int* __restrict__ cur, SpRec<T, W>* __restrict__ out,
+                                                   int* __restrict__ idx_out, int bid)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid * blockDim.x + threadIdx.x;
     constexpr int H = W / 2;
     LrRec<T> R;
     R.base = 0;
@@ -600,6 +608,13 @@ __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, i
         out[p] = D;
         if (idx_out) idx_out[p] = i;
     }
+}
+
+template <typename T, int W>
+__global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cur,
+                              SpRec<T, W>* __restrict__ out, int* __restrict__ idx_out)
+{
+    k_col_scatter_body<T, W>(P, rec, n, cur, out, idx_out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -800,10 +815,10 @@ __host__ __device__ __forceinline__ size_t zlines_bytes(int ncl, int cls)
 // cells; shared atomic adds resolve two warps meeting on a cell.
 // ---------------------------------------------------------------------------
 template <typename T, int W, int RM>
-__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
-                                                          const SpRec<T, W>* __restrict__ recs,
-                                                          const typename Cx<T>::t* __restrict__ tw2,
-                                                          typename Cx<T>::t* __restrict__ F1)
+__device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __restrict__ cstart,
+                                                   const SpRec<T, W>* __restrict__ recs,
+                                                   const typename Cx<T>::t* __restrict__ tw2,
+                                                   typename Cx<T>::t* __restrict__ F1, int bid)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -816,12 +831,12 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, c
     T* accf = reinterpret_cast<T*>(cb);  // real line rl, position z at float ((rl>>1) CS + z) 2 + (rl&1)
     SpRec<T, W>* srec = reinterpret_cast<SpRec<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const int by = fdiv(blockIdx.x, P.d_nbx);
-    const int bx = blockIdx.x - by * P.nbx;
+    const int by = fdiv(bid, P.d_nbx);
+    const int bx = bid - by * P.nbx;
     zero_cx(cb, ncl * CS);
 
     constexpr int H = W / 2;
-    const int s0 = cstart[blockIdx.x], s1 = cstart[blockIdx.x + 1];
+    const int s0 = cstart[bid], s1 = cstart[bid + 1];
     const int nslot = Ty * W;
     // deterministic mode: warp wid owns z in [zlo, zhi) and adds every record
     // of the block in order (plain adds: one writer per cell, ordered sums)
@@ -920,15 +935,24 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, c
     spz_unpack<T>(P, cb, F1, bx, by);
 }
 
+template <typename T, int W, int RM>
+__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
+                                                          const SpRec<T, W>* __restrict__ recs,
+                                                          const typename Cx<T>::t* __restrict__ tw2,
+                                                          typename Cx<T>::t* __restrict__ F1)
+{
+    k_spread_zfft_body<T, W, RM>(P, cstart, recs, tw2, F1, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // B / D: transforms along y.  One CTA per (c, x, chunk of 2^lmc z-modes).
 // forward: F1[c][x][y][mz] -> F2[c][x][my'][mz], my' = my + K1, |my| <= K1
 // inverse: F2 -> F1 (zero-padded to n1)
 // ---------------------------------------------------------------------------
 template <typename T, int RM>
-__global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::t* __restrict__ F1,
-                                                    typename Cx<T>::t* __restrict__ F2,
-                                                    const typename Cx<T>::t* __restrict__ tw1, int sign)
+__device__ __forceinline__ void k_fft_y_body(const FftYP& P, typename Cx<T>::t* __restrict__ F1,
+                                             typename Cx<T>::t* __restrict__ F2,
+                                             const typename Cx<T>::t* __restrict__ tw1, int sign, int bid)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -937,8 +961,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
     const int LS = P.ls;
     C* a = reinterpret_cast<C*>(smem_raw);
     const int nch = (nk + MC - 1) >> lmc;
-    const int cx = fdiv(blockIdx.x, P.d_nch);  // c * n0 + x
-    const int ch = blockIdx.x - cx * nch;
+    const int cx = fdiv(bid, P.d_nch);  // c * n0 + x
+    const int ch = bid - cx * nch;
     const int mz0 = ch << lmc;
     const int mcount = min(MC, nk - mz0);
     const int ny2 = 2 * K1 + 1;
@@ -992,17 +1016,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::
     }
 }
 
+template <typename T, int RM>
+__global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::t* __restrict__ F1,
+                                                    typename Cx<T>::t* __restrict__ F2,
+                                                    const typename Cx<T>::t* __restrict__ tw1, int sign)
+{
+    k_fft_y_body<T, RM>(P, F1, F2, tw1, sign, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // C: x forward FFT + k-space pass + x inverse FFT, in place on F2.
 // One CTA per (my', chunk of 2^lmc z-modes); the 3 components together (the
 // curl couples them).  tabs: e^{-k_d^2/4alpha^2} / F_d(m)^2 per axis.
 // ---------------------------------------------------------------------------
 template <typename T, int RM>
-__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
-                                                           typename Cx<T>::t* __restrict__ F2psi,
-                                                           const typename Cx<T>::t* __restrict__ tw0,
-                                                           const T* __restrict__ tab0, const T* __restrict__ tab1,
-                                                           const T* __restrict__ tab2)
+__device__ __forceinline__ void k_fft_x_kspace_body(const FftXP& P, typename Cx<T>::t* __restrict__ F2,
+                                                    typename Cx<T>::t* __restrict__ F2psi,
+                                                    const typename Cx<T>::t* __restrict__ tw0,
+                                                    const T* __restrict__ tab0, const T* __restrict__ tab1,
+                                                    const T* __restrict__ tab2, int bid)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1013,8 +1045,8 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P,
     const int want_psi = F2psi != nullptr;
     C* a = reinterpret_cast<C*>(smem_raw);  // lines [comp][mz], psi lines follow
     const int nch = (nk + MC - 1) >> lmc;
-    const int myp = fdiv(blockIdx.x, P.d_nch);
-    const int ch = blockIdx.x - myp * nch;
+    const int myp = fdiv(bid, P.d_nch);
+    const int ch = bid - myp * nch;
     const int mz0 = ch << lmc;
     const int mcount = min(MC, nk - mz0);
     C zero;
@@ -1147,7 +1179,7 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P,
             if (threadIdx.x == 0) {
                 double t = 0.0;
                 for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
-                P.epart[blockIdx.x] = t;
+                P.epart[bid] = t;
             }
         } else if ((threadIdx.x & 31) == 0 && esum != 0.0) {
             atomicAdd(P.energy, esum);
@@ -1172,6 +1204,16 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P,
             }
         }
     }
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
+                                                           typename Cx<T>::t* __restrict__ F2psi,
+                                                           const typename Cx<T>::t* __restrict__ tw0,
+                                                           const T* __restrict__ tab0, const T* __restrict__ tab1,
+                                                           const T* __restrict__ tab2)
+{
+    k_fft_x_kspace_body<T, RM>(P, F2, F2psi, tw0, tab0, tab1, tab2, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1273,11 +1315,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_fft_z_c2r(FftZP P, const typena
 // inside its block and adds it into the node's accumulator.
 // ---------------------------------------------------------------------------
 template <typename T, int W, int RM>
-__global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_zfft_interp(SpZP P, const int* __restrict__ cstart,
-                                                          const NdW<T, W>* __restrict__ nds,
-                                                          const typename Cx<T>::t* __restrict__ F1,
-                                                          const typename Cx<T>::t* __restrict__ tw2,
-                                                          T* __restrict__ vacc)
+__device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __restrict__ cstart,
+                                                   const NdW<T, W>* __restrict__ nds,
+                                                   const typename Cx<T>::t* __restrict__ F1,
+                                                   const typename Cx<T>::t* __restrict__ tw2, T* __restrict__ vacc,
+                                                   int bid)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1290,8 +1332,8 @@ __global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_
     const T* accf = reinterpret_cast<const T*>(cb);
     NdW<T, W>* srec = reinterpret_cast<NdW<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));
     const int tid = threadIdx.x;
-    const int by = fdiv(blockIdx.x, P.d_nbx);
-    const int bx = blockIdx.x - by * P.nbx;
+    const int by = fdiv(bid, P.d_nbx);
+    const int bx = bid - by * P.nbx;
     constexpr int H = W / 2;
     // the home ranges are fetched while the buffer is cleared
     int rb0, rlen;
@@ -1397,15 +1439,26 @@ __global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_
     }
 }
 
+template <typename T, int W, int RM>
+__global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_zfft_interp(SpZP P, const int* __restrict__ cstart,
+                                                          const NdW<T, W>* __restrict__ nds,
+                                                          const typename Cx<T>::t* __restrict__ F1,
+                                                          const typename Cx<T>::t* __restrict__ tw2,
+                                                          T* __restrict__ vacc)
+{
+    k_zfft_interp_body<T, W, RM>(P, cstart, nds, F1, tw2, vacc, blockIdx.x);
+}
+
 // One thread per node: grid cell and fraction (the interpolation's binning),
 // the 3 W kernel weights, and the node's rank within the block of its cell
 // (one atomic per run of equal blocks in a warp).
 template <typename T, int W>
-__global__ void k_node_w(InterpP P, int tx, int ty, int nbx, const double* __restrict__ nodes,
-                         NdW<T, W>* __restrict__ out, int* __restrict__ key, int* __restrict__ rank,
-                         int* __restrict__ cnt)
+__device__ __forceinline__ void k_node_w_body(const InterpP& P, int tx, int ty, int nbx,
+                                              const double* __restrict__ nodes, NdW<T, W>* __restrict__ out,
+                                              int* __restrict__ key, int* __restrict__ rank, int* __restrict__ cnt,
+                                              int bid)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = bid * blockDim.x + threadIdx.x;
     const bool live = j < P.N;
     constexpr int H = W / 2;
     int b = -1;
@@ -1447,12 +1500,29 @@ __global__ void k_node_w(InterpP P, int tx, int ty, int nbx, const double* __res
 }
 
 template <typename T, int W>
+__global__ void k_node_w(InterpP P, int tx, int ty, int nbx, const double* __restrict__ nodes,
+                         NdW<T, W>* __restrict__ out, int* __restrict__ key, int* __restrict__ rank,
+                         int* __restrict__ cnt)
+{
+    k_node_w_body<T, W>(P, tx, ty, nbx, nodes, out, key, rank, cnt, blockIdx.x);
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void k_node_scatter_body(int N, const NdW<T, W>* __restrict__ in,
+                                                    const int* __restrict__ key, const int* __restrict__ rank,
+                                                    const int* __restrict__ start, NdW<T, W>* __restrict__ out,
+                                                    int bid)
+{
+    const int j = bid * blockDim.x + threadIdx.x;
+    if (j < N) out[start[key[j]] + rank[j]] = in[j];
+}
+
+template <typename T, int W>
 __global__ void k_node_scatter(int N, const NdW<T, W>* __restrict__ in, const int* __restrict__ key,
                                const int* __restrict__ rank, const int* __restrict__ start,
                                NdW<T, W>* __restrict__ out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < N) out[start[key[j]] + rank[j]] = in[j];
+    k_node_scatter_body<T, W>(N, in, key, rank, start, out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1776,6 +1846,239 @@ cudaError_t launch_fft_z_c2r(const FftZP& P, const Work& w, cudaStream_t s, doub
     if (!w.grid) return cudaErrorInvalidValue;
     return by_rm<T>(P.plan2, FftZLaunch<T, T>{ P, w, (T*)w.grid, s });
 }
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch per stage for every member of a batch (member m
+// runs its blocks [bstart[m], bstart[m+1]) of the launch).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_col_count_b(const ColD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ColD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_col_count_body<T>(a.P, a.rec, a.n, a.cnt, bid);
+}
+
+template <typename T, int W>
+__global__ void k_col_scatter_b(const ColD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ColD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_col_scatter_body<T, W>(a.P, a.rec, a.n, a.cnt, (SpRec<T, W>*)a.out, nullptr, bid);
+}
+
+template <typename T, int W, int RM>
+__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft_b(const SpzD<T>* __restrict__ d,
+                                                                       const int* __restrict__ bs, int n)
+{
+    using C = typename Cx<T>::t;
+    int bid, nb;
+    const SpzD<T>& a = d[batch_member(bs, n, bid, nb)];
+    __shared__ SpZP sP;
+    batch_param_copy(sP, a.P);
+    k_spread_zfft_body<T, W, RM>(sP, a.cstart, (const SpRec<T, W>*)a.recs, (const C*)a.tw2, (C*)a.F1, bid);
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(kThreads, 2) k_fft_y_b(const FftYD<T>* __restrict__ d, const int* __restrict__ bs,
+                                                      int n)
+{
+    using C = typename Cx<T>::t;
+    int bid, nb;
+    const FftYD<T>& a = d[batch_member(bs, n, bid, nb)];
+    __shared__ FftYP sP;
+    batch_param_copy(sP, a.P);
+    k_fft_y_body<T, RM>(sP, (C*)a.F1, (C*)a.F2, (const C*)a.tw1, a.sign, bid);
+}
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace_b(const FftXD<T>* __restrict__ d,
+                                                                        const int* __restrict__ bs, int n)
+{
+    using C = typename Cx<T>::t;
+    int bid, nb;
+    const FftXD<T>& a = d[batch_member(bs, n, bid, nb)];
+    __shared__ FftXP sP;
+    batch_param_copy(sP, a.P);
+    k_fft_x_kspace_body<T, RM>(sP, (C*)a.F2, nullptr, (const C*)a.tw0, a.tab0, a.tab1, a.tab2, bid);
+}
+
+template <typename T, int W>
+__global__ void k_node_w_b(const NodeWD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const NodeWD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_node_w_body<T, W>(a.P, a.tx, a.ty, a.nbx, a.nodes, (NdW<T, W>*)a.rec, a.key, a.rank, a.cnt, bid);
+}
+
+template <typename T, int W>
+__global__ void k_node_scatter_b(const NodeWD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const NodeWD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_node_scatter_body<T, W>(a.P.N, (const NdW<T, W>*)a.rec, a.key, a.rank, a.cnt, (NdW<T, W>*)a.sorted, bid);
+}
+
+template <typename T, int W, int RM>
+__global__ void __launch_bounds__(z_threads_max<T>(), sizeof(T) == 4 ? 2 : 3) k_zfft_interp_b(
+    const SpzD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    using C = typename Cx<T>::t;
+    int bid, nb;
+    const SpzD<T>& a = d[batch_member(bs, n, bid, nb)];
+    __shared__ SpZP sP;
+    batch_param_copy(sP, a.P);
+    k_zfft_interp_body<T, W, RM>(sP, a.cstart, (const NdW<T, W>*)a.recs, (const C*)a.F1, (const C*)a.tw2, a.vacc,
+                                 bid);
+}
+
+#define BSW_BY_W(EXPR)                       \
+    switch (w) {                             \
+    case 2: { constexpr int W = 2; EXPR; break; }   \
+    case 4: { constexpr int W = 4; EXPR; break; }   \
+    case 6: { constexpr int W = 6; EXPR; break; }   \
+    case 8: { constexpr int W = 8; EXPR; break; }   \
+    case 10: { constexpr int W = 10; EXPR; break; } \
+    case 12: { constexpr int W = 12; EXPR; break; } \
+    case 14: { constexpr int W = 14; EXPR; break; } \
+    case 16: { constexpr int W = 16; EXPR; break; } \
+    default: return cudaErrorInvalidValue;   \
+    }
+
+template <typename T>
+cudaError_t launch_col_count_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_col_count_b<T><<<L.total, kThreads, 0, s>>>((const ColD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_col_scatter_b(int w, const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    BSW_BY_W((k_col_scatter_b<T, W><<<L.total, kThreads, 0, s>>>((const ColD<T>*)L.desc, L.bstart, L.n)));
+    return cudaGetLastError();
+}
+
+template <typename T, int W>
+static cudaError_t spz_b(const BatchL& L, cudaStream_t s)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_spread_zfft_b<T, W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    k_spread_zfft_b<T, W, 8><<<L.total, L.threads, L.smem, s>>>((const SpzD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread_zfft_b(int w, const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    BSW_BY_W(return (spz_b<T, W>(L, s)));
+    return cudaSuccess;
+}
+
+template <typename T>
+size_t fft_y_smem(const FftYP& P)
+{
+    return (size_t)(1 << P.lmc) * P.ls * sizeof(typename Cx<T>::t);
+}
+
+template <typename T>
+cudaError_t launch_fft_y_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fft_y_b<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    k_fft_y_b<T, 8><<<L.total, kThreads, L.smem, s>>>((const FftYD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t fft_x_smem(const FftXP& P)
+{
+    return (size_t)3 * (1 << P.lmc) * P.ls * sizeof(typename Cx<T>::t);
+}
+
+template <typename T>
+cudaError_t launch_fft_x_kspace_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_x_kspace_b<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    k_fft_x_kspace_b<T, 8><<<L.total, L.threads, L.smem, s>>>((const FftXD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_node_w_b(int w, const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    BSW_BY_W((k_node_w_b<T, W><<<L.total, kThreads, 0, s>>>((const NodeWD<T>*)L.desc, L.bstart, L.n)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_node_scatter_b(int w, const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    BSW_BY_W((k_node_scatter_b<T, W><<<L.total, kThreads, 0, s>>>((const NodeWD<T>*)L.desc, L.bstart, L.n)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t zfft_interp_smem(const SpZP& P)
+{
+    size_t r = 0;
+    const int w = P.w;
+    switch (w) {
+    case 2: r = sizeof(NdW<T, 2>); break;
+    case 4: r = sizeof(NdW<T, 4>); break;
+    case 6: r = sizeof(NdW<T, 6>); break;
+    case 8: r = sizeof(NdW<T, 8>); break;
+    case 10: r = sizeof(NdW<T, 10>); break;
+    case 12: r = sizeof(NdW<T, 12>); break;
+    case 14: r = sizeof(NdW<T, 14>); break;
+    default: r = sizeof(NdW<T, 16>); break;
+    }
+    return zlines_bytes<T>(3 * P.tx * P.ty / 2, P.cls) + kSpzChunk * r;
+}
+
+template <typename T, int W>
+static cudaError_t zi_b(const BatchL& L, cudaStream_t s)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_zfft_interp_b<T, W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    k_zfft_interp_b<T, W, 8><<<L.total, L.threads, L.smem, s>>>((const SpzD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zfft_interp_b(int w, const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    BSW_BY_W(return (zi_b<T, W>(L, s)));
+    return cudaSuccess;
+}
+#undef BSW_BY_W
+
+#define BSW_INST_B(T)                                                                  \
+    template cudaError_t launch_col_count_b<T>(const BatchL&, cudaStream_t);           \
+    template cudaError_t launch_col_scatter_b<T>(int, const BatchL&, cudaStream_t);    \
+    template cudaError_t launch_spread_zfft_b<T>(int, const BatchL&, cudaStream_t);    \
+    template cudaError_t launch_fft_y_b<T>(const BatchL&, cudaStream_t);               \
+    template cudaError_t launch_fft_x_kspace_b<T>(const BatchL&, cudaStream_t);        \
+    template cudaError_t launch_node_w_b<T>(int, const BatchL&, cudaStream_t);         \
+    template cudaError_t launch_node_scatter_b<T>(int, const BatchL&, cudaStream_t);   \
+    template cudaError_t launch_zfft_interp_b<T>(int, const BatchL&, cudaStream_t);    \
+    template size_t fft_y_smem<T>(const FftYP&);                                       \
+    template size_t fft_x_smem<T>(const FftXP&);                                       \
+    template size_t zfft_interp_smem<T>(const SpZP&);
+BSW_INST_B(float)
+BSW_INST_B(double)
+#undef BSW_INST_B
 
 template cudaError_t launch_col_sort<float>(const ColP&, const Work&, int, cudaStream_t, bool);
 template cudaError_t launch_col_sort<double>(const ColP&, const Work&, int, cudaStream_t, bool);

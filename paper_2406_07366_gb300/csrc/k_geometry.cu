@@ -180,16 +180,17 @@ __global__ void k_spline(const double* __restrict__ nodes, const int64_t* __rest
 // Sherman-Morrison vector) out of shared memory; all lanes apply the
 // correction and write the moments.  smem: 9 * nmax values of T.
 template <typename T>
-__global__ void k_spline_warp(const double* __restrict__ nodes, const int64_t* __restrict__ off,
-                              const double* __restrict__ shift, int nfil, int nmax, T* __restrict__ hseg,
-                              T* __restrict__ dp, T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ Tper)
+__device__ __forceinline__ void k_spline_warp_body(const double* __restrict__ nodes, const int64_t* __restrict__ off,
+                                                   const double* __restrict__ shift, int nfil, int nmax,
+                                                   T* __restrict__ hseg, T* __restrict__ dp, T* __restrict__ ds,
+                                                   T* __restrict__ Mm, T* __restrict__ Tper, int bid)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* sh_h = reinterpret_cast<T*>(sm_raw);  // n
     T* sh_dp = sh_h + nmax;                   // 3 n
     T* sh_r = sh_dp + 3 * nmax;               // 4 n: right-hand sides, then solutions
     T* sh_cp = sh_r + 4 * nmax;               // n: modified super-diagonal
-    const int f = blockIdx.x;
+    const int f = bid;
     if (f >= nfil) return;
     const int lane = threadIdx.x;
     const int64_t o = off[f];
@@ -282,6 +283,14 @@ __global__ void k_spline_warp(const double* __restrict__ nodes, const int64_t* _
     }
 }
 
+template <typename T>
+__global__ void k_spline_warp(const double* __restrict__ nodes, const int64_t* __restrict__ off,
+                              const double* __restrict__ shift, int nfil, int nmax, T* __restrict__ hseg,
+                              T* __restrict__ dp, T* __restrict__ ds, T* __restrict__ Mm, T* __restrict__ Tper)
+{
+    k_spline_warp_body<T>(nodes, off, shift, nfil, nmax, hseg, dp, ds, Mm, Tper, blockIdx.x);
+}
+
 // Wrap x into [0, L) (iL = 1/L); non-finite input maps to 0 and raises the flag.
 __device__ __forceinline__ double wrap_box(double x, double L, double iL, bool& bad)
 {
@@ -364,17 +373,20 @@ __device__ __forceinline__ void self_add(const T r[3], const T q[3], T alpha, T*
 }
 
 template <typename T>
-__global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __restrict__ fil_of,
-                        const int* __restrict__ prev, const int64_t* __restrict__ off, const double* __restrict__ shift,
-                        const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ ds,
-                        const T* __restrict__ Mm, const T* __restrict__ Tper, SrRec<T>* __restrict__ sr_rec,
-                        int* __restrict__ sr_key, LrRec<T>* __restrict__ lr_rec, int* __restrict__ lr_key,
-                        SrTgt<T>* __restrict__ tgt, double* __restrict__ vls, double* __restrict__ pls,
-                        double* __restrict__ part_local, double* __restrict__ part_self,
-                        double* __restrict__ psi_local, double* __restrict__ psi_self, int* __restrict__ status,
-                        const T* __restrict__ Dd)
+__device__ __forceinline__ void k_nodes_body(const GeomP& P, const double* __restrict__ nodes,
+                                             const int* __restrict__ fil_of, const int* __restrict__ prev,
+                                             const int64_t* __restrict__ off, const double* __restrict__ shift,
+                                             const T* __restrict__ hseg, const T* __restrict__ dp,
+                                             const T* __restrict__ ds, const T* __restrict__ Mm,
+                                             const T* __restrict__ Tper, SrRec<T>* __restrict__ sr_rec,
+                                             int* __restrict__ sr_key, LrRec<T>* __restrict__ lr_rec,
+                                             int* __restrict__ lr_key, SrTgt<T>* __restrict__ tgt,
+                                             double* __restrict__ vls, double* __restrict__ pls,
+                                             double* __restrict__ part_local, double* __restrict__ part_self,
+                                             double* __restrict__ psi_local, double* __restrict__ psi_self,
+                                             int* __restrict__ status, const T* __restrict__ Dd, int bid)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = bid * blockDim.x + threadIdx.x;
     if (j >= P.N) return;
     const int f = fil_of[j];
     const int jp = prev[j];
@@ -580,6 +592,73 @@ __global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __
     if (bad) flags |= ST_NONFINITE;
     if (flags) atomicOr(status, flags);
 }
+
+template <typename T>
+__global__ void k_nodes(GeomP P, const double* __restrict__ nodes, const int* __restrict__ fil_of,
+                        const int* __restrict__ prev, const int64_t* __restrict__ off, const double* __restrict__ shift,
+                        const T* __restrict__ hseg, const T* __restrict__ dp, const T* __restrict__ ds,
+                        const T* __restrict__ Mm, const T* __restrict__ Tper, SrRec<T>* __restrict__ sr_rec,
+                        int* __restrict__ sr_key, LrRec<T>* __restrict__ lr_rec, int* __restrict__ lr_key,
+                        SrTgt<T>* __restrict__ tgt, double* __restrict__ vls, double* __restrict__ pls,
+                        double* __restrict__ part_local, double* __restrict__ part_self,
+                        double* __restrict__ psi_local, double* __restrict__ psi_self, int* __restrict__ status,
+                        const T* __restrict__ Dd)
+{
+    k_nodes_body<T>(P, nodes, fil_of, prev, off, shift, hseg, dp, ds, Mm, Tper, sr_rec, sr_key, lr_rec, lr_key, tgt,
+        vls, pls, part_local, part_self, psi_local, psi_self, status, Dd, blockIdx.x);
+}
+
+// Batched forms: every member of a batch in one launch.
+template <typename T>
+__global__ void k_spline_warp_b(const SplineD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const SplineD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_spline_warp_body<T>(a.nodes, a.off, a.shift, a.nfil, a.nmax, a.hseg, a.dp, a.ds, a.Mm, a.Tper, bid);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_nodes_b(const NodesD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const NodesD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_nodes_body<T>(a.P, a.nodes, a.fil_of, a.prev, a.off, a.shift, a.hseg, a.dp, a.ds, a.Mm, a.Tper, a.sr_rec,
+                    a.sr_key, a.lr_rec, a.lr_key, a.tgt, a.vls, a.pls, nullptr, nullptr, nullptr, nullptr, a.status,
+                    a.Dd, bid);
+}
+
+template <typename T>
+size_t spline_smem(int nmax)
+{
+    return 9 * (size_t)nmax * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_spline_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total <= 0) return cudaSuccess;
+    if (L.smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_spline_warp_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L.smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_spline_warp_b<T><<<L.total, 32, L.smem, s>>>((const SplineD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nodes_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_nodes_b<T><<<L.total, 128, 0, s>>>((const NodesD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template size_t spline_smem<float>(int);
+template size_t spline_smem<double>(int);
+template cudaError_t launch_spline_b<float>(const BatchL&, cudaStream_t);
+template cudaError_t launch_spline_b<double>(const BatchL&, cudaStream_t);
+template cudaError_t launch_nodes_b<float>(const BatchL&, cudaStream_t);
+template cudaError_t launch_nodes_b<double>(const BatchL&, cudaStream_t);
 
 // Energy line integral (Sec. 2.4, Eq. kinetic_energy_streamfunction): per
 // filament, f_j = (psi_local + psi^(n) - psi^(f)_self)(s_j) . sdot(tau_j) at

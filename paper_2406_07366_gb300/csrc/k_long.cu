@@ -394,15 +394,42 @@ cudaError_t launch_interp(const InterpP& P, const double* nodes, const Work& w, 
 // long-range sums of the fused inverse-z interpolation, with the same sum
 // order as the interpolation kernel's epilogue.
 template <typename T>
-__global__ void k_interp_sum(int n3, const T* __restrict__ acc, const double* __restrict__ add_d,
-                             const double* __restrict__ add_t, double* __restrict__ out, double* __restrict__ part)
+__device__ __forceinline__ void k_interp_sum_body(int n3, const T* __restrict__ acc,
+                                                  const double* __restrict__ add_d, const double* __restrict__ add_t,
+                                                  double* __restrict__ out, double* __restrict__ part,
+                                                  int bid, int nb)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    for (int i = bid * blockDim.x + threadIdx.x; i < n3; i += nb * blockDim.x) {
         const double a = (double)acc[i];
         if (part) part[i] = a;
         if (out) out[i] = (a + (double)add_t[i]) + add_d[i];
     }
 }
+
+template <typename T>
+__global__ void k_interp_sum(int n3, const T* __restrict__ acc, const double* __restrict__ add_d,
+                             const double* __restrict__ add_t, double* __restrict__ out, double* __restrict__ part)
+{
+    k_interp_sum_body<T>(n3, acc, add_d, add_t, out, part, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void k_interp_sum_b(const SumD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const SumD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_interp_sum_body<T>(a.n3, a.acc, a.add_d, a.add_t, a.out, nullptr, bid, nb);
+}
+
+template <typename T>
+cudaError_t launch_interp_sum_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_interp_sum_b<T><<<L.total, 256, 0, s>>>((const SumD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_interp_sum_b<float>(const BatchL&, cudaStream_t);
+template cudaError_t launch_interp_sum_b<double>(const BatchL&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_interp_sum(int N, const Work& w, int what, double* out, double* part_long, cudaStream_t s)

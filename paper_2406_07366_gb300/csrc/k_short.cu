@@ -97,12 +97,13 @@ constexpr int kShortWarps = 8;  // warps per CTA of the warp-per-node kernel
 // has work however short the rows are.  Each lane finds the row of its candidate by a binary search over the
 // lanes' inclusive sums.  The per-lane partial sums are reduced at the end.
 template <typename T>
-__global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restrict__ tgt, const int* __restrict__ prev,
-                                               const int* __restrict__ start, const SrRec<T>* __restrict__ src,
-                                               double* __restrict__ vsr, double* __restrict__ psr)
+__device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __restrict__ tgt,
+                                             const int* __restrict__ prev, const int* __restrict__ start,
+                                             const SrRec<T>* __restrict__ src, double* __restrict__ vsr,
+                                             double* __restrict__ psr, int bid)
 {
     const int lane = threadIdx.x & 31;
-    const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int j = (int)((bid * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (j >= P.N) return;  // whole warps exit together
     const SrTgt<T> t = tgt[j];
     const int jp = prev[j];
@@ -254,6 +255,22 @@ __global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restr
             psr[3 * j + 2] = P.pref * (double)p2;
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_short(ShortP P, const SrTgt<T>* __restrict__ tgt, const int* __restrict__ prev,
+                                               const int* __restrict__ start, const SrRec<T>* __restrict__ src,
+                                               double* __restrict__ vsr, double* __restrict__ psr)
+{
+    k_short_body<T>(P, tgt, prev, start, src, vsr, psr, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_short_b(const ShortD<T>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ShortD<T>& a = d[batch_member(bs, n, bid, nb)];
+    k_short_body<T>(a.P, a.tgt, a.prev, a.start, a.src, a.vsr, a.psr, bid);
 }
 
 // ---------------------------------------------------------------------------
@@ -633,6 +650,16 @@ cudaError_t launch_short(const ShortP& P, const Work& w, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Batched: the warp-per-node kernel over every member (one warp per node).
+template <typename T>
+cudaError_t launch_short_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_short_b<T><<<L.total, 32 * kShortWarps, 0, s>>>((const ShortD<T>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_short_b<float>(const BatchL&, cudaStream_t);
+template cudaError_t launch_short_b<double>(const BatchL&, cudaStream_t);
 template cudaError_t launch_short<float>(const ShortP&, const Work&, cudaStream_t);
 template cudaError_t launch_short<double>(const ShortP&, const Work&, cudaStream_t);
 

@@ -12,10 +12,14 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 int scan_blocks(int n) { return (n + 1 + kScanTile - 1) / kScanTile; }
 
+__device__ __forceinline__ void count_body(const int* __restrict__ key, int n, int* __restrict__ cnt, int bid, int nb)
+{
+    for (int i = bid * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) atomicAdd(&cnt[key[i]], 1);
+}
+
 __global__ void k_count(const int* __restrict__ key, int n, int* __restrict__ cnt)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(&cnt[key[i]], 1);
+    count_body(key, n, cnt, blockIdx.x, gridDim.x);
 }
 
 // Block-wide inclusive scan of one value per thread; returns the block total.
@@ -46,10 +50,10 @@ __device__ __forceinline__ int block_scan_incl(int v, int* sh_warp, int& total)
 }
 
 // Phase 1: per-tile sums of cnt[0..n] (entry n counts as 0).
-__global__ void k_scan_reduce(const int* __restrict__ cnt, int n, int* __restrict__ part)
+__device__ __forceinline__ void scan_reduce_body(const int* __restrict__ cnt, int n, int* __restrict__ part, int bid)
 {
     __shared__ int sh[32];
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    const int base = bid * kScanTile + threadIdx.x * kScanItems;
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -58,11 +62,16 @@ __global__ void k_scan_reduce(const int* __restrict__ cnt, int n, int* __restric
     }
     int total;
     block_scan_incl(s, sh, total);
-    if (threadIdx.x == 0) part[blockIdx.x] = total;
+    if (threadIdx.x == 0) part[bid] = total;
+}
+
+__global__ void k_scan_reduce(const int* __restrict__ cnt, int n, int* __restrict__ part)
+{
+    scan_reduce_body(cnt, n, part, blockIdx.x);
 }
 
 // Phase 2: exclusive scan of the tile sums, one block, looping.
-__global__ void k_scan_parts(int* __restrict__ part, int nb)
+__device__ __forceinline__ void scan_parts_body(int* __restrict__ part, int nb)
 {
     __shared__ int sh[32];
     int carry = 0;
@@ -77,12 +86,14 @@ __global__ void k_scan_parts(int* __restrict__ part, int nb)
     }
 }
 
+__global__ void k_scan_parts(int* __restrict__ part, int nb) { scan_parts_body(part, nb); }
+
 // Phase 3: exclusive scan within each tile plus its offset, in place over
 // cnt[0..n]; cnt[n] becomes the grand total.
-__global__ void k_scan_apply(int* __restrict__ cnt, int n, const int* __restrict__ part)
+__device__ __forceinline__ void scan_apply_body(int* __restrict__ cnt, int n, const int* __restrict__ part, int bid)
 {
     __shared__ int sh[32];
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    const int base = bid * kScanTile + threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
 #pragma unroll
@@ -93,13 +104,18 @@ __global__ void k_scan_apply(int* __restrict__ cnt, int n, const int* __restrict
     }
     int total;
     const int inc = block_scan_incl(s, sh, total);
-    int run = part[blockIdx.x] + inc - s;
+    int run = part[bid] + inc - s;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int i = base + k;
         if (i <= n) cnt[i] = run;
         run += v[k];
     }
+}
+
+__global__ void k_scan_apply(int* __restrict__ cnt, int n, const int* __restrict__ part)
+{
+    scan_apply_body(cnt, n, part, blockIdx.x);
 }
 
 cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s)
@@ -114,15 +130,110 @@ cudaError_t scan_exclusive(int* cnt, int n, int* tmp, cudaStream_t s)
 // The order inside a bin follows the atomics; idx_out (if non-null) records
 // each copy's source index so that the bins can be re-ordered by it.
 template <typename R>
-__global__ void k_scatter(const int* __restrict__ key, const R* __restrict__ in, int n, int* __restrict__ cur,
-                          R* __restrict__ out, int* __restrict__ idx_out)
+__device__ __forceinline__ void scatter_body(const int* __restrict__ key, const R* __restrict__ in, int n,
+                                             int* __restrict__ cur, R* __restrict__ out, int* __restrict__ idx_out,
+                                             int bid, int nb)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = bid * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) {
         const int p = atomicAdd(&cur[key[i]], 1);
         out[p] = in[i];
         if (idx_out) idx_out[p] = i;
     }
 }
+
+template <typename R>
+__global__ void k_scatter(const int* __restrict__ key, const R* __restrict__ in, int n, int* __restrict__ cur,
+                          R* __restrict__ out, int* __restrict__ idx_out)
+{
+    scatter_body<R>(key, in, n, cur, out, idx_out, blockIdx.x, gridDim.x);
+}
+
+// ---- batched forms (one launch for every member of a batch) ----
+__global__ void k_zero_b(const ZeroD* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ZeroD& a = d[batch_member(bs, n, bid, nb)];
+    for (int i = bid * blockDim.x + threadIdx.x; i < a.n; i += nb * blockDim.x) a.p[i] = 0;
+}
+
+__global__ void k_copy_b(const CopyD* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const CopyD& a = d[batch_member(bs, n, bid, nb)];
+    for (int i = bid * blockDim.x + threadIdx.x; i < a.n; i += nb * blockDim.x) a.dst[i] = a.src[i];
+}
+
+__global__ void k_count_b(const CountD* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const CountD& a = d[batch_member(bs, n, bid, nb)];
+    count_body(a.key, a.n, a.cnt, bid, nb);
+}
+
+__global__ void k_scan_reduce_b(const ScanD* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ScanD& a = d[batch_member(bs, n, bid, nb)];
+    scan_reduce_body(a.cnt, a.n, a.part, bid);
+}
+
+__global__ void k_scan_parts_b(const ScanD* __restrict__ d, int n)
+{
+    const ScanD& a = d[blockIdx.x];
+    scan_parts_body(a.part, a.nb);
+}
+
+__global__ void k_scan_apply_b(const ScanD* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ScanD& a = d[batch_member(bs, n, bid, nb)];
+    scan_apply_body(a.cnt, a.n, a.part, bid);
+}
+
+template <typename R>
+__global__ void k_scatter_b(const ScatterD<R>* __restrict__ d, const int* __restrict__ bs, int n)
+{
+    int bid, nb;
+    const ScatterD<R>& a = d[batch_member(bs, n, bid, nb)];
+    scatter_body<R>(a.key, a.in, a.n, a.cur, a.out, nullptr, bid, nb);
+}
+
+cudaError_t launch_zero_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_zero_b<<<L.total, L.threads, 0, s>>>((const ZeroD*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_copy_b<<<L.total, L.threads, 0, s>>>((const CopyD*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_count_b<<<L.total, L.threads, 0, s>>>((const CountD*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_b(const BatchL& L1, const BatchL& L2, cudaStream_t s)
+{
+    if (L1.total <= 0) return cudaSuccess;
+    k_scan_reduce_b<<<L1.total, kScanThreads, 0, s>>>((const ScanD*)L1.desc, L1.bstart, L1.n);
+    k_scan_parts_b<<<L2.n, kScanThreads, 0, s>>>((const ScanD*)L2.desc, L2.n);
+    k_scan_apply_b<<<L1.total, kScanThreads, 0, s>>>((const ScanD*)L1.desc, L1.bstart, L1.n);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_scatter_b(const BatchL& L, cudaStream_t s)
+{
+    if (L.total > 0) k_scatter_b<R><<<L.total, L.threads, 0, s>>>((const ScatterD<R>*)L.desc, L.bstart, L.n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_scatter_b<SrRec<float>>(const BatchL&, cudaStream_t);
+template cudaError_t launch_scatter_b<SrRec<double>>(const BatchL&, cudaStream_t);
 
 // Warp per segment [start[s], start[s+1]): the copy with the r-th smallest key
 // goes to position start[s] + r (keys are distinct within a segment), records

@@ -1,9 +1,12 @@
 """Batches of independent configurations (``-m gpu``).
 
-Each member of a batch is evaluated by the same pipeline as a single
-context; the batch only changes how the members are issued (one CUDA graph,
-members on concurrent streams).  So every member must reproduce the result
-of its own single context, and, through that, the oracle.
+Each member of a batch is evaluated by the same stage kernels as a single
+context; the batch only changes how the members are issued: the staged group
+(small members, or BS_BATCH_STAGED) with one launch per stage for all its
+members (each running its own blocks with its own parameters), the other
+members (large, or BS_BATCH_PER_MEMBER) by themselves on concurrent streams,
+all in one CUDA graph.  So every member must reproduce the result of its own
+single context, and, through that, the oracle.
 """
 import math
 
@@ -49,16 +52,23 @@ def _single(B, p, f):
     return v
 
 
+ISSUE = {"staged": (1, 1, 1, 1, 1), "per_member": (0, 0, 0, 0, 0), "hybrid": (1, 0, 1, 0, 1)}
+
+
+@pytest.mark.parametrize("issue", sorted(ISSUE))
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_members_equal_single_contexts(prec):
+def test_batch_members_equal_single_contexts(prec, issue):
     B = _B()
     fs = _members()
     P = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
     params = [B.tangle_params(f.N, f.L, M_min=24, M_max=48, Q=2, w=8 if prec == "fp64" else 6, precision=P)
               for f in fs]
+    for p, g in zip(params, ISSUE[issue]):
+        p.flags |= B.BS_BATCH_STAGED if g else B.BS_BATCH_PER_MEMBER
     assert len({p.M[0] for p in params}) > 1  # the members have different grids
     s = torch.cuda.Stream()
     bt, nodes, vel = _run_batch(B, params, fs, s)
+    assert tuple(int(x) for x in bt.staged) == ISSUE[issue]
     off = bt.offsets
     assert list(np.diff(off)) == [f.N for f in fs]
     tol = 1e-12 if prec == "fp64" else 1e-6  # float atomics reorder the mixed sums
@@ -124,3 +134,54 @@ def test_batch_member_without_filaments_is_an_error():
         assert e.value.code == B.BS_ERR_STATE
     finally:
         B.bs_batch_destroy(b)
+
+
+def test_staged_batch_with_an_empty_member_and_mixed_widths():
+    """An empty member (no filaments) takes no blocks of the staged launches;
+    members of different kernel widths cannot share launches, so the member
+    whose width differs from the first grouped member's is issued by itself:
+    both give each member's single-context result."""
+    B = _B()
+    fs = _members(seed=61)[:2]
+    empty = W.Filaments(np.zeros((0, 3)), np.zeros(1, np.int64), np.zeros((0, 3), np.int32), fs[0].L, "empty")
+    for widths in ((8, 8, 8), (8, 8, 6)):
+        members = [fs[0], empty, fs[1]]
+        params = [B.tangle_params(max(f.N, 1), f.L, M_min=24, M_max=40, Q=2, w=wd, precision=B.BS_FP64)
+                  for f, wd in zip(members, widths)]
+        s = torch.cuda.Stream()
+        bt, nodes, vel = _run_batch(B, params, members, s)
+        assert list(bt.staged) == [True, False, widths[2] == 8]
+        off = bt.offsets
+        assert off[2] - off[1] == 0
+        for i in (0, 2):
+            ref = _single(B, params[i], members[i])
+            got = vel[off[i]:off[i + 1]]
+            assert (got - ref).abs().max().item() < 1e-12 * ref.abs().max().item(), (widths, i)
+        bt.close()
+
+
+def test_staged_group_follows_the_size_rule_and_flags():
+    """By default members of at most 8192 nodes join the staged group and
+    larger ones are issued by themselves; BS_BATCH_STAGED and
+    BS_BATCH_PER_MEMBER override the rule; both on one member is an error."""
+    B = _B()
+    small = W.fourier_tangle(nfil=20, N_l=50, seed=71)   # 1000 nodes
+    large = W.fourier_tangle(nfil=90, N_l=100, seed=72)  # 9000 nodes
+    fs = [small, large, small, large]
+    params = [B.tangle_params(f.N, f.L, M_min=24, M_max=48, Q=2, w=6, precision=B.BS_MIXED) for f in fs]
+    params[2].flags |= B.BS_BATCH_PER_MEMBER
+    params[3].flags |= B.BS_BATCH_STAGED
+    s = torch.cuda.Stream()
+    bt, nodes, vel = _run_batch(B, params, fs, s)
+    assert list(bt.staged) == [True, False, False, True]
+    off = bt.offsets
+    for i, (p, f) in enumerate(zip(params, fs)):
+        ref = _single(B, p, f)
+        got = vel[off[i]:off[i + 1]]
+        assert (got - ref).abs().max().item() < 1e-6 * ref.abs().max().item(), i
+    bt.close()
+    bad = B.tangle_params(small.N, small.L, M_min=24, M_max=32, Q=2, w=6, precision=B.BS_MIXED)
+    bad.flags |= B.BS_BATCH_STAGED | B.BS_BATCH_PER_MEMBER
+    with pytest.raises(B.BSError) as e:
+        B.bs_batch_create([bad], torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == B.BS_ERR_ARG
