@@ -312,7 +312,7 @@ int bs_rk4_launch(bs_ctx* ctx, int nsteps);
  * copied; BS_TIMING is ignored).  stream: cudaStream_t the batch runs on.
  * The staged group: members that take the plain velocity path (no
  * BS_WANT_PSI, BS_DETERMINISTIC, BS_FFT_CUFFT or BS_SHORT_TILED, cubic
- * curves, no subdivided local segments) and have at most 8192 nodes (or carry
+ * curves, no subdivided local segments) and have at most 2048 nodes (or carry
  * BS_BATCH_STAGED; never with BS_BATCH_PER_MEMBER), with the precision,
  * kernel width and z-column CTA size of the first of them.  Each stage of
  * the group's evaluation is ONE launch for all its members: member m runs

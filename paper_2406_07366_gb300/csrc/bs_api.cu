@@ -504,6 +504,9 @@ int alloc_grids(bs_ctx* c)
     }
     TRY(dalloc(c, c->alloc_g, &c->w.ktab, sizeof(T) * tab.size()));
     CUDA_TRY(cudaMemcpy(c->w.ktab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
+    // a copy from pageable memory may return before its DMA has landed, and
+    // the kernels run on streams that do not wait for the legacy stream
+    CUDA_TRY(cudaDeviceSynchronize());
     if (c->p.flags & BS_FFT_CUFFT) return make_plans<T>(c);
     return BS_OK;
 }
@@ -571,6 +574,8 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
         CUDA_TRY(cudaMemcpy(w.prev, prev.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
     }
     if (nf) CUDA_TRY(cudaMemcpy(w.shift, shift.data(), sizeof(double) * 3 * nf, cudaMemcpyHostToDevice));
+    // the copies from pageable memory may return before their DMA has landed
+    CUDA_TRY(cudaDeviceSynchronize());
     return BS_OK;
 }
 
@@ -1420,7 +1425,9 @@ int bs_status(bs_ctx* c)
     int st = 0;
     if (c->w.status) {
         CUDA_TRY(cudaMemcpy(&st, c->w.status, sizeof(int), cudaMemcpyDeviceToHost));
-        CUDA_TRY(cudaMemset(c->w.status, 0, sizeof(int)));
+        // cleared on the context's stream, before any later evaluation on it
+        CUDA_TRY(cudaMemsetAsync(c->w.status, 0, sizeof(int), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
     if (st & ST_NONFINITE) return fail(BS_ERR_NONFINITE, "non-finite node position");
     if (st & ST_GEOMETRY) return fail(BS_ERR_GEOMETRY, "a segment is longer than min(L)/4");
@@ -1458,7 +1465,7 @@ void bs_destroy(bs_ctx* c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
-    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);  // NULL: the legacy stream
     if (c->side) cudaStreamSynchronize(c->side);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
@@ -1489,12 +1496,13 @@ void bs_destroy(bs_ctx* c)
 // ---------------------------------------------------------------------------
 
 // Members up to this many nodes join the staged group by default.  Measured
-// on GB300 (mixed form, float32 kernels): 1024 members of ~400 nodes take
-// 12.2 ms staged against 20.0 ms issued one by one, 256 of ~1e3 nodes 6.8
-// against 7.7 ms; 64 members of 1e4..3e4 nodes take 19.2 against 16.1 ms and
-// 16 of ~1e5 nodes 12.2 against 11.4 ms (a stage ends only when its slowest
-// member does, where separate members overlap their stages).
-constexpr int64_t kStageMaxNodes = 8192;
+// on GB300 (mixed form, float32 kernels), staged against issued one by one:
+// 32 members of ~300 nodes 0.35 against 0.66 ms, 128 of ~300 1.13 against
+// 2.41 ms, 32 of ~1e3 0.94 against 1.08 ms, 128 of ~1e3 3.49 against 3.93 ms;
+// but 64 members of ~4e3 nodes 5.6 against 5.0 ms and 64 of 1e4..3e4 18.4
+// against 16.1 ms: a stage ends only when its slowest member does, where
+// separate members overlap their stages and kernel types.
+constexpr int64_t kStageMaxNodes = 2048;
 
 struct bs_batch {
     int nconf = 0;
@@ -1515,8 +1523,10 @@ struct bs_batch {
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> ev_done;
     cudaEvent_t ev_start = nullptr;
-    cudaStream_t side = nullptr;  // the staged group's short range
+    cudaStream_t gmain = nullptr;  // the staged group's long range
+    cudaStream_t side = nullptr;   // the staged group's short range
     cudaEvent_t ev_side = nullptr;
+    cudaEvent_t ev_group = nullptr;
     int device = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -1918,12 +1928,19 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
         }
         add(D, 256, 0);
     }
-    // upload, then turn the offsets into device pointers
+    // upload, then turn the offsets into device pointers.  The group's
+    // streams finish with the old tables first; the copy is ordered on the
+    // group's stream and waited for (a plain copy from pageable memory may
+    // return before its DMA lands, and the group's streams do not wait for
+    // the legacy stream it runs on).
+    CUDA_TRY(cudaStreamSynchronize(b->gmain));
+    CUDA_TRY(cudaStreamSynchronize(b->side));
     if (b->arena) cudaFree(b->arena);
     b->arena = nullptr;
     CUDA_TRY(cudaMalloc(&b->arena, A.bytes.size()));
     b->arena_bytes = A.bytes.size();
-    CUDA_TRY(cudaMemcpy(b->arena, A.bytes.data(), A.bytes.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpyAsync(b->arena, A.bytes.data(), A.bytes.size(), cudaMemcpyHostToDevice, b->gmain));
+    CUDA_TRY(cudaStreamSynchronize(b->gmain));
     for (BatchL& L : st) {
         L.desc = (const unsigned char*)b->arena + (size_t)L.desc;
         L.bstart = (const int*)((const unsigned char*)b->arena + (size_t)L.bstart);
@@ -2010,9 +2027,12 @@ int batch_issue(bs_batch* b, const double* nodes, double* vel)
     if (b->ngrouped > 0) {
         const int rc = batch_ensure_stages(b, nodes, vel);
         if (rc != BS_OK) return rc;
-        const int rs = group_f64(b) ? batch_issue_staged<double>(b, b->stream)
-                                    : batch_issue_staged<float>(b, b->stream);
+        CUDA_TRY(cudaStreamWaitEvent(b->gmain, b->ev_start, 0));
+        const int rs = group_f64(b) ? batch_issue_staged<double>(b, b->gmain)
+                                    : batch_issue_staged<float>(b, b->gmain);
         if (rs != BS_OK) return rs;
+        CUDA_TRY(cudaEventRecord(b->ev_group, b->gmain));
+        CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_group, 0));
     }
     for (size_t k = 0; k < b->pool.size(); ++k) {
         CUDA_TRY(cudaEventRecord(b->ev_done[k], b->pool[k]));
@@ -2030,16 +2050,19 @@ void bs_batch_destroy(bs_batch* b)
     if (!b) return;
     cudaSetDevice(b->device);
     for (cudaStream_t s : b->pool) cudaStreamSynchronize(s);
-    if (b->stream) cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->stream);
+    if (b->gmain) cudaStreamSynchronize(b->gmain);
+    if (b->side) cudaStreamSynchronize(b->side);
     batch_drop_graph(b);
     batch_drop_stages(b);
     for (bs_ctx* c : b->ctx) bs_destroy(c);
-    if (b->side) cudaStreamSynchronize(b->side);
     for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
     if (b->ev_start) cudaEventDestroy(b->ev_start);
     if (b->ev_side) cudaEventDestroy(b->ev_side);
+    if (b->ev_group) cudaEventDestroy(b->ev_group);
     for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
     if (b->side) cudaStreamDestroy(b->side);
+    if (b->gmain) cudaStreamDestroy(b->gmain);
     delete b;
 }
 
@@ -2053,6 +2076,11 @@ int bs_batch_create(bs_batch** out, int nconf, const bs_params* params, void* st
     b->node_off.assign(nconf + 1, 0);
     cudaError_t e = cudaGetDevice(&b->device);
     const int ns = std::min(nconf, 8);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    // the staged group's short range at the highest priority, as in a
+    // single context (17.2 against 17.7 ms for the 64-member batch staged
+    // whole); the pool and the group's long range at the default
     for (int k = 0; k < ns && e == cudaSuccess; ++k) {
         cudaStream_t s = nullptr;
         cudaEvent_t ev = nullptr;
@@ -2062,8 +2090,10 @@ int bs_batch_create(bs_batch** out, int nconf, const bs_params* params, void* st
         if (e == cudaSuccess) b->ev_done.push_back(ev);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gmain, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_side, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_group, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         const int rc = fail(BS_ERR_CUDA, "CUDA set-up failed: %s", cudaGetErrorString(e));
         bs_batch_destroy(b);
@@ -2165,7 +2195,11 @@ int bs_batch_status(bs_batch* b)
 {
     if (!b) return fail(BS_ERR_ARG, "null batch");
     CUDA_TRY(cudaSetDevice(b->device));
-    if (b->stream) CUDA_TRY(cudaStreamSynchronize(b->stream));
+    // every stream the batch issues on (the caller's may be the legacy one)
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (cudaStream_t s : b->pool) CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaStreamSynchronize(b->gmain));
+    CUDA_TRY(cudaStreamSynchronize(b->side));
     int first = BS_OK;
     for (int i = 0; i < b->nconf; ++i) {
         const int rc = bs_status(b->ctx[i]);

@@ -161,12 +161,12 @@ def test_staged_batch_with_an_empty_member_and_mixed_widths():
 
 
 def test_staged_group_follows_the_size_rule_and_flags():
-    """By default members of at most 8192 nodes join the staged group and
+    """By default members of at most 2048 nodes join the staged group and
     larger ones are issued by themselves; BS_BATCH_STAGED and
     BS_BATCH_PER_MEMBER override the rule; both on one member is an error."""
     B = _B()
     small = W.fourier_tangle(nfil=20, N_l=50, seed=71)   # 1000 nodes
-    large = W.fourier_tangle(nfil=90, N_l=100, seed=72)  # 9000 nodes
+    large = W.fourier_tangle(nfil=30, N_l=100, seed=72)  # 3000 nodes
     fs = [small, large, small, large]
     params = [B.tangle_params(f.N, f.L, M_min=24, M_max=48, Q=2, w=6, precision=B.BS_MIXED) for f in fs]
     params[2].flags |= B.BS_BATCH_PER_MEMBER
