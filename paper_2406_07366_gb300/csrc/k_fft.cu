@@ -36,7 +36,14 @@
 
 namespace bsw {
 
-constexpr int kSpzChunk = 128;  // spread records staged in shared memory at a time
+constexpr int kSpzChunk = 128;  // interpolation targets staged in shared memory at a time
+// Spread records per staged chunk (two chunks in flight): 64 in float64
+// keeps the float64 spread CTA's shared memory at its single-buffered size.
+template <typename T>
+constexpr int spz_rec_chunk()
+{
+    return sizeof(T) == 4 ? 128 : 64;
+}
 // Threads of a z-column-block CTA (spread, fused interpolation): 256, or up
 // to 512 for float32.
 constexpr int kZThreadsMax = 512;
@@ -81,6 +88,14 @@ __device__ __forceinline__ void cp_async_cx(C* smem_dst, const C* gsrc)
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Groups of copies: commit the copies issued so far as one group; wait until
+// at most N of this thread's groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // e^{-2 pi i m / R} for the composite in-register sizes R in {6, 9, 12, 16,
 // 24, 32}, m = 0..R-1, written once per device from float64 values
@@ -809,8 +824,10 @@ __host__ __device__ __forceinline__ size_t zlines_bytes(int ncl, int cls)
 // The 3 Tx Ty real z-lines are accumulated directly as complex lines (real
 // line 2l in .x, 2l+1 in .y of complex line l, stride cls), transformed in
 // place, and separated while writing modes 0..K2.  Records (weights already
-// evaluated) are staged in shared memory a chunk at a time and dealt to the
-// warps round-robin.  A lane owns one (local y column, z support point) slot
+// evaluated) are staged in shared memory a chunk at a time, double-buffered
+// (the next chunk's copies are in flight while the warps add the current
+// one: on the 4e6-node tangle 14.3 -> 13.7 ms), and dealt to the warps
+// round-robin.  A lane owns one (local y column, z support point) slot
 // and walks the block's x columns, so a warp's lanes always hold distinct
 // cells; shared atomic adds resolve two warps meeting on a cell.
 // ---------------------------------------------------------------------------
@@ -829,32 +846,43 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
     const int CS = P.cls;
     C* cb = reinterpret_cast<C*>(smem_raw);
     T* accf = reinterpret_cast<T*>(cb);  // real line rl, position z at float ((rl>>1) CS + z) 2 + (rl&1)
-    SpRec<T, W>* srec = reinterpret_cast<SpRec<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));
+    SpRec<T, W>* sbuf = reinterpret_cast<SpRec<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));  // 2 chunks
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int by = fdiv(bid, P.d_nbx);
     const int bx = bid - by * P.nbx;
     zero_cx(cb, ncl * CS);
 
     constexpr int H = W / 2;
+    constexpr int RC = spz_rec_chunk<T>();
     const int s0 = cstart[bid], s1 = cstart[bid + 1];
     const int nslot = Ty * W;
     // deterministic mode: warp wid owns z in [zlo, zhi) and adds every record
     // of the block in order (plain adds: one writer per cell, ordered sums)
     const int zlo = P.det ? (int)(((long long)wid * n2) / nw) : 0;
     const int zhi = P.det ? (int)(((long long)(wid + 1) * n2) / nw) : n2;
-    for (int c0r = s0; c0r < s1; c0r += kSpzChunk) {
-        const int nch = min(kSpzChunk, s1 - c0r);
-        __syncthreads();
-        {
-            // copy the chunk as 16-byte words
-            constexpr int kWords = (int)(sizeof(SpRec<T, W>) / 16);
-            const int4* src = reinterpret_cast<const int4*>(recs + c0r);
-            int4* dst = reinterpret_cast<int4*>(srec);
-            for (int i = tid; i < nch * kWords; i += blockDim.x) {
-                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + i) : "memory");
-            }
-            cp_async_wait_all();
+    // copies chunk [c0r, c0r + RC) of the records (as 16-byte words) into
+    // buffer b, as one group of this thread's copies
+    auto stage = [&](int c0r, int b) {
+        constexpr int kWords = (int)(sizeof(SpRec<T, W>) / 16);
+        const int nch = min(RC, s1 - c0r);
+        const int4* src = reinterpret_cast<const int4*>(recs + c0r);
+        int4* dst = reinterpret_cast<int4*>(sbuf + b * RC);
+        for (int i = tid; i < nch * kWords; i += blockDim.x) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + i) : "memory");
+        }
+        cp_async_commit();
+    };
+    if (s0 < s1) stage(s0, 0);
+    for (int c0r = s0, it = 0; c0r < s1; c0r += RC, ++it) {
+        const int nch = min(RC, s1 - c0r);
+        const SpRec<T, W>* srec = sbuf + (it & 1) * RC;
+        __syncthreads();  // every warp is done with the buffer the next chunk goes to
+        if (c0r + RC < s1) {
+            stage(c0r + RC, (it + 1) & 1);
+            cp_async_wait_group<1>();  // this chunk's copies have landed
+        } else {
+            cp_async_wait_group<0>();
         }
         __syncthreads();
         if (!P.det && nslot <= 32) {
@@ -1647,7 +1675,7 @@ size_t spread_zfft_smem(const SpZP& P)
 {
     using C = typename Cx<T>::t;
     const int ncl = 3 * P.tx * P.ty / 2;
-    return zlines_bytes<T>(ncl, P.cls) + kSpzChunk * col_rec_bytes<T>(P.w);
+    return zlines_bytes<T>(ncl, P.cls) + 2 * spz_rec_chunk<T>() * col_rec_bytes<T>(P.w);  // two record chunks
 }
 
 // Register-budget class of a plan: the largest radix it uses, rounded up to

@@ -48,12 +48,31 @@ __device__ __forceinline__ float erfcx_f(float x)
     constexpr float c[11] = { 1.441113045e-05f, 2.817091850e-01f, 2.866406861e-01f, 2.157398867e-01f,
                               3.128657818e-01f, -3.176314365e-01f, 7.893466267e-01f, -1.078447950e+00f,
                               7.163310796e-01f, -2.393311398e-01f, 3.276285984e-02f };
-    const float t = 1.0f / (1.0f + 0.5f * x);
+    const float t = __frcp_rn(1.0f + 0.5f * x);  // the correctly rounded 1 / (1 + x/2)
     float v = c[10];
 #pragma unroll
     for (int k = 9; k >= 0; --k) v = fmaf(v, t, c[k]);
     return v;
 }
+
+// 1 / sqrt(x) and exp(x) of the pair terms: float32 through the hardware
+// approximations (reciprocal square root; exp as 2^(x log2 e), whose scaled
+// argument costs about |x| 2^-24 relative, below 1e-6 for the |x| <= beta^2
+// the short range meets), float64 exact.  Measured on the 4e6-node tangle:
+// the short range 12.99 -> 11.89 ms with the accuracy against the converged
+// sum unchanged (rms 3.148e-6 / 3.150e-6).
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+template <typename T>
+__device__ __forceinline__ T exp_t(T x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return __expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 
 // erfc(x) given e = exp(-x^2): float32 through the fit above, float64 exact.
 template <typename T>
@@ -70,12 +89,12 @@ __device__ __forceinline__ void st_pair(T rx, T ry, T rz, T r2, const T* q, T al
                                         T& v2, T& p0, T& p1, T& p2)
 {
     const T two_over_sqrtpi = (T)1.12837916709551257390;
-    const T rr = sqrt(r2);
+    const T ir = rsqrt_t(r2);
+    const T rr = r2 * ir;
     const T x = alpha * rr;
-    const T e = exp(-x * x);
+    const T e = exp_t(-x * x);
     const T ec = erfc_e(x, e);
     const T g = ec + two_over_sqrtpi * x * e;
-    const T ir = (T)1 / rr;
     const T fv = g * ir * ir * ir;
     v0 += fv * (ry * q[2] - rz * q[1]);
     v1 += fv * (rz * q[0] - rx * q[2]);
@@ -213,12 +232,12 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
             rz = rz > (T)0.5 * L2 ? rz - L2 : (rz < (T)-0.5 * L2 ? rz + L2 : rz);
             const T r2 = rx * rx + ry * ry + rz * rz;
             if (r2 >= rc2 || r2 == (T)0) continue;
-            const T rr = sqrt(r2);
+            const T ir = rsqrt_t(r2);
+            const T rr = r2 * ir;
             const T x = alpha * rr;
-            const T e = exp(-x * x);
+            const T e = exp_t(-x * x);
             const T ec = erfc_e(x, e);
             const T g = ec + two_over_sqrtpi * x * e;
-            const T ir = (T)1 / rr;
             const T fv = g * ir * ir * ir;
             v0 += fv * (ry * S.q[2] - rz * S.q[1]);
             v1 += fv * (rz * S.q[0] - rx * S.q[2]);
