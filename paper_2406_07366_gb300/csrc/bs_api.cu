@@ -550,7 +550,8 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     TRY(dalloc(c, L, &w.lr_rec, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, &w.lr_sorted, sizeof(LrRec<T>) * NQ));
     TRY(dalloc(c, L, (void**)&w.lr_key, sizeof(int) * NQ));
-    TRY(dalloc(c, L, &w.col_rec, col_rec_bytes<T>(c->p.nufft_w) * NQ * (size_t)c->d.colcap));
+    TRY(dalloc(c, L, (void**)&w.col_rec, sizeof(int2) * NQ * (size_t)c->d.colcap));
+    TRY(dalloc(c, L, &w.col_pts, col_pt_bytes<T>(c->p.nufft_w) * NQ));
     if (c->d.fuse_interp) {
         TRY(dalloc(c, L, &w.nd_rec, nd_rec_bytes<T>(c->p.nufft_w) * N));
         TRY(dalloc(c, L, &w.nd_sorted, nd_rec_bytes<T>(c->p.nufft_w) * N));
@@ -561,8 +562,7 @@ int alloc_filaments(bs_ctx* c, const std::vector<int64_t>& off, const std::vecto
     if (c->p.flags & BS_DETERMINISTIC) {
         TRY(dalloc(c, L, (void**)&w.sr_idx, sizeof(int) * NQ));
         TRY(dalloc(c, L, &w.sr_sorted2, sizeof(SrRec<T>) * NQ));
-        TRY(dalloc(c, L, (void**)&w.col_idx, sizeof(int) * NQ * (size_t)c->d.colcap));
-        TRY(dalloc(c, L, &w.col_rec2, col_rec_bytes<T>(c->p.nufft_w) * NQ * (size_t)c->d.colcap));
+        TRY(dalloc(c, L, (void**)&w.col_rec2, sizeof(int2) * NQ * (size_t)c->d.colcap));
         TRY(dalloc(c, L, (void**)&w.lpart, sizeof(double) * std::max<size_t>(nf, 1)));
     }
     TRY(dalloc(c, L, (void**)&w.nodes_in, sizeof(double) * 3 * N));
@@ -1782,6 +1782,7 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
             e.n = (int)mem[m]->NQ;
             e.cnt = w.col_cnt;
             e.out = nullptr;
+            e.pts = nullptr;
             D.push_back(e);
             blk.push_back(cdiv(mem[m]->NQ, kThreads));
         }
@@ -1799,6 +1800,7 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
             e.n = (int)mem[m]->NQ;
             e.cnt = w.col_cur;
             e.out = w.col_rec;
+            e.pts = w.col_pts;
             D.push_back(e);
             blk.push_back(cdiv(mem[m]->NQ, kThreads));
         }
@@ -1814,6 +1816,7 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
             fill_spzp<T>(c, false, e.P);
             e.cstart = w.col_cnt;
             e.recs = w.col_rec;
+            e.pts = w.col_pts;
             e.tw2 = cx_at<T>(w.tw, c->d.ng[0] + c->d.ng[1]);
             e.F1 = w.spec;
             e.vacc = nullptr;
@@ -1910,6 +1913,7 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
             fill_spzp<T>(c, false, e.P);
             e.cstart = w.ncol_cnt;
             e.recs = w.nd_sorted;
+            e.pts = nullptr;
             e.tw2 = cx_at<T>(w.tw, c->d.ng[0] + c->d.ng[1]);
             e.F1 = w.spec;
             e.vacc = (T*)w.vacc;

@@ -43,16 +43,14 @@ template <typename T> struct __align__(16) SrTgt {
 
 // Long-range source: fractional grid position, charge, packed base index
 // (10 bits per axis).
-// Spread record of one point copied into one block of Tx x Ty z-columns
-// (Tx, Ty <= 4): the support start relative to the block (base: r0 + 128 |
-// (r1 + 128) << 8 | z index << 16), the charge, and the kernel weights
-// already evaluated: wx[lx] / wy[ly] for the block's local columns (zero
-// outside the support), wz[t] for the W support points along z.
-template <typename T, int W> struct __align__(16) SpRec {
-    int base;
+// Spread source with its charge and kernel weights along the three axes
+// (support point t of axis d at grid index ib_d - W/2 + 1 + t), written
+// once; every block of z-columns its support reaches holds its index.
+template <typename T, int W> struct __align__(16) SpPt {
+    int base;  // ib0 | ib1 << 10 | ib2 << 20
     T q[3];
-    T wx[4];
-    T wy[4];
+    T wx[W];
+    T wy[W];
     T wz[W];
 };
 
@@ -328,9 +326,8 @@ struct Work {
     // BS_DETERMINISTIC: the source index of every binned copy (scatter order),
     // the copies re-ordered by it, and float64 partial sums reduced in order
     int* sr_idx = nullptr;
-    int* col_idx = nullptr;
     void* sr_sorted2 = nullptr;
-    void* col_rec2 = nullptr;
+    int2* col_rec2 = nullptr; // the spread copies' entries in scatter order
     double* epart = nullptr;  // per-CTA energy partials of the x/k-space kernel
     double* lpart = nullptr;  // per-filament energy line integrals
     int nepart = 0;
@@ -339,7 +336,8 @@ struct Work {
     void* tw = nullptr;       // twiddles e^{-2 pi i j / n_d}, n0 + n1 + n2 complex
     void* f2 = nullptr;       // 3 x n0 x (2K1+1) x (K2+1) complex
     void* f2psi = nullptr;
-    void* col_rec = nullptr;  // duplicated spread records, by z-column block
+    int2* col_rec = nullptr;  // every copy's (source index, relative support start), by z-column block
+    void* col_pts = nullptr;  // SpPt per source (charge and kernel weights)
     int* col_cnt = nullptr;   // ncols + 1
     int* col_cur = nullptr;
     // fused inverse-z interpolation: the nodes with their weights, counting-
@@ -386,7 +384,7 @@ cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s
 template <typename T>
 cudaError_t launch_spread_zfft(const SpZP& P, const Work& w, cudaStream_t s);
 template <typename T>
-size_t col_rec_bytes(int w);
+size_t col_pt_bytes(int w);
 cudaError_t set_fft_constants();
 template <typename T>
 cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s);
@@ -431,6 +429,8 @@ template <typename R>
 cudaError_t launch_segsort(const int* start, int nseg, const R* in, const int* key, R* out, cudaStream_t s);
 cudaError_t launch_segsort_bytes(const int* start, int nseg, const void* in, const int* key, void* out,
                                  size_t rec_bytes, cudaStream_t s);
+// Warp per segment: the segment's pairs in increasing order of .x (distinct).
+cudaError_t launch_segsort_int2(const int* start, int nseg, const int2* in, int2* out, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_to_double(const void* in, double* out, int n, cudaStream_t s);
@@ -529,12 +529,14 @@ template <typename T> struct ColD {      // k_col_count (out unused) and k_col_s
     const LrRec<T>* rec;
     int n;
     int* cnt;                             // counts (count) or cursors (scatter)
-    void* out;                            // SpRec<T, W> copies
+    void* out;                            // int2 (source index, relative start) per copy (scatter)
+    void* pts;                            // SpPt<T, W>, one per source (scatter)
 };
 template <typename T> struct SpzD {      // k_spread_zfft and k_zfft_interp
     SpZP P;
     const int* cstart;
-    const void* recs;                     // SpRec<T, W> (spread) or NdW<T, W> (interpolation)
+    const void* recs;                     // int2 copy entries (spread) or NdW<T, W> (interpolation)
+    const void* pts;                      // SpPt<T, W> (spread)
     const void* tw2;
     void* F1;                             // written (spread) or read (interpolation)
     T* vacc;                              // interpolation sums

@@ -560,13 +560,14 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
     k_col_count_body<T>(P, rec, n, cnt, blockIdx.x);
 }
 
-// One thread per point: the 3 W kernel weights are evaluated once, then the
-// point is written into every block its support reaches, with the x and y
-// weights of that block's local columns picked out (zero outside the support).
+// One thread per point: the 3 W kernel weights are evaluated once and written
+// with the charge into pts[i]; every block its support reaches gets the pair
+// (i, support start relative to the block: r0 + 128 | (r1 + 128) << 8), 8
+// bytes per copy instead of the copy's weights.
 template <typename T, int W>
 __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>* __restrict__ rec, int n,
-                                                   int* __restrict__ cur, SpRec<T, W>* __restrict__ out,
-                                                   int* __restrict__ idx_out, int bid)
+                                                   int* __restrict__ cur, int2* __restrict__ out,
+                                                   SpPt<T, W>* __restrict__ pts, int bid)
 {
     const int i = bid * blockDim.x + threadIdx.x;
     constexpr int H = W / 2;
@@ -579,22 +580,23 @@ __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>
     }
     const int nk = __reduce_max_sync(0xffffffffu, nx * ny);
     if (nk == 0) return;
-    const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023, ib2 = (R.base >> 20) & 1023;
-    const T zeta = (T)P.zeta;
-    const T inorm = (T)P.inorm;
-    // weight of support point t along axis d: psi((f_d + H - 1 - t) / (W / 2))
-    T kx[W], ky[W];
-    SpRec<T, W> D;
+    const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023;
     if (i < n) {
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-            kx[t] = kb_val((R.f[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-            ky[t] = kb_val((R.f[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-            D.wz[t] = kb_val((R.f[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
-        }
+        // weight of support point t along axis d: psi((f_d + H - 1 - t) / (W / 2))
+        const T zeta = (T)P.zeta;
+        const T inorm = (T)P.inorm;
+        SpPt<T, W> D;
+        D.base = R.base;
         D.q[0] = R.q[0];
         D.q[1] = R.q[1];
         D.q[2] = R.q[2];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            D.wx[t] = kb_val((R.f[0] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+            D.wy[t] = kb_val((R.f[1] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+            D.wz[t] = kb_val((R.f[2] + (T)(H - 1 - t)) * ((T)2 / (T)W), zeta, inorm);
+        }
+        pts[i] = D;
     }
     for (int k = 0; k < nk; ++k) {
         const bool live = k < nx * ny;
@@ -603,33 +605,17 @@ __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>
         const int b = live ? col_wrap(bx, P.nbx) + P.nbx * col_wrap(by, P.nby) : -1;
         const int p = warp_rank(b, cur);
         if (!live) continue;
-        const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block
+        const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block (unwrapped block)
         const int r0 = ib0 - H + 1 - bx * P.tx;
-#pragma unroll
-        for (int ly = 0; ly < 4; ++ly) {
-            T v = (T)0;
-#pragma unroll
-            for (int t = 0; t < W; ++t) v = (t + r1 == ly) ? ky[t] : v;
-            D.wy[ly] = v;
-        }
-#pragma unroll
-        for (int lx = 0; lx < 4; ++lx) {
-            T v = (T)0;
-#pragma unroll
-            for (int t = 0; t < W; ++t) v = (t + r0 == lx) ? kx[t] : v;
-            D.wx[lx] = v;
-        }
-        D.base = (r0 + 128) | ((r1 + 128) << 8) | (ib2 << 16);
-        out[p] = D;
-        if (idx_out) idx_out[p] = i;
+        out[p] = make_int2(i, (r0 + 128) | ((r1 + 128) << 8));
     }
 }
 
 template <typename T, int W>
 __global__ void k_col_scatter(ColP P, const LrRec<T>* __restrict__ rec, int n, int* __restrict__ cur,
-                              SpRec<T, W>* __restrict__ out, int* __restrict__ idx_out)
+                              int2* __restrict__ out, SpPt<T, W>* __restrict__ pts)
 {
-    k_col_scatter_body<T, W>(P, rec, n, cur, out, idx_out, blockIdx.x);
+    k_col_scatter_body<T, W>(P, rec, n, cur, out, pts, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -823,17 +809,21 @@ __host__ __device__ __forceinline__ size_t zlines_bytes(int ncl, int cls)
 // A: spread + z real FFT.
 // The 3 Tx Ty real z-lines are accumulated directly as complex lines (real
 // line 2l in .x, 2l+1 in .y of complex line l, stride cls), transformed in
-// place, and separated while writing modes 0..K2.  Records (weights already
-// evaluated) are staged in shared memory a chunk at a time, double-buffered
-// (the next chunk's copies are in flight while the warps add the current
-// one: on the 4e6-node tangle 14.3 -> 13.7 ms), and dealt to the warps
-// round-robin.  A lane owns one (local y column, z support point) slot
-// and walks the block's x columns, so a warp's lanes always hold distinct
-// cells; shared atomic adds resolve two warps meeting on a cell.
+// place, and separated while writing modes 0..K2.  The block's sources come
+// as (index into the per-source records of charge and weights, support
+// start relative to the block) pairs written by the binning; a chunk of
+// records is gathered into shared memory with asynchronous copies,
+// double-buffered (the next chunk's copies are in flight while the warps add
+// the current one; each staging thread holds its next entry a chunk ahead),
+// and dealt to the warps round-robin.  A lane owns one (local y column, z
+// support point) slot and walks the block's x columns, so a warp's lanes
+// always hold distinct cells; shared atomic adds resolve two warps meeting
+// on a cell.
 // ---------------------------------------------------------------------------
 template <typename T, int W, int RM>
 __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __restrict__ cstart,
-                                                   const SpRec<T, W>* __restrict__ recs,
+                                                   const int2* __restrict__ cidx,
+                                                   const SpPt<T, W>* __restrict__ pts,
                                                    const typename Cx<T>::t* __restrict__ tw2,
                                                    typename Cx<T>::t* __restrict__ F1, int bid)
 {
@@ -846,7 +836,7 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
     const int CS = P.cls;
     C* cb = reinterpret_cast<C*>(smem_raw);
     T* accf = reinterpret_cast<T*>(cb);  // real line rl, position z at float ((rl>>1) CS + z) 2 + (rl&1)
-    SpRec<T, W>* sbuf = reinterpret_cast<SpRec<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));  // 2 chunks
+    SpPt<T, W>* sbuf = reinterpret_cast<SpPt<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));  // 2 chunks
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int by = fdiv(bid, P.d_nbx);
     const int bx = bid - by * P.nbx;
@@ -860,26 +850,39 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
     // of the block in order (plain adds: one writer per cell, ordered sums)
     const int zlo = P.det ? (int)(((long long)wid * n2) / nw) : 0;
     const int zhi = P.det ? (int)(((long long)(wid + 1) * n2) / nw) : n2;
-    // copies chunk [c0r, c0r + RC) of the records (as 16-byte words) into
-    // buffer b, as one group of this thread's copies
-    auto stage = [&](int c0r, int b) {
-        constexpr int kWords = (int)(sizeof(SpRec<T, W>) / 16);
-        const int nch = min(RC, s1 - c0r);
-        const int4* src = reinterpret_cast<const int4*>(recs + c0r);
-        int4* dst = reinterpret_cast<int4*>(sbuf + b * RC);
-        for (int i = tid; i < nch * kWords; i += blockDim.x) {
-            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + i) : "memory");
+    // thread tid < RC gathers the record of its copy into slot tid of buffer
+    // b (one group of this thread's copies; empty for the others) and writes
+    // the copy's relative support start beside it; the copy's entry is
+    // loaded a chunk ahead
+    __shared__ int s_rel[2][RC];
+    auto stage = [&](int b, int2 e) {
+        if (e.x >= 0) {
+            constexpr int kWords = (int)(sizeof(SpPt<T, W>) / 16);
+            const int4* src = reinterpret_cast<const int4*>(pts + e.x);
+            int4* dst = reinterpret_cast<int4*>(sbuf + b * RC + tid);
+#pragma unroll
+            for (int k = 0; k < kWords; ++k) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + k);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + k) : "memory");
+            }
+            s_rel[b][tid] = e.y;
         }
         cp_async_commit();
     };
-    if (s0 < s1) stage(s0, 0);
+    auto next_entry = [&](int c0r) {
+        return (tid < RC && c0r + tid < s1) ? __ldg(cidx + c0r + tid) : make_int2(-1, 0);
+    };
+    int2 nxt = next_entry(s0);
+    if (s0 < s1) stage(0, nxt);
+    nxt = next_entry(s0 + RC);
     for (int c0r = s0, it = 0; c0r < s1; c0r += RC, ++it) {
         const int nch = min(RC, s1 - c0r);
-        const SpRec<T, W>* srec = sbuf + (it & 1) * RC;
+        const SpPt<T, W>* srec = sbuf + (it & 1) * RC;
+        const int* srel = s_rel[it & 1];
         __syncthreads();  // every warp is done with the buffer the next chunk goes to
         if (c0r + RC < s1) {
-            stage(c0r + RC, (it + 1) & 1);
+            stage((it + 1) & 1, nxt);
+            nxt = next_entry(c0r + 2 * RC);
             cp_async_wait_group<1>();  // this chunk's copies have landed
         } else {
             cp_async_wait_group<0>();
@@ -894,20 +897,20 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
             const bool slot = lane < nslot;
             const int sx = Ty * CS, sc = txy * CS;
             for (int kk = wid; kk < nch; kk += nw) {
-                const SpRec<T, W>& R = srec[kk];
-                const int base = R.base;
-                const int r1 = ((base >> 8) & 255) - 128;
+                const SpPt<T, W>& R = srec[kk];
+                const int rr = srel[kk];
+                const int r1 = ((rr >> 8) & 255) - 128;
                 if (!slot || ly < r1 || ly > r1 + W - 1) continue;
-                const int ib2 = (base >> 16) & 1023;
-                const int r0 = (base & 255) - 128;
+                const int ib2 = (R.base >> 20) & 1023;
+                const int r0 = (rr & 255) - 128;
                 int z = ib2 - H + 1 + t;
                 z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
                 const int abase = ((ly >> 1) * CS + z) * 2 + (ly & 1);
-                const T wyz = R.wy[ly] * R.wz[t];
+                const T wyz = R.wy[ly - r1] * R.wz[t];
                 const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
                 const int lx0 = max(r0, 0), lx1 = min(r0 + W - 1, Tx - 1);  // the same in the whole warp
                 for (int lx = lx0; lx <= lx1; ++lx) {
-                    const T wv = R.wx[lx] * wyz;
+                    const T wv = R.wx[lx - r0] * wyz;
                     const int ad = abase + lx * sx;
                     atomicAdd(&accf[ad], wv * q0);
                     atomicAdd(&accf[ad + sc], wv * q1);
@@ -917,10 +920,10 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
             continue;
         }
         for (int kk = P.det ? 0 : wid; kk < nch; kk += P.det ? 1 : nw) {
-            const SpRec<T, W>& R = srec[kk];
-            const int base = R.base;
-            const int ib2 = (base >> 16) & 1023;
-            const int r0 = (base & 255) - 128, r1 = ((base >> 8) & 255) - 128;
+            const SpPt<T, W>& R = srec[kk];
+            const int rr = srel[kk];
+            const int ib2 = (R.base >> 20) & 1023;
+            const int r0 = (rr & 255) - 128, r1 = ((rr >> 8) & 255) - 128;
             const int a0 = max(r0, 0), e0 = min(r0 + W - 1, Tx - 1);
             const int a1 = max(r1, 0), e1 = min(r1 + W - 1, Ty - 1);
             const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
@@ -929,11 +932,11 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
                 if (ly < a1 || ly > e1) continue;
                 int z = ib2 - H + 1 + t;
                 z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
-                const T wyz = R.wy[ly] * R.wz[t];
+                const T wyz = R.wy[ly - r1] * R.wz[t];
                 if (P.det) {
                     if (z < zlo || z >= zhi) continue;
                     for (int lx = a0; lx <= e0; ++lx) {
-                        const T wv = R.wx[lx] * wyz;
+                        const T wv = R.wx[lx - r0] * wyz;
                         const int rl = lx * Ty + ly;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -945,7 +948,7 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
                     continue;
                 }
                 for (int lx = a0; lx <= e0; ++lx) {
-                    const T wv = R.wx[lx] * wyz;
+                    const T wv = R.wx[lx - r0] * wyz;
                     const int rl = lx * Ty + ly;  // real line of component 0
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -965,11 +968,12 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
 
 template <typename T, int W, int RM>
 __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, const int* __restrict__ cstart,
-                                                          const SpRec<T, W>* __restrict__ recs,
+                                                          const int2* __restrict__ cidx,
+                                                          const SpPt<T, W>* __restrict__ pts,
                                                           const typename Cx<T>::t* __restrict__ tw2,
                                                           typename Cx<T>::t* __restrict__ F1)
 {
-    k_spread_zfft_body<T, W, RM>(P, cstart, recs, tw2, F1, blockIdx.x);
+    k_spread_zfft_body<T, W, RM>(P, cstart, cidx, pts, tw2, F1, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1557,17 +1561,17 @@ __global__ void k_node_scatter(int N, const NdW<T, W>* __restrict__ in, const in
 // host launchers
 // ---------------------------------------------------------------------------
 template <typename T>
-size_t col_rec_bytes(int w)
+size_t col_pt_bytes(int w)
 {
     switch (w) {
-    case 2: return sizeof(SpRec<T, 2>);
-    case 4: return sizeof(SpRec<T, 4>);
-    case 6: return sizeof(SpRec<T, 6>);
-    case 8: return sizeof(SpRec<T, 8>);
-    case 10: return sizeof(SpRec<T, 10>);
-    case 12: return sizeof(SpRec<T, 12>);
-    case 14: return sizeof(SpRec<T, 14>);
-    case 16: return sizeof(SpRec<T, 16>);
+    case 2: return sizeof(SpPt<T, 2>);
+    case 4: return sizeof(SpPt<T, 4>);
+    case 6: return sizeof(SpPt<T, 6>);
+    case 8: return sizeof(SpPt<T, 8>);
+    case 10: return sizeof(SpPt<T, 10>);
+    case 12: return sizeof(SpPt<T, 12>);
+    case 14: return sizeof(SpPt<T, 14>);
+    case 16: return sizeof(SpPt<T, 16>);
     default: return 0;
     }
 }
@@ -1575,15 +1579,14 @@ size_t col_rec_bytes(int w)
 template <typename T, int W>
 static cudaError_t col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStream_t s, bool det)
 {
-    // deterministic: copies go to the second buffer with their point indices,
-    // then every column block is ordered by point index
+    // deterministic: the copies' entries go to the second buffer, then every
+    // column block is put in increasing source order
+    static_assert(sizeof(SpPt<T, W>) % 16 == 0, "records are gathered as 16-byte words");
     k_col_scatter<T, W><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(
-        P, (const LrRec<T>*)w.lr_rec, NQ, w.col_cur, (SpRec<T, W>*)(det ? w.col_rec2 : w.col_rec),
-        det ? w.col_idx : nullptr);
+        P, (const LrRec<T>*)w.lr_rec, NQ, w.col_cur, det ? w.col_rec2 : w.col_rec, (SpPt<T, W>*)w.col_pts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !det) return e;
-    static_assert(sizeof(SpRec<T, W>) % 16 == 0, "records are moved as 16-byte words");
-    return launch_segsort_bytes(w.col_cnt, P.ncols, w.col_rec2, w.col_idx, w.col_rec, sizeof(SpRec<T, W>), s);
+    return launch_segsort_int2(w.col_cnt, P.ncols, w.col_rec2, w.col_rec, s);
 }
 
 template <typename T>
@@ -1675,7 +1678,7 @@ size_t spread_zfft_smem(const SpZP& P)
 {
     using C = typename Cx<T>::t;
     const int ncl = 3 * P.tx * P.ty / 2;
-    return zlines_bytes<T>(ncl, P.cls) + 2 * spz_rec_chunk<T>() * col_rec_bytes<T>(P.w);  // two record chunks
+    return zlines_bytes<T>(ncl, P.cls) + 2 * spz_rec_chunk<T>() * col_pt_bytes<T>(P.w);  // two record chunks
 }
 
 // Register-budget class of a plan: the largest radix it uses, rounded up to
@@ -1711,7 +1714,8 @@ struct SpzLaunch {
             cudaFuncSetAttribute(k_spread_zfft<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_spread_zfft<T, W, RM><<<P.nbx * P.nby, z_threads<T>(P), sm, s>>>(
-            P, w.col_cnt, (const SpRec<T, W>*)w.col_rec, (const C*)w.tw + P.ng[0] + P.ng[1], (C*)w.spec);
+            P, w.col_cnt, w.col_rec, (const SpPt<T, W>*)w.col_pts, (const C*)w.tw + P.ng[0] + P.ng[1],
+            (C*)w.spec);
         return cudaGetLastError();
     }
 };
@@ -1892,7 +1896,7 @@ __global__ void k_col_scatter_b(const ColD<T>* __restrict__ d, const int* __rest
 {
     int bid, nb;
     const ColD<T>& a = d[batch_member(bs, n, bid, nb)];
-    k_col_scatter_body<T, W>(a.P, a.rec, a.n, a.cnt, (SpRec<T, W>*)a.out, nullptr, bid);
+    k_col_scatter_body<T, W>(a.P, a.rec, a.n, a.cnt, (int2*)a.out, (SpPt<T, W>*)a.pts, bid);
 }
 
 template <typename T, int W, int RM>
@@ -1904,7 +1908,8 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft_b(const S
     const SpzD<T>& a = d[batch_member(bs, n, bid, nb)];
     __shared__ SpZP sP;
     batch_param_copy(sP, a.P);
-    k_spread_zfft_body<T, W, RM>(sP, a.cstart, (const SpRec<T, W>*)a.recs, (const C*)a.tw2, (C*)a.F1, bid);
+    k_spread_zfft_body<T, W, RM>(sP, a.cstart, (const int2*)a.recs, (const SpPt<T, W>*)a.pts, (const C*)a.tw2,
+                                 (C*)a.F1, bid);
 }
 
 template <typename T, int RM>
@@ -2151,8 +2156,8 @@ cudaError_t set_fft_constants()
     return e;
 }
 
-template size_t col_rec_bytes<float>(int);
-template size_t col_rec_bytes<double>(int);
+template size_t col_pt_bytes<float>(int);
+template size_t col_pt_bytes<double>(int);
 template size_t spread_zfft_smem<float>(const SpZP&);
 template size_t spread_zfft_smem<double>(const SpZP&);
 

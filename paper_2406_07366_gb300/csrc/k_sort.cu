@@ -266,6 +266,32 @@ cudaError_t launch_segsort_bytes(const int* start, int nseg, const void* in, con
     return cudaGetLastError();
 }
 
+// Warp per segment [start[s], start[s+1]): its pairs in increasing order of
+// .x (distinct within a segment).
+__global__ void k_segsort_int2(const int* __restrict__ start, int nseg, const int2* __restrict__ in,
+                               int2* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int sg = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (sg >= nseg) return;
+    const int s0 = start[sg], n = start[sg + 1] - s0;
+    for (int a = lane; a < n; a += 32) {
+        const int2 ea = in[s0 + a];
+        int rank = 0;
+        for (int b = 0; b < n; ++b) rank += in[s0 + b].x < ea.x;
+        out[s0 + rank] = ea;
+    }
+}
+
+cudaError_t launch_segsort_int2(const int* start, int nseg, const int2* in, int2* out, cudaStream_t s)
+{
+    if (nseg <= 0) return cudaSuccess;
+    const int tb = 256;
+    const long long threads = 32LL * nseg;
+    k_segsort_int2<<<(unsigned)((threads + tb - 1) / tb), tb, 0, s>>>(start, nseg, in, out);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_segsort(const int* start, int nseg, const R* in, const int* key, R* out, cudaStream_t s)
 {
