@@ -113,8 +113,11 @@ constexpr int kShortWarps = 8;  // warps per CTA of the warp-per-node kernel
 // (2m+1)^2 neighbour rows (32 rows at a time; a row wrapping around the box
 // gives two ranges; rows and row ends beyond r_c are cut), prefix-sum their
 // lengths, then stride through the flattened candidate list, so every lane
-// has work however short the rows are.  Each lane finds the row of its candidate by a binary search over the
-// lanes' inclusive sums.  The per-lane partial sums are reduced at the end.
+// has work however short the rows are.  The non-empty rows go into a
+// per-warp table in shared memory; a lane finds the row of its candidate from
+// one OR-reduction per 32 candidates (which rows start in the window) and a
+// population count, and reads the row from the table.  The per-lane partial
+// sums are reduced at the end.
 template <typename T>
 __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __restrict__ tgt,
                                              const int* __restrict__ prev, const int* __restrict__ start,
@@ -122,6 +125,11 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
                                              double* __restrict__ psr, int bid)
 {
     const int lane = threadIdx.x & 31;
+    const int wslot = threadIdx.x >> 5;  // the warp's slot in the CTA's row tables
+    // per warp: a round's non-empty rows (first source of each run, run
+    // lengths, first candidate) and their y, z cell offsets
+    __shared__ int4 s_row[kShortWarps][32];
+    __shared__ int2 s_dyz[kShortWarps][32];
     const int j = (int)((bid * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (j >= P.N) return;  // whole warps exit together
     const SrTgt<T> t = tgt[j];
@@ -194,33 +202,41 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
             }
         }
         // inclusive prefix sum of the lanes' candidate counts
-        int inc = n0 + n1r;
+        const int nr = n0 + n1r;
+        int inc = nr;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += u;
         }
         const int total = __shfl_sync(0xffffffffu, inc, 31);
-        for (int cb = 0; cb < total; cb += 32) {  // warp-uniform trip count: every shuffle has all lanes
+        const int ex = inc - nr;  // the row's first candidate
+        // the non-empty rows in lane order, compacted into this warp's table
+        const unsigned nonempty = __ballot_sync(0xffffffffu, nr > 0);
+        if (nr > 0) {
+            const int ci = __popc(nonempty & ((1u << lane) - 1u));
+            s_row[wslot][ci] = make_int4(s0, n0, s1, ex);
+            s_dyz[wslot][ci] = make_int2(dyi, dzi);
+        }
+        __syncwarp();
+        // Candidate c belongs to the last non-empty row starting at or before
+        // it.  Per window of 32 candidates, bit b of M marks a row starting at
+        // cb + b; a lane's row is the one holding the window's first candidate
+        // minus one (jr) plus the starts up to its own candidate.
+        const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+        int jr = -1;
+        for (int cb = 0; cb < total; cb += 32) {  // warp-uniform trip count
+            const unsigned bit = (nr > 0 && ex >= cb && ex < cb + 32) ? (1u << (ex - cb)) : 0u;
+            const unsigned M = __reduce_or_sync(0xffffffffu, bit);
             const int c = cb + lane;
-            // owner lane: the first lane whose inclusive sum exceeds c
-            int lo = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int probe = __shfl_sync(0xffffffffu, inc, lo + step - 1);
-                if (probe <= c) lo += step;
-            }
-            lo = lo > 31 ? 31 : lo;
-            const int own_inc = __shfl_sync(0xffffffffu, inc, lo);
-            const int own_n0 = __shfl_sync(0xffffffffu, n0, lo);
-            const int own_n1 = __shfl_sync(0xffffffffu, n1r, lo);
-            const int own_s0 = __shfl_sync(0xffffffffu, s0, lo);
-            const int own_s1 = __shfl_sync(0xffffffffu, s1, lo);
-            const int own_dy = __shfl_sync(0xffffffffu, dyi, lo);
-            const int own_dz = __shfl_sync(0xffffffffu, dzi, lo);
+            const int own = jr + __popc(M & upto);
+            jr += __popc(M);
             if (c >= total) continue;
-            const int local = c - (own_inc - own_n0 - own_n1);
-            const int k = local < own_n0 ? own_s0 + local : own_s1 + (local - own_n0);
+            const int4 rw = s_row[wslot][own];
+            const int2 dyz = s_dyz[wslot][own];
+            const int own_dy = dyz.x, own_dz = dyz.y;
+            const int local = c - rw.w;
+            const int k = local < rw.y ? rw.x + local : rw.z + (local - rw.y);
             const SrRec<T> S = src[k];
             if (S.seg == j || S.seg == jp) continue;  // C_0 of the node (Eq. BS_on_vortex)
             T rx = (T)cdiff(S.cx, cx, nc0) * h0 + (S.o[0] - t.o[0]);
@@ -249,6 +265,7 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
                 p2 += fp * S.q[2];
             }
         }
+        __syncwarp();  // the table is rewritten by the next round of rows
     }
     // lane sums reduced in T (a float64 tree costs about 1.5 ms on the
     // 4e6-node tangle: float64 runs at 1/64 of the float32 rate here), the
