@@ -129,7 +129,8 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
     // per warp: a round's non-empty rows (first source of each run, run
     // lengths, first candidate) and their y, z cell offsets
     __shared__ int4 s_row[kShortWarps][32];
-    __shared__ int2 s_dyz[kShortWarps][32];
+    __shared__ int4 s_ofs[kShortWarps][32];   // x-cell offsets of the two runs, y and z cell offsets
+    __shared__ T s_dh[kShortWarps][32][2];    // y and z cell offsets times the cell edges
     const int j = (int)((bid * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (j >= P.N) return;  // whole warps exit together
     const SrTgt<T> t = tgt[j];
@@ -154,12 +155,17 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
     // keeps the cut conservative under rounding.
     const T rcm2 = rc2 * (T)1.0001;
     const T ih0 = (T)1 / h0;
+    // Candidates lie within m cells of the node's cell along each axis, so
+    // |r| < (m + 1) h; with at least 2 (m + 1) cells per axis that is below
+    // L/2 and the nearest cell image is already the minimum image: no wrap.
+    const bool wrap = nc0 < 2 * (m + 1) || nc1 < 2 * (m + 1) || nc2 < 2 * (m + 1);
 
     T v0 = 0, v1 = 0, v2 = 0, p0 = 0, p1 = 0, p2 = 0;
     for (int rb = 0; rb < nrows; rb += 32) {
         // this lane's row
         const int r = rb + lane;
         int s0 = 0, n0 = 0, s1 = 0, n1r = 0, dyi = 0, dzi = 0;
+        int xo0 = 0, xo1 = 0;  // x-cell offset from the node's cell: cell index + xo (per run)
         if (r < nrows) {
             const int iz = r / ny, iy = r - iz * ny;
             const int zc = fullz ? iz : imod(cz - m + iz, nc2);
@@ -186,10 +192,13 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
                     hi = cx + (hi > m ? m : hi);
                     if (lo < 0) {
                         xa0 = lo + nc0; xb0 = nc0 - 1; xa1 = 0; xb1 = hi;
+                        xo0 = -nc0 - cx; xo1 = -cx;
                     } else if (hi >= nc0) {
                         xa0 = lo; xb0 = nc0 - 1; xa1 = 0; xb1 = hi - nc0;
+                        xo0 = -cx; xo1 = nc0 - cx;
                     } else {
                         xa0 = lo; xb0 = hi;
+                        xo0 = -cx;
                     }
                 }
                 const int row = (zc * nc1 + yc) * nc0;
@@ -216,7 +225,9 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
         if (nr > 0) {
             const int ci = __popc(nonempty & ((1u << lane) - 1u));
             s_row[wslot][ci] = make_int4(s0, n0, s1, ex);
-            s_dyz[wslot][ci] = make_int2(dyi, dzi);
+            s_ofs[wslot][ci] = make_int4(xo0, xo1, dyi, dzi);
+            s_dh[wslot][ci][0] = (T)dyi * h1;
+            s_dh[wslot][ci][1] = (T)dzi * h2;
         }
         __syncwarp();
         // Candidate c belongs to the last non-empty row starting at or before
@@ -233,19 +244,27 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
             jr += __popc(M);
             if (c >= total) continue;
             const int4 rw = s_row[wslot][own];
-            const int2 dyz = s_dyz[wslot][own];
-            const int own_dy = dyz.x, own_dz = dyz.y;
             const int local = c - rw.w;
-            const int k = local < rw.y ? rw.x + local : rw.z + (local - rw.y);
+            const bool first = local < rw.y;
+            const int k = first ? rw.x + local : rw.z + (local - rw.y);
             const SrRec<T> S = src[k];
             if (S.seg == j || S.seg == jp) continue;  // C_0 of the node (Eq. BS_on_vortex)
-            T rx = (T)cdiff(S.cx, cx, nc0) * h0 + (S.o[0] - t.o[0]);
-            T ry = (T)own_dy * h1 + (S.o[1] - t.o[1]);
-            T rz = (T)own_dz * h2 + (S.o[2] - t.o[2]);
-            // exact minimum image when a cell difference sits at n/2
-            rx = rx > (T)0.5 * L0 ? rx - L0 : (rx < (T)-0.5 * L0 ? rx + L0 : rx);
-            ry = ry > (T)0.5 * L1 ? ry - L1 : (ry < (T)-0.5 * L1 ? ry + L1 : ry);
-            rz = rz > (T)0.5 * L2 ? rz - L2 : (rz < (T)-0.5 * L2 ? rz + L2 : rz);
+            T rx, ry, rz;
+            if (!wrap) {
+                const int4 of = s_ofs[wslot][own];
+                rx = (T)(S.cx + (first ? of.x : of.y)) * h0 + (S.o[0] - t.o[0]);
+                ry = s_dh[wslot][own][0] + (S.o[1] - t.o[1]);
+                rz = s_dh[wslot][own][1] + (S.o[2] - t.o[2]);
+            } else {
+                const int4 of = s_ofs[wslot][own];
+                rx = (T)cdiff(S.cx, cx, nc0) * h0 + (S.o[0] - t.o[0]);
+                ry = (T)of.z * h1 + (S.o[1] - t.o[1]);
+                rz = (T)of.w * h2 + (S.o[2] - t.o[2]);
+                // exact minimum image when a cell difference sits at n/2
+                rx = rx > (T)0.5 * L0 ? rx - L0 : (rx < (T)-0.5 * L0 ? rx + L0 : rx);
+                ry = ry > (T)0.5 * L1 ? ry - L1 : (ry < (T)-0.5 * L1 ? ry + L1 : ry);
+                rz = rz > (T)0.5 * L2 ? rz - L2 : (rz < (T)-0.5 * L2 ? rz + L2 : rz);
+            }
             const T r2 = rx * rx + ry * ry + rz * rz;
             if (r2 >= rc2 || r2 == (T)0) continue;
             const T ir = rsqrt_t(r2);
