@@ -456,11 +456,10 @@ def workload_params(spec, L, precision=BS_MIXED, flags=0) -> bs_params:
                        flags=flags)
 
 
-def tangle_batch_params(filaments, precision=BS_MIXED, flags=0):
+def tangle_batch_params(filaments, precision=BS_MIXED, flags=0, w=8):
     """Parameters of the members of a batch of tangles: beta = 3.5, grids of
-    32..128 modes matched to k_max (``tangle_params``), Q = 2, w = 6 for the
-    mixed form (8 for float64), sigma = 1.5."""
-    w = 6 if precision == BS_MIXED else 8
+    32..128 modes matched to k_max (``tangle_params``), Q = 2, kernel width w
+    (8: the 1e-6 setting of Table tab:performance, in both forms), sigma = 1.5."""
     return [tangle_params(f.N, f.L, beta=3.5, M_min=32, M_max=128, Q=2, w=w, sigma=1.5, precision=precision,
                           flags=flags) for f in filaments]
 

@@ -440,7 +440,7 @@ __device__ __forceinline__ void k_nodes_body(const GeomP& P, const double* __res
             int k = (int)(xw[c] * P.ihc[c]);
             k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
             ci[c] = k;
-            R.o[c] = (T)(xw[c] - k * P.hc[c]);
+            R.o[c] = (T)(xw[c] - (k + 0.5) * P.hc[c]);  // from the cell centre: half the magnitude
             R.q[c] = q[c];
         }
         R.cx = ci[0];
@@ -583,7 +583,7 @@ __device__ __forceinline__ void k_nodes_body(const GeomP& P, const double* __res
             int k = (int)(xw * P.ihc[c]);
             k = k < 0 ? 0 : (k >= P.nc[c] ? P.nc[c] - 1 : k);
             ci[c] = k;
-            tg.o[c] = (T)(xw - k * P.hc[c]);
+            tg.o[c] = (T)(xw - (k + 0.5) * P.hc[c]);
         }
         tg.cell = ci[0] + P.nc[0] * (ci[1] + P.nc[1] * ci[2]);
         tgt[j] = tg;

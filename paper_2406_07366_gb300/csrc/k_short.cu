@@ -155,6 +155,8 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
     // keeps the cut conservative under rounding.
     const T rcm2 = rc2 * (T)1.0001;
     const T ih0 = (T)1 / h0;
+    // offsets are from the cell centre; the node's position in its cell
+    const T ox = t.o[0] + (T)0.5 * h0, oy = t.o[1] + (T)0.5 * h1, oz = t.o[2] + (T)0.5 * h2;
     // Candidates lie within m cells of the node's cell along each axis, so
     // |r| < (m + 1) h; with at least 2 (m + 1) cells per axis that is below
     // L/2 and the nearest cell image is already the minimum image: no wrap.
@@ -174,8 +176,8 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
             dyi = cdiff(yc, cy, nc1);
             // gaps between the node and the row's y and z slabs
             T gy = (T)0, gz = (T)0;
-            if (!fully) gy = dyi > 0 ? dyi * h1 - t.o[1] : (dyi < 0 ? t.o[1] - (dyi + 1) * h1 : (T)0);
-            if (!fullz) gz = dzi > 0 ? dzi * h2 - t.o[2] : (dzi < 0 ? t.o[2] - (dzi + 1) * h2 : (T)0);
+            if (!fully) gy = dyi > 0 ? dyi * h1 - oy : (dyi < 0 ? oy - (dyi + 1) * h1 : (T)0);
+            if (!fullz) gz = dzi > 0 ? dzi * h2 - oz : (dzi < 0 ? oz - (dzi + 1) * h2 : (T)0);
             gy = gy > (T)0 ? gy : (T)0;
             gz = gz > (T)0 ? gz : (T)0;
             const T d2 = gy * gy + gz * gz;
@@ -187,7 +189,7 @@ __device__ __forceinline__ void k_short_body(const ShortP& P, const SrTgt<T>* __
                     xb0 = nc0 - 1;
                 } else {
                     const T ext = sqrt(rcm2 - d2);
-                    int lo = (int)floor((t.o[0] - ext) * ih0), hi = (int)floor((t.o[0] + ext) * ih0);
+                    int lo = (int)floor((ox - ext) * ih0), hi = (int)floor((ox + ext) * ih0);
                     lo = cx + (lo < -m ? -m : lo);
                     hi = cx + (hi > m ? m : hi);
                     if (lo < 0) {
@@ -488,9 +490,9 @@ __global__ void __launch_bounds__(kStWarps * 32) k_short_tile(ShortP P, const Sr
                 const SrRec<T> S = src[beg + k];
                 const int rx = fx ? S.cx - ox : imod(S.cx - fstx, nc0) - m;
                 StPos<T> sp;
-                sp.x = ((T)rx - cx0) * h0 + S.o[0];
-                sp.y = py * h1 + S.o[1];
-                sp.z = pz * h2 + S.o[2];
+                sp.x = ((T)rx - cx0 + (T)0.5) * h0 + S.o[0];  // offsets are from the cell centre
+                sp.y = (py + (T)0.5) * h1 + S.o[1];
+                sp.z = (pz + (T)0.5) * h2 + S.o[2];
                 sp.seg = S.seg;
                 spos[k - c0] = sp;
                 StChg<T> sq;
@@ -508,9 +510,9 @@ __global__ void __launch_bounds__(kStWarps * 32) k_short_tile(ShortP P, const Sr
             const SrTgt<T> tg = tgt[j];
             const int cell = tg.cell;
             const int tcx = cell % nc0 - ox, tcy = (cell / nc0) % nc1 - oy, tcz = cell / (nc0 * nc1) - oz;
-            const T px = ((T)tcx - cx0) * h0 + tg.o[0];
-            const T py = ((T)tcy - cy0) * h1 + tg.o[1];
-            const T pz = ((T)tcz - cz0) * h2 + tg.o[2];
+            const T px = ((T)tcx - cx0 + (T)0.5) * h0 + tg.o[0];
+            const T py = ((T)tcy - cy0 + (T)0.5) * h1 + tg.o[1];
+            const T pz = ((T)tcz - cz0 + (T)0.5) * h2 + tg.o[2];
             // the node's rows: staged rows within m cells (all rows of a full axis)
             const int iy0 = fy ? 0 : tcy, ny = fy ? cnty : 2 * m + 1;
             const int iz0 = fz ? 0 : tcz, nz = fz ? cntz : 2 * m + 1;

@@ -195,7 +195,7 @@ WORKLOADS = {
     "ellipses40": dict(gen=lambda: ellipses(), kappa=1.0, a=1e-6, delta=0.25, beta=3.5, M=64, Q=3, order=4,
                        sigma=1.5, w=8),
     "tangle1e5": dict(gen=lambda: fourier_tangle(1000, 100, seed=3), kappa=1.0, a=1e-6, delta=0.25, beta=3.5,
-                      M=256, Q=2, order=4, sigma=1.5, w=6),
+                      M=256, Q=2, order=4, sigma=1.5, w=8),
     "tangle4e6": dict(gen=lambda: fourier_tangle(20000, 200, seed=4), kappa=1.0, a=1e-6, delta=0.25, beta=3.5,
-                      M=512, Q=2, order=4, sigma=1.5, w=6),
+                      M=512, Q=2, order=4, sigma=1.5, w=8),
 }

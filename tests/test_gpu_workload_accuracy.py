@@ -7,7 +7,10 @@ tests/golden/make_oracle_samples.py, which calls only the oracle).  The
 gates are the rms relative errors of Sec. 5.1 (Eq. def_relative_errors):
   * float64 form: <= 1e-6, and within twice the Sec. 4 truncation estimate
     eps_v / v_rms (Eq. error_trunc_velocity) at beta = 3.5;
-  * mixed form (float32 kernels): <= 1e-5.
+  * mixed form (float32 kernels) at the workloads' w = 8: <= 1e-6, and every
+    sampled node within 1e-5;
+  * mixed form at w = 6 (the faster setting): <= 1e-5 (its worst nodes carry
+    the w = 6 NUFFT error of the long-range part, Appendix A).
 """
 import json
 import os
@@ -63,21 +66,21 @@ def _velocity(B, f, p):
     return out
 
 
-def _workload_params(B, name, prec):
-    spec = W.WORKLOADS[name]
+def _workload_params(B, name, prec, w=None):
+    spec = W.WORKLOADS[name] if w is None else dict(W.WORKLOADS[name], w=w)
     f = spec["gen"]()
     return f, B.workload_params(spec, f.L, prec)
 
 
 @pytest.mark.parametrize("name", ["tangle1e5", "tangle4e6"])
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_w6"])
 def test_benchmarked_tangle_against_oracle_samples(name, prec):
     """The random tangles of the benchmark (1000 x 100 nodes, M = 256; 20000 x
     200 nodes, M = 512), 256 sampled nodes each against the converged sum over
     every source."""
     import paper_2406_07366_gb300 as B
     doc = _golden(name)
-    f, p = _workload_params(B, name, B.BS_FP64 if prec == "fp64" else B.BS_MIXED)
+    f, p = _workload_params(B, name, B.BS_FP64 if prec == "fp64" else B.BS_MIXED, 6 if prec == "mixed_w6" else None)
     _same_nodes(f, doc)
     v = _velocity(B, f, p)
     assert np.all(np.isfinite(v))
@@ -94,6 +97,9 @@ def test_benchmarked_tangle_against_oracle_samples(name, prec):
         vrms = float(np.sqrt(np.mean(np.sum(vr ** 2, axis=1))))
         assert err < 1e-6, err
         assert err < 2 * eps_v / vrms, (err, eps_v / vrms)
+    elif prec == "mixed":
+        assert err < 1e-6, err
+        assert max_rel(v[tg], vr) < 1e-5
     else:
         assert err < 1e-5, err
         # the worst node stays within a few times the budget (the w = 6 NUFFT
@@ -103,8 +109,9 @@ def test_benchmarked_tangle_against_oracle_samples(name, prec):
 
 def test_benchmarked_batch_against_oracle_samples():
     """The 64-member batch of the benchmark (node counts log-uniform in
-    [1e3, 1e5], grids 41^3..128^3 modes, float32 kernels), 32 sampled nodes of
-    every member against the converged sum over that member's sources."""
+    [1e3, 1e5], grids 41^3..128^3 modes, float32 kernels, w = 8), 32 sampled
+    nodes of every member against the converged sum over that member's
+    sources."""
     import paper_2406_07366_gb300 as B
     doc = _golden("tangle_batch")
     fs = W.tangle_batch(nconf=64, seed=5)
@@ -125,4 +132,4 @@ def test_benchmarked_batch_against_oracle_samples():
         assert tg.size >= 32 or tg.size == f.N
         e = rms_rel(v[off[i]:off[i + 1]][tg], np.asarray(m["velocity"]))
         errs.append(e)
-    assert max(errs) < 1e-5, (int(np.argmax(errs)), max(errs))
+    assert max(errs) < 2e-6, (int(np.argmax(errs)), max(errs))
