@@ -200,6 +200,7 @@ struct Derived {
     // pruned-FFT pipeline
     FftPlan plan[3];
     int tx, ty, nbx, nby, ncols, colcap;  // z-column blocks; records per source at most
+    int nzb, ncolb;                       // z-buckets per block; bins of the spread copies (ncols nzb)
     int nshell;                            // spectrum shells reaching the mode cube's corner
     int lmcy, lmcx, yc;                   // log2 chunk sizes of the y and x passes; inverse-z chunk
     int zthreads;                         // threads of a z-column-block CTA (256 or 512)
@@ -311,6 +312,17 @@ int derive(const bs_params* p, Derived* d)
     d->nbx = d->ng[0] / d->tx;
     d->nby = d->ng[1] / d->ty;
     d->ncols = d->nbx * d->nby;
+    // the bucketed spread (copies of a block sorted by the z-bucket of their
+    // support start, partial sums in registers): even block height, a warp's
+    // lanes over (y column, z offset), two buckets' planes distinct; the
+    // deterministic mode keeps the record order of its own loop
+    {
+        const int W = p->nufft_w;
+        const bool bucketed = !(p->flags & BS_DETERMINISTIC) && d->ty % 2 == 0 && d->ty * W <= 32 &&
+                              d->ng[2] >= 2 * W;
+        d->nzb = bucketed ? (d->ng[2] + W - 1) / W : 1;
+        d->ncolb = d->ncols * d->nzb;
+    }
     d->colcap = ((p->nufft_w - 1) / d->tx + 2) * ((p->nufft_w - 1) / d->ty + 2);
     {
         const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
@@ -440,9 +452,9 @@ int alloc_grids(bs_ctx* c)
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.tile_cnt, sizeof(int) * (size_t)(d.ntiles + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.tile_cur, sizeof(int) * (size_t)(d.ntiles + 1)));
     TRY(dalloc(c, c->alloc_g, (void**)&c->w.scan_tmp2,
-               sizeof(int) * (size_t)std::max(scan_blocks(d.ntiles), scan_blocks(d.ncols))));
-    TRY(dalloc(c, c->alloc_g, (void**)&c->w.col_cnt, sizeof(int) * (size_t)(d.ncols + 1)));
-    TRY(dalloc(c, c->alloc_g, (void**)&c->w.col_cur, sizeof(int) * (size_t)(d.ncols + 1)));
+               sizeof(int) * (size_t)std::max(scan_blocks(d.ntiles), scan_blocks(d.ncolb))));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.col_cnt, sizeof(int) * (size_t)(d.ncolb + 1)));
+    TRY(dalloc(c, c->alloc_g, (void**)&c->w.col_cur, sizeof(int) * (size_t)(d.ncolb + 1)));
     {
         const size_t f2n = 3 * (size_t)d.ng[0] * (2 * d.K[1] + 1) * (d.K[2] + 1);
         TRY(dalloc(c, c->alloc_g, &c->w.f2, f2n * 2 * sizeof(T)));
@@ -679,6 +691,8 @@ void fill_colp(const bs_ctx* c, ColP& CP)
     CP.nby = d.nby;
     CP.ncols = d.ncols;
     CP.w = c->p.nufft_w;
+    CP.nzb = d.nzb;
+    CP.n2 = d.ng[2];
     CP.zeta = d.zeta;
     CP.inorm = 1.0 / (1.0 - exp(-2.0 * d.zeta));
 }
@@ -720,6 +734,7 @@ void fill_spzp(const bs_ctx* c, bool det, SpZP& SZ)
     SZ.nbx = d.nbx;
     SZ.nby = d.nby;
     SZ.w = p.nufft_w;
+    SZ.nzb = d.nzb;
     SZ.cls = line_stride(d.ng[2], 3 * d.tx * d.ty / 2, 128 / (2 * (int)sizeof(T)));
     SZ.ls = d.lsz;
     while (SZ.ls < SZ.cls) SZ.ls += 32;  // the real region also holds the complex lines
@@ -1768,10 +1783,11 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
         add(D, 256, 0);
     }
     auto col_cnt = [](bs_ctx* c) { return c->w.col_cnt; };
-    auto col_n = [](bs_ctx* c) { return c->d.ncols; };
+    auto colb_n = [](bs_ctx* c) { return c->d.ncolb; };  // spread bins: blocks x z-buckets
+    auto col_n = [](bs_ctx* c) { return c->d.ncols; };   // node bins: blocks
     auto col_tmp = [](bs_ctx* c) { return c->w.scan_tmp2; };
     auto col_cur = [](bs_ctx* c) { return c->w.col_cur; };
-    zero_stage(col_cnt, col_n);                                                            // 9 zero
+    zero_stage(col_cnt, colb_n);                                                           // 9 zero
     {   // 10 column count, 13 column scatter share the descriptor shape
         std::vector<ColD<T>> D;
         for (size_t m = 0; m < nm; ++m) {
@@ -1788,8 +1804,8 @@ int batch_build(bs_batch* b, const double* nodes, double* vel)
         }
         add(D, kThreads, 0);
     }
-    scan_stage(col_cnt, col_n, col_tmp);                                                   // 11, 12 scan
-    copy_stage(col_cnt, col_n, col_cur);                                                   // 13 copy
+    scan_stage(col_cnt, colb_n, col_tmp);                                                  // 11, 12 scan
+    copy_stage(col_cnt, colb_n, col_cur);                                                  // 13 copy
     {   // 14 column scatter
         std::vector<ColD<T>> D;
         for (size_t m = 0; m < nm; ++m) {

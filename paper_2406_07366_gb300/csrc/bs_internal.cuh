@@ -199,6 +199,8 @@ struct FftPlan {
 // Column binning of the spread records (blocks of tx x ty full z-columns).
 struct ColP {
     int tx, ty, nbx, nby, ncols, w;
+    int nzb;  // z-buckets per block (1: the copies of a block are not sorted by z)
+    int n2;   // grid points along z
     double zeta;   // kernel shape parameter
     double inorm;  // 1 / (1 - e^{-2 zeta}), the kernel's normalisation
 };
@@ -210,6 +212,7 @@ struct SpZP {
     int K[3];
     int tx, ty, nbx, nby;
     int w;
+    int nzb;            // z-buckets per block: > 1 selects the bucketed record loop
     int ls;             // padded stride of the real z-lines in shared memory
     int cls;            // complex line stride of the z FFT buffers
     double zeta;

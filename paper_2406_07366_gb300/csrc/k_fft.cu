@@ -44,6 +44,10 @@ constexpr int spz_rec_chunk()
 {
     return sizeof(T) == 4 ? 128 : 64;
 }
+// Spread copies per warp chunk in the bucketed record loop (two chunks per
+// warp in flight); with at most 512 threads in float32 and 256 in float64 the
+// warps' buffers fit in the two block-wide chunks above.
+constexpr int kSpzWarpChunk = 8;
 // Threads of a z-column-block CTA (spread, fused interpolation): 256, or up
 // to 512 for float32.
 constexpr int kZThreadsMax = 512;
@@ -533,22 +537,37 @@ __device__ __forceinline__ int col_wrap(int b, int nb)
     return b < 0 ? b + nb : (b >= nb ? b - nb : b);
 }
 
-// Copies per block.  The lanes of a warp take their k-th copies together,
-// one atomic per run of equal blocks (neighbouring points along a filament
+// Bin of a copy in block b: with P.nzb > 1 the copies of a block are further
+// sorted by the z-bucket of their support start (P.w planes per bucket) for
+// the bucketed spread; ib2 is the point's cell along z.
+__device__ __forceinline__ int col_bin(const ColP& P, int b, int ib2)
+{
+    if (P.nzb == 1) return b;
+    int z0 = ib2 - P.w / 2 + 1;
+    z0 = z0 < 0 ? z0 + P.n2 : z0;
+    return b * P.nzb + z0 / P.w;
+}
+
+// Copies per bin.  The lanes of a warp take their k-th copies together,
+// one atomic per run of equal bins (neighbouring points along a filament
 // mostly reach the same blocks).
 template <typename T>
 __device__ __forceinline__ void k_col_count_body(const ColP& P, const LrRec<T>* __restrict__ rec, int n,
                                                  int* __restrict__ cnt, int bid)
 {
     const int i = bid * blockDim.x + threadIdx.x;
-    int x0 = 0, nx = 0, y0 = 0, ny = 0;
-    if (i < n) col_span(P, rec[i].base, x0, nx, y0, ny);
+    int x0 = 0, nx = 0, y0 = 0, ny = 0, ib2 = 0;
+    if (i < n) {
+        const int base = rec[i].base;
+        col_span(P, base, x0, nx, y0, ny);
+        ib2 = (base >> 20) & 1023;
+    }
     const int nk = __reduce_max_sync(0xffffffffu, nx * ny);
     for (int k = 0; k < nk; ++k) {
         int b = -1;
         if (k < nx * ny) {
             const int ky = k / nx;
-            b = col_wrap(x0 + (k - ky * nx), P.nbx) + P.nbx * col_wrap(y0 + ky, P.nby);
+            b = col_bin(P, col_wrap(x0 + (k - ky * nx), P.nbx) + P.nbx * col_wrap(y0 + ky, P.nby), ib2);
         }
         warp_rank(b, cnt);
     }
@@ -602,7 +621,7 @@ __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>
         const bool live = k < nx * ny;
         const int kyi = live ? k / nx : 0;
         const int bx = x0 + (k - kyi * nx), by = y0 + kyi;
-        const int b = live ? col_wrap(bx, P.nbx) + P.nbx * col_wrap(by, P.nby) : -1;
+        const int b = live ? col_bin(P, col_wrap(bx, P.nbx) + P.nbx * col_wrap(by, P.nby), (R.base >> 20) & 1023) : -1;
         const int p = warp_rank(b, cur);
         if (!live) continue;
         const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block (unwrapped block)
@@ -820,6 +839,138 @@ __host__ __device__ __forceinline__ size_t zlines_bytes(int ncl, int cls)
 // always hold distinct cells; shared atomic adds resolve two warps meeting
 // on a cell.
 // ---------------------------------------------------------------------------
+// Bucketed record loop.  The block's copies come sorted by the z-bucket of
+// their support start (W planes per bucket, col_bin).  Warp wid takes an
+// equal share of them in that order and gathers them, 8 at a time, into its
+// own two buffers.  Lane (ly, t) holds in registers the sums of its cells
+// (lx, ly, zs + t) and (lx, ly, zs + W + t), lx < TX, for the 3 components,
+// zs the start of the warp's current bucket: a copy whose support starts at
+// plane zs + d (0 <= d < W) reaches the first cell when t >= d (weight
+// t - d), else the second (weight t - d + W), so every lane adds to one cell
+// per copy.  When the warp's bucket changes the first cells are added to the
+// block's lines (shared atomics: a neighbouring warp may hold the same
+// cells) and the second ones take their place; a jump of more than one
+// bucket adds both.  The lines see 3 TX atomic adds per lane and bucket
+// instead of per lane and copy.  Needs an even Ty, Ty W <= 32 and n2 >= 2 W
+// (the 2 W cells of a lane's window are distinct planes).
+template <typename T, int W, int TX>
+__device__ __forceinline__ void spread_bucketed(const SpZP& P, int s0, int s1, const int2* __restrict__ cidx,
+                                                const SpPt<T, W>* __restrict__ pts, SpPt<T, W>* sbuf, T* accf)
+{
+    constexpr int H = W / 2;
+    constexpr int RCW = kSpzWarpChunk;
+    constexpr int kWords = (int)(sizeof(SpPt<T, W>) / 16);
+    constexpr int kIt = (RCW * kWords + 31) / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int n2 = P.ng[2], Ty = P.ty, CS = P.cls;
+    const int sx = Ty * CS, sc = TX * Ty * CS;  // float offsets of lx + 1 and of component c + 1
+    const long long n = s1 - s0;
+    const int e0 = s0 + (int)((wid * n) / nw), e1 = s0 + (int)(((wid + 1) * n) / nw);
+    if (e0 >= e1) return;
+    SpPt<T, W>* wb = sbuf + wid * 2 * RCW;
+    const int ly = lane / W, t = lane - ly * W;
+    const bool slot = lane < Ty * W;
+    const int ab0 = ((ly >> 1) * CS) * 2 + (ly & 1);  // float offset of (lx 0, ly, z 0, component 0)
+    T lo[TX][3], hi[TX][3];
+#pragma unroll
+    for (int a = 0; a < TX; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[a][c] = 0;
+            hi[a][c] = 0;
+        }
+    auto flush = [&](const T (&v)[TX][3], int z) {
+        z = z >= n2 ? z - n2 : z;
+        if (slot) {
+            const int ab = ab0 + 2 * z;
+#pragma unroll
+            for (int a = 0; a < TX; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(&accf[ab + a * sx + c * sc], v[a][c]);
+        }
+    };
+    // gathers the copies [c0, min(c0 + RCW, e1)) into buffer b; lane k < RCW
+    // keeps copy k's relative support start
+    auto stage = [&](int b, int c0) {
+        const int2 e = (lane < RCW && c0 + lane < e1) ? __ldg(cidx + c0 + lane) : make_int2(-1, 0);
+#pragma unroll
+        for (int k = 0; k < kIt; ++k) {
+            const int wd = lane + 32 * k;
+            const int r = wd / kWords;
+            const int src = __shfl_sync(0xffffffffu, e.x, r < RCW ? r : 0);
+            if (wd < RCW * kWords && src >= 0) {
+                const int4* g = reinterpret_cast<const int4*>(pts + src) + (wd - r * kWords);
+                int4* d = reinterpret_cast<int4*>(wb + b * RCW + r) + (wd - r * kWords);
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(d);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+            }
+        }
+        cp_async_commit();
+        return e.y;
+    };
+    int zs = -1;  // start of the warp's current bucket (none yet)
+    int relc = stage(0, e0);
+    for (int c0 = e0, it = 0; c0 < e1; c0 += RCW, ++it) {
+        int reln = 0;
+        if (c0 + RCW < e1) {
+            reln = stage((it + 1) & 1, c0 + RCW);
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
+        }
+        __syncwarp();
+        const SpPt<T, W>* rb = wb + (it & 1) * RCW;
+        const int nch = min(RCW, e1 - c0);
+        for (int k = 0; k < nch; ++k) {
+            const int rr = __shfl_sync(0xffffffffu, relc, k);
+            const SpPt<T, W>& R = rb[k];
+            int zb = ((R.base >> 20) & 1023) - H + 1;
+            zb = zb < 0 ? zb + n2 : zb;
+            const int zsb = zb - zb % W;
+            if (zsb != zs) {  // the same in the whole warp
+                if (zs >= 0) {
+                    flush(lo, zs + t);
+                    if (zsb != zs + W) flush(hi, zs + W + t);
+#pragma unroll
+                    for (int a = 0; a < TX; ++a)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            lo[a][c] = zsb == zs + W ? hi[a][c] : (T)0;
+                            hi[a][c] = 0;
+                        }
+                }
+                zs = zsb;
+            }
+            const int d = zb - zs;
+            const int r0 = (rr & 255) - 128, jy = ly - (((rr >> 8) & 255) - 128);
+            if (slot && jy >= 0 && jy < W) {
+                const bool first = t >= d;
+                const T wyz = R.wy[jy] * R.wz[first ? t - d : t - d + W];
+                const T wl = first ? wyz : (T)0, wh = first ? (T)0 : wyz;
+                const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
+#pragma unroll
+                for (int a = 0; a < TX; ++a) {
+                    const int jx = a - r0;  // the same in the whole warp
+                    if (jx >= 0 && jx < W) {
+                        const T wx = R.wx[jx];
+                        const T vl = wx * wl, vh = wx * wh;
+                        lo[a][0] += vl * q0;
+                        lo[a][1] += vl * q1;
+                        lo[a][2] += vl * q2;
+                        hi[a][0] += vh * q0;
+                        hi[a][1] += vh * q1;
+                        hi[a][2] += vh * q2;
+                    }
+                }
+            }
+        }
+        __syncwarp();  // every lane is done with this buffer before it is refilled
+        relc = reln;
+    }
+    flush(lo, zs + t);
+    flush(hi, zs + W + t);
+}
+
 template <typename T, int W, int RM>
 __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __restrict__ cstart,
                                                    const int2* __restrict__ cidx,
@@ -844,8 +995,20 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
 
     constexpr int H = W / 2;
     constexpr int RC = spz_rec_chunk<T>();
-    const int s0 = cstart[bid], s1 = cstart[bid + 1];
+    const int s0 = cstart[bid * P.nzb], s1 = cstart[(bid + 1) * P.nzb];
     const int nslot = Ty * W;
+    if (P.nzb > 1) {
+        __syncthreads();  // the lines are zeroed
+        switch (Tx) {
+        case 1: spread_bucketed<T, W, 1>(P, s0, s1, cidx, pts, sbuf, accf); break;
+        case 2: spread_bucketed<T, W, 2>(P, s0, s1, cidx, pts, sbuf, accf); break;
+        default: spread_bucketed<T, W, 4>(P, s0, s1, cidx, pts, sbuf, accf); break;
+        }
+        __syncthreads();
+        fft_fwd_dif<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
+        spz_unpack<T>(P, cb, F1, bx, by);
+        return;
+    }
     // deterministic mode: warp wid owns z in [zlo, zhi) and adds every record
     // of the block in order (plain adds: one writer per cell, ordered sums)
     const int zlo = P.det ? (int)(((long long)wid * n2) / nw) : 0;
@@ -888,7 +1051,7 @@ __device__ __forceinline__ void k_spread_zfft_body(const SpZP& P, const int* __r
             cp_async_wait_group<0>();
         }
         __syncthreads();
-        if (!P.det && nslot <= 32) {
+        if (!P.det && nslot <= 32 && (Ty & 1) == 0) {
             // Fast path: every lane owns the same (y column, z offset) slot in
             // every record, so its slot indices and the parity of its real line
             // are fixed; the shared address of (lx, component c) is
@@ -1586,7 +1749,7 @@ static cudaError_t col_scatter_w(const ColP& P, const Work& w, int NQ, cudaStrea
         P, (const LrRec<T>*)w.lr_rec, NQ, w.col_cur, det ? w.col_rec2 : w.col_rec, (SpPt<T, W>*)w.col_pts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !det) return e;
-    return launch_segsort_int2(w.col_cnt, P.ncols, w.col_rec2, w.col_rec, s);
+    return launch_segsort_int2(w.col_cnt, P.ncols * P.nzb, w.col_rec2, w.col_rec, s);
 }
 
 template <typename T>
@@ -1608,13 +1771,14 @@ static cudaError_t launch_col_scatter_w(const ColP& P, const Work& w, int NQ, cu
 template <typename T>
 cudaError_t launch_col_sort(const ColP& P, const Work& w, int NQ, cudaStream_t s, bool det)
 {
-    cudaError_t e = cudaMemsetAsync(w.col_cnt, 0, sizeof(int) * (size_t)(P.ncols + 1), s);
+    const int nbins = P.ncols * P.nzb;
+    cudaError_t e = cudaMemsetAsync(w.col_cnt, 0, sizeof(int) * (size_t)(nbins + 1), s);
     if (e != cudaSuccess) return e;
     if (NQ > 0) k_col_count<T><<<(NQ + kThreads - 1) / kThreads, kThreads, 0, s>>>(P, (const LrRec<T>*)w.lr_rec, NQ,
                                                                                   w.col_cnt);
-    e = scan_exclusive(w.col_cnt, P.ncols, w.scan_tmp2, s);
+    e = scan_exclusive(w.col_cnt, nbins, w.scan_tmp2, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(w.col_cur, w.col_cnt, sizeof(int) * (size_t)P.ncols, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(w.col_cur, w.col_cnt, sizeof(int) * (size_t)nbins, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     if (NQ > 0)
         e = launch_col_scatter_w<T>(P, w, NQ, s, det);

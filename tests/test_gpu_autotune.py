@@ -63,7 +63,9 @@ def test_tile_autotune_changes_speed_not_results(prec):
     P = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
     base = B.make_params(f.L, beta=3.5, M=96, Q=2, w=6 if prec == "mixed" else 8, precision=P)
     nodes = torch.from_numpy(f.nodes).cuda()
-    cands = [(0, 0, 0, 0), (2, 4, 256, 2), (4, 4, 256, 3), (1, 2, 256, 1), (4, 4, 512, 2), (3, 4, 256, 2)]
+    # (2, 1): a block one column high takes the spread's generic record loop
+    cands = [(0, 0, 0, 0), (2, 4, 256, 2), (4, 4, 256, 3), (1, 2, 256, 1), (4, 4, 512, 2), (3, 4, 256, 2),
+             (2, 1, 256, 2)]
     best, ms = B.bs_autotune_tiles(base, f.offsets, f.closing, nodes, cands, reps=2)
     assert ms[5] == -1.0  # block_x = 3 is not a tile shape
     if prec == "fp64":
