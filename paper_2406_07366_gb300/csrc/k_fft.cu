@@ -581,8 +581,9 @@ __global__ void k_col_count(ColP P, const LrRec<T>* __restrict__ rec, int n, int
 
 // One thread per point: the 3 W kernel weights are evaluated once and written
 // with the charge into pts[i]; every block its support reaches gets the pair
-// (i, support start relative to the block: r0 + 128 | (r1 + 128) << 8), 8
-// bytes per copy instead of the copy's weights.
+// (i, support start relative to the block: r0 + 128 | (r1 + 128) << 8, with
+// the z support start's bucket and offset above), 8 bytes per copy instead
+// of the copy's weights.
 template <typename T, int W>
 __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>* __restrict__ rec, int n,
                                                    int* __restrict__ cur, int2* __restrict__ out,
@@ -600,6 +601,14 @@ __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>
     const int nk = __reduce_max_sync(0xffffffffu, nx * ny);
     if (nk == 0) return;
     const int ib0 = R.base & 1023, ib1 = (R.base >> 10) & 1023;
+    // z support start z0 = zs + d, zs a multiple of W: d in bits 16-19, zs in
+    // bits 20-29 of the copy's entry (read by the bucketed spread)
+    int zbits = 0;
+    {
+        int z0 = ((R.base >> 20) & 1023) - H + 1;
+        z0 = z0 < 0 ? z0 + P.n2 : z0;
+        zbits = ((z0 % W) << 16) | ((z0 - z0 % W) << 20);
+    }
     if (i < n) {
         // weight of support point t along axis d: psi((f_d + H - 1 - t) / (W / 2))
         const T zeta = (T)P.zeta;
@@ -626,7 +635,7 @@ __device__ __forceinline__ void k_col_scatter_body(const ColP& P, const LrRec<T>
         if (!live) continue;
         const int r1 = ib1 - H + 1 - by * P.ty;  // support start relative to the block (unwrapped block)
         const int r0 = ib0 - H + 1 - bx * P.tx;
-        out[p] = make_int2(i, (r0 + 128) | ((r1 + 128) << 8));
+        out[p] = make_int2(i, (r0 + 128) | ((r1 + 128) << 8) | zbits);
     }
 }
 
@@ -924,9 +933,7 @@ __device__ __forceinline__ void spread_bucketed(const SpZP& P, int s0, int s1, c
         for (int k = 0; k < nch; ++k) {
             const int rr = __shfl_sync(0xffffffffu, relc, k);
             const SpPt<T, W>& R = rb[k];
-            int zb = ((R.base >> 20) & 1023) - H + 1;
-            zb = zb < 0 ? zb + n2 : zb;
-            const int zsb = zb - zb % W;
+            const int zsb = rr >> 20;
             if (zsb != zs) {  // the same in the whole warp
                 if (zs >= 0) {
                     flush(lo, zs + t);
@@ -941,17 +948,28 @@ __device__ __forceinline__ void spread_bucketed(const SpZP& P, int s0, int s1, c
                 }
                 zs = zsb;
             }
-            const int d = zb - zs;
+            const int d = (rr >> 16) & 15;
             const int r0 = (rr & 255) - 128, jy = ly - (((rr >> 8) & 255) - 128);
-            if (slot && jy >= 0 && jy < W) {
+            if (slot && (unsigned)jy < (unsigned)W) {
                 const bool first = t >= d;
-                const T wyz = R.wy[jy] * R.wz[first ? t - d : t - d + W];
+                const int tz = (W & (W - 1)) == 0 ? ((t - d) & (W - 1)) : (first ? t - d : t - d + W);
+                const T wyz = R.wy[jy] * R.wz[tz];
                 const T wl = first ? wyz : (T)0, wh = first ? (T)0 : wyz;
-                const T q0 = R.q[0], q1 = R.q[1], q2 = R.q[2];
+                T q0, q1, q2;
+                if constexpr (sizeof(T) == 4) {
+                    const float4 bq = *reinterpret_cast<const float4*>(&R);  // base, q[0..2]
+                    q0 = bq.y;
+                    q1 = bq.z;
+                    q2 = bq.w;
+                } else {
+                    q0 = R.q[0];
+                    q1 = R.q[1];
+                    q2 = R.q[2];
+                }
 #pragma unroll
                 for (int a = 0; a < TX; ++a) {
                     const int jx = a - r0;  // the same in the whole warp
-                    if (jx >= 0 && jx < W) {
+                    if ((unsigned)jx < (unsigned)W) {
                         const T wx = R.wx[jx];
                         const T vl = wx * wl, vh = wx * wh;
                         lo[a][0] += vl * q0;
