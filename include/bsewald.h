@@ -399,7 +399,8 @@ int bs_autotune_tiles(const bs_params* base, int nfil, const int64_t* offsets, c
                       const double* nodes, int ncand, const int* cand, int reps, bs_params* best, float* ms_out);
 
 /* Synchronise the stream and return the device status word as a status
- * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY); clears it. */
+ * code (BS_OK, BS_ERR_NONFINITE, BS_ERR_GEOMETRY, BS_ERR_TIMEOUT when a
+ * kernel's bounded wait for its tensor copies gave up); clears it. */
 int bs_status(bs_ctx* ctx);
 
 /*

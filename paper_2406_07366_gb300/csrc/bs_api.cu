@@ -379,6 +379,11 @@ struct bs_ctx {
     double* rk = nullptr;  // RK4 workspace: k1..k4 and the stage positions, 5 x N x 3
     cudaGraph_t rk_graph = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
+    // tensor-copy descriptor of F1 for the y pass, built for the buffer
+    // tmy_for (rebuilt if the grids move)
+    CUtensorMap tmy;
+    const void* tmy_for = nullptr;
+    bool tmy_ok = false;
 };
 
 namespace {
@@ -763,6 +768,21 @@ void fill_fftyp(const bs_ctx* c, FftYP& YP)
     YP.rev = c->w.rev + d.ng[0];
     YP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcy) - 1) >> d.lmcy));
     YP.d_lines = make_fastdiv(1u << d.lmcy);
+    // tensor-copy boxes of at most 256 rows, a multiple of 8 rows each (whole
+    // 128-byte units in shared memory)
+    YP.tnb = (d.ng[1] + 255) / 256;
+    YP.tby = ((d.ng[1] + YP.tnb - 1) / YP.tnb + 7) & ~7;
+}
+
+// The y pass's descriptor of F1 (null: the per-element copy path).
+template <typename T>
+const CUtensorMap* tmap_y(bs_ctx* c, const FftYP& YP)
+{
+    if (c->tmy_for != c->w.spec) {
+        c->tmy_ok = make_tmap_y<T>(c->w.spec, YP, &c->tmy);
+        c->tmy_for = c->w.spec;
+    }
+    return c->tmy_ok ? &c->tmy : nullptr;
 }
 
 // The x pass with the velocity's k-space pass (no energy, spectrum or psi).
@@ -881,7 +901,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         rec(c, 5, s);
         FftYP YP;
         fill_fftyp<T>(c, YP);
-        CE(launch_fft_y<T>(YP, w, w.f2, -1, s));
+        CE(launch_fft_y<T>(YP, w, w.f2, -1, s, tmap_y<T>(c, YP)));
         rec(c, 6, s);
         FftXP XP;
         fill_fftxp<T>(c, XP);
@@ -896,7 +916,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
                                  : fail(BS_ERR_CUDA, "spectrum kernel launch failed");
         CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
         rec(c, 7, s);
-        CE(launch_fft_y<T>(YP, w, w.f2, +1, s));
+        CE(launch_fft_y<T>(YP, w, w.f2, +1, s, tmap_y<T>(c, YP)));
         if (fused) {
             rec(c, 8, s);
             CE(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -946,7 +966,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         } else {
             FftYP YP;
             fill_fftyp<T>(c, YP);
-            CE(launch_fft_y<T>(YP, w, w.f2psi, +1, s));
+            CE(launch_fft_y<T>(YP, w, w.f2psi, +1, s, tmap_y<T>(c, YP)));
             FftZP ZP;
             for (int k = 0; k < 3; ++k) {
                 ZP.ng[k] = d.ng[k];
@@ -1446,6 +1466,7 @@ int bs_status(bs_ctx* c)
     }
     if (st & ST_NONFINITE) return fail(BS_ERR_NONFINITE, "non-finite node position");
     if (st & ST_GEOMETRY) return fail(BS_ERR_GEOMETRY, "a segment is longer than min(L)/4");
+    if (st & ST_TIMEOUT) return fail(BS_ERR_TIMEOUT, "a tensor copy did not complete within its wait limit");
     return BS_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations of the bsewald CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (tensor-copy descriptors; encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
@@ -16,7 +17,7 @@ constexpr size_t kSplineSmemMax = 96 * 1024;  // warp-per-filament spline fit up
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 // Device status bits (bs_status).
-enum : int { ST_NONFINITE = 1, ST_GEOMETRY = 2 };
+enum : int { ST_NONFINITE = 1, ST_GEOMETRY = 2, ST_TIMEOUT = 4 };
 
 // Short-range source: offset from its cell origin, charge, x-cell index and
 // the global index of its segment (the node at the segment start).
@@ -226,6 +227,7 @@ struct FftYP {
     int K[3];
     int lmc;            // log2 of the chunk of z-modes per CTA
     int ls;             // line stride in shared memory
+    int tby, tnb;       // tensor copies of F1 (tnb > 0): rows per box, boxes per CTA
     FftPlan plan1;
     const int* rev;
     FastDiv d_nch, d_lines;
@@ -390,7 +392,13 @@ template <typename T>
 size_t col_pt_bytes(int w);
 cudaError_t set_fft_constants();
 template <typename T>
-cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s);
+cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s,
+                         const CUtensorMap* tm_f1 = nullptr);
+// Tensor-copy descriptor of F1 for the y pass: 3-D (2 nk reals, n1 rows,
+// 3 n0 lines), box (2 MC, tby, 1); false where the layout does not allow it
+// (float32 with an odd nk: rows not 16-byte multiples; MC < 2).
+template <typename T>
+bool make_tmap_y(void* F1, const FftYP& P, CUtensorMap* tm);
 template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s);
 // Inverse z transform into the real grid (w.grid), or, with out64, into a

@@ -32,6 +32,9 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cudaTypedefs.h>
+#include <string.h>
+
 #include "bs_internal.cuh"
 
 namespace bsw {
@@ -99,6 +102,70 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait_group()
 {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---- tensor copies (TMA) with an mbarrier, one phase per CTA ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of the barrier, at most about 2^31 clock cycles
+// (about a second); false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;
+    return true;
+}
+// Generic-proxy writes to shared memory made visible to the tensor copies.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Tiled 3-D tensor copy global -> shared (box of the map at x, y, z), its
+// bytes counted on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+// Tiled 3-D tensor copy shared -> global; elements outside the tensor are
+// not written.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int x, int y, int z, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(tm),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_commit_and_wait_read()
+{
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// First 128-byte aligned byte of the dynamic shared memory (tensor copies
+// need it; the launches ask for 128 more bytes).
+__device__ __forceinline__ unsigned char* smem_align128(unsigned char* p)
+{
+    return p + ((128u - (smem_u32(p) & 127u)) & 127u);
 }
 
 // e^{-2 pi i m / R} for the composite in-register sizes R in {6, 9, 12, 16,
@@ -259,7 +326,11 @@ __device__ __forceinline__ void apply_twiddles(typename Cx<T>::t* x, const typen
     for (int q = 1; q < R; ++q) x[q] = cmul(x[q], w[q]);
 }
 
-template <typename T, int R, bool DIF>
+// Line layouts: line-major (TR false: element e of line l at l ls + e) or
+// mode-major (TR true: at e nlines + l, the order a tiled bulk copy of rows
+// of consecutive modes leaves in shared memory; consecutive lanes on
+// consecutive lines read consecutive words).
+template <typename T, int R, bool DIF, bool TR = false>
 __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, int nlines, const FastDiv& dl, int ls,
                                          int n, int st, const FastDiv& sd, int tws,
                                          const typename Cx<T>::t* __restrict__ tw)
@@ -289,21 +360,22 @@ __device__ __forceinline__ void fft_pass(typename Cx<T>::t* __restrict__ buf, in
         }
         const int b = fdiv(i, sd);
         const int j = i - b * st;
-        C* p = buf + line * ls + b * L + j;
+        const int es = TR ? nlines : 1;  // element stride
+        C* p = TR ? buf + line + (b * L + j) * es : buf + line * ls + b * L + j;
         C x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = p[q * st];
+        for (int q = 0; q < R; ++q) x[q] = p[q * st * es];
         if (!DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * tws);
         dft<T, R, S>(x);
         if (DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * tws);
 #pragma unroll
-        for (int q = 0; q < R; ++q) p[q * st] = x[q];
+        for (int q = 0; q < R; ++q) p[q * st * es] = x[q];
     }
 }
 
 // The same pass with the plan and the line count fixed at compile time
 // (every stride, twiddle step and index division becomes a constant).
-template <typename T, int R, bool DIF, int N, int ST, int TWS, int NL>
+template <typename T, int R, bool DIF, int N, int ST, int TWS, int NL, bool TR>
 __device__ __forceinline__ void fft_pass_c(typename Cx<T>::t* __restrict__ buf, int ls,
                                            const typename Cx<T>::t* __restrict__ tw)
 {
@@ -322,44 +394,45 @@ __device__ __forceinline__ void fft_pass_c(typename Cx<T>::t* __restrict__ buf, 
         if (pad && line >= NL) continue;
         const int b = i / ST;
         const int j = i % ST;
-        C* p = buf + line * ls + b * L + j;
+        constexpr int ES = TR ? NL : 1;  // element stride
+        C* p = TR ? buf + line + (b * L + j) * ES : buf + line * ls + b * L + j;
         C x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = p[q * ST];
+        for (int q = 0; q < R; ++q) x[q] = p[q * ST * ES];
         if (!DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * TWS);
         dft<T, R, S>(x);
         if (DIF && j > 0) apply_twiddles<T, R, S>(x, tw, j * TWS);
 #pragma unroll
-        for (int q = 0; q < R; ++q) p[q * ST] = x[q];
+        for (int q = 0; q < R; ++q) p[q * ST * ES] = x[q];
     }
 }
 
 // Transform of plan (Rs...) with N = product of the radices and NL lines:
 // forward passes in plan order (stride N / R0 first), inverse in reverse.
-template <typename T, int NL, int N, int ST, int TWS, int R, int... Rest>
+template <typename T, bool TR, int NL, int N, int ST, int TWS, int R, int... Rest>
 __device__ __forceinline__ void fft_c_fwd(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
 {
-    fft_pass_c<T, R, true, N, ST / R, TWS, NL>(buf, ls, tw);
+    fft_pass_c<T, R, true, N, ST / R, TWS, NL, TR>(buf, ls, tw);
     __syncthreads();
-    if constexpr (sizeof...(Rest) > 0) fft_c_fwd<T, NL, N, ST / R, TWS * R, Rest...>(buf, ls, tw);
+    if constexpr (sizeof...(Rest) > 0) fft_c_fwd<T, TR, NL, N, ST / R, TWS * R, Rest...>(buf, ls, tw);
 }
 
-template <typename T, int NL, int N, int ST, int TWS, int R, int... Rest>
+template <typename T, bool TR, int NL, int N, int ST, int TWS, int R, int... Rest>
 __device__ __forceinline__ void fft_c_inv(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
 {
-    if constexpr (sizeof...(Rest) > 0) fft_c_inv<T, NL, N, ST / R, TWS * R, Rest...>(buf, ls, tw);
-    fft_pass_c<T, R, false, N, ST / R, TWS, NL>(buf, ls, tw);
+    if constexpr (sizeof...(Rest) > 0) fft_c_inv<T, TR, NL, N, ST / R, TWS * R, Rest...>(buf, ls, tw);
+    fft_pass_c<T, R, false, N, ST / R, TWS, NL, TR>(buf, ls, tw);
     __syncthreads();
 }
 
-template <typename T, bool DIF, int NL, int... Rs>
+template <typename T, bool DIF, bool TR, int NL, int... Rs>
 __device__ __forceinline__ void fft_c(typename Cx<T>::t* buf, int ls, const typename Cx<T>::t* __restrict__ tw)
 {
     constexpr int N = (Rs * ...);
     if constexpr (DIF)
-        fft_c_fwd<T, NL, N, N, 1, Rs...>(buf, ls, tw);
+        fft_c_fwd<T, TR, NL, N, N, 1, Rs...>(buf, ls, tw);
     else
-        fft_c_inv<T, NL, N, N, 1, Rs...>(buf, ls, tw);
+        fft_c_inv<T, TR, NL, N, N, 1, Rs...>(buf, ls, tw);
 }
 
 template <int... Rs>
@@ -376,30 +449,30 @@ __device__ __forceinline__ bool plan_is(const FftPlan& pl)
 // Plans with a compiled form (float): 384 = 8 x 8 x 6 at 12, 16 or 24 lines
 // (the 1e5-node tangle), 768 = 8 x 6 x 4 x 4 at 6, 8, 12 or 16 lines (the 4e6-node
 // tangle), 192 = 8 x 6 x 4 at 16 or 24 lines (the largest batch members).
-template <typename T, bool DIF>
+template <typename T, bool DIF, bool TR = false>
 __device__ __forceinline__ bool fft_const(typename Cx<T>::t* buf, int nlines, int ls, const FftPlan& pl,
                                           const typename Cx<T>::t* __restrict__ tw)
 {
     if constexpr (sizeof(T) == 4) {
         if (plan_is<8, 8, 6>(pl)) {
             switch (nlines) {
-            case 12: fft_c<T, DIF, 12, 8, 8, 6>(buf, ls, tw); return true;
-            case 16: fft_c<T, DIF, 16, 8, 8, 6>(buf, ls, tw); return true;
-            case 24: fft_c<T, DIF, 24, 8, 8, 6>(buf, ls, tw); return true;
+            case 12: fft_c<T, DIF, TR, 12, 8, 8, 6>(buf, ls, tw); return true;
+            case 16: fft_c<T, DIF, TR, 16, 8, 8, 6>(buf, ls, tw); return true;
+            case 24: fft_c<T, DIF, TR, 24, 8, 8, 6>(buf, ls, tw); return true;
             default: break;
             }
         } else if (plan_is<8, 6, 4, 4>(pl)) {
             switch (nlines) {
-            case 6: fft_c<T, DIF, 6, 8, 6, 4, 4>(buf, ls, tw); return true;
-            case 8: fft_c<T, DIF, 8, 8, 6, 4, 4>(buf, ls, tw); return true;
-            case 12: fft_c<T, DIF, 12, 8, 6, 4, 4>(buf, ls, tw); return true;
-            case 16: fft_c<T, DIF, 16, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 6: fft_c<T, DIF, TR, 6, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 8: fft_c<T, DIF, TR, 8, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 12: fft_c<T, DIF, TR, 12, 8, 6, 4, 4>(buf, ls, tw); return true;
+            case 16: fft_c<T, DIF, TR, 16, 8, 6, 4, 4>(buf, ls, tw); return true;
             default: break;
             }
         } else if (plan_is<8, 6, 4>(pl)) {
             switch (nlines) {
-            case 16: fft_c<T, DIF, 16, 8, 6, 4>(buf, ls, tw); return true;
-            case 24: fft_c<T, DIF, 24, 8, 6, 4>(buf, ls, tw); return true;
+            case 16: fft_c<T, DIF, TR, 16, 8, 6, 4>(buf, ls, tw); return true;
+            case 24: fft_c<T, DIF, TR, 24, 8, 6, 4>(buf, ls, tw); return true;
             default: break;
             }
         }
@@ -407,12 +480,12 @@ __device__ __forceinline__ bool fft_const(typename Cx<T>::t* buf, int nlines, in
     return false;
 }
 
-template <typename T, bool DIF, int RM>
+template <typename T, bool DIF, int RM, bool TR = false>
 __device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls,
                                           const FftPlan& pl, int s, const typename Cx<T>::t* __restrict__ tw)
 {
     const int R = pl.r[s];
-#define BSW_PASS(RR) fft_pass<T, RR, DIF>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw)
+#define BSW_PASS(RR) fft_pass<T, RR, DIF, TR>(buf, nlines, dl, ls, pl.n, pl.st[s], pl.sd[s], pl.tws[s], tw)
     // only the radices up to RM are compiled into this kernel (register budget)
     switch (R) {
     case 32: if constexpr (RM >= 32) BSW_PASS(32); break;
@@ -432,22 +505,22 @@ __device__ __forceinline__ void fft_stage(typename Cx<T>::t* buf, int nlines, co
 
 // Forward transform (decimation in frequency), natural order in, frequency
 // k left at position rev(k).
-template <typename T, int RM>
+template <typename T, int RM, bool TR = false>
 __device__ __forceinline__ void fft_fwd_dif(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
-    if (fft_const<T, true>(buf, nlines, ls, pl, tw)) return;
-    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true, RM>(buf, nlines, dl, ls, pl, s, tw);
+    if (fft_const<T, true, TR>(buf, nlines, ls, pl, tw)) return;
+    for (int s = 0; s < pl.nr; ++s) fft_stage<T, true, RM, TR>(buf, nlines, dl, ls, pl, s, tw);
 }
 
 // Inverse transform (decimation in time), frequency k taken at position
 // rev(k), natural order out.
-template <typename T, int RM>
+template <typename T, int RM, bool TR = false>
 __device__ __forceinline__ void fft_inv_dit(typename Cx<T>::t* buf, int nlines, const FastDiv& dl, int ls, const FftPlan& pl,
                             const typename Cx<T>::t* __restrict__ tw)
 {
-    if (fft_const<T, false>(buf, nlines, ls, pl, tw)) return;
-    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false, RM>(buf, nlines, dl, ls, pl, s, tw);
+    if (fft_const<T, false, TR>(buf, nlines, ls, pl, tw)) return;
+    for (int s = pl.nr - 1; s >= 0; --s) fft_stage<T, false, RM, TR>(buf, nlines, dl, ls, pl, s, tw);
 }
 
 
@@ -866,7 +939,6 @@ template <typename T, int W, int TX>
 __device__ __forceinline__ void spread_bucketed(const SpZP& P, int s0, int s1, const int2* __restrict__ cidx,
                                                 const SpPt<T, W>* __restrict__ pts, SpPt<T, W>* sbuf, T* accf)
 {
-    constexpr int H = W / 2;
     constexpr int RCW = kSpzWarpChunk;
     constexpr int kWords = (int)(sizeof(SpPt<T, W>) / 16);
     constexpr int kIt = (RCW * kWords + 31) / 32;
@@ -1163,10 +1235,21 @@ __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_spread_zfft(SpZP P, c
 // inverse: F2 -> F1 (zero-padded to n1)
 // ---------------------------------------------------------------------------
 template <typename T, int RM>
+__device__ __forceinline__ void k_fft_y_tma(const FftYP& P, typename Cx<T>::t* __restrict__ F1,
+                                            typename Cx<T>::t* __restrict__ F2,
+                                            const typename Cx<T>::t* __restrict__ tw1, int sign, int bid,
+                                            const CUtensorMap* tm, int* status);
+
+template <typename T, int RM>
 __device__ __forceinline__ void k_fft_y_body(const FftYP& P, typename Cx<T>::t* __restrict__ F1,
                                              typename Cx<T>::t* __restrict__ F2,
-                                             const typename Cx<T>::t* __restrict__ tw1, int sign, int bid)
+                                             const typename Cx<T>::t* __restrict__ tw1, int sign, int bid,
+                                             const CUtensorMap* tm = nullptr, int* status = nullptr)
 {
+    if (tm) {
+        k_fft_y_tma<T, RM>(P, F1, F2, tw1, sign, bid, tm, status);
+        return;
+    }
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.ng[1], K1 = P.K[1], nk = P.K[2] + 1;
@@ -1229,12 +1312,90 @@ __device__ __forceinline__ void k_fft_y_body(const FftYP& P, typename Cx<T>::t* 
     }
 }
 
+// The y pass with the F1 rows moved by tensor copies (tnb > 0).  The CTA's
+// line set (the MC modes mz0.. of the n1 rows of one (c, x)) sits mode-major
+// in shared memory, row y at y MC: exactly the layout of tnb boxes of tby
+// rows of 2 MC reals.  Forward: one thread issues the boxes (rows past n1
+// and modes past K2 arrive as zeros) and the block waits on an mbarrier,
+// then transforms and writes the |my| <= K1 rows of F2 (thread per mode,
+// digit-reversed rows).  Inverse: the F2 rows are gathered with per-element
+// asynchronous copies into their digit-reversed rows (the zero padding
+// written directly), transformed, and one thread stores the natural-order
+// rows with tensor copies (rows past n1, modes past K2 are not written).
+template <typename T, int RM>
+__device__ __forceinline__ void k_fft_y_tma(const FftYP& P, typename Cx<T>::t* __restrict__ F1,
+                                            typename Cx<T>::t* __restrict__ F2,
+                                            const typename Cx<T>::t* __restrict__ tw1, int sign, int bid,
+                                            const CUtensorMap* tm, int* status)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    C* a = reinterpret_cast<C*>(smem_align128(smem_raw));
+    const int n1 = P.ng[1], K1 = P.K[1], nk = P.K[2] + 1;
+    const int lmc = P.lmc, MC = 1 << lmc;
+    const int nch = (nk + MC - 1) >> lmc;
+    const int cx = fdiv(bid, P.d_nch);  // c * n0 + x
+    const int ch = bid - cx * nch;
+    const int mz0 = ch << lmc;
+    const int mcount = min(MC, nk - mz0);
+    const int ny2 = 2 * K1 + 1;
+    const int l = threadIdx.x & (MC - 1);
+    const int r0 = threadIdx.x >> lmc, rstep = blockDim.x >> lmc;
+    const bool live = l < mcount;
+    const int boxc = P.tby * MC;  // complex values per box
+    if (sign < 0) {
+        if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&s_bar, (unsigned)(P.tnb * boxc * sizeof(C)));
+            for (int b = 0; b < P.tnb; ++b) tma_load_3d(a + (size_t)b * boxc, tm, 2 * mz0, b * P.tby, cx, &s_bar);
+        }
+        if (!mbar_wait_bounded(&s_bar, 0)) {
+            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        fft_fwd_dif<T, RM, true>(a, MC, P.d_lines, 0, P.plan1, tw1);
+        if (live) {
+            C* dst = F2 + ((size_t)cx * ny2 + r0) * nk + mz0 + l;
+            const size_t dstep = (size_t)rstep * nk;
+            for (int myp = r0; myp < ny2; myp += rstep, dst += dstep) {
+                const int my = myp - K1;
+                *dst = a[P.rev[my < 0 ? my + n1 : my] * MC + l];
+            }
+        }
+    } else {
+        C zero;
+        zero.x = 0;
+        zero.y = 0;
+        const C* src = F2 + ((size_t)cx * ny2) * nk + mz0 + l;
+        for (int y = r0; y < n1; y += rstep) {  // y: frequency index
+            const int my = y <= n1 / 2 ? y : y - n1;
+            C* d = &a[P.rev[y] * MC + l];
+            if (live && my >= -K1 && my <= K1)
+                cp_async_cx(d, src + (size_t)(my + K1) * nk);
+            else
+                *d = zero;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        fft_inv_dit<T, RM, true>(a, MC, P.d_lines, 0, P.plan1, tw1);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < P.tnb; ++b) tma_store_3d(tm, 2 * mz0, b * P.tby, cx, a + (size_t)b * boxc);
+            tma_store_commit_and_wait_read();
+        }
+    }
+}
+
 template <typename T, int RM>
 __global__ void __launch_bounds__(kThreads, 2) k_fft_y(FftYP P, typename Cx<T>::t* __restrict__ F1,
                                                     typename Cx<T>::t* __restrict__ F2,
-                                                    const typename Cx<T>::t* __restrict__ tw1, int sign)
+                                                    const typename Cx<T>::t* __restrict__ tw1, int sign,
+                                                    const __grid_constant__ CUtensorMap tm, int* status)
 {
-    k_fft_y_body<T, RM>(P, F1, F2, tw1, sign, blockIdx.x);
+    k_fft_y_body<T, RM>(P, F1, F2, tw1, sign, blockIdx.x, P.tnb > 0 ? &tm : nullptr, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -1974,27 +2135,78 @@ struct FftYLaunch {
     void* f2;
     int sign;
     cudaStream_t s;
+    const CUtensorMap* tm;
     template <int RM>
     cudaError_t run()
     {
         using C = typename Cx<T>::t;
         const int MC = 1 << P.lmc;
-        const size_t sm = (size_t)MC * P.ls * sizeof(C);
+        FftYP Q = P;
+        CUtensorMap map;
+        if (tm && Q.tnb > 0) {
+            map = *tm;
+        } else {
+            Q.tnb = 0;
+            memset(&map, 0, sizeof map);
+        }
+        size_t sm = (size_t)MC * P.ls * sizeof(C);
+        if (Q.tnb > 0) sm = (size_t)MC * std::max(P.ls, Q.tnb * Q.tby) * sizeof(C) + 128;
         cudaError_t e = cudaFuncSetAttribute(k_fft_y<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         const int nk = P.K[2] + 1;
         const int nch = (nk + MC - 1) / MC;
-        k_fft_y<T, RM><<<3 * P.ng[0] * nch, kThreads, sm, s>>>(P, (C*)w.spec, (C*)f2, (const C*)w.tw + P.ng[0],
-                                                                sign);
+        k_fft_y<T, RM><<<3 * P.ng[0] * nch, kThreads, sm, s>>>(Q, (C*)w.spec, (C*)f2, (const C*)w.tw + P.ng[0],
+                                                                sign, map, w.status);
         return cudaGetLastError();
     }
 };
 
 template <typename T>
-cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s)
+cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s, const CUtensorMap* tm_f1)
 {
-    return by_rm<T>(P.plan1, FftYLaunch<T>{ P, w, f2, sign, s });
+    return by_rm<T>(P.plan1, FftYLaunch<T>{ P, w, f2, sign, s, tm_f1 });
 }
+
+// cuTensorMapEncodeTiled through the runtime (no link against the driver
+// library); null when the driver does not offer it.
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+template <typename T>
+bool make_tmap_y(void* F1, const FftYP& P, CUtensorMap* tm)
+{
+    const int MC = 1 << P.lmc, nk = P.K[2] + 1;
+    // rows 16-byte multiples, box start (2 mz0 reals, mz0 a multiple of MC)
+    // on a 16-byte boundary, box rows on 128-byte boundaries in shared memory
+    if (MC < 2 || (sizeof(T) == 4 && nk % 2 != 0) || P.tnb <= 0 || P.tby <= 0 || P.tby > 256 ||
+        (P.tby * MC * 2 * sizeof(T)) % 128 != 0 || P.tnb * P.tby < P.ng[1])
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dim[3] = { (cuuint64_t)2 * nk, (cuuint64_t)P.ng[1], (cuuint64_t)3 * P.ng[0] };
+    const cuuint64_t stride[2] = { (cuuint64_t)2 * nk * sizeof(T), (cuuint64_t)2 * nk * sizeof(T) * P.ng[1] };
+    const cuuint32_t box[3] = { (cuuint32_t)(2 * MC), (cuuint32_t)P.tby, 1 };
+    const cuuint32_t estr[3] = { 1, 1, 1 };
+    const CUresult r = enc(tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                           F1, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+template bool make_tmap_y<float>(void*, const FftYP&, CUtensorMap*);
+template bool make_tmap_y<double>(void*, const FftYP&, CUtensorMap*);
 
 template <typename T>
 struct FftXLaunch {
@@ -2305,8 +2517,8 @@ template cudaError_t launch_node_bin<float>(const ColP&, const InterpP&, const d
 template cudaError_t launch_node_bin<double>(const ColP&, const InterpP&, const double*, const Work&, cudaStream_t);
 template size_t nd_rec_bytes<float>(int);
 template size_t nd_rec_bytes<double>(int);
-template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, cudaStream_t);
-template cudaError_t launch_fft_y<double>(const FftYP&, const Work&, void*, int, cudaStream_t);
+template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, cudaStream_t, const CUtensorMap*);
+template cudaError_t launch_fft_y<double>(const FftYP&, const Work&, void*, int, cudaStream_t, const CUtensorMap*);
 template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool, cudaStream_t);
 template cudaError_t launch_fft_x_kspace<double>(const FftXP&, const Work&, bool, cudaStream_t);
 template cudaError_t launch_fft_z_c2r<float>(const FftZP&, const Work&, cudaStream_t, double*);
