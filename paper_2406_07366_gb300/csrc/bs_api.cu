@@ -384,6 +384,10 @@ struct bs_ctx {
     CUtensorMap tmy;
     const void* tmy_for = nullptr;
     bool tmy_ok = false;
+    // the same for F2 in the x pass
+    CUtensorMap tmx;
+    const void* tmx_for = nullptr;
+    bool tmx_ok = false;
 };
 
 namespace {
@@ -475,10 +479,13 @@ int alloc_grids(bs_ctx* c)
             }
         TRY(dalloc(c, c->alloc_g, &c->w.tw, sizeof(T) * tw.size()));
         CUDA_TRY(cudaMemcpy(c->w.tw, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice));
-        std::vector<int> rev(ntw);
+        // positions of frequency k per axis, then the frequency at each
+        // position of an x line (the inverse of the first table)
+        std::vector<int> rev(ntw + d.ng[0]);
         o = 0;
         for (int ax = 0; ax < 3; ++ax)
             for (int k = 0; k < d.ng[ax]; ++k) rev[o++] = rev_pos_host(k, d.plan[ax]);
+        for (int k = 0; k < d.ng[0]; ++k) rev[ntw + rev[k]] = k;
         TRY(dalloc(c, c->alloc_g, (void**)&c->w.rev, sizeof(int) * rev.size()));
         CUDA_TRY(cudaMemcpy(c->w.rev, rev.data(), sizeof(int) * rev.size(), cudaMemcpyHostToDevice));
     }
@@ -774,6 +781,17 @@ void fill_fftyp(const bs_ctx* c, FftYP& YP)
     YP.tby = ((d.ng[1] + YP.tnb - 1) / YP.tnb + 7) & ~7;
 }
 
+// The x pass's descriptor of F2 (null: the per-element copy path).
+template <typename T>
+const CUtensorMap* tmap_x(bs_ctx* c, const FftXP& XP)
+{
+    if (c->tmx_for != c->w.f2) {
+        c->tmx_ok = make_tmap_x<T>(c->w.f2, XP, &c->tmx);
+        c->tmx_for = c->w.f2;
+    }
+    return c->tmx_ok ? &c->tmx : nullptr;
+}
+
 // The y pass's descriptor of F1 (null: the per-element copy path).
 template <typename T>
 const CUtensorMap* tmap_y(bs_ctx* c, const FftYP& YP)
@@ -803,6 +821,10 @@ void fill_fftxp(const bs_ctx* c, FftXP& XP)
     XP.scale = p.kappa / (p.L[0] * p.L[1] * p.L[2]);
     XP.plan0 = d.plan[0];
     XP.rev = c->w.rev;
+    XP.irev = c->w.rev + d.ng[0] + d.ng[1] + d.ng[2];
+    // tensor-copy boxes of at most 256 x rows, a multiple of 16 rows each
+    XP.tnbx = (d.ng[0] + 255) / 256;
+    XP.tbx = ((d.ng[0] + XP.tnbx - 1) / XP.tnbx + 15) & ~15;
     XP.d_nch = make_fastdiv((unsigned)((d.K[2] + 1 + (1 << d.lmcx) - 1) >> d.lmcx));
     XP.d_n0 = make_fastdiv((unsigned)d.ng[0]);
     XP.d_lines = make_fastdiv(3u << d.lmcx);
@@ -914,7 +936,7 @@ int run(bs_ctx* c, const double* nodes, double* vel, double* psi, double* parts,
         if (spectrum) return (int)launch_fft_x_kspace<T>(XP, w, false, s) == (int)cudaSuccess
                                  ? BS_OK
                                  : fail(BS_ERR_CUDA, "spectrum kernel launch failed");
-        CE(launch_fft_x_kspace<T>(XP, w, want_psi, s));
+        CE(launch_fft_x_kspace<T>(XP, w, want_psi, s, tmap_x<T>(c, XP)));
         rec(c, 7, s);
         CE(launch_fft_y<T>(YP, w, w.f2, +1, s, tmap_y<T>(c, YP)));
         if (fused) {

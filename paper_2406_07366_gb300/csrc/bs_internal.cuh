@@ -239,6 +239,8 @@ struct FftXP {
     int lmc;            // log2 of the chunk of z-modes per CTA
     int nthreads;       // threads per CTA (256, or 512 for float32 on large grids)
     int ls;             // line stride in shared memory
+    int tbx, tnbx;      // tensor copies of F2 (tnbx > 0): x rows per box, boxes per CTA
+    const int* irev;    // frequency at each position of an x line after the forward transform
     double kk[3];
     double scale;
     FftPlan plan0;
@@ -394,6 +396,14 @@ cudaError_t set_fft_constants();
 template <typename T>
 cudaError_t launch_fft_y(const FftYP& P, const Work& w, void* f2, int sign, cudaStream_t s,
                          const CUtensorMap* tm_f1 = nullptr);
+template <typename T>
+cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s,
+                                const CUtensorMap* tm_f2);
+// Tensor-copy descriptor of F2 for the x pass: 4-D (2 nk reals, 3 components,
+// n0 x rows, 2 K1 + 1 y modes), box (2 MC, 3, tbx, 1), which lands as x rows
+// of the 3 MC lines' modes; false where the layout does not allow it.
+template <typename T>
+bool make_tmap_x(void* F2, const FftXP& P, CUtensorMap* tm);
 // Tensor-copy descriptor of F1 for the y pass: 3-D (2 nk reals, n1 rows,
 // 3 n0 lines), box (2 MC, tby, 1); false where the layout does not allow it
 // (float32 with an odd nk: rows not 16-byte multiples; MC < 2).

@@ -156,6 +156,21 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int x, int y
                  "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
                  : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int x, int y, int z, int w,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* tm, int x, int y, int z, int w, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(tm),
+                 "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(src))
+                 : "memory");
+}
 __device__ __forceinline__ void tma_store_commit_and_wait_read()
 {
     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
@@ -1580,14 +1595,115 @@ __device__ __forceinline__ void k_fft_x_kspace_body(const FftXP& P, typename Cx<
     }
 }
 
+// The x pass of the velocity (no psi, spectrum or deterministic energy) with
+// F2 moved by tensor copies (tnbx > 0).  The boxes land as x rows of the
+// 3 MC lines' modes (line c MC + l, mode-major: x row at x 3 MC), the forward
+// transform runs on that layout, the k-space pass walks positions (a thread
+// per (position, mode), the frequency from the inverse digit-reversal
+// table, so that consecutive lanes read consecutive words), the inverse
+// transform returns natural order and one thread stores the rows back.
+// Modes past K2 arrive as zeros and are not written back.
+template <typename T, int RM>
+__device__ __forceinline__ void k_fft_x_tma(const FftXP& P, typename Cx<T>::t* __restrict__ F2,
+                                            const typename Cx<T>::t* __restrict__ tw0, const T* __restrict__ tab0,
+                                            const T* __restrict__ tab1, const T* __restrict__ tab2, int bid,
+                                            const CUtensorMap* tm, int* status)
+{
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    C* a = reinterpret_cast<C*>(smem_align128(smem_raw));
+    const int n0 = P.ng[0], K0 = P.K[0], K1 = P.K[1], nk = P.K[2] + 1;
+    const int lmc = P.lmc, MC = 1 << lmc, NL = 3 * MC;
+    const int nch = (nk + MC - 1) >> lmc;
+    const int myp = fdiv(bid, P.d_nch);
+    const int ch = bid - myp * nch;
+    const int mz0 = ch << lmc;
+    const int mcount = min(MC, nk - mz0);
+    const int boxc = P.tbx * NL;  // complex values per box
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&s_bar, (unsigned)(P.tnbx * boxc * sizeof(C)));
+        for (int b = 0; b < P.tnbx; ++b)
+            tma_load_4d(a + (size_t)b * boxc, tm, 2 * mz0, 0, b * P.tbx, myp, &s_bar);
+    }
+    if (!mbar_wait_bounded(&s_bar, 0)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        return;
+    }
+    fft_fwd_dif<T, RM, true>(a, NL, P.d_lines, 0, P.plan0, tw0);
+    // k-space pass: frequency (mx, my, mz) of line (c, lk) sits at position
+    // p with irev[p] = xi
+    const int my = myp - K1;
+    const int amy = my < 0 ? -my : my;
+    double esum = 0.0;
+    const T kk0 = (T)P.kk[0], kk1 = (T)P.kk[1], kk2 = (T)P.kk[2];
+    const T scale = (T)P.scale;
+    C zero;
+    zero.x = 0;
+    zero.y = 0;
+    for (int i = threadIdx.x; i < (n0 << lmc); i += blockDim.x) {
+        const int lk = i & (MC - 1), p = i >> lmc;
+        const int xi = P.irev[p];
+        const int mx = xi <= n0 / 2 ? xi : xi - n0;
+        const int amx = mx < 0 ? -mx : mx;
+        const int mz = mz0 + lk;
+        C* r = a + (size_t)p * NL + lk;  // component c at r[c MC]
+        if (lk >= mcount || amx > K0 || (mx == 0 && my == 0 && mz == 0)) {
+            r[0] = zero;
+            r[MC] = zero;
+            r[2 * MC] = zero;
+            continue;
+        }
+        C w0 = r[0], w1 = r[MC], w2 = r[2 * MC];
+        const T k0 = kk0 * (T)mx, k1 = kk1 * (T)my, k2 = kk2 * (T)mz;
+        const T ksq = k0 * k0 + k1 * k1 + k2 * k2;
+        const T mult = scale * tab0[amx] * tab1[amy] * tab2[mz] / ksq;
+        if (P.energy) {
+            const double f2 = (double)w0.x * w0.x + (double)w0.y * w0.y + (double)w1.x * w1.x +
+                              (double)w1.y * w1.y + (double)w2.x * w2.x + (double)w2.y * w2.y;
+            esum += (mz > 0 ? 1.0 : 0.5) * P.scale * (double)mult * f2;
+        }
+        w0.x *= mult; w0.y *= mult;
+        w1.x *= mult; w1.y *= mult;
+        w2.x *= mult; w2.y *= mult;
+        // i k x w
+        const T cr0 = k1 * w2.x - k2 * w1.x, ci0 = k1 * w2.y - k2 * w1.y;
+        const T cr1 = k2 * w0.x - k0 * w2.x, ci1 = k2 * w0.y - k0 * w2.y;
+        const T cr2 = k0 * w1.x - k1 * w0.x, ci2 = k0 * w1.y - k1 * w0.y;
+        C o;
+        o.x = -ci0; o.y = cr0; r[0] = o;
+        o.x = -ci1; o.y = cr1; r[MC] = o;
+        o.x = -ci2; o.y = cr2; r[2 * MC] = o;
+    }
+    if (P.energy) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        if ((threadIdx.x & 31) == 0 && esum != 0.0) atomicAdd(P.energy, esum);
+    }
+    __syncthreads();
+    fft_inv_dit<T, RM, true>(a, NL, P.d_lines, 0, P.plan0, tw0);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < P.tnbx; ++b) tma_store_4d(tm, 2 * mz0, 0, b * P.tbx, myp, a + (size_t)b * boxc);
+        tma_store_commit_and_wait_read();
+    }
+}
+
 template <typename T, int RM>
 __global__ void __launch_bounds__(z_threads_max<T>(), 2) k_fft_x_kspace(FftXP P, typename Cx<T>::t* __restrict__ F2,
                                                            typename Cx<T>::t* __restrict__ F2psi,
                                                            const typename Cx<T>::t* __restrict__ tw0,
                                                            const T* __restrict__ tab0, const T* __restrict__ tab1,
-                                                           const T* __restrict__ tab2)
+                                                           const T* __restrict__ tab2,
+                                                           const __grid_constant__ CUtensorMap tm, int* status)
 {
-    k_fft_x_kspace_body<T, RM>(P, F2, F2psi, tw0, tab0, tab1, tab2, blockIdx.x);
+    if (P.tnbx > 0)
+        k_fft_x_tma<T, RM>(P, F2, tw0, tab0, tab1, tab2, blockIdx.x, &tm, status);
+    else
+        k_fft_x_kspace_body<T, RM>(P, F2, F2psi, tw0, tab0, tab1, tab2, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -2209,18 +2325,52 @@ template bool make_tmap_y<float>(void*, const FftYP&, CUtensorMap*);
 template bool make_tmap_y<double>(void*, const FftYP&, CUtensorMap*);
 
 template <typename T>
+bool make_tmap_x(void* F2, const FftXP& P, CUtensorMap* tm)
+{
+    const int MC = 1 << P.lmc, nk = P.K[2] + 1, n0 = P.ng[0], ny2 = 2 * P.K[1] + 1;
+    // rows 16-byte multiples, box start (2 mz0 reals) on a 16-byte boundary,
+    // boxes on 128-byte boundaries in shared memory
+    if (MC < 2 || (sizeof(T) == 4 && nk % 2 != 0) || P.tnbx <= 0 || P.tbx <= 0 || P.tbx > 256 ||
+        ((size_t)P.tbx * 3 * MC * 2 * sizeof(T)) % 128 != 0 || P.tnbx * P.tbx < n0 || !P.irev)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t row = (cuuint64_t)2 * nk * sizeof(T);
+    const cuuint64_t dim[4] = { (cuuint64_t)2 * nk, 3, (cuuint64_t)n0, (cuuint64_t)ny2 };
+    const cuuint64_t stride[3] = { row * ny2 * n0, row * ny2, row };  // component, x, y mode
+    const cuuint32_t box[4] = { (cuuint32_t)(2 * MC), 3, (cuuint32_t)P.tbx, 1 };
+    const cuuint32_t estr[4] = { 1, 1, 1, 1 };
+    const CUresult r = enc(tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                           F2, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+template bool make_tmap_x<float>(void*, const FftXP&, CUtensorMap*);
+template bool make_tmap_x<double>(void*, const FftXP&, CUtensorMap*);
+
+template <typename T>
 struct FftXLaunch {
     const FftXP& P;
     const Work& w;
     bool want_psi;
     cudaStream_t s;
+    const CUtensorMap* tm;
     template <int RM>
     cudaError_t run()
     {
         using C = typename Cx<T>::t;
         const int MC = 1 << P.lmc;
         const int nl = (want_psi ? 6 : 3) * MC;
+        FftXP Q = P;
+        CUtensorMap map;
+        if (tm && Q.tnbx > 0 && !want_psi && !P.spectrum && !P.epart) {
+            map = *tm;
+        } else {
+            Q.tnbx = 0;
+            memset(&map, 0, sizeof map);
+        }
         size_t sm = (size_t)nl * P.ls * sizeof(C);
+        if (Q.tnbx > 0) sm = (size_t)3 * MC * Q.tnbx * Q.tbx * sizeof(C) + 128;
         if (P.spectrum) sm = std::max(sm, (size_t)3 * MC * P.ls * sizeof(C) + sizeof(double) * (size_t)P.nbins);
         if (P.epart) sm += sizeof(double) * (kZThreadsMax / 32);
         cudaError_t e =
@@ -2234,7 +2384,7 @@ struct FftXLaunch {
         const T* tab2 = tab1 + (P.K[1] + 1);
         const int nt = P.nthreads > 0 && P.nthreads <= z_threads_max<T>() ? P.nthreads : kThreads;
         k_fft_x_kspace<T, RM><<<(2 * P.K[1] + 1) * nch, nt, sm, s>>>(
-            P, (C*)w.f2, want_psi ? (C*)w.f2psi : nullptr, (const C*)w.tw, tab0, tab1, tab2);
+            Q, (C*)w.f2, want_psi ? (C*)w.f2psi : nullptr, (const C*)w.tw, tab0, tab1, tab2, map, w.status);
         return cudaGetLastError();
     }
 };
@@ -2242,7 +2392,14 @@ struct FftXLaunch {
 template <typename T>
 cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s)
 {
-    return by_rm<T>(P.plan0, FftXLaunch<T>{ P, w, want_psi, s });
+    return by_rm<T>(P.plan0, FftXLaunch<T>{ P, w, want_psi, s, nullptr });
+}
+
+template <typename T>
+cudaError_t launch_fft_x_kspace(const FftXP& P, const Work& w, bool want_psi, cudaStream_t s,
+                                const CUtensorMap* tm_f2)
+{
+    return by_rm<T>(P.plan0, FftXLaunch<T>{ P, w, want_psi, s, tm_f2 });
 }
 
 template <typename T, typename TO>
@@ -2517,6 +2674,8 @@ template cudaError_t launch_node_bin<float>(const ColP&, const InterpP&, const d
 template cudaError_t launch_node_bin<double>(const ColP&, const InterpP&, const double*, const Work&, cudaStream_t);
 template size_t nd_rec_bytes<float>(int);
 template size_t nd_rec_bytes<double>(int);
+template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool, cudaStream_t, const CUtensorMap*);
+template cudaError_t launch_fft_x_kspace<double>(const FftXP&, const Work&, bool, cudaStream_t, const CUtensorMap*);
 template cudaError_t launch_fft_y<float>(const FftYP&, const Work&, void*, int, cudaStream_t, const CUtensorMap*);
 template cudaError_t launch_fft_y<double>(const FftYP&, const Work&, void*, int, cudaStream_t, const CUtensorMap*);
 template cudaError_t launch_fft_x_kspace<float>(const FftXP&, const Work&, bool, cudaStream_t);
