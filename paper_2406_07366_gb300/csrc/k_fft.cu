@@ -1904,21 +1904,33 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
             const int lx0 = max(r0, 0), lx1 = min(r0 + W - 1, Tx - 1);
             const int ly0 = max(r1, 0), ly1 = min(r1 + W - 1, Ty - 1);
             T a0 = 0, a1 = 0, a2 = 0;
-            for (int ly = ly0; ly <= ly1; ++ly) {
-                const T wy = R.wy[ly - r1];
+            // the rows ly = 2 lp and 2 lp + 1 of a column pair are the two
+            // halves of one complex line: one 2-word read per position gives
+            // both (the half outside the support weighted by 0)
+            using T2 = typename Cx<T>::t;
+            for (int lp = ly0 >> 1; lp <= ly1 >> 1; ++lp) {
+                const int le = 2 * lp, lo = le + 1;
+                const T wye = le >= ly0 ? R.wy[le - r1] : (T)0;
+                const T wyo = lo <= ly1 ? R.wy[lo - r1] : (T)0;
                 for (int lx = lx0; lx <= lx1; ++lx) {
-                    const T* row = accf + (ly >> 1) * 2 * CS + (ly & 1) + lx * Ty * CS;
-                    T s0 = 0, s1 = 0, s2 = 0;
+                    const T* row = accf + lp * 2 * CS + lx * Ty * CS;
+                    T e0 = 0, e1 = 0, e2 = 0, o0 = 0, o1 = 0, o2 = 0;
 #pragma unroll
                     for (int t = 0; t < W; ++t) {
-                        s0 += wz[t] * row[zo[t]];
-                        s1 += wz[t] * row[zo[t] + sc];
-                        s2 += wz[t] * row[zo[t] + 2 * sc];
+                        const T2 v0 = *reinterpret_cast<const T2*>(row + zo[t]);
+                        const T2 v1 = *reinterpret_cast<const T2*>(row + zo[t] + sc);
+                        const T2 v2 = *reinterpret_cast<const T2*>(row + zo[t] + 2 * sc);
+                        e0 += wz[t] * v0.x;
+                        o0 += wz[t] * v0.y;
+                        e1 += wz[t] * v1.x;
+                        o1 += wz[t] * v1.y;
+                        e2 += wz[t] * v2.x;
+                        o2 += wz[t] * v2.y;
                     }
-                    const T wxy = R.wx[lx - r0] * wy;
-                    a0 += wxy * s0;
-                    a1 += wxy * s1;
-                    a2 += wxy * s2;
+                    const T wx = R.wx[lx - r0];
+                    a0 += wx * (wye * e0 + wyo * o0);
+                    a1 += wx * (wye * e1 + wyo * o1);
+                    a2 += wx * (wye * e2 + wyo * o2);
                 }
             }
             const size_t j = (size_t)R.j;
