@@ -747,7 +747,8 @@ void fill_spzp(const bs_ctx* c, bool det, SpZP& SZ)
     SZ.nby = d.nby;
     SZ.w = p.nufft_w;
     SZ.nzb = d.nzb;
-    SZ.cls = line_stride(d.ng[2], 3 * d.tx * d.ty / 2, 128 / (2 * (int)sizeof(T)));
+    // room for the interpolation's periodic halo of w - 1 positions
+    SZ.cls = line_stride(d.ng[2] + p.nufft_w - 1, 3 * d.tx * d.ty / 2, 128 / (2 * (int)sizeof(T)));
     SZ.ls = d.lsz;
     while (SZ.ls < SZ.cls) SZ.ls += 32;  // the real region also holds the complex lines
     SZ.zeta = d.zeta;

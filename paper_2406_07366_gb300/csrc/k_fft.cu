@@ -1872,6 +1872,14 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
     const int ncand = r_pre[nr];
     home_stage(srec, nds, r_beg, r_pre, nr, 0, min(kSpzChunk, ncand));  // in flight during the transform
     fft_inv_dit<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
+    // periodic halo: positions n2 .. n2 + W - 2 of every line repeat 0 .. W - 2
+    // (the line stride leaves room), so a node's W positions from its support
+    // start taken modulo n2 are contiguous
+    for (int i = tid; i < ncl * (W - 1); i += blockDim.x) {
+        const int l = i / (W - 1), t = i - l * (W - 1);
+        cb[l * CS + n2 + t] = cb[l * CS + t];
+    }
+    __syncthreads();
     // real line rl = c txy + lx Ty + ly at position z is the float
     // ((rl >> 1) CS + z) 2 + (rl & 1) = rbase(lx, ly) + 2 z + c txy CS
     const int sc = txy * CS;
@@ -1893,14 +1901,10 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
             const int r1 = home_rel((base >> 10) & 1023, H, by * Ty, Ty, n1, W);
             if (r0 > Tx - 1 || r0 + W - 1 < 0 || r1 > Ty - 1 || r1 + W - 1 < 0) continue;
             const int z0 = ((base >> 20) & 1023) - H + 1;
-            int zo[W];
+            const int zb2 = 2 * (z0 < 0 ? z0 + n2 : z0);  // float offset of the first position
             T wz[W];
 #pragma unroll
-            for (int t = 0; t < W; ++t) {
-                const int z = z0 + t;
-                zo[t] = 2 * (z < 0 ? z + n2 : (z >= n2 ? z - n2 : z));
-                wz[t] = R.wz[t];
-            }
+            for (int t = 0; t < W; ++t) wz[t] = R.wz[t];
             const int lx0 = max(r0, 0), lx1 = min(r0 + W - 1, Tx - 1);
             const int ly0 = max(r1, 0), ly1 = min(r1 + W - 1, Ty - 1);
             T a0 = 0, a1 = 0, a2 = 0;
@@ -1913,13 +1917,13 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
                 const T wye = le >= ly0 ? R.wy[le - r1] : (T)0;
                 const T wyo = lo <= ly1 ? R.wy[lo - r1] : (T)0;
                 for (int lx = lx0; lx <= lx1; ++lx) {
-                    const T* row = accf + lp * 2 * CS + lx * Ty * CS;
+                    const T* row = accf + lp * 2 * CS + lx * Ty * CS + zb2;
                     T e0 = 0, e1 = 0, e2 = 0, o0 = 0, o1 = 0, o2 = 0;
 #pragma unroll
                     for (int t = 0; t < W; ++t) {
-                        const T2 v0 = *reinterpret_cast<const T2*>(row + zo[t]);
-                        const T2 v1 = *reinterpret_cast<const T2*>(row + zo[t] + sc);
-                        const T2 v2 = *reinterpret_cast<const T2*>(row + zo[t] + 2 * sc);
+                        const T2 v0 = *reinterpret_cast<const T2*>(row + 2 * t);
+                        const T2 v1 = *reinterpret_cast<const T2*>(row + sc + 2 * t);
+                        const T2 v2 = *reinterpret_cast<const T2*>(row + 2 * sc + 2 * t);
                         e0 += wz[t] * v0.x;
                         o0 += wz[t] * v0.y;
                         e1 += wz[t] * v1.x;
