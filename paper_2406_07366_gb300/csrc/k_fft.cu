@@ -39,7 +39,6 @@
 
 namespace bsw {
 
-constexpr int kSpzChunk = 128;  // interpolation targets staged in shared memory at a time
 // Spread records per staged chunk (two chunks in flight): 64 in float64
 // keeps the float64 spread CTA's shared memory at its single-buffered size.
 template <typename T>
@@ -788,24 +787,6 @@ __device__ __forceinline__ void home_prefix(int* r_pre)
     r_pre[lane + 1] = v0;
     r_pre[lane + 33] = v1;
     if (lane == 0) r_pre[0] = 0;
-}
-
-// Starts the asynchronous copy of candidates [c0, c0 + nch) of the gathered
-// ranges into shared memory (records are whole 16-byte words).
-template <typename R>
-__device__ __forceinline__ void home_stage(R* srec, const R* __restrict__ recs, const int* r_beg, const int* r_pre,
-                                           int nr, int c0, int nch)
-{
-    constexpr int kWords = (int)(sizeof(R) / 16);
-    int4* dst = reinterpret_cast<int4*>(srec);
-    for (int i = threadIdx.x; i < nch * kWords; i += blockDim.x) {
-        const int k = c0 + i / kWords, wd = i % kWords;
-        int r = 0;
-        while (r + 1 < nr && r_pre[r + 1] <= k) ++r;
-        const int4* src = reinterpret_cast<const int4*>(recs + r_beg[r] + (k - r_pre[r])) + wd;
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
-    }
 }
 
 // Support start of a point relative to a block (cell index ib, block start
@@ -1820,7 +1801,6 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
     const int CS = P.cls;
     C* cb = reinterpret_cast<C*>(smem_raw);
     const T* accf = reinterpret_cast<const T*>(cb);
-    NdW<T, W>* srec = reinterpret_cast<NdW<T, W>*>(smem_raw + zlines_bytes<T>(ncl, CS));
     const int tid = threadIdx.x;
     const int by = fdiv(bid, P.d_nbx);
     const int bx = bid - by * P.nbx;
@@ -1870,7 +1850,6 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
     }
     __syncthreads();
     const int ncand = r_pre[nr];
-    home_stage(srec, nds, r_beg, r_pre, nr, 0, min(kSpzChunk, ncand));  // in flight during the transform
     fft_inv_dit<T, RM>(cb, ncl, P.d_ncl, CS, P.plan2, tw2);
     // periodic halo: positions n2 .. n2 + W - 2 of every line repeat 0 .. W - 2
     // (the line stride leaves room), so a node's W positions from its support
@@ -1883,17 +1862,14 @@ __device__ __forceinline__ void k_zfft_interp_body(const SpZP& P, const int* __r
     // real line rl = c txy + lx Ty + ly at position z is the float
     // ((rl >> 1) CS + z) 2 + (rl & 1) = rbase(lx, ly) + 2 z + c txy CS
     const int sc = txy * CS;
-    for (int c0 = 0; c0 < ncand; c0 += kSpzChunk) {
-        const int nch = min(kSpzChunk, ncand - c0);
-        if (c0 != 0) {
-            __syncthreads();
-            home_stage(srec, nds, r_beg, r_pre, nr, c0, nch);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        // a thread per node: its W^3 support clipped to the block
-        for (int kk = tid; kk < nch; kk += blockDim.x) {
-            const NdW<T, W>& R = srec[kk];
+    // a thread per candidate node of the gathered home ranges, its record read
+    // from global memory (consecutive threads on consecutive records of a
+    // range, mostly L2 hits); no block-wide waits, so every warp works
+    int r = 0;  // range of candidate k (k only grows for a thread)
+    {
+        for (int k = tid; k < ncand; k += blockDim.x) {
+            while (r + 1 < nr && r_pre[r + 1] <= k) ++r;
+            const NdW<T, W>& R = nds[r_beg[r] + (k - r_pre[r])];
             const int base = R.base;
             // support start relative to the block, taking the periodic image
             // that meets it (the grid is wider than W + T)
@@ -2226,7 +2202,7 @@ struct ZiLaunch {
     cudaError_t run()
     {
         using C = typename Cx<T>::t;
-        const size_t sm = zlines_bytes<T>(3 * P.tx * P.ty / 2, P.cls) + kSpzChunk * sizeof(NdW<T, W>);
+        const size_t sm = zlines_bytes<T>(3 * P.tx * P.ty / 2, P.cls);
         cudaError_t e =
             cudaFuncSetAttribute(k_zfft_interp<T, W, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -2630,19 +2606,7 @@ cudaError_t launch_node_scatter_b(int w, const BatchL& L, cudaStream_t s)
 template <typename T>
 size_t zfft_interp_smem(const SpZP& P)
 {
-    size_t r = 0;
-    const int w = P.w;
-    switch (w) {
-    case 2: r = sizeof(NdW<T, 2>); break;
-    case 4: r = sizeof(NdW<T, 4>); break;
-    case 6: r = sizeof(NdW<T, 6>); break;
-    case 8: r = sizeof(NdW<T, 8>); break;
-    case 10: r = sizeof(NdW<T, 10>); break;
-    case 12: r = sizeof(NdW<T, 12>); break;
-    case 14: r = sizeof(NdW<T, 14>); break;
-    default: r = sizeof(NdW<T, 16>); break;
-    }
-    return zlines_bytes<T>(3 * P.tx * P.ty / 2, P.cls) + kSpzChunk * r;
+    return zlines_bytes<T>(3 * P.tx * P.ty / 2, P.cls);
 }
 
 template <typename T, int W>
