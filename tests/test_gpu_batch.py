@@ -80,6 +80,30 @@ def test_batch_members_equal_single_contexts(prec, issue):
     bt.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("M", [47, 95])
+def test_tensor_copy_passes_equal_per_element_passes(prec, M):
+    """With K_z + 1 even (M = 47: 24 z-modes on a 72-point grid; M = 95: 48 on
+    144) a single context's y and x passes move their rows with tensor copies,
+    while the staged batch kernels move the same rows with per-element copies.
+    The transforms, the k-space step and every sum are the same, so one member
+    staged by itself reproduces its single context (float64 to 1e-12; float32
+    up to the order of its atomic sums)."""
+    B = _B()
+    f = W.fourier_tangle(nfil=24, N_l=32, seed=91, amp=2 * math.pi / 48)
+    P = B.BS_FP64 if prec == "fp64" else B.BS_MIXED
+    p = B.make_params(f.L, beta=3.5, M=M, Q=2, w=8 if prec == "fp64" else 6, precision=P)
+    p.flags |= B.BS_BATCH_STAGED
+    s = torch.cuda.Stream()
+    bt, nodes, vel = _run_batch(B, [p], [f], s)
+    assert tuple(int(x) for x in bt.staged) == (1,)
+    got = vel.clone()
+    bt.close()
+    ref = _single(B, p, f)
+    err = (got - ref).abs().max().item() / ref.abs().max().item()
+    assert err < (1e-12 if prec == "fp64" else 1e-6), err
+
+
 def test_batch_replay_follows_new_positions_and_matches_oracle():
     """The captured batch reads the node buffer at replay time; after
     deforming the curves in place, each member matches the oracle's
